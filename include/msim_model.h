@@ -1,0 +1,65 @@
+/*
+ * msim_model.h -- model description consumed by msim_create (host memory, caller-owned).
+ *
+ * A musculoskeletal model in the sense of the paper's Methods ("Whole-body musculoskeletal
+ * model", "Muscle-tendon dynamics", "Contact modeling"): a tree of rigid bodies joined by
+ * hinge DoFs, Hill-type muscle-tendon units routed through via points, and contact spheres
+ * against the ground plane z = 0.
+ *
+ * Geometry conventions:
+ *   - Bodies are listed parents first: body_parent[b] < b, -1 = the fixed world.
+ *   - Body b owns body_ndof[b] in {1,2,3} hinge DoFs, numbered consecutively in body order.
+ *   - Frame of body b = frame of its parent * translate(body_offset[b]) * Rot(a_0, q_0) * ...
+ *     * Rot(a_{k-1}, q_{k-1}), each axis a_j (dof_axis, unit) given in the frame just before
+ *     its hinge.  The body origin is the joint origin.
+ *   - body_com, body_inertia (xx, yy, zz, xy, xz, yz about the COM), point_pos, sphere_pos
+ *     are in the body frame.  Units: m, kg, s, N.
+ *   - Muscle k runs through points muscle_point_start[k] .. muscle_point_start[k+1]-1
+ *     (origin first).  Consecutive points must lie on the same body or on a descendant of
+ *     it, all on the one ancestor chain from the origin body to the insertion body.
+ *   - dof_limit[2d], dof_limit[2d+1] = lo, hi [rad]; lo >= hi disables the limit.
+ *
+ * Limits of this build: n_dofs <= 255, n_bodies <= 255, max DoF depth <= 63, points per
+ * muscle <= 8, DoFs crossed per muscle <= 12, n_spheres <= 32, n_muscles <= 4096.
+ */
+#ifndef MSIM_MODEL_H
+#define MSIM_MODEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t n_bodies, n_dofs, n_muscles, n_points, n_spheres;
+    const int32_t* body_parent;        /* [n_bodies] */
+    const int32_t* body_ndof;          /* [n_bodies] */
+    const float* body_offset;          /* [n_bodies][3] */
+    const float* body_mass;            /* [n_bodies] */
+    const float* body_com;             /* [n_bodies][3] */
+    const float* body_inertia;         /* [n_bodies][6] */
+    const float* dof_axis;             /* [n_dofs][3] */
+    const float* dof_limit;            /* [n_dofs][2] */
+    const float* dof_damping;          /* [n_dofs], N m s / rad */
+    const int32_t* muscle_point_start; /* [n_muscles + 1] */
+    const float* muscle_fmax;          /* [n_muscles] maximum isometric force F_max (Eq. 1) */
+    const float* muscle_lopt;          /* [n_muscles] optimal fibre length */
+    const float* muscle_lslack;        /* [n_muscles] tendon slack length (recorded; rigid tendon) */
+    const int32_t* point_body;         /* [n_points] */
+    const float* point_pos;            /* [n_points][3] */
+    const int32_t* sphere_body;        /* [n_spheres] */
+    const float* sphere_pos;           /* [n_spheres][3] */
+    const float* sphere_radius;        /* [n_spheres] */
+    float gravity[3];                  /* m / s^2 */
+    float contact_k, contact_c;        /* penalty stiffness N/m and damping N s/m */
+    float contact_mu, contact_eps;     /* Coulomb coefficient, friction smoothing velocity m/s */
+    float limit_k, limit_c;            /* joint-limit stiffness N m/rad, damping N m s/rad */
+    float tau_act, tau_deact;          /* activation / deactivation time constants (Eq. 2) */
+    float vmax_per_lopt;               /* maximum contraction velocity in l_opt per second */
+} msim_model_desc;
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSIM_MODEL_H */

@@ -13,12 +13,12 @@
  *      R = -dL/dq, written out from the point Jacobians                          [EoM, J_m(q)]
  *   4. normalised fibre length / velocity: l_m = 1 + (L - L0)/l_opt, v_m = (dL/dt)/(10 l_opt)
  *   5. Hill force  F = F_max [act f_l(l_m) f_v(v_m) + f_p(l_m)]                    [Eq. 1]
- *   6. joint torques tau_m = R^T F, penalty ground contact (tau_ext), joint limits
+ *   6. joint torques tau_m = R^T F, penalty ground contact (tau_ext), joint-limit penalty
  *   7. bias C(q, qd) by world-frame Newton-Euler, M(q) column by column from the same
  *      Newton-Euler routine (q_dd = e_i, no gravity, qd = 0)                       [EoM]
  *   8. M q_dd + C = R^T F + tau_ext solved by dense Cholesky; velocity-dependent forces
- *      (muscle force-velocity, contact damping and friction, joint damping) are taken
- *      linearly implicit: (M + dt D) q_dd = rhs
+ *      (muscle force-velocity, contact damping and friction, joint damping) and the
+ *      joint-limit penalty are taken linearly implicit: (M + dt D) q_dd = rhs
  *   9. semi-implicit Euler: qd += dt q_dd, q += dt qd, act = clamp(act + dt act_dot, 0, 1)
  *
  * The paper does not print f_l, f_v, f_p (it cites Millard 2013), the tendon model, the contact
@@ -386,15 +386,19 @@ void ora_contact(const ora_model* M, const double* Rb, const double* pb, const d
 }
 
 /* ---------------------------------------------------------------- joint limits and damping
- * Outside [lo, hi] (enabled when lo < hi): tau = -k_l (q - hi) - c_l qd above, k_l (lo - q) - c_l qd
- * below.  Joint damping: tau -= b qd.  Dj (diagonal) receives d(-tau)/d qd for the implicit step. */
-void ora_joint_limits(const ora_model* M, const double* q, const double* qd, double* tau_l, double* Dj) {
+ * Outside [lo, hi] (enabled when lo < hi) a penalty spring-damper acts, taken linearly implicit in
+ * position and velocity: its torque is evaluated at the end-of-step state predicted by
+ * qd' = qd + dt qdd, q' = q + dt qd', i.e. tau = -k_l (q - hi + dt qd') - c_l qd' above hi (and
+ * symmetrically below lo).  The explicit part goes to tau_l, the part proportional to qdd to Dj
+ * (the system matrix receives dt * Dj = dt c_l + dt^2 k_l).  Joint damping: tau -= b qd, Dj += b. */
+void ora_joint_limits(const ora_model* M, double dt, const double* q, const double* qd, double* tau_l, double* Dj) {
     for (int d = 0; d < M->n; ++d) {
         double lo = M->dof_limit[2 * d], hi = M->dof_limit[2 * d + 1];
         double t = -M->dof_damping[d] * qd[d], dd = M->dof_damping[d];
+        double kk = M->limit_k, cc = M->limit_c;
         if (lo < hi) {
-            if (q[d] > hi) { t += -M->limit_k * (q[d] - hi) - M->limit_c * qd[d]; dd += M->limit_c; }
-            else if (q[d] < lo) { t += M->limit_k * (lo - q[d]) - M->limit_c * qd[d]; dd += M->limit_c; }
+            if (q[d] > hi) { t += -kk * (q[d] - hi) - (kk * dt + cc) * qd[d]; dd += cc + kk * dt; }
+            else if (q[d] < lo) { t += kk * (lo - q[d]) - (kk * dt + cc) * qd[d]; dd += cc + kk * dt; }
         }
         tau_l[d] = t;
         if (Dj) Dj[d] = dd;
@@ -503,7 +507,7 @@ int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, c
         }
     }
     ora_contact(M, Rb, pb, s, o, qd, tau_c, M->implicit_damping ? D : NULL, out ? out->sphere_force : NULL);
-    ora_joint_limits(M, q, qd, tau_l, Dj);
+    ora_joint_limits(M, dt, q, qd, tau_l, Dj);
     ora_rnea(M, q, qd, zero, 1, C);
     ora_mass_matrix(M, q, Mm);
     for (int i = 0; i < n; ++i) {

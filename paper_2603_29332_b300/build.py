@@ -1,0 +1,50 @@
+"""Build the CUDA library in-tree: ``libmsim.so`` next to this file, for sm_103a only.
+
+``python -m paper_2603_29332_b300.build`` (or ``__graft_entry__.build()``) runs nvcc once per
+changed source set; the result is loaded by :mod:`paper_2603_29332_b300.msim`.
+"""
+import hashlib
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIB = os.path.join(HERE, "libmsim.so")
+SOURCES = ["msim_api.cu", "step_kernels.cu"]
+HEADERS = ["image.h", "kernels.h", "dfloat.cuh"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "-Xcompiler", "-Wall", "--expt-relaxed-constexpr"]
+
+
+def _digest():
+    h = hashlib.sha256()
+    for f in SOURCES + HEADERS:
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    for f in ("msim.h", "msim_model.h"):
+        h.update(open(os.path.join(ROOT, "include", f), "rb").read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
+def build(force=False, verbose=False):
+    stamp = LIB + ".sha256"
+    dig = _digest()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read().strip() == dig:
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["nvcc"] + ARCH + FLAGS + ["-I", os.path.join(ROOT, "include"), "-o", tmp] + \
+          [os.path.join(CSRC, s) for s in SOURCES] + ["-lcudart"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(dig + "\n")
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

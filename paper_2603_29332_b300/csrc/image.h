@@ -1,0 +1,98 @@
+// image.h -- flat device image of one model, and the per-environment shared-memory workspace.
+//
+// The image is one contiguous, 16-byte aligned blob: a header, then fixed-size records and
+// small index tables.  A step kernel copies it into shared memory with one bulk copy
+// (cp.async.bulk) per block and keeps it resident across substeps and environments.
+#pragma once
+#include <stdint.h>
+
+namespace msim {
+
+constexpr int kMaxPts = 8;      // path points per muscle
+constexpr int kMaxCross = 12;   // DoFs crossed by one muscle
+constexpr int kMaxDepth = 63;   // DoF tree depth
+constexpr int kMaxModels = 8;
+constexpr int kMaxSpheres = 32;
+constexpr int kFiStride = 26;   // floats per body in the fi workspace
+
+struct alignas(16) BodyRec {    // 64 B
+    float off[3];               // joint origin in the parent frame (world for roots)
+    float mass;
+    float com[3];               // body frame
+    int32_t parent;             // -1: world
+    float I[6];                 // inertia about the COM, body frame: xx yy zz xy xz yz
+    int16_t dof0, ndof;         // hinge DoFs of this body
+    int16_t child0, nchild;     // range in the child table
+};
+
+struct alignas(16) DofRec {     // 32 B
+    float axis[3];              // unit, frame before the hinge
+    float lo, hi;               // limits (lo >= hi: none)
+    float damp;                 // joint damping
+    int32_t row;                // packed row start (lower triangle, ancestors by depth)
+    int16_t parent;             // parent DoF (-1: none)
+    uint8_t depth;              // number of ancestor DoFs
+    uint8_t body;
+};
+
+struct alignas(16) MuscleRec {  // 32 B
+    float fmax;
+    float inv_lopt;             // 1 / l_opt
+    float L0;                   // reference length L(q = 0), filled on the device at create
+    float inv_vmax;             // 1 / (vmax_per_lopt * l_opt)
+    int32_t p0;                 // first path point
+    int32_t x0;                 // first entry in the crossed-DoF table (== offset in sparse R)
+    uint8_t np, nx;             // number of points, number of crossed DoFs
+    uint16_t pad0;
+    int32_t pad1;
+};
+
+struct alignas(16) PointRec {   // 16 B
+    float pos[3];               // body frame
+    int32_t body_cross;         // body | (crossed DoFs at or above this point's body) << 8
+};
+
+struct alignas(16) SphereRec {  // 32 B
+    float pos[3];
+    float radius;
+    int32_t body;
+    int32_t last_dof;           // the DoF whose frame carries the sphere
+    int32_t pad[2];
+};
+
+struct alignas(16) ImgHeader {
+    int32_t n, m, nb, np, ns;
+    int32_t n_packed;           // sum over DoFs of (depth + 1)
+    int32_t nnz;                // crossed-DoF entries of all muscles (non-zeros of R)
+    int32_t n_blevels, n_dlevels, max_depth, n_tri, total_bytes;
+    // byte offsets of the sections
+    int32_t o_body, o_dof, o_muscle, o_sphere, o_cross, o_border, o_blevel, o_child, o_anc, o_dorder, o_dlevel,
+        o_tri, o_point, staged_bytes, points_in_smem, o_pad0;
+    // per-environment workspace layout (float offsets inside the environment's slot)
+    int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_y, w_sph, w_rk, w_floats, w_pad0, w_pad1, w_pad2,
+        w_pad3;
+    float gravity[3];
+    float contact_k, contact_c, contact_mu, contact_eps2;
+    float limit_k, limit_c, tau_act, tau_deact;
+    float fp_den;               // exp(4) - 1 of the passive curve
+    float fp_slope;             // slope of the passive curve's linear extension
+    float pad[3];
+};
+
+// Per environment workspace (floats), laid out by the host (msim_api.cu):
+//   q[n], qd[n]                       state, resident across substeps (act stays in global memory)
+//   frame[nb][12]                     body rotation (9, row-major) and origin (3), world
+//   v[nb][6]                          spatial velocity [w; v_O] (Plücker, world origin)
+//   fi[nb][26]                        body force [n; f] (6, FP32) and spatial inertia about the
+//                                     world origin (m, h, Ibar) as 10 float-float pairs (20),
+//                                     summed over subtrees in place
+//   S[n][6]                           joint motion axis [s; o x s]
+//   A[max(n_packed, 3 nb)][2]         packed M + dt D as float-float (hi, lo) pairs, factorised in
+//                                     place; holds the bias accelerations a[nb][6] (FP32) during
+//                                     the first pass
+//   rhs[n]                            R^T F + tau_c + tau_l - C (FP32)
+//   y[n][2]                           float-float solution of the two triangular solves
+//   sph[ns][12]                       per-sphere contact point, force, damping, flags
+//   rk[kMaxCross][32]                 per-lane moment arms of the muscle being processed
+
+}  // namespace msim

@@ -1,0 +1,748 @@
+// msim_api.cu -- C ABI of the batched muscle-driven forward-dynamics library (include/msim.h).
+//
+// Host side only: validates model descriptions, builds the flat device images (image.h),
+// owns the state buffers and launches the kernels of step_kernels.cu.  No dynamics arithmetic
+// runs on the host: even the reference muscle lengths L0 = L(q = 0) are computed by the device
+// kernel at create time.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/msim.h"
+#include "image.h"
+#include "kernels.h"
+
+using namespace msim;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct ModelHost {
+    ImgHeader hdr;
+    std::vector<uint8_t> blob;
+    std::vector<int32_t> dof_parent, dof_depth, packed_row, mus_ptr, mus_dof;
+};
+
+int pad4(int x) { return (x + 3) & ~3; }
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+bool finite_all(const float* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+#define FAIL(...)                                            \
+    do {                                                     \
+        char buf_[256];                                      \
+        std::snprintf(buf_, sizeof(buf_), __VA_ARGS__);      \
+        err = buf_;                                          \
+        return false;                                        \
+    } while (0)
+
+bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
+    const int nb = d.n_bodies, n = d.n_dofs, m = d.n_muscles, np = d.n_points, ns = d.n_spheres;
+    if (nb < 1 || nb > 255) FAIL("n_bodies must be in [1, 255] (got %d)", nb);
+    if (n < 1 || n > 255) FAIL("n_dofs must be in [1, 255] (got %d)", n);
+    if (m < 0 || m > 4096) FAIL("n_muscles must be in [0, 4096] (got %d)", m);
+    if (ns < 0 || ns > kMaxSpheres) FAIL("n_spheres must be in [0, %d] (got %d)", kMaxSpheres, ns);
+    if (np < 0 || np < 2 * m) FAIL("n_points must be >= 2 n_muscles");
+    if (!d.body_parent || !d.body_ndof || !d.body_offset || !d.body_mass || !d.body_com || !d.body_inertia ||
+        !d.dof_axis)
+        FAIL("missing body or DoF array");
+    if (m > 0 && (!d.muscle_point_start || !d.muscle_fmax || !d.muscle_lopt || !d.point_body || !d.point_pos))
+        FAIL("missing muscle array");
+    if (ns > 0 && (!d.sphere_body || !d.sphere_pos || !d.sphere_radius)) FAIL("missing sphere array");
+    if (!finite_all(d.body_offset, 3 * nb) || !finite_all(d.body_mass, nb) || !finite_all(d.body_com, 3 * nb) ||
+        !finite_all(d.body_inertia, 6 * nb) || !finite_all(d.dof_axis, 3 * n))
+        FAIL("non-finite body or DoF parameter");
+
+    // ---- DoF tree
+    std::vector<int> dof0(nb), dof_body(n), dpar(n), depth(n), bdepth(nb);
+    int acc = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int pb = d.body_parent[b];
+        if (pb < -1 || pb >= b) FAIL("body_parent[%d] = %d must be in [-1, %d)", b, pb, b);
+        const int k = d.body_ndof[b];
+        if (k < 1 || k > 3) FAIL("body_ndof[%d] = %d must be 1..3", b, k);
+        dof0[b] = acc;
+        for (int j = 0; j < k; ++j) {
+            const int dd = acc + j;
+            dof_body[dd] = b;
+            dpar[dd] = (j > 0) ? dd - 1 : (pb < 0 ? -1 : dof0[pb] + d.body_ndof[pb] - 1);
+            depth[dd] = dpar[dd] < 0 ? 0 : depth[dpar[dd]] + 1;
+            if (depth[dd] > kMaxDepth) FAIL("DoF depth above %d", kMaxDepth);
+        }
+        acc += k;
+        bdepth[b] = pb < 0 ? 0 : bdepth[pb] + 1;
+    }
+    if (acc != n) FAIL("sum of body_ndof (%d) != n_dofs (%d)", acc, n);
+    for (int i = 0; i < n; ++i) {
+        const float* a = d.dof_axis + 3 * i;
+        const double nrm = std::sqrt(double(a[0]) * a[0] + double(a[1]) * a[1] + double(a[2]) * a[2]);
+        if (std::fabs(nrm - 1.0) > 1e-4) FAIL("dof_axis[%d] is not a unit vector", i);
+    }
+    std::vector<int> row(n);
+    int nM = 0, max_depth = 0;
+    for (int i = 0; i < n; ++i) {
+        row[i] = nM;
+        nM += depth[i] + 1;
+        max_depth = std::max(max_depth, depth[i]);
+    }
+    std::vector<uint8_t> anc(nM);
+    for (int i = 0; i < n; ++i)
+        for (int a = i; a >= 0; a = dpar[a]) anc[row[i] + depth[a]] = (uint8_t)a;
+
+    // body levels and children
+    const int n_bl = *std::max_element(bdepth.begin(), bdepth.end()) + 1;
+    std::vector<uint8_t> border;
+    std::vector<int16_t> blevel(n_bl + 1, 0);
+    for (int l = 0; l < n_bl; ++l) {
+        blevel[l] = (int16_t)border.size();
+        for (int b = 0; b < nb; ++b)
+            if (bdepth[b] == l) border.push_back((uint8_t)b);
+    }
+    blevel[n_bl] = (int16_t)border.size();
+    std::vector<uint8_t> child;
+    std::vector<int> child0(nb), nchild(nb);
+    for (int b = 0; b < nb; ++b) {
+        child0[b] = (int)child.size();
+        for (int c = b + 1; c < nb; ++c)
+            if (d.body_parent[c] == b) child.push_back((uint8_t)c);
+        nchild[b] = (int)child.size() - child0[b];
+    }
+    // DoF levels
+    const int n_dl = max_depth + 1;
+    std::vector<uint8_t> dorder;
+    std::vector<int16_t> dlevel(n_dl + 1, 0);
+    for (int l = 0; l < n_dl; ++l) {
+        dlevel[l] = (int16_t)dorder.size();
+        for (int i = 0; i < n; ++i)
+            if (depth[i] == l) dorder.push_back((uint8_t)i);
+    }
+    dlevel[n_dl] = (int16_t)dorder.size();
+    // pair table: p -> (ia, ib), ib <= ia, row by row
+    std::vector<uint16_t> tri;
+    for (int ia = 0; ia <= max_depth; ++ia)
+        for (int ib = 0; ib <= ia; ++ib) tri.push_back((uint16_t)(ia | (ib << 8)));
+
+    // ---- muscles
+    std::vector<MuscleRec> mus(m);
+    std::vector<PointRec> pts(np);
+    std::vector<uint8_t> cross;
+    std::vector<int32_t> mus_ptr(m + 1, 0), mus_dof;
+    if (m > 0) {
+        if (d.muscle_point_start[0] != 0 || d.muscle_point_start[m] != np)
+            FAIL("muscle_point_start must start at 0 and end at n_points");
+        if (!finite_all(d.point_pos, 3 * np) || !finite_all(d.muscle_fmax, m) || !finite_all(d.muscle_lopt, m))
+            FAIL("non-finite muscle parameter");
+    }
+    for (int k = 0; k < m; ++k) {
+        const int j0 = d.muscle_point_start[k], j1 = d.muscle_point_start[k + 1];
+        const int cnt = j1 - j0;
+        if (cnt < 2 || cnt > kMaxPts) FAIL("muscle %d has %d points (allowed 2..%d)", k, cnt, kMaxPts);
+        if (!(d.muscle_lopt[k] > 0.f) || !(d.muscle_fmax[k] >= 0.f)) FAIL("muscle %d: l_opt must be > 0", k);
+        for (int j = j0; j < j1; ++j)
+            if (d.point_body[j] < 0 || d.point_body[j] >= nb) FAIL("point %d: body out of range", j);
+        const int A = d.point_body[j0], B = d.point_body[j1 - 1];
+        std::vector<int> chain;   // bodies strictly below A down to B, root to leaf
+        int b = B;
+        while (b != A && b >= 0) {
+            chain.push_back(b);
+            b = d.body_parent[b];
+        }
+        if (b != A) FAIL("muscle %d: insertion body is not a descendant of the origin body", k);
+        std::reverse(chain.begin(), chain.end());
+        auto pos_of = [&](int body) -> int {
+            if (body == A) return 0;
+            for (size_t t = 0; t < chain.size(); ++t)
+                if (chain[t] == body) return (int)t + 1;
+            return -1;
+        };
+        std::vector<int> ccount(chain.size() + 1, 0);
+        for (size_t t = 0; t < chain.size(); ++t) ccount[t + 1] = ccount[t] + d.body_ndof[chain[t]];
+        const int nx = ccount.back();
+        if (nx > kMaxCross) FAIL("muscle %d crosses %d DoFs (max %d)", k, nx, kMaxCross);
+        int prev = 0;
+        for (int j = j0; j < j1; ++j) {
+            const int t = pos_of(d.point_body[j]);
+            if (t < 0 || t < prev) FAIL("muscle %d: path points must follow the origin-to-insertion chain", k);
+            prev = t;
+            PointRec& P = pts[j];
+            P.pos[0] = d.point_pos[3 * j]; P.pos[1] = d.point_pos[3 * j + 1]; P.pos[2] = d.point_pos[3 * j + 2];
+            P.body_cross = d.point_body[j] | (ccount[t] << 8);
+        }
+        MuscleRec& M = mus[k];
+        std::memset(&M, 0, sizeof(M));
+        M.fmax = d.muscle_fmax[k];
+        M.inv_lopt = 1.f / d.muscle_lopt[k];
+        M.L0 = 0.f;
+        M.inv_vmax = 1.f / (d.vmax_per_lopt * d.muscle_lopt[k]);
+        M.p0 = j0;
+        M.x0 = (int32_t)cross.size();
+        M.np = (uint8_t)cnt;
+        M.nx = (uint8_t)nx;
+        for (size_t t = 0; t < chain.size(); ++t)
+            for (int j = 0; j < d.body_ndof[chain[t]]; ++j) {
+                cross.push_back((uint8_t)(dof0[chain[t]] + j));
+                mus_dof.push_back(dof0[chain[t]] + j);
+            }
+        mus_ptr[k + 1] = (int32_t)cross.size();
+    }
+    if (!(d.vmax_per_lopt > 0.f) || !(d.tau_act > 0.f) || !(d.tau_deact > 0.f)) FAIL("time constants must be > 0");
+
+    // ---- spheres
+    std::vector<SphereRec> sph(ns);
+    for (int i = 0; i < ns; ++i) {
+        const int b = d.sphere_body[i];
+        if (b < 0 || b >= nb) FAIL("sphere %d: body out of range", i);
+        std::memset(&sph[i], 0, sizeof(SphereRec));
+        for (int c = 0; c < 3; ++c) sph[i].pos[c] = d.sphere_pos[3 * i + c];
+        sph[i].radius = d.sphere_radius[i];
+        sph[i].body = b;
+        sph[i].last_dof = dof0[b] + d.body_ndof[b] - 1;
+    }
+
+    // ---- records
+    std::vector<BodyRec> bodies(nb);
+    for (int b = 0; b < nb; ++b) {
+        BodyRec& B = bodies[b];
+        std::memset(&B, 0, sizeof(B));
+        for (int c = 0; c < 3; ++c) { B.off[c] = d.body_offset[3 * b + c]; B.com[c] = d.body_com[3 * b + c]; }
+        B.mass = d.body_mass[b];
+        B.parent = d.body_parent[b];
+        for (int c = 0; c < 6; ++c) B.I[c] = d.body_inertia[6 * b + c];
+        B.dof0 = (int16_t)dof0[b];
+        B.ndof = (int16_t)d.body_ndof[b];
+        B.child0 = (int16_t)child0[b];
+        B.nchild = (int16_t)nchild[b];
+    }
+    std::vector<DofRec> dofs(n);
+    for (int i = 0; i < n; ++i) {
+        DofRec& D = dofs[i];
+        std::memset(&D, 0, sizeof(D));
+        for (int c = 0; c < 3; ++c) D.axis[c] = d.dof_axis[3 * i + c];
+        D.lo = d.dof_limit ? d.dof_limit[2 * i] : 0.f;
+        D.hi = d.dof_limit ? d.dof_limit[2 * i + 1] : 0.f;
+        D.damp = d.dof_damping ? d.dof_damping[i] : 0.f;
+        D.row = row[i];
+        D.parent = (int16_t)dpar[i];
+        D.depth = (uint8_t)depth[i];
+        D.body = (uint8_t)dof_body[i];
+    }
+
+    // ---- header and blob
+    ImgHeader& h = out.hdr;
+    std::memset(&h, 0, sizeof(h));
+    h.n = n; h.m = m; h.nb = nb; h.np = np; h.ns = ns;
+    h.n_packed = nM;
+    h.nnz = (int32_t)cross.size();
+    h.n_blevels = n_bl;
+    h.n_dlevels = n_dl;
+    h.max_depth = max_depth;
+    h.n_tri = (int32_t)tri.size();
+    size_t off = align16(sizeof(ImgHeader));
+    auto place = [&](size_t bytes) {
+        const size_t o = off;
+        off = align16(off + bytes);
+        return (int32_t)o;
+    };
+    h.o_body = place(sizeof(BodyRec) * nb);
+    h.o_dof = place(sizeof(DofRec) * n);
+    h.o_muscle = place(sizeof(MuscleRec) * m);
+    h.o_sphere = place(sizeof(SphereRec) * ns);
+    h.o_cross = place(cross.size());
+    h.o_border = place(border.size());
+    h.o_blevel = place(sizeof(int16_t) * blevel.size());
+    h.o_child = place(child.size());
+    h.o_anc = place(anc.size());
+    h.o_dorder = place(dorder.size());
+    h.o_dlevel = place(sizeof(int16_t) * dlevel.size());
+    h.o_tri = place(sizeof(uint16_t) * tri.size());
+    h.o_point = place(sizeof(PointRec) * np);   // last: may stay in global memory (staging split)
+    h.total_bytes = (int32_t)off;
+    // per-environment workspace
+    int w = 0;
+    auto slot = [&](int floats) {
+        const int o = w;
+        w += pad4(floats);
+        return o;
+    };
+    h.w_q = slot(n);
+    h.w_qd = slot(n);
+    h.w_frame = slot(12 * nb);
+    h.w_v = slot(6 * nb);
+    h.w_fi = slot(kFiStride * nb);
+    h.w_S = slot(6 * n);
+    h.w_A = slot(2 * std::max(nM, 3 * nb));
+    h.w_rhs = slot(n);
+    h.w_y = slot(2 * n);
+    h.w_sph = slot(12 * ns);
+    h.w_rk = slot(kMaxCross * 32);
+    h.w_floats = w;
+    for (int c = 0; c < 3; ++c) h.gravity[c] = d.gravity[c];
+    h.contact_k = d.contact_k;
+    h.contact_c = d.contact_c;
+    h.contact_mu = d.contact_mu;
+    h.contact_eps2 = d.contact_eps * d.contact_eps;
+    h.limit_k = d.limit_k;
+    h.limit_c = d.limit_c;
+    h.tau_act = d.tau_act;
+    h.tau_deact = d.tau_deact;
+    const double e4 = std::exp(4.0);
+    h.fp_den = (float)(e4 - 1.0);
+    h.fp_slope = (float)((4.0 / 0.6) * e4 / (e4 - 1.0));
+
+    out.blob.assign(h.total_bytes, 0);
+    auto put = [&](int32_t o, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(out.blob.data() + o, src, bytes);
+    };
+    put(0, &h, sizeof(h));
+    put(h.o_body, bodies.data(), sizeof(BodyRec) * nb);
+    put(h.o_dof, dofs.data(), sizeof(DofRec) * n);
+    put(h.o_muscle, mus.data(), sizeof(MuscleRec) * m);
+    put(h.o_point, pts.data(), sizeof(PointRec) * np);
+    put(h.o_sphere, sph.data(), sizeof(SphereRec) * ns);
+    put(h.o_cross, cross.data(), cross.size());
+    put(h.o_border, border.data(), border.size());
+    put(h.o_blevel, blevel.data(), sizeof(int16_t) * blevel.size());
+    put(h.o_child, child.data(), child.size());
+    put(h.o_anc, anc.data(), anc.size());
+    put(h.o_dorder, dorder.data(), dorder.size());
+    put(h.o_dlevel, dlevel.data(), sizeof(int16_t) * dlevel.size());
+    put(h.o_tri, tri.data(), sizeof(uint16_t) * tri.size());
+
+    out.dof_parent.assign(dpar.begin(), dpar.end());
+    out.dof_depth.assign(depth.begin(), depth.end());
+    out.packed_row.assign(row.begin(), row.end());
+    out.mus_ptr = mus_ptr;
+    out.mus_dof = mus_dof;
+    return true;
+}
+#undef FAIL
+
+}  // namespace
+
+struct msim_handle_ {
+    int device = 0;
+    int n_models = 0, n_envs = 0, pitch_n = 0, pitch_m = 0;
+    float dt = 0.f;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    ModelHost models[kMaxModels];
+    uint8_t* d_img[kMaxModels] = {};
+    int env_begin[kMaxModels + 1] = {};
+    int epb[kMaxModels] = {};
+    int pts_smem[kMaxModels] = {};
+    float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *exc_stage = nullptr;
+    uint32_t* env_status = nullptr;
+    uint32_t* gflags = nullptr;
+    unsigned long long* timers = nullptr;   // profiling builds (MSIM_PHASE_TIMERS) only
+    std::string err;
+};
+
+namespace {
+
+msim_status cuda_fail(msim_handle h, cudaError_t e, const char* what) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    if (h) h->err = buf; else g_create_error = buf;
+    return (e == cudaErrorMemoryAllocation) ? MSIM_ERR_OOM : MSIM_ERR_CUDA;
+}
+
+msim_status arg_fail(msim_handle h, const char* what) {
+    if (h) h->err = what; else g_create_error = what;
+    return MSIM_ERR_ARG;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+void free_all(msim_handle h) {
+    for (int i = 0; i < kMaxModels; ++i)
+        if (h->d_img[i]) cudaFree(h->d_img[i]);
+    cudaFree(h->q); cudaFree(h->qd); cudaFree(h->act); cudaFree(h->qdd); cudaFree(h->force);
+    cudaFree(h->exc_stage); cudaFree(h->env_status); cudaFree(h->gflags);
+    if (h->timers) cudaFree(h->timers);
+}
+
+int model_grid(msim_handle h, int i) {
+    const int ne = h->env_begin[i + 1] - h->env_begin[i];
+    const int groups = (ne + h->epb[i] - 1) / h->epb[i];
+    const size_t smem = step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i]);
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * h->epb[i], smem));
+    return std::max(1, std::min(groups, h->num_sms * per_sm));
+}
+
+StepArgs base_args(msim_handle h, int i) {
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.img = h->d_img[i];
+    a.points_in_smem = h->pts_smem[i];
+    a.staged_bytes = h->pts_smem[i] ? h->models[i].hdr.total_bytes : h->models[i].hdr.o_point;
+    a.env_begin = h->env_begin[i];
+    a.env_end = h->env_begin[i + 1];
+    a.q = h->q; a.qd = h->qd; a.act = h->act;
+    a.pitch_n = h->pitch_n; a.pitch_m = h->pitch_m;
+    a.qdd_out = h->qdd; a.force_out = h->force;
+    a.env_status = h->env_status; a.gflags = h->gflags;
+    a.dt = h->dt;
+    a.envs_per_block = h->epb[i];
+    a.timers = h->timers;
+    return a;
+}
+
+int max_epb(msim_handle h, int i, bool pts) {
+    const ImgHeader& hd = h->models[i].hdr;
+    const size_t fixed = step_smem_bytes(hd, 0, pts);
+    const size_t per = (size_t)hd.w_floats * sizeof(float);
+    if (fixed + per > h->smem_optin) return 0;
+    return std::min((int)((h->smem_optin - fixed) / per), kMaxEnvsPerBlock);
+}
+
+// Default launch shape: as many environments per block as shared memory holds (<= 8, <= the
+// model's environments), path points staged in shared memory unless that leaves fewer than 4.
+void auto_launch(msim_handle h, int i) {
+    const int ne = h->env_begin[i + 1] - h->env_begin[i];
+    int e_in = std::min(max_epb(h, i, true), 8), e_out = std::min(max_epb(h, i, false), 8);
+    if (ne > 0) { e_in = std::min(e_in, ne); e_out = std::min(e_out, ne); }
+    if (e_in >= 4 || (e_in >= 1 && e_in >= e_out)) { h->pts_smem[i] = 1; h->epb[i] = e_in; }
+    else { h->pts_smem[i] = 0; h->epb[i] = e_out; }
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t msim_version(void) { return 1; }
+
+const char* msim_last_error(msim_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+msim_status msim_create(const msim_create_args* args, msim_handle* out) {
+    g_create_error.clear();
+    if (!args || !out) return arg_fail(nullptr, "msim_create: NULL argument");
+    *out = nullptr;
+    if (args->n_models < 1 || args->n_models > kMaxModels) return arg_fail(nullptr, "n_models must be 1..8");
+    if (!args->models || !args->envs_per_model) return arg_fail(nullptr, "models / envs_per_model is NULL");
+    if (!(args->dt > 0.f) || !std::isfinite(args->dt)) return arg_fail(nullptr, "dt must be > 0");
+    if (args->geometry_mode != 0) {
+        g_create_error = "geometry_mode: only 0 (exact via-point geometry) is provided by this entry point";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    msim_handle h = new msim_handle_();
+    h->device = args->device;
+    h->n_models = args->n_models;
+    h->dt = args->dt;
+    int total = 0, nmax = 0, mmax = 0;
+    for (int i = 0; i < args->n_models; ++i) {
+        if (args->envs_per_model[i] < 0) {
+            delete h;
+            return arg_fail(nullptr, "envs_per_model must be >= 0");
+        }
+        std::string err;
+        if (!build_image(args->models[i], h->models[i], err)) {
+            g_create_error = "model " + std::to_string(i) + ": " + err;
+            delete h;
+            return MSIM_ERR_MODEL;
+        }
+        h->env_begin[i] = total;
+        total += args->envs_per_model[i];
+        nmax = std::max(nmax, args->models[i].n_dofs);
+        mmax = std::max(mmax, args->models[i].n_muscles);
+    }
+    h->env_begin[args->n_models] = total;
+    if (total < 1 || total > (1 << 24)) {
+        delete h;
+        return arg_fail(nullptr, "total environments must be in [1, 2^24]");
+    }
+    h->n_envs = total;
+    h->pitch_n = pad4(nmax);
+    h->pitch_m = pad4(std::max(mmax, 1));
+
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) { msim_status s = cuda_fail(nullptr, e, "cudaSetDevice"); delete h; return s; }
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, h->device);
+    h->num_sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    h->smem_optin = (size_t)v;
+    e = set_step_smem_limit(h->smem_optin);
+    if (e != cudaSuccess) { msim_status s = cuda_fail(nullptr, e, "smem attribute"); delete h; return s; }
+
+    const size_t rn = (size_t)total * h->pitch_n * sizeof(float), rm = (size_t)total * h->pitch_m * sizeof(float);
+#define ALLOC(ptr, bytes)                                                        \
+    do {                                                                         \
+        e = cudaMalloc(&(ptr), (bytes));                                         \
+        if (e != cudaSuccess) {                                                  \
+            msim_status s_ = cuda_fail(nullptr, e, "cudaMalloc " #ptr);          \
+            free_all(h);                                                         \
+            delete h;                                                            \
+            return s_;                                                           \
+        }                                                                        \
+    } while (0)
+    ALLOC(h->q, rn); ALLOC(h->qd, rn); ALLOC(h->qdd, rn);
+    ALLOC(h->act, rm); ALLOC(h->force, rm); ALLOC(h->exc_stage, rm);
+    ALLOC(h->env_status, sizeof(uint32_t) * total);
+    ALLOC(h->gflags, sizeof(uint32_t));
+#ifdef MSIM_PHASE_TIMERS
+    ALLOC(h->timers, sizeof(unsigned long long) * 8);
+    cudaMemset(h->timers, 0, sizeof(unsigned long long) * 8);
+#endif
+    cudaMemset(h->q, 0, rn); cudaMemset(h->qd, 0, rn); cudaMemset(h->qdd, 0, rn);
+    cudaMemset(h->act, 0, rm); cudaMemset(h->force, 0, rm); cudaMemset(h->exc_stage, 0, rm);
+    cudaMemset(h->env_status, 0, sizeof(uint32_t) * total);
+    cudaMemset(h->gflags, 0, sizeof(uint32_t));
+
+    // device images; reference lengths L0 = L(q = 0) from the device geometry code
+    float *zq = nullptr, *zm = nullptr, *Lbuf = nullptr;
+    ALLOC(zq, sizeof(float) * h->pitch_n * 2);
+    ALLOC(zm, sizeof(float) * h->pitch_m * 3);
+    Lbuf = zm + 2 * h->pitch_m;
+    cudaMemset(zq, 0, sizeof(float) * h->pitch_n * 2);
+    cudaMemset(zm, 0, sizeof(float) * h->pitch_m * 3);
+    for (int i = 0; i < h->n_models; ++i) {
+        const ModelHost& M = h->models[i];
+        ALLOC(h->d_img[i], M.blob.size());
+        e = cudaMemcpy(h->d_img[i], M.blob.data(), M.blob.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && M.hdr.m > 0) {
+            StepArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.img = h->d_img[i];
+            a.staged_bytes = M.hdr.o_point;
+            a.points_in_smem = 0;
+            a.env_begin = 0; a.env_end = 1;
+            a.q = zq; a.qd = zq + h->pitch_n; a.act = zm; a.exc = zm + h->pitch_m;
+            a.pitch_n = h->pitch_n; a.pitch_m = h->pitch_m;
+            a.env_status = h->env_status; a.gflags = h->gflags;
+            a.n_sub = 1; a.dt = h->dt; a.envs_per_block = 1;
+            a.ev.L = Lbuf;
+            const size_t smem = step_smem_bytes(M.hdr, 1, false);
+            if (smem > h->smem_optin) {
+                g_create_error = "model " + std::to_string(i) + " does not fit in shared memory";
+                cudaFree(zq); cudaFree(zm); free_all(h); delete h;
+                return MSIM_ERR_MODEL;
+            }
+            e = launch_eval(a, 1, smem, 0);
+            if (e == cudaSuccess) e = launch_set_l0(h->d_img[i], Lbuf, M.hdr.m, 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        if (e != cudaSuccess) {
+            msim_status s = cuda_fail(nullptr, e, "model image upload / L0");
+            cudaFree(zq); cudaFree(zm); free_all(h); delete h;
+            return s;
+        }
+        auto_launch(h, i);
+        if (h->epb[i] < 1) {
+            g_create_error = "model " + std::to_string(i) + " does not fit in shared memory";
+            cudaFree(zq); cudaFree(zm); free_all(h); delete h;
+            return MSIM_ERR_MODEL;
+        }
+    }
+#undef ALLOC
+    cudaFree(zq);
+    cudaFree(zm);
+    cudaMemset(h->gflags, 0, sizeof(uint32_t));
+    cudaMemset(h->env_status, 0, sizeof(uint32_t) * total);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { msim_status s = cuda_fail(nullptr, e, "create"); free_all(h); delete h; return s; }
+    *out = h;
+    return MSIM_OK;
+}
+
+msim_status msim_destroy(msim_handle h) {
+    if (!h) return MSIM_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return MSIM_OK;
+}
+
+msim_status msim_get_dims(msim_handle h, msim_dims* out) {
+    if (!h || !out) return arg_fail(h, "msim_get_dims: NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_envs = h->n_envs;
+    out->n_models = h->n_models;
+    out->pitch_n = h->pitch_n;
+    out->pitch_m = h->pitch_m;
+    for (int i = 0; i <= h->n_models; ++i) out->env_begin[i] = h->env_begin[i];
+    for (int i = 0; i < h->n_models; ++i) {
+        const ImgHeader& hd = h->models[i].hdr;
+        out->n_dofs[i] = hd.n;
+        out->n_muscles[i] = hd.m;
+        out->n_bodies[i] = hd.nb;
+        out->nnz[i] = hd.nnz;
+        out->n_packed[i] = hd.n_packed;
+        out->envs_per_block[i] = h->epb[i];
+        out->image_bytes[i] = hd.total_bytes;
+        out->workspace_bytes_per_env[i] = hd.w_floats * (int)sizeof(float);
+        out->points_in_smem[i] = h->pts_smem[i];
+    }
+    return MSIM_OK;
+}
+
+msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_per_block, int32_t stage_points) {
+    if (!h || model < 0 || model >= h->n_models) return arg_fail(h, "msim_set_launch: bad handle or model");
+    if (envs_per_block < 0 || envs_per_block > kMaxEnvsPerBlock) return arg_fail(h, "envs_per_block must be 0..16");
+    if (stage_points < -1 || stage_points > 1) return arg_fail(h, "stage_points must be -1, 0 or 1");
+    if (envs_per_block == 0 && stage_points == -1) {
+        auto_launch(h, model);
+        return MSIM_OK;
+    }
+    const bool pts = stage_points == -1 ? (h->pts_smem[model] != 0) : (stage_points == 1);
+    int e = envs_per_block;
+    if (e == 0) e = std::min(max_epb(h, model, pts), 8);
+    if (e < 1 || step_smem_bytes(h->models[model].hdr, e, pts) > h->smem_optin)
+        return arg_fail(h, "msim_set_launch: shared memory does not fit");
+    h->epb[model] = e;
+    h->pts_smem[model] = pts ? 1 : 0;
+    return MSIM_OK;
+}
+
+msim_status msim_reset(msim_handle h, const float* q0, const float* qd0, const float* act0, const int32_t* env_ids,
+                       int32_t n_ids, msim_stream_t stream) {
+    if (!h) return arg_fail(h, "msim_reset: NULL handle");
+    if (env_ids && (n_ids < 0 || n_ids > h->n_envs)) return arg_fail(h, "msim_reset: n_ids out of range");
+    if (!aligned16(q0) || !aligned16(qd0) || !aligned16(act0)) return arg_fail(h, "msim_reset: unaligned pointer");
+    const int rows = env_ids ? n_ids : h->n_envs;
+    cudaSetDevice(h->device);
+    cudaError_t e = launch_reset(h->q, h->qd, h->act, h->env_status, q0, qd0, act0, env_ids, rows, h->pitch_n,
+                                 h->pitch_m, h->n_envs, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_reset");
+}
+
+msim_status msim_step(msim_handle h, const float* excitations, int32_t n_substeps, msim_stream_t stream) {
+    if (!h || !excitations) return arg_fail(h, "msim_step: NULL argument");
+    if (n_substeps < 1 || n_substeps > 100000) return arg_fail(h, "msim_step: n_substeps must be 1..100000");
+    if (!aligned16(excitations)) return arg_fail(h, "msim_step: excitations not 16-byte aligned");
+    cudaSetDevice(h->device);
+    for (int i = 0; i < h->n_models; ++i) {
+        if (h->env_begin[i + 1] == h->env_begin[i]) continue;
+        StepArgs a = base_args(h, i);
+        a.exc = excitations;
+        a.n_sub = n_substeps;
+        const cudaError_t e = launch_step(a, model_grid(h, i), step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i]),
+                                          (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "msim_step launch");
+    }
+    return MSIM_OK;
+}
+
+msim_status msim_step_host(msim_handle h, const float* excitations_host, int32_t n_substeps, float* q_host,
+                           float* qd_host, msim_stream_t stream) {
+    if (!h || !excitations_host) return arg_fail(h, "msim_step_host: NULL argument");
+    cudaSetDevice(h->device);
+    const size_t rm = (size_t)h->n_envs * h->pitch_m * sizeof(float);
+    const size_t rn = (size_t)h->n_envs * h->pitch_n * sizeof(float);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->exc_stage, excitations_host, rm, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "msim_step_host H2D");
+    msim_status st = msim_step(h, h->exc_stage, n_substeps, stream);
+    if (st != MSIM_OK) return st;
+    if (q_host) e = cudaMemcpyAsync(q_host, h->q, rn, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && qd_host) e = cudaMemcpyAsync(qd_host, h->qd, rn, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_step_host D2H");
+}
+
+msim_status msim_get_state(msim_handle h, float* q, float* qd, float* act, float* qdd, float* muscle_force,
+                           uint32_t* env_status, msim_stream_t stream) {
+    if (!h) return arg_fail(h, "msim_get_state: NULL handle");
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rn = (size_t)h->n_envs * h->pitch_n * sizeof(float);
+    const size_t rm = (size_t)h->n_envs * h->pitch_m * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (q) e = cudaMemcpyAsync(q, h->q, rn, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && qd) e = cudaMemcpyAsync(qd, h->qd, rn, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && qdd) e = cudaMemcpyAsync(qdd, h->qdd, rn, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && act) e = cudaMemcpyAsync(act, h->act, rm, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && muscle_force) e = cudaMemcpyAsync(muscle_force, h->force, rm, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && env_status)
+        e = cudaMemcpyAsync(env_status, h->env_status, sizeof(uint32_t) * h->n_envs, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_get_state");
+}
+
+msim_status msim_get_status(msim_handle h, uint32_t* global_flags) {
+    if (!h || !global_flags) return arg_fail(h, "msim_get_status: NULL argument");
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(global_flags, h->gflags, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "msim_get_status");
+    if (*global_flags & (MSIM_ENV_NONFINITE | MSIM_ENV_NOT_SPD)) return MSIM_ERR_STATE;
+    if (*global_flags & MSIM_FLAG_TIMEOUT) return MSIM_ERR_TIMEOUT;
+    return MSIM_OK;
+}
+
+msim_status msim_clear_status(msim_handle h, msim_stream_t stream) {
+    if (!h) return arg_fail(h, "msim_clear_status: NULL handle");
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaMemsetAsync(h->env_status, 0, sizeof(uint32_t) * h->n_envs, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->gflags, 0, sizeof(uint32_t), (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_clear_status");
+}
+
+msim_status msim_eval(msim_handle h, const float* q, const float* qd, const float* act, const float* exc,
+                      const msim_eval_out* out, msim_stream_t stream) {
+    if (!h || !q || !qd || !act || !exc || !out) return arg_fail(h, "msim_eval: NULL argument");
+    int need_nnz = 0, need_packed = 0;
+    for (int i = 0; i < h->n_models; ++i) {
+        need_nnz = std::max(need_nnz, h->models[i].hdr.nnz);
+        need_packed = std::max(need_packed, h->models[i].hdr.n_packed);
+    }
+    if (out->R && out->nnz_pitch < need_nnz) return arg_fail(h, "msim_eval: nnz_pitch too small");
+    if ((out->M || out->A) && out->packed_pitch < need_packed) return arg_fail(h, "msim_eval: packed_pitch too small");
+    cudaSetDevice(h->device);
+    for (int i = 0; i < h->n_models; ++i) {
+        if (h->env_begin[i + 1] == h->env_begin[i]) continue;
+        StepArgs a = base_args(h, i);
+        a.q = const_cast<float*>(q);
+        a.qd = const_cast<float*>(qd);
+        a.act = const_cast<float*>(act);
+        a.exc = exc;
+        a.qdd_out = nullptr;
+        a.force_out = nullptr;
+        a.n_sub = 1;
+        a.ev.L = out->L; a.ev.lm = out->lm; a.ev.vm = out->vm; a.ev.force = out->force; a.ev.act_next = out->act_next;
+        a.ev.R = out->R; a.ev.tau_m = out->tau_m; a.ev.tau_c = out->tau_c; a.ev.tau_l = out->tau_l;
+        a.ev.bias = out->bias; a.ev.rhs = out->rhs; a.ev.qdd = out->qdd; a.ev.M = out->M; a.ev.A = out->A;
+        a.ev.nnz_pitch = out->nnz_pitch; a.ev.packed_pitch = out->packed_pitch;
+        const cudaError_t e = launch_eval(a, model_grid(h, i), step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i]),
+                                          (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "msim_eval launch");
+    }
+    return MSIM_OK;
+}
+
+msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_parent, int32_t* dof_depth,
+                            int32_t* packed_row, int32_t* muscle_dof_ptr, int32_t* muscle_dof) {
+    if (!h || model < 0 || model >= h->n_models) return arg_fail(h, "msim_get_layout: bad handle or model");
+    const ModelHost& M = h->models[model];
+    auto cp = [](int32_t* dst, const std::vector<int32_t>& v) {
+        if (dst && !v.empty()) std::memcpy(dst, v.data(), sizeof(int32_t) * v.size());
+    };
+    cp(dof_parent, M.dof_parent);
+    cp(dof_depth, M.dof_depth);
+    cp(packed_row, M.packed_row);
+    cp(muscle_dof_ptr, M.mus_ptr);
+    cp(muscle_dof, M.mus_dof);
+    return MSIM_OK;
+}
+
+#ifdef MSIM_PHASE_TIMERS
+// Profiling builds only: per-phase cycle sums over all warps since the last reset.
+MSIM_API msim_status msim_debug_phase_cycles(msim_handle h, unsigned long long* out8, int32_t reset) {
+    if (!h || !out8 || !h->timers) return arg_fail(h, "msim_debug_phase_cycles: unavailable");
+    cudaDeviceSynchronize();
+    cudaMemcpy(out8, h->timers, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost);
+    if (reset) cudaMemset(h->timers, 0, sizeof(unsigned long long) * 8);
+    return MSIM_OK;
+}
+#endif
+
+}  // extern "C"

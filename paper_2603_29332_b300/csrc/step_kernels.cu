@@ -1,0 +1,868 @@
+// step_kernels.cu -- the batched muscle-driven forward-dynamics substep on sm_103a.
+//
+// Mapping: one warp per environment, several environments per block sharing one copy of the
+// model image in shared memory (staged by cp.async.bulk + mbarrier, kept resident across all
+// substeps and all environments the block processes).  Blocks are persistent: each loops over
+// groups of environments.  Per substep and environment (paper, Methods: Eq. 1, Eq. 2 and the
+// generalised-coordinate equations of motion):
+//   1. kinematics, top-down over body levels: frames, joint axes S, spatial velocities, bias
+//      accelerations (gravity as a base acceleration), body forces f = I a + v x* I v and
+//      spatial inertias, all in world Plücker coordinates so that subtree sums need no
+//      transforms;
+//   2. bottom-up over body levels: subtree sums of forces and inertias; rhs = -C = -S^T f;
+//   3. CRBA: M(d, a) = S_a^T (I^c_d S_d) for every DoF and each of its ancestors (tree-packed);
+// Precision: kinematics, forces, muscles and contact in FP32; the parallel-axis terms of the
+// inertias, their subtree sums, the entries of M and the factorisation / solves in float-float
+// (dfloat.cuh).  FP32 geometry perturbs the mechanism consistently and costs ~1e-6 in q_dd,
+// but independent FP32 rounding of the entries of the ill-conditioned M costs up to ~1e-3.
+//   4. muscles, one lane per muscle: via-point lengths, moment arms R = -dL/dq of the crossed
+//      DoFs, Hill force (Eq. 1), activation update (Eq. 2), rhs += R^T F and
+//      A += dt R^T (dF/dLdot) R (linearly implicit force-velocity damping);
+//   5. penalty ground contact with smoothed Coulomb friction, rhs += J^T F, A += dt J^T D J;
+//   6. joint-limit penalty (linearly implicit in position and velocity) and joint damping;
+//   7. tree-sparse factorisation A = L^T L (no fill-in), leaves first, by DoF depth levels;
+//   8. solves L^T y = rhs (leaves first) and L qdd = y (root first);
+//   9. semi-implicit Euler.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dfloat.cuh"
+#include "image.h"
+#include "kernels.h"
+
+namespace msim {
+
+namespace {
+
+constexpr uint32_t kEnvNonFinite = 0x1u;
+constexpr uint32_t kEnvNotSpd = 0x2u;
+constexpr uint32_t kFlagTimeout = 0x100u;
+constexpr long long kWaitLimit = 1LL << 22;   // bounded mbarrier wait (iterations of try_wait)
+
+struct Tables {
+    const ImgHeader* H;
+    const BodyRec* body;
+    const DofRec* dof;
+    const MuscleRec* mus;
+    const PointRec* pt;
+    const SphereRec* sph;
+    const uint8_t* cross;
+    const uint8_t* border;
+    const int16_t* blevel;
+    const uint8_t* child;
+    const uint8_t* anc;
+    const uint8_t* dorder;
+    const int16_t* dlevel;
+    const uint16_t* tri;
+};
+
+__device__ __forceinline__ Tables make_tables(const uint8_t* img) {
+    Tables t;
+    t.H = reinterpret_cast<const ImgHeader*>(img);
+    const ImgHeader& h = *t.H;
+    t.body = reinterpret_cast<const BodyRec*>(img + h.o_body);
+    t.dof = reinterpret_cast<const DofRec*>(img + h.o_dof);
+    t.mus = reinterpret_cast<const MuscleRec*>(img + h.o_muscle);
+    t.pt = reinterpret_cast<const PointRec*>(img + h.o_point);
+    t.sph = reinterpret_cast<const SphereRec*>(img + h.o_sphere);
+    t.cross = img + h.o_cross;
+    t.border = img + h.o_border;
+    t.blevel = reinterpret_cast<const int16_t*>(img + h.o_blevel);
+    t.child = img + h.o_child;
+    t.anc = img + h.o_anc;
+    t.dorder = img + h.o_dorder;
+    t.dlevel = reinterpret_cast<const int16_t*>(img + h.o_dlevel);
+    t.tri = reinterpret_cast<const uint16_t*>(img + h.o_tri);
+    return t;
+}
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+// out = R v (R row-major 3x3)
+__device__ __forceinline__ void rot3(const float* R, const float v[3], float out[3]) {
+    out[0] = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
+    out[1] = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
+    out[2] = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+}
+
+// ------------------------------------------------------------------ bulk staging of the image
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (long long i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Copies `bytes` (multiple of 16) from global `src` to shared `dst` with bulk async copies
+// completing on one mbarrier.  Every thread of the block must call it.  Returns false (and
+// sets the timeout flag) if the bounded wait expired.
+__device__ bool stage_image(uint8_t* dst, const uint8_t* src, int bytes, uint64_t* bar, uint32_t* gflags) {
+    const uint32_t mb = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+        const uint32_t d = smem_u32(dst);
+        constexpr int kChunk = 32768;
+        for (int off = 0; off < bytes; off += kChunk) {
+            const int sz = (bytes - off) < kChunk ? (bytes - off) : kChunk;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    d + off),
+                "l"(src + off), "r"(sz), "r"(mb)
+                : "memory");
+        }
+    }
+    bool ok = mbar_wait(mb, 0);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(gflags, kFlagTimeout);
+        mbar_wait(mb, 0);   // give copies still in flight a second bounded chance to land
+    }
+    return ok;
+}
+
+// ------------------------------------------------------------------ phase 1: kinematics
+__device__ void phase_kinematics(const Tables& T, float* ws, int lane) {
+    const ImgHeader& H = *T.H;
+    const float* q = ws + H.w_q;
+    const float* qd = ws + H.w_qd;
+    float* frame = ws + H.w_frame;
+    float* V = ws + H.w_v;
+    float* FI = ws + H.w_fi;
+    float* S = ws + H.w_S;
+    float* Acc = ws + H.w_A;   // bias accelerations live in the A region during this pass
+    for (int l = 0; l < H.n_blevels; ++l) {
+        const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const int b = T.border[i];
+            const BodyRec& B = T.body[b];
+            float R[9], p[3], w[3], vl[3], aw[3], al[3];
+            if (B.parent < 0) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.f : 0.f;
+                p[0] = B.off[0]; p[1] = B.off[1]; p[2] = B.off[2];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { w[k] = 0.f; vl[k] = 0.f; aw[k] = 0.f; al[k] = -H.gravity[k]; }
+            } else {
+                const float* Fp = frame + 12 * B.parent;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) R[k] = Fp[k];
+                rot3(R, B.off, p);
+                p[0] += Fp[9]; p[1] += Fp[10]; p[2] += Fp[11];
+                const float* Vp = V + 6 * B.parent;
+                const float* Ap = Acc + 6 * B.parent;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    w[k] = Vp[k]; vl[k] = Vp[3 + k]; aw[k] = Ap[k]; al[k] = Ap[3 + k];
+                }
+            }
+            for (int j = 0; j < B.ndof; ++j) {
+                const int d = B.dof0 + j;
+                const DofRec& D = T.dof[d];
+                float s[3], ps[3];
+                rot3(R, D.axis, s);
+                cross3(p, s, ps);
+                float* Sd = S + 6 * d;
+                Sd[0] = s[0]; Sd[1] = s[1]; Sd[2] = s[2]; Sd[3] = ps[0]; Sd[4] = ps[1]; Sd[5] = ps[2];
+                const float qdj = qd[d];
+                const float sw[3] = {s[0] * qdj, s[1] * qdj, s[2] * qdj};
+                const float sl[3] = {ps[0] * qdj, ps[1] * qdj, ps[2] * qdj};
+                float c1[3], c2[3], c3[3];
+                cross3(w, sw, c1);      // a += v x (S qd)
+                cross3(w, sl, c2);
+                cross3(vl, sw, c3);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    aw[k] += c1[k];
+                    al[k] += c2[k] + c3[k];
+                    w[k] += sw[k];
+                    vl[k] += sl[k];
+                }
+                // R <- R Rot(axis, q) = c R + s (rows x axis) + (1 - c) (R axis) axis^T
+                float sn, cs;
+                sincosf(q[d], &sn, &cs);
+                const float* ax = D.axis;
+                const float omc = 1.f - cs;
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const float r0 = R[3 * r], r1 = R[3 * r + 1], r2 = R[3 * r + 2];
+                    const float x0 = r1 * ax[2] - r2 * ax[1];
+                    const float x1 = r2 * ax[0] - r0 * ax[2];
+                    const float x2 = r0 * ax[1] - r1 * ax[0];
+                    R[3 * r] = cs * r0 + sn * x0 + omc * s[r] * ax[0];
+                    R[3 * r + 1] = cs * r1 + sn * x1 + omc * s[r] * ax[1];
+                    R[3 * r + 2] = cs * r2 + sn * x2 + omc * s[r] * ax[2];
+                }
+            }
+            float* Fb = frame + 12 * b;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Fb[k] = R[k];
+            Fb[9] = p[0]; Fb[10] = p[1]; Fb[11] = p[2];
+            float* Vb = V + 6 * b;
+            float* Ab = Acc + 6 * b;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { Vb[k] = w[k]; Vb[3 + k] = vl[k]; Ab[k] = aw[k]; Ab[3 + k] = al[k]; }
+            // spatial inertia about the world origin: m, h = m c, Ibar = R Ic R^T + m (|c|^2 1 - c c^T).
+            // R Ic R^T in FP32 (a consistent perturbation of the body's own inertia); the
+            // parallel-axis part, exact products of the FP32 COM, in float-float.
+            const float m = B.mass;
+            float c[3];
+            rot3(R, B.com, c);
+            c[0] += p[0]; c[1] += p[1]; c[2] += p[2];
+            const float I9[9] = {B.I[0], B.I[3], B.I[4], B.I[3], B.I[1], B.I[5], B.I[4], B.I[5], B.I[2]};
+            float TI[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    TI[3 * r + cc] = R[3 * r] * I9[cc] + R[3 * r + 1] * I9[3 + cc] + R[3 * r + 2] * I9[6 + cc];
+            const df c00 = two_prod(c[0], c[0]), c11 = two_prod(c[1], c[1]), c22 = two_prod(c[2], c[2]);
+            const df cc2 = df_add(df_add(c00, c11), c22);
+            df Ibd[6];   // xx yy zz xy xz yz
+            {
+                const float rxx = TI[0] * R[0] + TI[1] * R[1] + TI[2] * R[2];
+                const float ryy = TI[3] * R[3] + TI[4] * R[4] + TI[5] * R[5];
+                const float rzz = TI[6] * R[6] + TI[7] * R[7] + TI[8] * R[8];
+                const float rxy = TI[0] * R[3] + TI[1] * R[4] + TI[2] * R[5];
+                const float rxz = TI[0] * R[6] + TI[1] * R[7] + TI[2] * R[8];
+                const float ryz = TI[3] * R[6] + TI[4] * R[7] + TI[5] * R[8];
+                Ibd[0] = df_add_f(df_mul_f(df_add(cc2, df_neg(c00)), m), rxx);
+                Ibd[1] = df_add_f(df_mul_f(df_add(cc2, df_neg(c11)), m), ryy);
+                Ibd[2] = df_add_f(df_mul_f(df_add(cc2, df_neg(c22)), m), rzz);
+                Ibd[3] = df_add_f(df_neg(df_mul_f(two_prod(c[0], c[1]), m)), rxy);
+                Ibd[4] = df_add_f(df_neg(df_mul_f(two_prod(c[0], c[2]), m)), rxz);
+                Ibd[5] = df_add_f(df_neg(df_mul_f(two_prod(c[1], c[2]), m)), ryz);
+            }
+            const df hd[3] = {two_prod(m, c[0]), two_prod(m, c[1]), two_prod(m, c[2])};
+            // FP32 body force from the rounded inertia: f = I a + v x* (I v)
+            const float h[3] = {hd[0].hi, hd[1].hi, hd[2].hi};
+            const float Ib[6] = {Ibd[0].hi, Ibd[1].hi, Ibd[2].hi, Ibd[3].hi, Ibd[4].hi, Ibd[5].hi};
+            auto imul = [&](const float xw[3], const float xl[3], float ow[3], float ol[3]) {
+                float t1[3], t2[3];
+                cross3(h, xl, t1);
+                cross3(h, xw, t2);
+                ow[0] = Ib[0] * xw[0] + Ib[3] * xw[1] + Ib[4] * xw[2] + t1[0];
+                ow[1] = Ib[3] * xw[0] + Ib[1] * xw[1] + Ib[5] * xw[2] + t1[1];
+                ow[2] = Ib[4] * xw[0] + Ib[5] * xw[1] + Ib[2] * xw[2] + t1[2];
+                ol[0] = m * xl[0] - t2[0];
+                ol[1] = m * xl[1] - t2[1];
+                ol[2] = m * xl[2] - t2[2];
+            };
+            float Ivw[3], Ivl[3], Iaw[3], Ial[3];
+            imul(w, vl, Ivw, Ivl);
+            imul(aw, al, Iaw, Ial);
+            float t1[3], t2[3], t3[3];
+            cross3(w, Ivw, t1);
+            cross3(vl, Ivl, t2);
+            cross3(w, Ivl, t3);
+            float* fi = FI + kFiStride * b;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                fi[k] = Iaw[k] + t1[k] + t2[k];
+                fi[3 + k] = Ial[k] + t3[k];
+            }
+            df* Id = reinterpret_cast<df*>(fi + 6);   // m, h[3], Ibar[6]
+            Id[0] = df_make(m);
+            Id[1] = hd[0]; Id[2] = hd[1]; Id[3] = hd[2];
+#pragma unroll
+            for (int e = 0; e < 6; ++e) Id[4 + e] = Ibd[e];
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ phase 2: subtree sums, bias
+__device__ void phase_subtree(const Tables& T, float* ws, int lane) {
+    const ImgHeader& H = *T.H;
+    float* FI = ws + H.w_fi;
+    const float* S = ws + H.w_S;
+    float* rhs = ws + H.w_rhs;
+    for (int l = H.n_blevels - 1; l >= 0; --l) {
+        const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const int b = T.border[i];
+            const BodyRec& B = T.body[b];
+            float* fi = FI + kFiStride * b;
+            float f[6];
+            df I[10];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) f[k] = fi[k];
+            const df* Ib = reinterpret_cast<const df*>(fi + 6);
+#pragma unroll
+            for (int k = 0; k < 10; ++k) I[k] = Ib[k];
+            for (int c = 0; c < B.nchild; ++c) {
+                const float* fc = FI + kFiStride * T.child[B.child0 + c];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) f[k] += fc[k];
+                const df* Ic = reinterpret_cast<const df*>(fc + 6);
+#pragma unroll
+                for (int k = 0; k < 10; ++k) I[k] = df_add(I[k], Ic[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) fi[k] = f[k];
+            df* Io = reinterpret_cast<df*>(fi + 6);
+#pragma unroll
+            for (int k = 0; k < 10; ++k) Io[k] = I[k];
+            for (int j = 0; j < B.ndof; ++j) {
+                const int d = B.dof0 + j;
+                const float* Sd = S + 6 * d;
+                rhs[d] = -(Sd[0] * f[0] + Sd[1] * f[1] + Sd[2] * f[2] + Sd[3] * f[3] + Sd[4] * f[4] + Sd[5] * f[5]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ phase 3: CRBA (float-float)
+__device__ void phase_crba(const Tables& T, float* ws, int lane) {
+    const ImgHeader& H = *T.H;
+    const float* FI = ws + H.w_fi;
+    const float* S = ws + H.w_S;
+    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    for (int d = lane; d < H.n; d += 32) {
+        const DofRec& D = T.dof[d];
+        const df* I = reinterpret_cast<const df*>(FI + kFiStride * D.body + 6);
+        const df m = I[0];
+        const df h0 = I[1], h1 = I[2], h2 = I[3];
+        const df* Ib = I + 4;   // xx yy zz xy xz yz
+        const float* Sd = S + 6 * d;
+        const float s0 = Sd[0], s1 = Sd[1], s2 = Sd[2], p0 = Sd[3], p1 = Sd[4], p2 = Sd[5];
+        // F = I^c S: Fw = Ibar s + h x ps, Fl = m ps - h x s
+        df Fw[3], Fl[3];
+        Fw[0] = df_add(df_add(df_add(df_mul_f(Ib[0], s0), df_mul_f(Ib[3], s1)), df_mul_f(Ib[4], s2)),
+                       df_add(df_mul_f(h1, p2), df_neg(df_mul_f(h2, p1))));
+        Fw[1] = df_add(df_add(df_add(df_mul_f(Ib[3], s0), df_mul_f(Ib[1], s1)), df_mul_f(Ib[5], s2)),
+                       df_add(df_mul_f(h2, p0), df_neg(df_mul_f(h0, p2))));
+        Fw[2] = df_add(df_add(df_add(df_mul_f(Ib[4], s0), df_mul_f(Ib[5], s1)), df_mul_f(Ib[2], s2)),
+                       df_add(df_mul_f(h0, p1), df_neg(df_mul_f(h1, p0))));
+        Fl[0] = df_add(df_mul_f(m, p0), df_neg(df_add(df_mul_f(h1, s2), df_neg(df_mul_f(h2, s1)))));
+        Fl[1] = df_add(df_mul_f(m, p1), df_neg(df_add(df_mul_f(h2, s0), df_neg(df_mul_f(h0, s2)))));
+        Fl[2] = df_add(df_mul_f(m, p2), df_neg(df_add(df_mul_f(h0, s1), df_neg(df_mul_f(h1, s0)))));
+        const int row = D.row;
+        for (int k = 0; k <= D.depth; ++k) {
+            const float* Sa = S + 6 * T.anc[row + k];
+            df acc = df_mul_f(Fw[0], Sa[0]);
+            acc = df_fma_f(acc, Fw[1], Sa[1]);
+            acc = df_fma_f(acc, Fw[2], Sa[2]);
+            acc = df_fma_f(acc, Fl[0], Sa[3]);
+            acc = df_fma_f(acc, Fl[1], Sa[4]);
+            acc = df_fma_f(acc, Fl[2], Sa[5]);
+            A[row + k] = acc;
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ Hill curves (Eq. 1)
+// Readings of the curves the paper takes from Millard 2013 (not printed there): Gaussian
+// active force-length of width 0.45, exponential passive curve reaching 1 at 1.6 l_opt with a
+// linear extension, Hill hyperbola when shortening and a saturating branch (to 1.4) when
+// lengthening, slope 5 at v = 0 on both sides.
+__device__ __forceinline__ float hill_fl(float l) {
+    const float x = l - 1.f;
+    return expf(-x * x * (1.f / 0.45f));
+}
+__device__ __forceinline__ float hill_fp(float l, float den, float slope) {
+    if (l <= 1.f) return 0.f;
+    if (l <= 1.6f) return (expf((l - 1.f) * (4.f / 0.6f)) - 1.f) / den;
+    return 1.f + slope * (l - 1.6f);
+}
+__device__ __forceinline__ float hill_fv(float v) {
+    if (v < -1.f) return 0.f;
+    if (v <= 0.f) return (1.f + v) / (1.f - 4.f * v);
+    return 1.f + 0.4f * v / (v + 0.08f);
+}
+__device__ __forceinline__ float hill_dfv(float v) {
+    if (v < -1.f) return 0.f;
+    if (v <= 0.f) {
+        const float den = 1.f - 4.f * v;
+        return 5.f / (den * den);
+    }
+    const float den = v + 0.08f;
+    return 0.032f / (den * den);
+}
+
+// ------------------------------------------------------------------ phase 4: muscles
+// act: this environment's activation row in global memory (read; written unless EVAL).
+template <bool EVAL>
+__device__ void phase_muscles(const Tables& T, float* ws, int lane, float dt, const float* exc, float* act,
+                              float* force_out, const EvalPtrs* ev) {
+    const ImgHeader& H = *T.H;
+    const float* qd = ws + H.w_qd;
+    const float* frame = ws + H.w_frame;
+    const float* S = ws + H.w_S;
+    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    float* rhs = ws + H.w_rhs;
+    float* rk = ws + H.w_rk;
+    for (int k = lane; k < H.m; k += 32) {
+        const MuscleRec M = T.mus[k];
+        const float a = act[k];
+        const float u = fminf(fmaxf(exc[k], 0.f), 1.f);
+        PointRec P = T.pt[M.p0];
+        int b = P.body_cross & 0xff;
+        int cprev = P.body_cross >> 8;
+        float x0[3];
+        rot3(frame + 12 * b, P.pos, x0);
+        x0[0] += frame[12 * b + 9]; x0[1] += frame[12 * b + 10]; x0[2] += frame[12 * b + 11];
+        float L = 0.f, ldot = 0.f;
+        for (int j = 1; j < M.np; ++j) {
+            P = T.pt[M.p0 + j];
+            b = P.body_cross & 0xff;
+            const int c = P.body_cross >> 8;
+            float x1[3];
+            rot3(frame + 12 * b, P.pos, x1);
+            x1[0] += frame[12 * b + 9]; x1[1] += frame[12 * b + 10]; x1[2] += frame[12 * b + 11];
+            const float dv[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
+            const float len2 = dot3(dv, dv);
+            const float inv = rsqrtf(len2);
+            L += len2 * inv;
+            const float uu[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+            for (int i = cprev; i < c; ++i) {
+                const int d = T.cross[M.x0 + i];
+                const float* Sd = S + 6 * d;
+                const float* o = frame + 12 * T.dof[d].body + 9;
+                const float r[3] = {x1[0] - o[0], x1[1] - o[1], x1[2] - o[2]};
+                float rxu[3];
+                cross3(r, uu, rxu);
+                const float Rv = -(Sd[0] * rxu[0] + Sd[1] * rxu[1] + Sd[2] * rxu[2]);   // R = -dL/dq
+                rk[i * 32 + lane] = Rv;
+                ldot -= Rv * qd[d];
+            }
+            x0[0] = x1[0]; x0[1] = x1[1]; x0[2] = x1[2];
+            cprev = c;
+        }
+        const float lm = 1.f + (L - M.L0) * M.inv_lopt;
+        const float vm = ldot * M.inv_vmax;
+        const float fl = hill_fl(lm);
+        const float F = M.fmax * (a * fl * hill_fv(vm) + hill_fp(lm, H.fp_den, H.fp_slope));
+        const float dFdl = M.fmax * a * fl * hill_dfv(vm) * M.inv_vmax;
+        const float tau = (u > a) ? H.tau_act * (0.5f + 1.5f * a) : H.tau_deact / (0.5f + 1.5f * a);
+        const float an = fminf(fmaxf(a + dt * (u - a) / tau, 0.f), 1.f);
+        if (!EVAL) act[k] = an;
+        if (force_out) force_out[k] = F;
+        // rhs += R^T F; A += dt R^T (dF/dLdot) R as g g^T with g = sqrt(dt dF/dLdot) R, added to
+        // the low words of the float-float entries (renormalised before the factorisation)
+        const float sq = sqrtf(dt * dFdl);
+        for (int i = 0; i < M.nx; ++i) {
+            const int d = T.cross[M.x0 + i];
+            const float Ri = rk[i * 32 + lane];
+            atomicAdd(&rhs[d], Ri * F);
+            if (EVAL && ev->tau_m) atomicAdd(&ev->tau_m[d], Ri * F);
+            if (sq != 0.f) {
+                const int row = T.dof[d].row;
+                const float gi = sq * Ri;
+                for (int i2 = 0; i2 <= i; ++i2) {
+                    const int d2 = T.cross[M.x0 + i2];
+                    atomicAdd(&A[row + T.dof[d2].depth].lo, gi * (sq * rk[i2 * 32 + lane]));
+                }
+            }
+        }
+        if (EVAL) {
+            if (ev->L) ev->L[k] = L;
+            if (ev->lm) ev->lm[k] = lm;
+            if (ev->vm) ev->vm[k] = vm;
+            if (ev->force) ev->force[k] = F;
+            if (ev->act_next) ev->act_next[k] = an;
+            if (ev->R)
+                for (int i = 0; i < M.nx; ++i) ev->R[M.x0 + i] = rk[i * 32 + lane];
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ phase 5: contact
+template <bool EVAL>
+__device__ void phase_contact(const Tables& T, float* ws, int lane, float dt, const EvalPtrs* ev) {
+    const ImgHeader& H = *T.H;
+    if (H.ns == 0) return;
+    const float* frame = ws + H.w_frame;
+    const float* V = ws + H.w_v;
+    const float* S = ws + H.w_S;
+    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    float* rhs = ws + H.w_rhs;
+    float* sph = ws + H.w_sph;
+    for (int i = lane; i < H.ns; i += 32) {
+        const SphereRec& Sp = T.sph[i];
+        const float* fr = frame + 12 * Sp.body;
+        float x[3];
+        rot3(fr, Sp.pos, x);
+        x[0] += fr[9]; x[1] += fr[10]; x[2] += fr[11];
+        const float depth = Sp.radius - x[2];
+        const float y[3] = {x[0], x[1], x[2] - Sp.radius};   // lowest point of the sphere
+        const float* Vb = V + 6 * Sp.body;
+        float wy[3];
+        cross3(Vb, y, wy);
+        const float vy[3] = {Vb[3] + wy[0], Vb[4] + wy[1], Vb[5] + wy[2]};
+        const float fn = H.contact_k * depth - H.contact_c * vy[2];
+        float* o = sph + 12 * i;
+        o[0] = y[0]; o[1] = y[1]; o[2] = y[2];
+        if (depth > 0.f && fn > 0.f) {
+            const float sm = sqrtf(vy[0] * vy[0] + vy[1] * vy[1] + H.contact_eps2);
+            const float mfs = H.contact_mu * fn / sm;
+            o[3] = -mfs * vy[0]; o[4] = -mfs * vy[1]; o[5] = fn;
+            // square roots of dt * damping: A += (h J)^T (h J) per axis
+            o[6] = sqrtf(dt * mfs); o[7] = o[6]; o[8] = sqrtf(dt * H.contact_c);
+            o[9] = 1.f;
+        } else {
+            o[3] = o[4] = o[5] = o[6] = o[7] = o[8] = 0.f;
+            o[9] = 0.f;
+        }
+    }
+    __syncwarp();
+    for (int i = 0; i < H.ns; ++i) {
+        const float* o = sph + 12 * i;
+        if (o[9] == 0.f) continue;
+        const int dl = T.sph[i].last_dof;
+        const int rowl = T.dof[dl].row;
+        const int dep = T.dof[dl].depth;
+        const int npairs = (dep + 1) * (dep + 2) / 2;
+        for (int p = lane; p < npairs; p += 32) {
+            const int tv = T.tri[p];
+            const int ia = tv & 0xff, ib = tv >> 8;
+            const int da = T.anc[rowl + ia], db = T.anc[rowl + ib];
+            const float* Sa = S + 6 * da;
+            const float* Sb = S + 6 * db;
+            const float* oa = frame + 12 * T.dof[da].body + 9;
+            const float* ob = frame + 12 * T.dof[db].body + 9;
+            const float ra[3] = {o[0] - oa[0], o[1] - oa[1], o[2] - oa[2]};
+            const float rb[3] = {o[0] - ob[0], o[1] - ob[1], o[2] - ob[2]};
+            float Ja[3], Jb[3];
+            cross3(Sa, ra, Ja);
+            cross3(Sb, rb, Jb);
+            const float val = (o[6] * Ja[0]) * (o[6] * Jb[0]) + (o[7] * Ja[1]) * (o[7] * Jb[1]) +
+                              (o[8] * Ja[2]) * (o[8] * Jb[2]);
+            atomicAdd(&A[T.dof[da].row + ib].lo, val);
+            if (ia == ib) {
+                const float t = Ja[0] * o[3] + Ja[1] * o[4] + Ja[2] * o[5];
+                atomicAdd(&rhs[da], t);
+                if (EVAL && ev->tau_c) atomicAdd(&ev->tau_c[da], t);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ phase 6: limits, damping
+template <bool EVAL>
+__device__ void phase_limits(const Tables& T, float* ws, int lane, float dt, const EvalPtrs* ev) {
+    const ImgHeader& H = *T.H;
+    const float* q = ws + H.w_q;
+    const float* qd = ws + H.w_qd;
+    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    float* rhs = ws + H.w_rhs;
+    for (int d = lane; d < H.n; d += 32) {
+        const DofRec& D = T.dof[d];
+        const float qv = q[d], qdv = qd[d];
+        // limit spring-damper evaluated at the predicted end-of-step state (linearly implicit
+        // in position and velocity): explicit part to rhs, dt c_l + dt^2 k_l to the diagonal
+        float t = -D.damp * qdv, dd = D.damp;
+        if (D.lo < D.hi) {
+            const float kd = H.limit_k * dt + H.limit_c;
+            if (qv > D.hi) { t += -H.limit_k * (qv - D.hi) - kd * qdv; dd += kd; }
+            else if (qv < D.lo) { t += H.limit_k * (D.lo - qv) - kd * qdv; dd += kd; }
+        }
+        rhs[d] += t;
+        A[D.row + D.depth].lo += dt * dd;
+        if (EVAL && ev->tau_l) ev->tau_l[d] = t;
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ phase 7-8: factor and solve
+// A = L^T L with L lower triangular in the tree pattern (no fill-in), eliminating DoFs leaves
+// first, in float-float.  Row k of the packed storage holds (k, ancestor at depth j) at
+// row + j; after the factorisation the diagonal slot holds 1 / L_kk.
+__device__ bool phase_factor_solve(const Tables& T, float* ws, int lane) {
+    const ImgHeader& H = *T.H;
+    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    const float* rhs = ws + H.w_rhs;
+    df* Y = reinterpret_cast<df*>(ws + H.w_y);
+    bool ok = true;
+    for (int t = lane; t < H.n_packed; t += 32) A[t] = df_norm(A[t].hi, A[t].lo);
+    for (int d = lane; d < H.n; d += 32) Y[d] = df_make(rhs[d]);
+    __syncwarp();
+    for (int l = H.n_dlevels - 1; l >= 0; --l) {
+        const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const DofRec& D = T.dof[T.dorder[i]];
+            df akk = A[D.row + D.depth];
+            if (!(akk.hi > 0.f)) { ok = false; akk = df_make(1.f); }
+            const df inv = df_recip(df_sqrt(akk));
+            A[D.row + D.depth] = inv;
+            for (int j = 0; j < D.depth; ++j) A[D.row + j] = df_mul(A[D.row + j], inv);
+        }
+        __syncwarp();
+        for (int i = i0; i < i1; ++i) {
+            const DofRec& D = T.dof[T.dorder[i]];
+            const int np = D.depth * (D.depth + 1) / 2;
+            for (int p = lane; p < np; p += 32) {
+                const int tv = T.tri[p];
+                const int ja = tv & 0xff, jb = tv >> 8;          // jb <= ja < depth
+                const int a = T.anc[D.row + ja];
+                df* t = &A[T.dof[a].row + jb];
+                *t = df_fms(*t, A[D.row + ja], A[D.row + jb]);
+            }
+            __syncwarp();
+        }
+    }
+    // L^T y = rhs, leaves first
+    for (int l = H.n_dlevels - 1; l >= 0; --l) {
+        const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const int k = T.dorder[i];
+            const DofRec& D = T.dof[k];
+            Y[k] = df_mul(Y[k], A[D.row + D.depth]);
+        }
+        __syncwarp();
+        for (int i = i0; i < i1; ++i) {
+            const int k = T.dorder[i];
+            const DofRec& D = T.dof[k];
+            const df yk = Y[k];
+            for (int j = lane; j < D.depth; j += 32) {
+                df* t = &Y[T.anc[D.row + j]];
+                *t = df_fms(*t, A[D.row + j], yk);
+            }
+            __syncwarp();
+        }
+    }
+    // L x = y, root first (x overwrites y)
+    for (int l = 0; l < H.n_dlevels; ++l) {
+        const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const int k = T.dorder[i];
+            const DofRec& D = T.dof[k];
+            df s = Y[k];
+            for (int j = 0; j < D.depth; ++j) s = df_fms(s, A[D.row + j], Y[T.anc[D.row + j]]);
+            Y[k] = df_mul(s, A[D.row + D.depth]);
+        }
+        __syncwarp();
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// ------------------------------------------------------------------ one substep
+// With MSIM_PHASE_TIMERS defined (profiling builds only), lane 0 of every warp adds the cycles
+// spent in each phase to timers[0..7].
+#ifdef MSIM_PHASE_TIMERS
+#define PHASE_MARK(i)                                                               \
+    do {                                                                            \
+        const long long t_ = clock64();                                             \
+        if (lane == 0 && timers) atomicAdd(&timers[(i)], (unsigned long long)(t_ - t0_)); \
+        t0_ = clock64();                                                            \
+    } while (0)
+#else
+#define PHASE_MARK(i) \
+    do {              \
+    } while (0)
+#endif
+
+template <bool EVAL>
+__device__ uint32_t substep(const Tables& T, float* ws, int lane, float dt, const float* exc, float* act,
+                            float* force_out, const EvalPtrs* ev, unsigned long long* timers) {
+    const ImgHeader& H = *T.H;
+#ifdef MSIM_PHASE_TIMERS
+    long long t0_ = clock64();
+#else
+    (void)timers;
+#endif
+    phase_kinematics(T, ws, lane);
+    PHASE_MARK(0);
+    phase_subtree(T, ws, lane);
+    PHASE_MARK(1);
+    phase_crba(T, ws, lane);
+    PHASE_MARK(2);
+    const df* A = reinterpret_cast<const df*>(ws + H.w_A);
+    if (EVAL) {
+        for (int t = lane; t < H.n_packed; t += 32)
+            if (ev->M) ev->M[t] = A[t].hi + A[t].lo;
+        for (int d = lane; d < H.n; d += 32)
+            if (ev->bias) ev->bias[d] = -ws[H.w_rhs + d];
+        __syncwarp();
+    }
+    phase_muscles<EVAL>(T, ws, lane, dt, exc, act, force_out, ev);
+    PHASE_MARK(3);
+    phase_contact<EVAL>(T, ws, lane, dt, ev);
+    PHASE_MARK(4);
+    phase_limits<EVAL>(T, ws, lane, dt, ev);
+    PHASE_MARK(5);
+    if (EVAL) {
+        for (int t = lane; t < H.n_packed; t += 32)
+            if (ev->A) ev->A[t] = A[t].hi + A[t].lo;
+        for (int d = lane; d < H.n; d += 32)
+            if (ev->rhs) ev->rhs[d] = ws[H.w_rhs + d];
+        __syncwarp();
+    }
+    const bool ok = phase_factor_solve(T, ws, lane);
+    PHASE_MARK(6);
+    uint32_t st = ok ? 0u : kEnvNotSpd;
+    const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
+    if (!EVAL) {
+        float* q = ws + H.w_q;
+        float* qd = ws + H.w_qd;
+        for (int d = lane; d < H.n; d += 32) {
+            const float v = qd[d] + dt * (Y[d].hi + Y[d].lo);
+            qd[d] = v;
+            q[d] += dt * v;
+        }
+        __syncwarp();
+    } else if (ev->qdd) {
+        for (int d = lane; d < H.n; d += 32) ev->qdd[d] = Y[d].hi + Y[d].lo;
+    }
+    return st;
+}
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ void load_row(float* dst, const float* src, int count, int lane) {
+    for (int i = lane; i < count; i += 32) dst[i] = src[i];
+}
+
+template <bool EVAL>
+__global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    uint8_t* img = smem + 16;
+    if (!stage_image(img, a.img, a.staged_bytes, bar, a.gflags)) return;
+    Tables T = make_tables(img);
+    if (!a.points_in_smem) T.pt = reinterpret_cast<const PointRec*>(a.img + T.H->o_point);
+    const ImgHeader& H = *T.H;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* ws_all = reinterpret_cast<float*>(img + ((a.staged_bytes + 127) & ~127));
+    float* ws = ws_all + (size_t)warp * H.w_floats;
+    const int n_envs = a.env_end - a.env_begin;
+    const int n_groups = (n_envs + a.envs_per_block - 1) / a.envs_per_block;
+    for (int g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        const int e = a.env_begin + g * a.envs_per_block + warp;
+        if (e >= a.env_end) continue;
+        const size_t rn = (size_t)e * a.pitch_n, rm = (size_t)e * a.pitch_m;
+        load_row(ws + H.w_q, a.q + rn, H.n, lane);
+        load_row(ws + H.w_qd, a.qd + rn, H.n, lane);
+        __syncwarp();
+        uint32_t st = 0;
+        if (EVAL) {
+            EvalPtrs ev = a.ev;
+            auto off = [&](float* p, size_t pitch) { return p ? p + (size_t)e * pitch : p; };
+            ev.L = off(ev.L, a.pitch_m); ev.lm = off(ev.lm, a.pitch_m); ev.vm = off(ev.vm, a.pitch_m);
+            ev.force = off(ev.force, a.pitch_m); ev.act_next = off(ev.act_next, a.pitch_m);
+            ev.R = off(ev.R, ev.nnz_pitch);
+            ev.tau_m = off(ev.tau_m, a.pitch_n); ev.tau_c = off(ev.tau_c, a.pitch_n);
+            ev.tau_l = off(ev.tau_l, a.pitch_n); ev.bias = off(ev.bias, a.pitch_n); ev.rhs = off(ev.rhs, a.pitch_n);
+            ev.qdd = off(ev.qdd, a.pitch_n);
+            ev.M = off(ev.M, ev.packed_pitch); ev.A = off(ev.A, ev.packed_pitch);
+            for (int d = lane; d < H.n; d += 32) {
+                if (ev.tau_m) ev.tau_m[d] = 0.f;
+                if (ev.tau_c) ev.tau_c[d] = 0.f;
+                if (ev.tau_l) ev.tau_l[d] = 0.f;
+            }
+            __syncwarp();
+            st |= substep<true>(T, ws, lane, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, a.timers);
+        } else {
+            for (int s = 0; s < a.n_sub; ++s) {
+                const bool last = (s == a.n_sub - 1);
+                st |= substep<false>(T, ws, lane, a.dt, a.exc + rm, a.act + rm,
+                                     (last && a.force_out) ? a.force_out + rm : nullptr, nullptr, a.timers);
+            }
+            bool bad = false;
+            const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
+            for (int d = lane; d < H.n; d += 32) {
+                const float v0 = ws[H.w_q + d], v1 = ws[H.w_qd + d];
+                bad |= !(isfinite(v0) && isfinite(v1));
+                a.q[rn + d] = v0;
+                a.qd[rn + d] = v1;
+                if (a.qdd_out) a.qdd_out[rn + d] = Y[d].hi + Y[d].lo;
+            }
+            for (int k = lane; k < H.m; k += 32) bad |= !isfinite(a.act[rm + k]);
+            if (__any_sync(0xffffffffu, bad)) st |= kEnvNonFinite;
+        }
+        if (st && lane == 0) {
+            atomicOr(&a.env_status[e], st);
+            atomicOr(a.gflags, st);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_set_l0(uint8_t* img, const float* L, int m) {
+    const ImgHeader* H = reinterpret_cast<const ImgHeader*>(img);
+    MuscleRec* mus = reinterpret_cast<MuscleRec*>(img + H->o_muscle);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) mus[k].L0 = L[k];
+}
+
+__global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, const float* q0, const float* qd0,
+                        const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m, int n_envs) {
+    const int r = blockIdx.x;
+    if (r >= n_rows) return;
+    const int e = ids ? ids[r] : r;
+    if (e < 0 || e >= n_envs) return;
+    for (int i = threadIdx.x; i < pitch_n; i += blockDim.x) {
+        q[(size_t)e * pitch_n + i] = q0 ? q0[(size_t)r * pitch_n + i] : 0.f;
+        qd[(size_t)e * pitch_n + i] = qd0 ? qd0[(size_t)r * pitch_n + i] : 0.f;
+    }
+    for (int i = threadIdx.x; i < pitch_m; i += blockDim.x)
+        act[(size_t)e * pitch_m + i] = act0 ? act0[(size_t)r * pitch_m + i] : 0.f;
+    if (threadIdx.x == 0) status[e] = 0u;
+}
+
+}  // namespace
+
+size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem) {
+    const size_t staged = points_in_smem ? (size_t)h.total_bytes : (size_t)h.o_point;
+    return 16 + ((staged + 127) & ~(size_t)127) + (size_t)epb * h.w_floats * sizeof(float);
+}
+
+int step_blocks_per_sm(int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false>, threads, smem) != cudaSuccess) return 1;
+    return n;
+}
+
+cudaError_t set_step_smem_limit(size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
+    k_step<false><<<grid, 32 * a.envs_per_block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
+    k_step<true><<<grid, 32 * a.envs_per_block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_l0(uint8_t* img, const float* L, int m, cudaStream_t s) {
+    k_set_l0<<<(m + 255) / 256, 256, 0, s>>>(img, L, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, const float* q0, const float* qd0,
+                         const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m, int n_envs,
+                         cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    k_reset<<<n_rows, 128, 0, s>>>(q, qd, act, status, q0, qd0, act0, ids, n_rows, pitch_n, pitch_m, n_envs);
+    return cudaGetLastError();
+}
+
+}  // namespace msim

@@ -72,8 +72,8 @@ class Model:
     contact_c: float = 1.0e3
     contact_mu: float = 0.9
     contact_eps: float = 0.1
-    limit_k: float = 100.0
-    limit_c: float = 1.0
+    limit_k: float = 1000.0
+    limit_c: float = 10.0
     tau_act: float = TAU_ACT
     tau_deact: float = TAU_DEACT
     vmax_per_lopt: float = 10.0
@@ -235,7 +235,7 @@ def make_model(name, body_parent, body_ndof, body_offset, body_mass, body_com, b
 # model; "upper" and "lower" are the two extra skeletons of the mixed-size batch.
 CONFIGS = {
     "c0_tiny": dict(n_bodies=8, n_dofs=14, n_muscles=40, max_points=4, max_span=2, limits=False,
-                    contact=False, seed=0),
+                    contact=False, seed=0, max_dof_per_body=2),
     "c1_whole": dict(n_bodies=60, n_dofs=90, n_muscles=700, max_points=6, max_span=3, limits=True,
                      contact=True, seed=1),
     "c2_upper": dict(n_bodies=20, n_dofs=30, n_muscles=250, max_points=6, max_span=3, limits=True,
@@ -246,20 +246,23 @@ CONFIGS = {
 
 
 def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, limits, contact, seed,
-             n_legs=2, spheres_per_foot=4, sphere_radius=0.03):
+             n_legs=2, spheres_per_foot=4, sphere_radius=0.03, max_dof_per_body=3):
     """Draw one synthetic skeleton + muscle model.
 
     Tree: a root body, then limb chains of U{3..8} bodies each, the parent of each chain drawn
     uniformly over existing bodies (with contact, the first two chains hang down from the root
     as legs).  Link length U(0.2, 0.5) m, mass U(1, 8) kg, capsule inertia with radius 0.1 x
-    length.  DoFs: one per body, then incremented at random (max 3) up to ``n_dofs``.
+    length.  DoFs: one per body, then incremented at random (max ``max_dof_per_body``) up to
+    ``n_dofs``; a 3-DoF body is a ball joint as three hinges with orthonormal axes.
     Muscles: U{2..max_points} path points; insertion body B, origin body A = the ancestor
     ``span`` joints up (span U{1..min(max_span, points-1)}); one point on each body of the A..B
     chain (origin at U(0.6, 0.95) of A's length, insertion at U(0.05, 0.4) of B's, the others at
     U(0.1, 0.9)), extra points on random chain bodies; radial offset U(0.02, 0.06) m; redrawn if a
     segment is shorter than 1 cm at q = 0.
     F_max U(100, 3000) N, l_opt U(0.05, 0.3) m, l_slack = U(1.0, 1.5) x l_opt.
-    Limits (if enabled) lo = -U(0.5, 2), hi = U(0.5, 2) rad.  Contact: 4 spheres of radius
+    Limits (if enabled) lo = -U(0.5, 2), hi = U(0.5, 2) rad, except the middle hinge of a ball
+    joint: +-U(0.5, 1.0) rad, which keeps it away from gimbal lock at 90 deg (where the three
+    hinge axes span only two directions and M(q) is singular).  Contact: 4 spheres of radius
     3 cm on the last body of each leg; the root is lifted so that the lowest sphere touches
     z = 0 at q = 0.
     """
@@ -301,8 +304,9 @@ def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, li
 
     # DoF allocation
     ndof = np.ones(B, dtype=np.int32)
+    assert n_dofs <= max_dof_per_body * B
     while ndof.sum() < n_dofs:
-        cand = np.nonzero(ndof < 3)[0]
+        cand = np.nonzero(ndof < max_dof_per_body)[0]
         ndof[rng.choice(cand)] += 1
     assert ndof.sum() == n_dofs
     axes = []
@@ -388,6 +392,11 @@ def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, li
 
     if limits:
         lim = np.stack([-rng.uniform(0.5, 2.0, size=n_dofs), rng.uniform(0.5, 2.0, size=n_dofs)], axis=1)
+        starts = np.concatenate([[0], np.cumsum(ndof)[:-1]])
+        for b in range(B):
+            if ndof[b] == 3:
+                mid = starts[b] + 1
+                lim[mid] = [-rng.uniform(0.5, 1.0), rng.uniform(0.5, 1.0)]
     else:
         lim = np.zeros((n_dofs, 2))
 

@@ -391,11 +391,13 @@ def test_contact_static_penetration():
 
 
 def test_joint_limit_static_deflection():
-    """A horizontal pendulum held by its upper limit at 0 rests at q = m g lc / k_l."""
+    """A horizontal pendulum held by its upper limit at 0 rests at q = m g lc cos q / k_l (the
+    implicit treatment of the penalty changes the transient, not the equilibrium)."""
     base = hm.pendulum(mass=1.0, lc=0.1)
     mass, lc, g = base.body_mass[0], base.body_com[0][0], -base.gravity[2]
     mdl = mg.make_model("lim", base.body_parent, base.body_ndof, base.body_offset, base.body_mass, base.body_com,
                         base.body_inertia, base.dof_axis, dof_limit=[[-1.0, 0.0]], limit_k=100.0, limit_c=1.0)
+    assert mdl.limit_k == 100.0
     om = ora.OracleModel(mdl)
     q, qd, act = np.zeros((1, 1)), np.zeros((1, 1)), np.zeros((1, 0))
     for _ in range(50):
@@ -407,6 +409,26 @@ def test_joint_limit_static_deflection():
     for _ in range(100):
         x = mass * g * lc * math.cos(x) / mdl.limit_k
     assert qs == pytest.approx(x, rel=1e-6)
+
+
+def test_implicit_limit_penalty_is_backward_euler_of_the_spring_damper():
+    """Outside a limit the penalty is evaluated at the predicted end-of-step state: the solved
+    q_dd satisfies M q_dd = -C - k_l (q - hi + dt qd') - c_l qd' with qd' = qd + dt q_dd."""
+    base = hm.pendulum(mass=1.0, lc=0.1)
+    mdl = mg.make_model("lim2", base.body_parent, base.body_ndof, base.body_offset, base.body_mass, base.body_com,
+                        base.body_inertia, base.dof_axis, dof_limit=[[-1.0, 0.0]], limit_k=5000.0, limit_c=20.0)
+    om = ora.OracleModel(mdl)
+    dt, q, qd = 1e-3, 0.3, 2.0
+    r = ora.evaluate(om, dt, [q], [qd], np.zeros(0), np.zeros(0))
+    x = r["qdd"][0]
+    qd1 = qd + dt * x
+    lhs = r["M"][0, 0] * x + r["bias"][0]
+    assert lhs == pytest.approx(-mdl.limit_k * (q - 0.0 + dt * qd1) - mdl.limit_c * qd1, rel=1e-12)
+    # unconditionally stable: a very stiff limit on a light pendulum does not blow up
+    q_, qd_, act = np.array([[0.5]]), np.zeros((1, 1)), np.zeros((1, 0))
+    for _ in range(20):
+        q_, qd_, act, *_ = ora.step(om, 1e-2, q_, qd_, act, np.zeros((1, 0)), 10)
+    assert abs(q_[0, 0]) < 0.05 and np.isfinite(qd_[0, 0])
 
 
 def test_implicit_muscle_damping_is_the_force_velocity_jacobian():
