@@ -88,6 +88,13 @@ __device__ __forceinline__ df df_sqrt(df x) {
     const float r = ((x.hi - yy.hi) - yy.lo + x.lo) * (0.5f / y);
     return fast_two_sum(y, r);
 }
+// 1 / sqrt(x), x > 0: FP32 reciprocal square root plus one Newton step y (1 + (1 - x y^2) / 2)
+__device__ __forceinline__ df df_rsqrt(df x) {
+    const float y = rsqrtf(x.hi);
+    const df yy = two_prod(y, y);
+    const df e = df_add_f(df_neg(df_mul(x, yy)), 1.f);   // 1 - x y^2, small
+    return fast_two_sum(y, y * e.hi * 0.5f);
+}
 // renormalise an arbitrary pair (|lo| may exceed |hi|)
 __device__ __forceinline__ df df_norm(float hi, float lo) { return two_sum(hi, lo); }
 

@@ -35,6 +35,8 @@ struct alignas(16) DofRec {     // 32 B
     uint8_t body;
 };
 
+// Muscle records are sorted by (points, crossed DoFs) so that the 32 muscles a warp handles
+// together run the same loop trip counts; `orig` is the muscle's index in the caller's order.
 struct alignas(16) MuscleRec {  // 32 B
     float fmax;
     float inv_lopt;             // 1 / l_opt
@@ -43,9 +45,16 @@ struct alignas(16) MuscleRec {  // 32 B
     int32_t p0;                 // first path point
     int32_t x0;                 // first entry in the crossed-DoF table (== offset in sparse R)
     uint8_t np, nx;             // number of points, number of crossed DoFs
-    uint16_t pad0;
-    int32_t pad1;
+    uint8_t dep0, pad0;         // depth of the first crossed DoF (the others follow it, +1 each)
+    int32_t orig;
 };
+
+// Crossed-DoF table entry: dof | body << 8 | packed row << 16.  A muscle's crossed DoFs form
+// one contiguous ancestor chain, so entry (d_i, d_j), j <= i, of the packed matrix is at
+// row(d_i) + dep0 + j.
+__host__ __device__ inline int cross_dof(uint32_t c) { return c & 0xff; }
+__host__ __device__ inline int cross_body(uint32_t c) { return (c >> 8) & 0xff; }
+__host__ __device__ inline int cross_row(uint32_t c) { return c >> 16; }
 
 struct alignas(16) PointRec {   // 16 B
     float pos[3];               // body frame
@@ -67,9 +76,9 @@ struct alignas(16) ImgHeader {
     int32_t n_blevels, n_dlevels, max_depth, n_tri, total_bytes;
     // byte offsets of the sections
     int32_t o_body, o_dof, o_muscle, o_sphere, o_cross, o_border, o_blevel, o_child, o_anc, o_dorder, o_dlevel,
-        o_tri, o_point, staged_bytes, points_in_smem, o_pad0;
+        o_tri, o_point, o_rowanc, o_crba, o_pad0;
     // per-environment workspace layout (float offsets inside the environment's slot)
-    int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_y, w_sph, w_rk, w_floats, w_pad0, w_pad1, w_pad2,
+    int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_racc, w_y, w_sph, w_rk, w_pad0, w_pad1, w_pad2,
         w_pad3;
     float gravity[3];
     float contact_k, contact_c, contact_mu, contact_eps2;
@@ -89,10 +98,15 @@ struct alignas(16) ImgHeader {
 //   S[n][6]                           joint motion axis [s; o x s]
 //   A[max(n_packed, 3 nb)][2]         packed M + dt D as float-float (hi, lo) pairs, factorised in
 //                                     place; holds the bias accelerations a[nb][6] (FP32) during
-//                                     the first pass
-//   rhs[n]                            R^T F + tau_c + tau_l - C (FP32)
+//                                     the first pass, then the damping sums dt D as fixed-point
+//                                     int32 pairs (see fx_red) until the mass matrix is added
+//   rhs[n]                            tau_l - C (FP32)
+//   racc[n][2]                        R^T F + tau_c as fixed-point int32 pairs
 //   y[n][2]                           float-float solution of the two triangular solves
 //   sph[ns][12]                       per-sphere contact point, force, damping, flags
-//   rk[kMaxCross][32]                 per-lane moment arms of the muscle being processed
+//   rk[kMaxCross][32 wpe]             per-lane moment arms of the muscle being processed (last)
+
+// floats per environment slot for a group of `wpe` warps per environment
+__host__ __device__ inline int ws_floats(const ImgHeader& h, int wpe) { return h.w_rk + kMaxCross * 32 * wpe; }
 
 }  // namespace msim

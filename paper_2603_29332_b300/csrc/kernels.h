@@ -29,12 +29,13 @@ struct StepArgs {
     int n_sub;
     float dt;
     int envs_per_block;
+    int wpe;                      // warps per environment: 1, 2 or 4
     EvalPtrs ev;                  // used by the eval kernel only
     unsigned long long* timers;   // per-phase cycle counters (profiling builds only)
 };
 
 // dynamic shared memory of a launch with `epb` environments per block
-size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem);
+size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem, int wpe);
 constexpr int kMaxEnvsPerBlock = 16;
 
 cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
@@ -44,6 +45,6 @@ cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, cons
                          const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m, int n_envs,
                          cudaStream_t s);
 cudaError_t set_step_smem_limit(size_t bytes);
-int step_blocks_per_sm(int threads, size_t smem);
+int step_blocks_per_sm(int threads, size_t smem, int wpe);
 
 }  // namespace msim

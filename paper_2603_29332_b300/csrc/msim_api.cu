@@ -96,8 +96,13 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         max_depth = std::max(max_depth, depth[i]);
     }
     std::vector<uint8_t> anc(nM);
+    std::vector<uint16_t> rowanc(nM);   // packed row start of the ancestor of each entry
     for (int i = 0; i < n; ++i)
-        for (int a = i; a >= 0; a = dpar[a]) anc[row[i] + depth[a]] = (uint8_t)a;
+        for (int a = i; a >= 0; a = dpar[a]) {
+            anc[row[i] + depth[a]] = (uint8_t)a;
+            rowanc[row[i] + depth[a]] = (uint16_t)row[a];
+        }
+    if (nM > 65535) FAIL("packed mass matrix above 65535 entries");
 
     // body levels and children
     const int n_bl = *std::max_element(bdepth.begin(), bdepth.end()) + 1;
@@ -127,6 +132,38 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             if (depth[i] == l) dorder.push_back((uint8_t)i);
     }
     dlevel[n_dl] = (int16_t)dorder.size();
+    // CRBA work order: DoFs by decreasing packed-row length, dealt to the 32 lanes in a snake
+    // (0..31, 31..0, ...) so that every lane gets a similar number of entries
+    std::vector<int> byrow(n);
+    for (int i = 0; i < n; ++i) byrow[i] = i;
+    std::stable_sort(byrow.begin(), byrow.end(), [&](int a, int b) { return depth[a] > depth[b]; });
+    std::vector<uint8_t> crba_order(n);
+    {
+        std::vector<std::vector<int>> lanes(32);
+        for (int i = 0; i < n; ++i) {
+            const int round = i / 32, pos = i % 32;
+            lanes[(round % 2 == 0) ? pos : 31 - pos].push_back(byrow[i]);
+        }
+        // slot t = lane + 32 * r holds the r-th DoF of lane `lane`
+        std::vector<int> slot(n, -1);
+        for (int ln = 0; ln < 32; ++ln)
+            for (size_t r = 0; r < lanes[ln].size(); ++r) {
+                const size_t t = ln + 32 * r;
+                if (t < (size_t)n) slot[t] = lanes[ln][r];
+            }
+        // any slot left empty (ragged last round) takes the remaining DoFs in order
+        std::vector<char> used(n, 0);
+        for (int t = 0; t < n; ++t)
+            if (slot[t] >= 0) used[slot[t]] = 1;
+        int next = 0;
+        for (int t = 0; t < n; ++t) {
+            if (slot[t] >= 0) continue;
+            while (used[next]) ++next;
+            slot[t] = next;
+            used[next] = 1;
+        }
+        for (int t = 0; t < n; ++t) crba_order[t] = (uint8_t)slot[t];
+    }
     // pair table: p -> (ia, ib), ib <= ia, row by row
     std::vector<uint16_t> tri;
     for (int ia = 0; ia <= max_depth; ++ia)
@@ -135,7 +172,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     // ---- muscles
     std::vector<MuscleRec> mus(m);
     std::vector<PointRec> pts(np);
-    std::vector<uint8_t> cross;
+    std::vector<uint32_t> cross;
     std::vector<int32_t> mus_ptr(m + 1, 0), mus_dof;
     if (m > 0) {
         if (d.muscle_point_start[0] != 0 || d.muscle_point_start[m] != np)
@@ -188,13 +225,20 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         M.x0 = (int32_t)cross.size();
         M.np = (uint8_t)cnt;
         M.nx = (uint8_t)nx;
+        M.dep0 = nx > 0 ? (uint8_t)depth[dof0[chain[0]]] : 0;
+        M.orig = k;
         for (size_t t = 0; t < chain.size(); ++t)
             for (int j = 0; j < d.body_ndof[chain[t]]; ++j) {
-                cross.push_back((uint8_t)(dof0[chain[t]] + j));
-                mus_dof.push_back(dof0[chain[t]] + j);
+                const int dd = dof0[chain[t]] + j;
+                cross.push_back((uint32_t)dd | ((uint32_t)chain[t] << 8) | ((uint32_t)row[dd] << 16));
+                mus_dof.push_back(dd);
             }
         mus_ptr[k + 1] = (int32_t)cross.size();
     }
+    // records sorted by (points, crossed DoFs): a warp's 32 lanes then share loop trip counts
+    std::stable_sort(mus.begin(), mus.end(), [](const MuscleRec& a, const MuscleRec& b) {
+        return a.np != b.np ? a.np < b.np : a.nx < b.nx;
+    });
     if (!(d.vmax_per_lopt > 0.f) || !(d.tau_act > 0.f) || !(d.tau_deact > 0.f)) FAIL("time constants must be > 0");
 
     // ---- spheres
@@ -257,7 +301,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.o_dof = place(sizeof(DofRec) * n);
     h.o_muscle = place(sizeof(MuscleRec) * m);
     h.o_sphere = place(sizeof(SphereRec) * ns);
-    h.o_cross = place(cross.size());
+    h.o_cross = place(sizeof(uint32_t) * cross.size());
     h.o_border = place(border.size());
     h.o_blevel = place(sizeof(int16_t) * blevel.size());
     h.o_child = place(child.size());
@@ -265,6 +309,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.o_dorder = place(dorder.size());
     h.o_dlevel = place(sizeof(int16_t) * dlevel.size());
     h.o_tri = place(sizeof(uint16_t) * tri.size());
+    h.o_rowanc = place(sizeof(uint16_t) * rowanc.size());
+    h.o_crba = place(crba_order.size());
     h.o_point = place(sizeof(PointRec) * np);   // last: may stay in global memory (staging split)
     h.total_bytes = (int32_t)off;
     // per-environment workspace
@@ -282,10 +328,10 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.w_S = slot(6 * n);
     h.w_A = slot(2 * std::max(nM, 3 * nb));
     h.w_rhs = slot(n);
+    h.w_racc = slot(2 * n);
     h.w_y = slot(2 * n);
     h.w_sph = slot(12 * ns);
-    h.w_rk = slot(kMaxCross * 32);
-    h.w_floats = w;
+    h.w_rk = w;   // last: its size depends on the warps per environment (ws_floats)
     for (int c = 0; c < 3; ++c) h.gravity[c] = d.gravity[c];
     h.contact_k = d.contact_k;
     h.contact_c = d.contact_c;
@@ -309,7 +355,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     put(h.o_muscle, mus.data(), sizeof(MuscleRec) * m);
     put(h.o_point, pts.data(), sizeof(PointRec) * np);
     put(h.o_sphere, sph.data(), sizeof(SphereRec) * ns);
-    put(h.o_cross, cross.data(), cross.size());
+    put(h.o_cross, cross.data(), sizeof(uint32_t) * cross.size());
     put(h.o_border, border.data(), border.size());
     put(h.o_blevel, blevel.data(), sizeof(int16_t) * blevel.size());
     put(h.o_child, child.data(), child.size());
@@ -317,6 +363,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     put(h.o_dorder, dorder.data(), dorder.size());
     put(h.o_dlevel, dlevel.data(), sizeof(int16_t) * dlevel.size());
     put(h.o_tri, tri.data(), sizeof(uint16_t) * tri.size());
+    put(h.o_rowanc, rowanc.data(), sizeof(uint16_t) * rowanc.size());
+    put(h.o_crba, crba_order.data(), crba_order.size());
 
     out.dof_parent.assign(dpar.begin(), dpar.end());
     out.dof_depth.assign(depth.begin(), depth.end());
@@ -340,6 +388,7 @@ struct msim_handle_ {
     int env_begin[kMaxModels + 1] = {};
     int epb[kMaxModels] = {};
     int pts_smem[kMaxModels] = {};
+    int wpe[kMaxModels] = {};
     float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *exc_stage = nullptr;
     uint32_t* env_status = nullptr;
     uint32_t* gflags = nullptr;
@@ -374,8 +423,8 @@ void free_all(msim_handle h) {
 int model_grid(msim_handle h, int i) {
     const int ne = h->env_begin[i + 1] - h->env_begin[i];
     const int groups = (ne + h->epb[i] - 1) / h->epb[i];
-    const size_t smem = step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i]);
-    const int per_sm = std::max(1, step_blocks_per_sm(32 * h->epb[i], smem));
+    const size_t smem = step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i], h->wpe[i]);
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * h->wpe[i] * h->epb[i], smem, h->wpe[i]));
     return std::max(1, std::min(groups, h->num_sms * per_sm));
 }
 
@@ -393,25 +442,30 @@ StepArgs base_args(msim_handle h, int i) {
     a.env_status = h->env_status; a.gflags = h->gflags;
     a.dt = h->dt;
     a.envs_per_block = h->epb[i];
+    a.wpe = h->wpe[i];
     a.timers = h->timers;
     return a;
 }
 
-int max_epb(msim_handle h, int i, bool pts) {
+int max_epb(msim_handle h, int i, bool pts, int wpe) {
     const ImgHeader& hd = h->models[i].hdr;
-    const size_t fixed = step_smem_bytes(hd, 0, pts);
-    const size_t per = (size_t)hd.w_floats * sizeof(float);
+    const size_t fixed = step_smem_bytes(hd, 0, pts, wpe);
+    const size_t per = (size_t)ws_floats(hd, wpe) * sizeof(float);
     if (fixed + per > h->smem_optin) return 0;
-    return std::min((int)((h->smem_optin - fixed) / per), kMaxEnvsPerBlock);
+    const int lim = wpe == 1 ? kMaxEnvsPerBlock : std::min(15, 16 / wpe);   // 512 threads, 15 named barriers
+    return std::min((int)((h->smem_optin - fixed) / per), lim);
 }
 
-// Default launch shape: as many environments per block as shared memory holds (<= 8, <= the
-// model's environments), path points staged in shared memory unless that leaves fewer than 4.
+// Default launch shape: two warps per environment, as many environments per block as shared
+// memory holds (<= 8, <= the model's environments); the path points are staged in shared memory
+// only when that costs no environment per block (otherwise they are read through the cache).
 void auto_launch(msim_handle h, int i) {
     const int ne = h->env_begin[i + 1] - h->env_begin[i];
-    int e_in = std::min(max_epb(h, i, true), 8), e_out = std::min(max_epb(h, i, false), 8);
+    const int w = 2;
+    int e_in = std::min(max_epb(h, i, true, w), 8), e_out = std::min(max_epb(h, i, false, w), 8);
     if (ne > 0) { e_in = std::min(e_in, ne); e_out = std::min(e_out, ne); }
-    if (e_in >= 4 || (e_in >= 1 && e_in >= e_out)) { h->pts_smem[i] = 1; h->epb[i] = e_in; }
+    h->wpe[i] = w;
+    if (e_in >= 1 && e_in >= e_out) { h->pts_smem[i] = 1; h->epb[i] = e_in; }
     else { h->pts_smem[i] = 0; h->epb[i] = e_out; }
 }
 
@@ -490,8 +544,8 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
     ALLOC(h->env_status, sizeof(uint32_t) * total);
     ALLOC(h->gflags, sizeof(uint32_t));
 #ifdef MSIM_PHASE_TIMERS
-    ALLOC(h->timers, sizeof(unsigned long long) * 8);
-    cudaMemset(h->timers, 0, sizeof(unsigned long long) * 8);
+    ALLOC(h->timers, sizeof(unsigned long long) * 16);
+    cudaMemset(h->timers, 0, sizeof(unsigned long long) * 16);
 #endif
     cudaMemset(h->q, 0, rn); cudaMemset(h->qd, 0, rn); cudaMemset(h->qdd, 0, rn);
     cudaMemset(h->act, 0, rm); cudaMemset(h->force, 0, rm); cudaMemset(h->exc_stage, 0, rm);
@@ -519,9 +573,9 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
             a.q = zq; a.qd = zq + h->pitch_n; a.act = zm; a.exc = zm + h->pitch_m;
             a.pitch_n = h->pitch_n; a.pitch_m = h->pitch_m;
             a.env_status = h->env_status; a.gflags = h->gflags;
-            a.n_sub = 1; a.dt = h->dt; a.envs_per_block = 1;
+            a.n_sub = 1; a.dt = h->dt; a.envs_per_block = 1; a.wpe = 1;
             a.ev.L = Lbuf;
-            const size_t smem = step_smem_bytes(M.hdr, 1, false);
+            const size_t smem = step_smem_bytes(M.hdr, 1, false, 1);
             if (smem > h->smem_optin) {
                 g_create_error = "model " + std::to_string(i) + " does not fit in shared memory";
                 cudaFree(zq); cudaFree(zm); free_all(h); delete h;
@@ -580,27 +634,33 @@ msim_status msim_get_dims(msim_handle h, msim_dims* out) {
         out->n_packed[i] = hd.n_packed;
         out->envs_per_block[i] = h->epb[i];
         out->image_bytes[i] = hd.total_bytes;
-        out->workspace_bytes_per_env[i] = hd.w_floats * (int)sizeof(float);
+        out->workspace_bytes_per_env[i] = ws_floats(hd, h->wpe[i]) * (int)sizeof(float);
         out->points_in_smem[i] = h->pts_smem[i];
+        out->warps_per_env[i] = h->wpe[i];
     }
     return MSIM_OK;
 }
 
-msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_per_block, int32_t stage_points) {
+msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_per_block, int32_t stage_points,
+                            int32_t warps_per_env) {
     if (!h || model < 0 || model >= h->n_models) return arg_fail(h, "msim_set_launch: bad handle or model");
     if (envs_per_block < 0 || envs_per_block > kMaxEnvsPerBlock) return arg_fail(h, "envs_per_block must be 0..16");
     if (stage_points < -1 || stage_points > 1) return arg_fail(h, "stage_points must be -1, 0 or 1");
-    if (envs_per_block == 0 && stage_points == -1) {
+    if (warps_per_env != 0 && warps_per_env != 1 && warps_per_env != 2 && warps_per_env != 4)
+        return arg_fail(h, "warps_per_env must be 0, 1, 2 or 4");
+    if (envs_per_block == 0 && stage_points == -1 && warps_per_env == 0) {
         auto_launch(h, model);
         return MSIM_OK;
     }
     const bool pts = stage_points == -1 ? (h->pts_smem[model] != 0) : (stage_points == 1);
+    const int w = warps_per_env == 0 ? h->wpe[model] : warps_per_env;
     int e = envs_per_block;
-    if (e == 0) e = std::min(max_epb(h, model, pts), 8);
-    if (e < 1 || step_smem_bytes(h->models[model].hdr, e, pts) > h->smem_optin)
-        return arg_fail(h, "msim_set_launch: shared memory does not fit");
+    if (e == 0) e = std::min(max_epb(h, model, pts, w), 8);
+    if (e < 1 || e > max_epb(h, model, pts, w) || step_smem_bytes(h->models[model].hdr, e, pts, w) > h->smem_optin)
+        return arg_fail(h, "msim_set_launch: shared memory or thread limit exceeded");
     h->epb[model] = e;
     h->pts_smem[model] = pts ? 1 : 0;
+    h->wpe[model] = w;
     return MSIM_OK;
 }
 
@@ -626,7 +686,8 @@ msim_status msim_step(msim_handle h, const float* excitations, int32_t n_substep
         StepArgs a = base_args(h, i);
         a.exc = excitations;
         a.n_sub = n_substeps;
-        const cudaError_t e = launch_step(a, model_grid(h, i), step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i]),
+        const cudaError_t e = launch_step(a, model_grid(h, i),
+                                          step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i], h->wpe[i]),
                                           (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "msim_step launch");
     }
@@ -712,7 +773,8 @@ msim_status msim_eval(msim_handle h, const float* q, const float* qd, const floa
         a.ev.R = out->R; a.ev.tau_m = out->tau_m; a.ev.tau_c = out->tau_c; a.ev.tau_l = out->tau_l;
         a.ev.bias = out->bias; a.ev.rhs = out->rhs; a.ev.qdd = out->qdd; a.ev.M = out->M; a.ev.A = out->A;
         a.ev.nnz_pitch = out->nnz_pitch; a.ev.packed_pitch = out->packed_pitch;
-        const cudaError_t e = launch_eval(a, model_grid(h, i), step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i]),
+        const cudaError_t e = launch_eval(a, model_grid(h, i),
+                                          step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i], h->wpe[i]),
                                           (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "msim_eval launch");
     }
@@ -739,8 +801,8 @@ msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_parent, i
 MSIM_API msim_status msim_debug_phase_cycles(msim_handle h, unsigned long long* out8, int32_t reset) {
     if (!h || !out8 || !h->timers) return arg_fail(h, "msim_debug_phase_cycles: unavailable");
     cudaDeviceSynchronize();
-    cudaMemcpy(out8, h->timers, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost);
-    if (reset) cudaMemset(h->timers, 0, sizeof(unsigned long long) * 8);
+    cudaMemcpy(out8, h->timers, sizeof(unsigned long long) * 16, cudaMemcpyDeviceToHost);
+    if (reset) cudaMemset(h->timers, 0, sizeof(unsigned long long) * 16);
     return MSIM_OK;
 }
 #endif

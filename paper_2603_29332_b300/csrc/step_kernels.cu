@@ -1,16 +1,18 @@
 // step_kernels.cu -- the batched muscle-driven forward-dynamics substep on sm_103a.
 //
-// Mapping: one warp per environment, several environments per block sharing one copy of the
-// model image in shared memory (staged by cp.async.bulk + mbarrier, kept resident across all
-// substeps and all environments the block processes).  Blocks are persistent: each loops over
-// groups of environments.  Per substep and environment (paper, Methods: Eq. 1, Eq. 2 and the
+// Mapping: a group of WPE warps (1, 2 or 4) per environment, several environments per block
+// sharing one copy of the model image in shared memory (staged by cp.async.bulk + mbarrier,
+// kept resident across all substeps and all environments the block processes).  A group
+// synchronises on its own named barrier.  Blocks are persistent: each loops over groups of
+// environments.  Per substep and environment (paper, Methods: Eq. 1, Eq. 2 and the
 // generalised-coordinate equations of motion):
 //   1. kinematics, top-down over body levels: frames, joint axes S, spatial velocities, bias
 //      accelerations (gravity as a base acceleration), body forces f = I a + v x* I v and
 //      spatial inertias, all in world Plücker coordinates so that subtree sums need no
 //      transforms;
 //   2. bottom-up over body levels: subtree sums of forces and inertias; rhs = -C = -S^T f;
-//   3. CRBA: M(d, a) = S_a^T (I^c_d S_d) for every DoF and each of its ancestors (tree-packed);
+//   3. CRBA: M(d, a) = S_a^T (I^c_d S_d) for every DoF and each of its ancestors (tree-packed),
+//      added to the damping terms of steps 4-5, which run before it;
 // Precision: kinematics, forces, muscles and contact in FP32; the parallel-axis terms of the
 // inertias, their subtree sums, the entries of M and the factorisation / solves in float-float
 // (dfloat.cuh).  FP32 geometry perturbs the mechanism consistently and costs ~1e-6 in q_dd,
@@ -46,7 +48,7 @@ struct Tables {
     const MuscleRec* mus;
     const PointRec* pt;
     const SphereRec* sph;
-    const uint8_t* cross;
+    const uint32_t* cross;
     const uint8_t* border;
     const int16_t* blevel;
     const uint8_t* child;
@@ -54,6 +56,8 @@ struct Tables {
     const uint8_t* dorder;
     const int16_t* dlevel;
     const uint16_t* tri;
+    const uint16_t* rowanc;
+    const uint8_t* crba_order;
 };
 
 __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
@@ -65,7 +69,7 @@ __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     t.mus = reinterpret_cast<const MuscleRec*>(img + h.o_muscle);
     t.pt = reinterpret_cast<const PointRec*>(img + h.o_point);
     t.sph = reinterpret_cast<const SphereRec*>(img + h.o_sphere);
-    t.cross = img + h.o_cross;
+    t.cross = reinterpret_cast<const uint32_t*>(img + h.o_cross);
     t.border = img + h.o_border;
     t.blevel = reinterpret_cast<const int16_t*>(img + h.o_blevel);
     t.child = img + h.o_child;
@@ -73,6 +77,8 @@ __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     t.dorder = img + h.o_dorder;
     t.dlevel = reinterpret_cast<const int16_t*>(img + h.o_dlevel);
     t.tri = reinterpret_cast<const uint16_t*>(img + h.o_tri);
+    t.rowanc = reinterpret_cast<const uint16_t*>(img + h.o_rowanc);
+    t.crba_order = img + h.o_crba;
     return t;
 }
 
@@ -89,6 +95,86 @@ __device__ __forceinline__ void rot3(const float* R, const float v[3], float out
     out[0] = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
     out[1] = R[3] * v[0] + R[4] * v[1] + R[5] * v[2];
     out[2] = R[6] * v[0] + R[7] * v[1] + R[8] * v[2];
+}
+
+// Profiling builds (MSIM_PHASE_TIMERS): lane 0 adds cycles since the previous mark to a slot.
+#ifdef MSIM_PHASE_TIMERS
+#define SUB_T0() long long st0_ = clock64()
+#define SUB_MARK(i)                                                                               \
+    do {                                                                                          \
+        const long long t_ = clock64();                                                           \
+        if (g.lane == 0 && g_timers) atomicAdd(&g_timers[(i)], (unsigned long long)(t_ - st0_));   \
+        st0_ = clock64();                                                                         \
+    } while (0)
+__device__ unsigned long long* g_timers = nullptr;
+#else
+#define SUB_T0() \
+    do {         \
+    } while (0)
+#define SUB_MARK(i) \
+    do {            \
+    } while (0)
+#endif
+
+// The threads working on one environment: WPE warps, N = 32 WPE lanes, synchronised on named
+// barrier `bar` (one per environment slot of the block; id 0 is __syncthreads).
+template <int WPE>
+struct Grp {
+    static constexpr int N = 32 * WPE;
+    int lane;   // 0 .. N-1
+    int wl;     // lane within the warp
+    int wi;     // warp within the group
+    int bar;
+    __device__ __forceinline__ void sync() const {
+        if (WPE == 1) __syncwarp();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(N) : "memory");
+    }
+    __device__ __forceinline__ bool all(bool v) const {
+        if (WPE == 1) return __all_sync(0xffffffffu, v);
+        uint32_t r;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred p, %2, %3, p;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(r) : "r"((uint32_t)v), "r"(bar), "n"(N) : "memory");
+        return r != 0;
+    }
+    __device__ __forceinline__ bool any(bool v) const {
+        if (WPE == 1) return __any_sync(0xffffffffu, v);
+        uint32_t r;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred p, %2, %3, p;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(r) : "r"((uint32_t)v), "r"(bar), "n"(N) : "memory");
+        return r != 0;
+    }
+};
+
+// Exact, order-independent accumulation in shared memory with native 32-bit integer reductions
+// (shared-memory float atomics are emulated with compare-and-swap loops and serialise under
+// contention).  A value v is split into a coarse word round(v 2^8) and a fine word holding the
+// remainder at 2^-28; each word is reduced with red.shared.add.u32.  Range +-8e6, resolution
+// 3.7e-9, exact sums for up to 2^12 contributions per target.
+constexpr float kFxCoarse = 256.f;          // 2^8
+constexpr float kFxInvCoarse = 1.f / 256.f;
+constexpr float kFxFine = 268435456.f;      // 2^28
+constexpr float kFxInvFine = 1.f / 268435456.f;
+
+__device__ __forceinline__ void red_add_i32(int32_t* p, int32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(v));
+}
+__device__ __forceinline__ void fx_red(int32_t* acc2, float v) {
+    const int32_t hi = __float2int_rn(v * kFxCoarse);
+    const float rem = fmaf(-static_cast<float>(hi), kFxInvCoarse, v);
+    const int32_t lo = __float2int_rn(rem * kFxFine);
+    red_add_i32(acc2, hi);
+    red_add_i32(acc2 + 1, lo);
+}
+__device__ __forceinline__ df df_from_i32(int32_t x) {
+    const float f = __int2float_rn(x);
+    const long long r = static_cast<long long>(x) - __float2ll_rn(f);
+    return {f, static_cast<float>(r)};
+}
+__device__ __forceinline__ df fx_decode(int32_t hi, int32_t lo) {
+    const df a = df_from_i32(hi), b = df_from_i32(lo);
+    return df_add({a.hi * kFxInvCoarse, a.lo * kFxInvCoarse}, {b.hi * kFxInvFine, b.lo * kFxInvFine});
 }
 
 // ------------------------------------------------------------------ bulk staging of the image
@@ -143,7 +229,8 @@ __device__ bool stage_image(uint8_t* dst, const uint8_t* src, int bytes, uint64_
 }
 
 // ------------------------------------------------------------------ phase 1: kinematics
-__device__ void phase_kinematics(const Tables& T, float* ws, int lane) {
+template <int WPE>
+__device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
     const float* q = ws + H.w_q;
     const float* qd = ws + H.w_qd;
@@ -154,7 +241,7 @@ __device__ void phase_kinematics(const Tables& T, float* ws, int lane) {
     float* Acc = ws + H.w_A;   // bias accelerations live in the A region during this pass
     for (int l = 0; l < H.n_blevels; ++l) {
         const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
-        for (int i = i0 + lane; i < i1; i += 32) {
+        for (int i = i0 + g.lane; i < i1; i += g.N) {
             const int b = T.border[i];
             const BodyRec& B = T.body[b];
             float R[9], p[3], w[3], vl[3], aw[3], al[3];
@@ -288,19 +375,20 @@ __device__ void phase_kinematics(const Tables& T, float* ws, int lane) {
 #pragma unroll
             for (int e = 0; e < 6; ++e) Id[4 + e] = Ibd[e];
         }
-        __syncwarp();
+        g.sync();
     }
 }
 
 // ------------------------------------------------------------------ phase 2: subtree sums, bias
-__device__ void phase_subtree(const Tables& T, float* ws, int lane) {
+template <int WPE>
+__device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
     float* FI = ws + H.w_fi;
     const float* S = ws + H.w_S;
     float* rhs = ws + H.w_rhs;
     for (int l = H.n_blevels - 1; l >= 0; --l) {
         const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
-        for (int i = i0 + lane; i < i1; i += 32) {
+        for (int i = i0 + g.lane; i < i1; i += g.N) {
             const int b = T.border[i];
             const BodyRec& B = T.body[b];
             float* fi = FI + kFiStride * b;
@@ -330,17 +418,22 @@ __device__ void phase_subtree(const Tables& T, float* ws, int lane) {
                 rhs[d] = -(Sd[0] * f[0] + Sd[1] * f[1] + Sd[2] * f[2] + Sd[3] * f[3] + Sd[4] * f[4] + Sd[5] * f[5]);
             }
         }
-        __syncwarp();
+        g.sync();
     }
 }
 
 // ------------------------------------------------------------------ phase 3: CRBA (float-float)
-__device__ void phase_crba(const Tables& T, float* ws, int lane) {
+// Adds M to the damping sums already accumulated (fixed point) in the same storage.  DoFs are
+// taken in the image's balanced order (similar entry counts per lane).
+template <int WPE>
+__device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float* evM) {
     const ImgHeader& H = *T.H;
     const float* FI = ws + H.w_fi;
     const float* S = ws + H.w_S;
     df* A = reinterpret_cast<df*>(ws + H.w_A);
-    for (int d = lane; d < H.n; d += 32) {
+    const int32_t* Ai = reinterpret_cast<const int32_t*>(ws + H.w_A);
+    for (int t = g.lane; t < H.n; t += g.N) {
+        const int d = T.crba_order[t];
         const DofRec& D = T.dof[d];
         const df* I = reinterpret_cast<const df*>(FI + kFiStride * D.body + 6);
         const df m = I[0];
@@ -368,10 +461,12 @@ __device__ void phase_crba(const Tables& T, float* ws, int lane) {
             acc = df_fma_f(acc, Fl[0], Sa[3]);
             acc = df_fma_f(acc, Fl[1], Sa[4]);
             acc = df_fma_f(acc, Fl[2], Sa[5]);
-            A[row + k] = acc;
+            if (evM) evM[row + k] = acc.hi + acc.lo;
+            const df dsum = fx_decode(Ai[2 * (row + k)], Ai[2 * (row + k) + 1]);
+            A[row + k] = df_add(acc, dsum);
         }
     }
-    __syncwarp();
+    g.sync();
 }
 
 // ------------------------------------------------------------------ Hill curves (Eq. 1)
@@ -404,54 +499,62 @@ __device__ __forceinline__ float hill_dfv(float v) {
 }
 
 // ------------------------------------------------------------------ phase 4: muscles
-// act: this environment's activation row in global memory (read; written unless EVAL).
-template <bool EVAL>
-__device__ void phase_muscles(const Tables& T, float* ws, int lane, float dt, const float* exc, float* act,
+// One lane per muscle.  act: this environment's activation row in global memory (read;
+// written unless EVAL).  Returns true if a force was not finite.
+template <bool EVAL, int WPE>
+__device__ bool phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc, float* act,
                               float* force_out, const EvalPtrs* ev) {
     const ImgHeader& H = *T.H;
     const float* qd = ws + H.w_qd;
     const float* frame = ws + H.w_frame;
     const float* S = ws + H.w_S;
-    df* A = reinterpret_cast<df*>(ws + H.w_A);
-    float* rhs = ws + H.w_rhs;
-    float* rk = ws + H.w_rk;
-    for (int k = lane; k < H.m; k += 32) {
-        const MuscleRec M = T.mus[k];
+    int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);   // damping sums, fixed point
+    int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
+    float* rk = ws + H.w_rk;                                  // [kMaxCross][N]
+    bool bad = false;
+    SUB_T0();
+    for (int r = g.lane; r < H.m; r += g.N) {
+        const MuscleRec M = T.mus[r];
+        const int k = M.orig;
         const float a = act[k];
         const float u = fminf(fmaxf(exc[k], 0.f), 1.f);
         PointRec P = T.pt[M.p0];
         int b = P.body_cross & 0xff;
         int cprev = P.body_cross >> 8;
+        const float* fb = frame + 12 * b;
         float x0[3];
-        rot3(frame + 12 * b, P.pos, x0);
-        x0[0] += frame[12 * b + 9]; x0[1] += frame[12 * b + 10]; x0[2] += frame[12 * b + 11];
+        rot3(fb, P.pos, x0);
+        x0[0] += fb[9]; x0[1] += fb[10]; x0[2] += fb[11];
         float L = 0.f, ldot = 0.f;
         for (int j = 1; j < M.np; ++j) {
             P = T.pt[M.p0 + j];
             b = P.body_cross & 0xff;
             const int c = P.body_cross >> 8;
+            fb = frame + 12 * b;
             float x1[3];
-            rot3(frame + 12 * b, P.pos, x1);
-            x1[0] += frame[12 * b + 9]; x1[1] += frame[12 * b + 10]; x1[2] += frame[12 * b + 11];
+            rot3(fb, P.pos, x1);
+            x1[0] += fb[9]; x1[1] += fb[10]; x1[2] += fb[11];
             const float dv[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
             const float len2 = dot3(dv, dv);
             const float inv = rsqrtf(len2);
             L += len2 * inv;
             const float uu[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
             for (int i = cprev; i < c; ++i) {
-                const int d = T.cross[M.x0 + i];
+                const uint32_t ce = T.cross[M.x0 + i];
+                const int d = cross_dof(ce);
                 const float* Sd = S + 6 * d;
-                const float* o = frame + 12 * T.dof[d].body + 9;
-                const float r[3] = {x1[0] - o[0], x1[1] - o[1], x1[2] - o[2]};
+                const float* o = frame + 12 * cross_body(ce) + 9;
+                const float rr[3] = {x1[0] - o[0], x1[1] - o[1], x1[2] - o[2]};
                 float rxu[3];
-                cross3(r, uu, rxu);
+                cross3(rr, uu, rxu);
                 const float Rv = -(Sd[0] * rxu[0] + Sd[1] * rxu[1] + Sd[2] * rxu[2]);   // R = -dL/dq
-                rk[i * 32 + lane] = Rv;
+                rk[i * g.N + g.lane] = Rv;
                 ldot -= Rv * qd[d];
             }
             x0[0] = x1[0]; x0[1] = x1[1]; x0[2] = x1[2];
             cprev = c;
         }
+        SUB_MARK(8);
         const float lm = 1.f + (L - M.L0) * M.inv_lopt;
         const float vm = ldot * M.inv_vmax;
         const float fl = hill_fl(lm);
@@ -461,20 +564,28 @@ __device__ void phase_muscles(const Tables& T, float* ws, int lane, float dt, co
         const float an = fminf(fmaxf(a + dt * (u - a) / tau, 0.f), 1.f);
         if (!EVAL) act[k] = an;
         if (force_out) force_out[k] = F;
-        // rhs += R^T F; A += dt R^T (dF/dLdot) R as g g^T with g = sqrt(dt dF/dLdot) R, added to
-        // the low words of the float-float entries (renormalised before the factorisation)
+        SUB_MARK(9);
+        // rhs += R^T F; A += dt R^T (dF/dLdot) R as g g^T with g = sqrt(dt dF/dLdot) R.  All
+        // operands are loaded first, then the reductions issue back to back.
         const float sq = sqrtf(dt * dFdl);
-        for (int i = 0; i < M.nx; ++i) {
-            const int d = T.cross[M.x0 + i];
-            const float Ri = rk[i * 32 + lane];
-            atomicAdd(&rhs[d], Ri * F);
-            if (EVAL && ev->tau_m) atomicAdd(&ev->tau_m[d], Ri * F);
-            if (sq != 0.f) {
-                const int row = T.dof[d].row;
-                const float gi = sq * Ri;
-                for (int i2 = 0; i2 <= i; ++i2) {
-                    const int d2 = T.cross[M.x0 + i2];
-                    atomicAdd(&A[row + T.dof[d2].depth].lo, gi * (sq * rk[i2 * 32 + lane]));
+        bad |= !(isfinite(F) && isfinite(sq));
+        float Rr[kMaxCross];
+        uint32_t cr[kMaxCross];
+#pragma unroll
+        for (int i = 0; i < kMaxCross; ++i) {
+            Rr[i] = i < M.nx ? rk[i * g.N + g.lane] : 0.f;
+            cr[i] = i < M.nx ? T.cross[M.x0 + i] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kMaxCross; ++i) {
+            if (i < M.nx) {
+                fx_red(&racc[2 * cross_dof(cr[i])], Rr[i] * F);
+                if (EVAL && ev->tau_m) atomicAdd(&ev->tau_m[cross_dof(cr[i])], Rr[i] * F);
+                if (sq != 0.f) {
+                    const float gi = sq * Rr[i];
+                    const int base = cross_row(cr[i]) + M.dep0;
+#pragma unroll
+                    for (int j = 0; j <= i; ++j) fx_red(&Ai[2 * (base + j)], gi * (sq * Rr[j]));
                 }
             }
         }
@@ -485,24 +596,25 @@ __device__ void phase_muscles(const Tables& T, float* ws, int lane, float dt, co
             if (ev->force) ev->force[k] = F;
             if (ev->act_next) ev->act_next[k] = an;
             if (ev->R)
-                for (int i = 0; i < M.nx; ++i) ev->R[M.x0 + i] = rk[i * 32 + lane];
+                for (int i = 0; i < M.nx; ++i) ev->R[M.x0 + i] = Rr[i];
         }
+        SUB_MARK(10);
     }
-    __syncwarp();
+    return g.any(bad);   // also orders the reductions before the next phase
 }
 
 // ------------------------------------------------------------------ phase 5: contact
-template <bool EVAL>
-__device__ void phase_contact(const Tables& T, float* ws, int lane, float dt, const EvalPtrs* ev) {
+template <bool EVAL, int WPE>
+__device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const EvalPtrs* ev) {
     const ImgHeader& H = *T.H;
     if (H.ns == 0) return;
     const float* frame = ws + H.w_frame;
     const float* V = ws + H.w_v;
     const float* S = ws + H.w_S;
-    df* A = reinterpret_cast<df*>(ws + H.w_A);
-    float* rhs = ws + H.w_rhs;
+    int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);
+    int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
     float* sph = ws + H.w_sph;
-    for (int i = lane; i < H.ns; i += 32) {
+    for (int i = g.lane; i < H.ns; i += g.N) {
         const SphereRec& Sp = T.sph[i];
         const float* fr = frame + 12 * Sp.body;
         float x[3];
@@ -529,7 +641,7 @@ __device__ void phase_contact(const Tables& T, float* ws, int lane, float dt, co
             o[9] = 0.f;
         }
     }
-    __syncwarp();
+    g.sync();
     for (int i = 0; i < H.ns; ++i) {
         const float* o = sph + 12 * i;
         if (o[9] == 0.f) continue;
@@ -537,41 +649,56 @@ __device__ void phase_contact(const Tables& T, float* ws, int lane, float dt, co
         const int rowl = T.dof[dl].row;
         const int dep = T.dof[dl].depth;
         const int npairs = (dep + 1) * (dep + 2) / 2;
-        for (int p = lane; p < npairs; p += 32) {
-            const int tv = T.tri[p];
-            const int ia = tv & 0xff, ib = tv >> 8;
-            const int da = T.anc[rowl + ia], db = T.anc[rowl + ib];
-            const float* Sa = S + 6 * da;
-            const float* Sb = S + 6 * db;
-            const float* oa = frame + 12 * T.dof[da].body + 9;
-            const float* ob = frame + 12 * T.dof[db].body + 9;
-            const float ra[3] = {o[0] - oa[0], o[1] - oa[1], o[2] - oa[2]};
-            const float rb[3] = {o[0] - ob[0], o[1] - ob[1], o[2] - ob[2]};
-            float Ja[3], Jb[3];
-            cross3(Sa, ra, Ja);
-            cross3(Sb, rb, Jb);
-            const float val = (o[6] * Ja[0]) * (o[6] * Jb[0]) + (o[7] * Ja[1]) * (o[7] * Jb[1]) +
-                              (o[8] * Ja[2]) * (o[8] * Jb[2]);
-            atomicAdd(&A[T.dof[da].row + ib].lo, val);
-            if (ia == ib) {
-                const float t = Ja[0] * o[3] + Ja[1] * o[4] + Ja[2] * o[5];
-                atomicAdd(&rhs[da], t);
-                if (EVAL && ev->tau_c) atomicAdd(&ev->tau_c[da], t);
+        for (int p0 = g.lane; p0 < npairs; p0 += 2 * g.N) {
+            float val[2], tdiag[2];
+            int tgt[2], dd[2];
+            bool on[2], diag[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int p = p0 + g.N * u;
+                on[u] = p < npairs;
+                const int tv = T.tri[on[u] ? p : 0];
+                const int ia = tv & 0xff, ib = tv >> 8;
+                const int da = T.anc[rowl + ia], db = T.anc[rowl + ib];
+                const float* Sa = S + 6 * da;
+                const float* Sb = S + 6 * db;
+                const float* oa = frame + 12 * T.dof[da].body + 9;
+                const float* ob = frame + 12 * T.dof[db].body + 9;
+                const float ra[3] = {o[0] - oa[0], o[1] - oa[1], o[2] - oa[2]};
+                const float rb[3] = {o[0] - ob[0], o[1] - ob[1], o[2] - ob[2]};
+                float Ja[3], Jb[3];
+                cross3(Sa, ra, Ja);
+                cross3(Sb, rb, Jb);
+                val[u] = (o[6] * Ja[0]) * (o[6] * Jb[0]) + (o[7] * Ja[1]) * (o[7] * Jb[1]) +
+                         (o[8] * Ja[2]) * (o[8] * Jb[2]);
+                tgt[u] = T.dof[da].row + ib;
+                dd[u] = da;
+                diag[u] = ia == ib;
+                tdiag[u] = Ja[0] * o[3] + Ja[1] * o[4] + Ja[2] * o[5];
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (!on[u]) continue;
+                fx_red(&Ai[2 * tgt[u]], val[u]);
+                if (diag[u]) {
+                    fx_red(&racc[2 * dd[u]], tdiag[u]);
+                    if (EVAL && ev->tau_c) atomicAdd(&ev->tau_c[dd[u]], tdiag[u]);
+                }
             }
         }
     }
-    __syncwarp();
+    g.sync();
 }
 
 // ------------------------------------------------------------------ phase 6: limits, damping
-template <bool EVAL>
-__device__ void phase_limits(const Tables& T, float* ws, int lane, float dt, const EvalPtrs* ev) {
+template <bool EVAL, int WPE>
+__device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const EvalPtrs* ev) {
     const ImgHeader& H = *T.H;
     const float* q = ws + H.w_q;
     const float* qd = ws + H.w_qd;
     df* A = reinterpret_cast<df*>(ws + H.w_A);
     float* rhs = ws + H.w_rhs;
-    for (int d = lane; d < H.n; d += 32) {
+    for (int d = g.lane; d < H.n; d += g.N) {
         const DofRec& D = T.dof[d];
         const float qv = q[d], qdv = qd[d];
         // limit spring-damper evaluated at the predicted end-of-step state (linearly implicit
@@ -583,93 +710,124 @@ __device__ void phase_limits(const Tables& T, float* ws, int lane, float dt, con
             else if (qv < D.lo) { t += H.limit_k * (D.lo - qv) - kd * qdv; dd += kd; }
         }
         rhs[d] += t;
-        A[D.row + D.depth].lo += dt * dd;
+        A[D.row + D.depth] = df_add_f(A[D.row + D.depth], dt * dd);
         if (EVAL && ev->tau_l) ev->tau_l[d] = t;
     }
-    __syncwarp();
+    g.sync();
 }
 
 // ------------------------------------------------------------------ phase 7-8: factor and solve
 // A = L^T L with L lower triangular in the tree pattern (no fill-in), eliminating DoFs leaves
 // first, in float-float.  Row k of the packed storage holds (k, ancestor at depth j) at
-// row + j; after the factorisation the diagonal slot holds 1 / L_kk.
-__device__ bool phase_factor_solve(const Tables& T, float* ws, int lane) {
+// row + j; after the factorisation the diagonal slot holds 1 / L_kk.  The right-hand side is
+// carried as one more column, so L^T y = rhs is solved during the elimination; L qdd = y
+// follows root first, the nodes of a level in parallel.
+template <int WPE>
+__device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
     df* A = reinterpret_cast<df*>(ws + H.w_A);
     const float* rhs = ws + H.w_rhs;
     df* Y = reinterpret_cast<df*>(ws + H.w_y);
+    const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
     bool ok = true;
-    for (int t = lane; t < H.n_packed; t += 32) A[t] = df_norm(A[t].hi, A[t].lo);
-    for (int d = lane; d < H.n; d += 32) Y[d] = df_make(rhs[d]);
-    __syncwarp();
+    SUB_T0();
+    for (int d = g.lane; d < H.n; d += g.N) Y[d] = df_add_f(fx_decode(racc[2 * d], racc[2 * d + 1]), rhs[d]);
+    g.sync();
     for (int l = H.n_dlevels - 1; l >= 0; --l) {
         const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
-        for (int i = i0 + lane; i < i1; i += 32) {
+        // pivots of this level (1 / L_kk into the diagonal slots)
+        for (int i = i0 + g.lane; i < i1; i += g.N) {
             const DofRec& D = T.dof[T.dorder[i]];
             df akk = A[D.row + D.depth];
             if (!(akk.hi > 0.f)) { ok = false; akk = df_make(1.f); }
-            const df inv = df_recip(df_sqrt(akk));
-            A[D.row + D.depth] = inv;
-            for (int j = 0; j < D.depth; ++j) A[D.row + j] = df_mul(A[D.row + j], inv);
+            A[D.row + D.depth] = df_rsqrt(akk);
         }
-        __syncwarp();
+        g.sync();
+        SUB_MARK(11);
+        // scale rows and rhs of the level's nodes: L_kj = A_kj / L_kk, y_k = b_k / L_kk
         for (int i = i0; i < i1; ++i) {
-            const DofRec& D = T.dof[T.dorder[i]];
+            const int k = T.dorder[i];
+            const DofRec& D = T.dof[k];
+            const df inv = A[D.row + D.depth];
+            for (int j = g.lane; j <= D.depth; j += g.N) {
+                if (j < D.depth) A[D.row + j] = df_mul(A[D.row + j], inv);
+                else Y[k] = df_mul(Y[k], inv);
+            }
+        }
+        g.sync();
+        SUB_MARK(12);
+        // eliminate node by node: A_ab -= L_ka L_kb for ancestors b <= a of k (four independent
+        // updates per lane per iteration, loads first), then y_a -= L_ka y_k
+        for (int i = i0; i < i1; ++i) {
+            const int k = T.dorder[i];
+            const DofRec& D = T.dof[k];
             const int np = D.depth * (D.depth + 1) / 2;
-            for (int p = lane; p < np; p += 32) {
-                const int tv = T.tri[p];
-                const int ja = tv & 0xff, jb = tv >> 8;          // jb <= ja < depth
-                const int a = T.anc[D.row + ja];
-                df* t = &A[T.dof[a].row + jb];
-                *t = df_fms(*t, A[D.row + ja], A[D.row + jb]);
+            const df* Lk = A + D.row;
+            for (int p0 = g.lane; p0 < np; p0 += 4 * g.N) {
+                df* tg[4];
+                df av[4], xv[4], yv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int p = p0 + g.N * u;
+                    const int tv = T.tri[p < np ? p : 0];
+                    const int ja = tv & 0xff, jb = tv >> 8;      // jb <= ja < depth
+                    tg[u] = &A[T.rowanc[D.row + ja] + jb];
+                    xv[u] = Lk[ja];
+                    yv[u] = Lk[jb];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) av[u] = *tg[u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (p0 + g.N * u < np) *tg[u] = df_fms(av[u], xv[u], yv[u]);
             }
-            __syncwarp();
-        }
-    }
-    // L^T y = rhs, leaves first
-    for (int l = H.n_dlevels - 1; l >= 0; --l) {
-        const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
-        for (int i = i0 + lane; i < i1; i += 32) {
-            const int k = T.dorder[i];
-            const DofRec& D = T.dof[k];
-            Y[k] = df_mul(Y[k], A[D.row + D.depth]);
-        }
-        __syncwarp();
-        for (int i = i0; i < i1; ++i) {
-            const int k = T.dorder[i];
-            const DofRec& D = T.dof[k];
             const df yk = Y[k];
-            for (int j = lane; j < D.depth; j += 32) {
+            for (int j = g.lane; j < D.depth; j += g.N) {
                 df* t = &Y[T.anc[D.row + j]];
-                *t = df_fms(*t, A[D.row + j], yk);
+                *t = df_fms(*t, Lk[j], yk);
             }
-            __syncwarp();
+            g.sync();
         }
+        SUB_MARK(13);
     }
-    // L x = y, root first (x overwrites y)
+    // L x = y, root first (x overwrites y).  The nodes of a level are dealt round-robin to the
+    // group's warps; inside a warp each node gets a group of lanes that reduces its dot product
+    // over the ancestors with shuffles.
     for (int l = 0; l < H.n_dlevels; ++l) {
         const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
-        for (int i = i0 + lane; i < i1; i += 32) {
-            const int k = T.dorder[i];
+        const int nkw = (i1 - i0 - g.wi + WPE - 1) / WPE;   // nodes handled by this warp
+        for (int c0 = 0; c0 < nkw; c0 += 32) {
+            const int nk = min(nkw - c0, 32);
+            int gs = 32;
+            while (gs > 1 && gs * nk > 32) gs >>= 1;          // lanes per node
+            const int grp = g.wl / gs, li = g.wl % gs;
+            const bool act = grp < nk;
+            const int k = T.dorder[i0 + g.wi + WPE * (c0 + (act ? grp : 0))];
             const DofRec& D = T.dof[k];
-            df s = Y[k];
-            for (int j = 0; j < D.depth; ++j) s = df_fms(s, A[D.row + j], Y[T.anc[D.row + j]]);
-            Y[k] = df_mul(s, A[D.row + D.depth]);
+            df part = df_make(0.f);
+            if (act)
+                for (int j = li; j < D.depth; j += gs) part = df_add(part, df_mul(A[D.row + j], Y[T.anc[D.row + j]]));
+            for (int o = gs >> 1; o > 0; o >>= 1) {
+                const df w = {__shfl_xor_sync(0xffffffffu, part.hi, o), __shfl_xor_sync(0xffffffffu, part.lo, o)};
+                part = df_add(part, w);
+            }
+            if (act && li == 0) Y[k] = df_mul(df_add(Y[k], df_neg(part)), A[D.row + D.depth]);
         }
-        __syncwarp();
+        g.sync();
     }
-    return __all_sync(0xffffffffu, ok);
+    SUB_MARK(14);
+    return g.all(ok);
 }
 
 // ------------------------------------------------------------------ one substep
-// With MSIM_PHASE_TIMERS defined (profiling builds only), lane 0 of every warp adds the cycles
-// spent in each phase to timers[0..7].
+// With MSIM_PHASE_TIMERS defined (profiling builds only), lane 0 of every group adds the
+// cycles spent in each phase to timers[0..7].
 #ifdef MSIM_PHASE_TIMERS
-#define PHASE_MARK(i)                                                               \
-    do {                                                                            \
-        const long long t_ = clock64();                                             \
-        if (lane == 0 && timers) atomicAdd(&timers[(i)], (unsigned long long)(t_ - t0_)); \
-        t0_ = clock64();                                                            \
+#define PHASE_MARK(i)                                                                   \
+    do {                                                                                \
+        const long long t_ = clock64();                                                 \
+        if (g.lane == 0 && timers) atomicAdd(&timers[(i)], (unsigned long long)(t_ - t0_)); \
+        t0_ = clock64();                                                                \
     } while (0)
 #else
 #define PHASE_MARK(i) \
@@ -677,8 +835,8 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, int lane) {
     } while (0)
 #endif
 
-template <bool EVAL>
-__device__ uint32_t substep(const Tables& T, float* ws, int lane, float dt, const float* exc, float* act,
+template <bool EVAL, int WPE>
+__device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc, float* act,
                             float* force_out, const EvalPtrs* ev, unsigned long long* timers) {
     const ImgHeader& H = *T.H;
 #ifdef MSIM_PHASE_TIMERS
@@ -686,78 +844,95 @@ __device__ uint32_t substep(const Tables& T, float* ws, int lane, float dt, cons
 #else
     (void)timers;
 #endif
-    phase_kinematics(T, ws, lane);
+    phase_kinematics(T, ws, g);
     PHASE_MARK(0);
-    phase_subtree(T, ws, lane);
+    phase_subtree(T, ws, g);
     PHASE_MARK(1);
-    phase_crba(T, ws, lane);
+    {   // fixed-point accumulators: damping sums in the A storage (the bias accelerations it held
+        // are no longer needed), rhs sums beside it
+        int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);
+        for (int t = g.lane; t < 2 * H.n_packed; t += g.N) Ai[t] = 0;
+        int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
+        for (int t = g.lane; t < 2 * H.n; t += g.N) racc[t] = 0;
+    }
+    if (EVAL) {
+        for (int d = g.lane; d < H.n; d += g.N)
+            if (ev->bias) ev->bias[d] = -ws[H.w_rhs + d];
+    }
+    g.sync();
+    const bool bad = phase_muscles<EVAL>(T, ws, g, dt, exc, act, force_out, ev);
+    PHASE_MARK(3);
+    phase_contact<EVAL>(T, ws, g, dt, ev);
+    PHASE_MARK(4);
+    phase_crba(T, ws, g, EVAL ? ev->M : nullptr);
     PHASE_MARK(2);
+    phase_limits<EVAL>(T, ws, g, dt, ev);
+    PHASE_MARK(5);
     const df* A = reinterpret_cast<const df*>(ws + H.w_A);
     if (EVAL) {
-        for (int t = lane; t < H.n_packed; t += 32)
-            if (ev->M) ev->M[t] = A[t].hi + A[t].lo;
-        for (int d = lane; d < H.n; d += 32)
-            if (ev->bias) ev->bias[d] = -ws[H.w_rhs + d];
-        __syncwarp();
-    }
-    phase_muscles<EVAL>(T, ws, lane, dt, exc, act, force_out, ev);
-    PHASE_MARK(3);
-    phase_contact<EVAL>(T, ws, lane, dt, ev);
-    PHASE_MARK(4);
-    phase_limits<EVAL>(T, ws, lane, dt, ev);
-    PHASE_MARK(5);
-    if (EVAL) {
-        for (int t = lane; t < H.n_packed; t += 32)
+        for (int t = g.lane; t < H.n_packed; t += g.N)
             if (ev->A) ev->A[t] = A[t].hi + A[t].lo;
-        for (int d = lane; d < H.n; d += 32)
-            if (ev->rhs) ev->rhs[d] = ws[H.w_rhs + d];
-        __syncwarp();
+        const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
+        for (int d = g.lane; d < H.n; d += g.N) {
+            const df r = df_add_f(fx_decode(racc[2 * d], racc[2 * d + 1]), ws[H.w_rhs + d]);
+            if (ev->rhs) ev->rhs[d] = r.hi + r.lo;
+        }
+        g.sync();
     }
-    const bool ok = phase_factor_solve(T, ws, lane);
+    const bool ok = phase_factor_solve(T, ws, g);
     PHASE_MARK(6);
-    uint32_t st = ok ? 0u : kEnvNotSpd;
+    uint32_t st = (ok ? 0u : kEnvNotSpd) | (bad ? kEnvNonFinite : 0u);
     const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
     if (!EVAL) {
         float* q = ws + H.w_q;
         float* qd = ws + H.w_qd;
-        for (int d = lane; d < H.n; d += 32) {
+        for (int d = g.lane; d < H.n; d += g.N) {
             const float v = qd[d] + dt * (Y[d].hi + Y[d].lo);
             qd[d] = v;
             q[d] += dt * v;
         }
-        __syncwarp();
+        g.sync();
     } else if (ev->qdd) {
-        for (int d = lane; d < H.n; d += 32) ev->qdd[d] = Y[d].hi + Y[d].lo;
+        for (int d = g.lane; d < H.n; d += g.N) ev->qdd[d] = Y[d].hi + Y[d].lo;
     }
     return st;
 }
 
 // ------------------------------------------------------------------ kernels
-__device__ __forceinline__ void load_row(float* dst, const float* src, int count, int lane) {
-    for (int i = lane; i < count; i += 32) dst[i] = src[i];
-}
-
-template <bool EVAL>
+template <bool EVAL, int WPE>
 __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     uint8_t* img = smem + 16;
     if (!stage_image(img, a.img, a.staged_bytes, bar, a.gflags)) return;
+#ifdef MSIM_PHASE_TIMERS
+    if (threadIdx.x == 0 && blockIdx.x == 0) g_timers = a.timers;
+    __syncthreads();
+#endif
     Tables T = make_tables(img);
     if (!a.points_in_smem) T.pt = reinterpret_cast<const PointRec*>(a.img + T.H->o_point);
     const ImgHeader& H = *T.H;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int slot = warp / WPE;
+    Grp<WPE> g;
+    g.wl = threadIdx.x & 31;
+    g.wi = warp % WPE;
+    g.lane = g.wi * 32 + g.wl;
+    g.bar = 1 + slot;
+    const int ws_stride = ws_floats(H, WPE);
     float* ws_all = reinterpret_cast<float*>(img + ((a.staged_bytes + 127) & ~127));
-    float* ws = ws_all + (size_t)warp * H.w_floats;
+    float* ws = ws_all + (size_t)slot * ws_stride;
     const int n_envs = a.env_end - a.env_begin;
     const int n_groups = (n_envs + a.envs_per_block - 1) / a.envs_per_block;
-    for (int g = blockIdx.x; g < n_groups; g += gridDim.x) {
-        const int e = a.env_begin + g * a.envs_per_block + warp;
+    for (int gi = blockIdx.x; gi < n_groups; gi += gridDim.x) {
+        const int e = a.env_begin + gi * a.envs_per_block + slot;
         if (e >= a.env_end) continue;
         const size_t rn = (size_t)e * a.pitch_n, rm = (size_t)e * a.pitch_m;
-        load_row(ws + H.w_q, a.q + rn, H.n, lane);
-        load_row(ws + H.w_qd, a.qd + rn, H.n, lane);
-        __syncwarp();
+        for (int i = g.lane; i < H.n; i += g.N) {
+            ws[H.w_q + i] = a.q[rn + i];
+            ws[H.w_qd + i] = a.qd[rn + i];
+        }
+        g.sync();
         uint32_t st = 0;
         if (EVAL) {
             EvalPtrs ev = a.ev;
@@ -769,43 +944,43 @@ __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
             ev.tau_l = off(ev.tau_l, a.pitch_n); ev.bias = off(ev.bias, a.pitch_n); ev.rhs = off(ev.rhs, a.pitch_n);
             ev.qdd = off(ev.qdd, a.pitch_n);
             ev.M = off(ev.M, ev.packed_pitch); ev.A = off(ev.A, ev.packed_pitch);
-            for (int d = lane; d < H.n; d += 32) {
+            for (int d = g.lane; d < H.n; d += g.N) {
                 if (ev.tau_m) ev.tau_m[d] = 0.f;
                 if (ev.tau_c) ev.tau_c[d] = 0.f;
                 if (ev.tau_l) ev.tau_l[d] = 0.f;
             }
-            __syncwarp();
-            st |= substep<true>(T, ws, lane, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, a.timers);
+            g.sync();
+            st |= substep<true>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, a.timers);
         } else {
             for (int s = 0; s < a.n_sub; ++s) {
                 const bool last = (s == a.n_sub - 1);
-                st |= substep<false>(T, ws, lane, a.dt, a.exc + rm, a.act + rm,
+                st |= substep<false>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
                                      (last && a.force_out) ? a.force_out + rm : nullptr, nullptr, a.timers);
             }
             bool bad = false;
             const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
-            for (int d = lane; d < H.n; d += 32) {
+            for (int d = g.lane; d < H.n; d += g.N) {
                 const float v0 = ws[H.w_q + d], v1 = ws[H.w_qd + d];
                 bad |= !(isfinite(v0) && isfinite(v1));
                 a.q[rn + d] = v0;
                 a.qd[rn + d] = v1;
                 if (a.qdd_out) a.qdd_out[rn + d] = Y[d].hi + Y[d].lo;
             }
-            for (int k = lane; k < H.m; k += 32) bad |= !isfinite(a.act[rm + k]);
-            if (__any_sync(0xffffffffu, bad)) st |= kEnvNonFinite;
+            for (int k = g.lane; k < H.m; k += g.N) bad |= !isfinite(a.act[rm + k]);
+            if (g.any(bad)) st |= kEnvNonFinite;
         }
-        if (st && lane == 0) {
+        if (st && g.lane == 0) {
             atomicOr(&a.env_status[e], st);
             atomicOr(a.gflags, st);
         }
-        __syncwarp();
+        g.sync();
     }
 }
 
 __global__ void k_set_l0(uint8_t* img, const float* L, int m) {
     const ImgHeader* H = reinterpret_cast<const ImgHeader*>(img);
     MuscleRec* mus = reinterpret_cast<MuscleRec*>(img + H->o_muscle);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) mus[k].L0 = L[k];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) mus[r].L0 = L[mus[r].orig];
 }
 
 __global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, const float* q0, const float* qd0,
@@ -825,30 +1000,44 @@ __global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, const
 
 }  // namespace
 
-size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem) {
+size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem, int wpe) {
     const size_t staged = points_in_smem ? (size_t)h.total_bytes : (size_t)h.o_point;
-    return 16 + ((staged + 127) & ~(size_t)127) + (size_t)epb * h.w_floats * sizeof(float);
+    return 16 + ((staged + 127) & ~(size_t)127) + (size_t)epb * ws_floats(h, wpe) * sizeof(float);
 }
 
-int step_blocks_per_sm(int threads, size_t smem) {
+int step_blocks_per_sm(int threads, size_t smem, int wpe) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false>, threads, smem) != cudaSuccess) return 1;
-    return n;
+    cudaError_t e;
+    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, 4>, threads, smem);
+    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, 2>, threads, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, 1>, threads, smem);
+    return e == cudaSuccess ? n : 1;
 }
 
 cudaError_t set_step_smem_limit(size_t bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const int b = (int)bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_step<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
 }
 
 cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
-    k_step<false><<<grid, 32 * a.envs_per_block, smem, s>>>(a);
+    const int threads = 32 * a.wpe * a.envs_per_block;
+    if (a.wpe == 4) k_step<false, 4><<<grid, threads, smem, s>>>(a);
+    else if (a.wpe == 2) k_step<false, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<false, 1><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
-    k_step<true><<<grid, 32 * a.envs_per_block, smem, s>>>(a);
+    const int threads = 32 * a.wpe * a.envs_per_block;
+    if (a.wpe == 4) k_step<true, 4><<<grid, threads, smem, s>>>(a);
+    else if (a.wpe == 2) k_step<true, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<true, 1><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -49,7 +49,8 @@ class Dims(C.Structure):
                 ("env_begin", C.c_int32 * 9), ("n_dofs", C.c_int32 * 8), ("n_muscles", C.c_int32 * 8),
                 ("n_bodies", C.c_int32 * 8), ("nnz", C.c_int32 * 8), ("n_packed", C.c_int32 * 8),
                 ("envs_per_block", C.c_int32 * 8), ("image_bytes", C.c_int32 * 8),
-                ("workspace_bytes_per_env", C.c_int32 * 8), ("points_in_smem", C.c_int32 * 8)]
+                ("workspace_bytes_per_env", C.c_int32 * 8), ("points_in_smem", C.c_int32 * 8),
+                ("warps_per_env", C.c_int32 * 8)]
 
 
 _EVAL_FIELDS = ("L", "lm", "vm", "force", "act_next", "R", "tau_m", "tau_c", "tau_l", "bias", "rhs", "qdd", "M", "A")
@@ -86,7 +87,7 @@ def load_library(path=LIB_PATH):
     lib.msim_clear_status.argtypes = [vp, vp]
     lib.msim_eval.argtypes = [vp, vp, vp, vp, vp, C.POINTER(EvalOut), vp]
     lib.msim_get_layout.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
-    lib.msim_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+    lib.msim_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     lib.msim_last_error.argtypes = [vp]
     lib.msim_last_error.restype = C.c_char_p
     lib.msim_version.restype = C.c_int32
@@ -240,8 +241,9 @@ class Sim:
     def clear_status(self, stream=None):
         self._check(self.lib.msim_clear_status(self.h, _stream_ptr(stream)))
 
-    def set_launch(self, model, envs_per_block, stage_points=-1):
-        self._check(self.lib.msim_set_launch(self.h, int(model), int(envs_per_block), int(stage_points)))
+    def set_launch(self, model, envs_per_block=0, stage_points=-1, warps_per_env=0):
+        self._check(self.lib.msim_set_launch(self.h, int(model), int(envs_per_block), int(stage_points),
+                                             int(warps_per_env)))
         self._check(self.lib.msim_get_dims(self.h, C.byref(self.dims)))
 
     def eval(self, q, qd, act, exc, stream=None):
