@@ -96,6 +96,19 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic(envs):
+    """DRAM bytes per step launch from the committed ncu summary, or None if the kernel sources
+    changed since those counters were taken."""
+    try:
+        from paper_2603_29332_b300 import build
+        d = json.load(open(os.path.join(ROOT, "profiles", "k_step_traffic.json")))
+        if d.get("source_digest") != build._digest():
+            return None
+        return d["dram_bytes_per_env_per_launch"] * envs
+    except Exception:
+        return None
+
+
 def cpu_baseline(model, envs=512, substeps=20):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
     sys.path.insert(0, ROOT)
@@ -208,7 +221,8 @@ def run_gpu(args, rank, world, local_rank):
     clocks = clk.summary()
     peak_max = fp32_peak_tflops(2032.0)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
-            "traffic": None, "kernel": "k_step (one launch per bench step)",
+            "traffic": measured_traffic(E), "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "kernel": "k_step (one launch per bench step)",
             "flops_per_env_substep": fl,
             "peak_note": "FP32 FMA peak 148 SMs x 128 lanes x 2 x 2032 MHz (no FP32 figure in MEASURED_PEAKS.json)"}
     if clocks:
