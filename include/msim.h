@@ -168,6 +168,19 @@ MSIM_API msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_
 MSIM_API msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_per_block, int32_t stage_points,
                                      int32_t warps_per_env);
 
+/* msim_gemm_bf16 -- the tensor-core building block of the learned parts (surrogate, policy):
+ *   C = act(A B^T + bias), A [M][K] BF16 with row pitch lda, B [N][K] BF16 with row pitch ldb
+ *   (both K-contiguous; pitches multiples of 8 elements, bases 16-byte aligned), accumulated in
+ *   FP32 on the tcgen05 tensor cores; C row-major with pitch ldc, FP32 (c_bf16 = 0) or BF16
+ *   (c_bf16 = 1); bias optional [N] FP32; act 0 = none, 1 = SiLU, 2 = sigmoid; Z optional BF16
+ *   copy of the pre-activation (pitch ldz).  err (optional device uint32) gets bit 0 if a bounded
+ *   wait inside the kernel expired.  Device pointers; asynchronous on `stream`.
+ *   MSIM_ERR_ARG on bad sizes or alignment, MSIM_ERR_UNSUPPORTED if the driver lacks tensor maps.
+ *   The paper has no GEMM of its own; its networks are 3-layer MLPs (Methods). */
+MSIM_API msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ldb, const float* bias, void* C,
+                                    int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t c_bf16, int32_t act, void* Z,
+                                    int32_t ldz, uint32_t* err, msim_stream_t stream);
+
 /* msim_last_error -- text of the last failure on this handle (or of the last failed create
  *   when h is NULL).  Owned by the library, valid until the next call. */
 MSIM_API const char* msim_last_error(msim_handle h);

@@ -1,0 +1,292 @@
+// gemm_tc.cu -- BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   C[m][n] = act( sum_k A[m][k] B[n][k] + bias[n] )      (both operands K-contiguous)
+//
+// One 128 x BN output tile per block, 192 threads in three roles:
+//   warp 0   TMA producer: 2-D tiled bulk copies (128-byte swizzle) of A and B K-slices into a
+//            ring of STAGES shared-memory slots, completion counted on the slot's `full` mbarrier;
+//   warp 1   allocates BN TMEM columns for the FP32 accumulator; one elected thread issues
+//            tcgen05.mma (kind::f16, M = 128, N = BN, K = 16 per instruction, 4 per 64-wide slice)
+//            and tcgen05.commit to release each slot (`empty`) and, at the end, the accumulator;
+//   warps 2-5 epilogue: tcgen05.ld of their 32 TMEM lanes, bias, activation, stores (FP32 or BF16,
+//            optionally also the pre-activation in BF16).
+// Every wait on an mbarrier is bounded; on expiry the block records an error code, skips its
+// stores and still frees its TMEM.  Out-of-range rows / columns of A and B read as zero (TMA
+// fill), so M, N and K need not be multiples of the tile; only the row pitches must be multiples
+// of 8 elements (16 bytes) and the base addresses 16-byte aligned.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gemm_tc.h"
+
+namespace msim {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;                 // 64 BF16 = 128 bytes = one swizzle row
+constexpr int kStages = 3;
+constexpr long long kSpinLimit = 1LL << 24;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+// bounded parity wait; false if the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    const uint32_t a = saddr(b);
+    for (long long i = 0; i < kSpinLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+// instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, both K-major, M x N
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float act_fn(float x, int act) {
+    if (act == 1) return x / (1.f + __expf(-x));     // SiLU
+    if (act == 2) return 1.f / (1.f + __expf(-x));   // sigmoid
+    return x;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kStages * kABytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    int* failed = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    const int ktiles = (p.K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        for (int kt = 0; kt < ktiles; ++kt) {
+            const int s = kt % kStages;
+            const uint32_t ph = (kt / kStages) & 1;
+            if (kt >= kStages && !mbar_wait(&empty[s], ph ^ 1)) {
+                atomicExch(failed, 1);
+                break;
+            }
+            mbar_expect_tx(&full[s], kABytes + kBBytes);
+            tma_load_2d(sA + s * kABytes, &tmA, kt * kBK, m0, &full[s]);
+            tma_load_2d(sB + s * kBBytes, &tmB, kt * kBK, n0, &full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = instr_desc(kBM, BN);
+        for (int kt = 0; kt < ktiles; ++kt) {
+            const int s = kt % kStages;
+            const uint32_t ph = (kt / kStages) & 1;
+            if (!mbar_wait(&full[s], ph)) {
+                atomicExch(failed, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = saddr(sA + s * kABytes), b0 = saddr(sB + s * kBBytes);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint64_t ad = smem_desc(a0 + kk * 32), bd = smem_desc(b0 + kk * 32);
+                const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             saddr(&empty[s]))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(done))
+                     : "memory");
+    } else if (warp >= 2) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. output rows of that quarter
+        const bool ok = mbar_wait(done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int quarter = warp & 3;
+        const int row = m0 + quarter * 32 + lane;
+        const bool store = ok && (*reinterpret_cast<volatile int*>(failed) == 0);
+        if (!ok) atomicExch(failed, 1);
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (!store || row >= p.M) continue;
+            const int cn = n0 + c;
+            float v[16], z[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                z[j] = __uint_as_float(r[j]) + ((p.bias && cn + j < p.N) ? p.bias[cn + j] : 0.f);
+                v[j] = act_fn(z[j], p.act);
+            }
+            const bool full_chunk = (cn + 16 <= p.N) && p.vec_ok;
+            if (p.c_bf16) {
+                __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(p.C) + (size_t)row * p.ldc + cn;
+                if (full_chunk) {
+                    uint4 w[2];
+                    uint32_t* wp = reinterpret_cast<uint32_t*>(w);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        wp[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    reinterpret_cast<uint4*>(C)[0] = w[0];
+                    reinterpret_cast<uint4*>(C)[1] = w[1];
+                } else {
+                    for (int j = 0; j < 16 && cn + j < p.N; ++j) C[j] = __float2bfloat16_rn(v[j]);
+                }
+            } else {
+                float* C = reinterpret_cast<float*>(p.C) + (size_t)row * p.ldc + cn;
+                if (full_chunk) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        reinterpret_cast<float4*>(C)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                } else {
+                    for (int j = 0; j < 16 && cn + j < p.N; ++j) C[j] = v[j];
+                }
+            }
+            if (p.Z) {
+                __nv_bfloat16* Zp = reinterpret_cast<__nv_bfloat16*>(p.Z) + (size_t)row * p.ldz + cn;
+                for (int j = 0; j < 16 && cn + j < p.N; ++j) Zp[j] = __float2bfloat16_rn(z[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && *failed && p.err) atomicOr(p.err, 1u);
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encode() {
+    if (g_encode) return true;
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return true;
+}
+
+// 2-D tensor map over a row-major [rows][ld] BF16 matrix with `cols` valid columns; box of
+// 64 columns x box_rows rows, 128-byte swizzle, zero fill out of range.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+constexpr size_t gemm_smem() {
+    return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
+}
+
+template <int BN>
+cudaError_t launch_bn(const GemmArgs& a, const void* A, int lda, const void* B, int ldb, cudaStream_t s) {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, a.M, a.K, lda, kBM) || !make_map(&mb, B, a.N, a.K, ldb, BN)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<BN>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((a.N + BN - 1) / BN, (a.M + kBM - 1) / kBM);
+    k_gemm<BN><<<grid, 192, gemm_smem<BN>(), s>>>(ma, mb, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, GemmArgs args, cudaStream_t s) {
+    if (!get_encode()) return cudaErrorNotSupported;
+    if (args.M <= 0 || args.N <= 0 || args.K <= 0) return cudaErrorInvalidValue;
+    if ((lda % 8) || (ldb % 8) || (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+        return cudaErrorInvalidValue;
+    const int vec_align = args.c_bf16 ? 8 : 4;
+    args.vec_ok = (args.ldc % vec_align == 0) && ((reinterpret_cast<uintptr_t>(args.C) & 15) == 0);
+    if (args.N > 128) return launch_bn<256>(args, A, lda, B, ldb, s);
+    return launch_bn<128>(args, A, lda, B, ldb, s);
+}
+
+}  // namespace msim

@@ -1,0 +1,25 @@
+// gemm_tc.h -- BF16 tensor-core GEMM (tcgen05) used by the geometry surrogate and the policy MLP.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace msim {
+
+struct GemmArgs {
+    int M, N, K;          // C is M x N, reduction over K
+    void* C;              // output, row-major, pitch ldc elements
+    int ldc;
+    int c_bf16;           // 1: BF16 output, 0: FP32 output
+    const float* bias;    // optional, [N]
+    int act;              // 0: none, 1: SiLU, 2: sigmoid
+    void* Z;              // optional BF16 pre-activation output (pitch ldz)
+    int ldz;
+    uint32_t* err;        // optional device word: bit 0 set if a bounded wait expired
+    int vec_ok;           // set by gemm_bf16_tc
+};
+
+// C = act(A B^T + bias): A [M][K] BF16 (pitch lda), B [N][K] BF16 (pitch ldb), pitches multiples
+// of 8, bases 16-byte aligned.  Asynchronous on stream s.
+cudaError_t gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, GemmArgs args, cudaStream_t s);
+
+}  // namespace msim

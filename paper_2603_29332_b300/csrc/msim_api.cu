@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/msim.h"
+#include "gemm_tc.h"
 #include "image.h"
 #include "kernels.h"
 
@@ -794,6 +795,25 @@ msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_parent, i
     cp(muscle_dof_ptr, M.mus_ptr);
     cp(muscle_dof, M.mus_dof);
     return MSIM_OK;
+}
+
+msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ldb, const float* bias, void* C,
+                           int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t c_bf16, int32_t act, void* Z,
+                           int32_t ldz, uint32_t* err, msim_stream_t stream) {
+    if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || lda < K || ldb < K || ldc < N || act < 0 || act > 2 ||
+        (Z && ldz < N))
+        return arg_fail(nullptr, "msim_gemm_bf16: bad argument");
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc; g.c_bf16 = c_bf16 ? 1 : 0; g.bias = bias; g.act = act;
+    g.Z = Z; g.ldz = ldz; g.err = err;
+    const cudaError_t e = gemm_bf16_tc(A, lda, B, ldb, g, (cudaStream_t)stream);
+    if (e == cudaErrorNotSupported) {
+        g_create_error = "msim_gemm_bf16: tensor-map encoding unavailable";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    if (e == cudaErrorInvalidValue) return arg_fail(nullptr, "msim_gemm_bf16: pitch or alignment not supported");
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_gemm_bf16");
 }
 
 #ifdef MSIM_PHASE_TIMERS

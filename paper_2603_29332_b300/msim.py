@@ -62,7 +62,7 @@ class EvalOut(C.Structure):
 
 EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_step", "msim_step_host",
            "msim_get_state", "msim_get_status", "msim_clear_status", "msim_eval", "msim_get_layout",
-           "msim_set_launch", "msim_last_error", "msim_version")
+           "msim_set_launch", "msim_gemm_bf16", "msim_last_error", "msim_version")
 
 _lib = None
 
@@ -88,6 +88,8 @@ def load_library(path=LIB_PATH):
     lib.msim_eval.argtypes = [vp, vp, vp, vp, vp, C.POINTER(EvalOut), vp]
     lib.msim_get_layout.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
     lib.msim_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    lib.msim_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                   C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
     lib.msim_last_error.argtypes = [vp]
     lib.msim_last_error.restype = C.c_char_p
     lib.msim_version.restype = C.c_int32
@@ -268,6 +270,24 @@ class Sim:
                                                               "muscle_dof_ptr", "muscle_dof")]))
         a["muscle_dof"] = a["muscle_dof"][:nnz]
         return a
+
+
+def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=None):
+    """C = act(A B^T + bias) on the tensor cores (msim_gemm_bf16).  A [M, K], B [N, K]: BF16 CUDA
+    tensors with unit column stride and row pitches multiple of 8."""
+    import torch
+    lib = load_library()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), device=A.device, dtype=torch.bfloat16 if out_bf16 else torch.float32)
+    st = lib.msim_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                            None if bias is None else bias.data_ptr(), C.data_ptr(), C.stride(0), M, N, K,
+                            1 if out_bf16 else 0, act, None if Z is None else Z.data_ptr(),
+                            0 if Z is None else Z.stride(0), None if err is None else err.data_ptr(),
+                            _stream_ptr(stream))
+    if st != MSIM_OK:
+        raise MsimError(st, lib.msim_last_error(None).decode())
+    return C
 
 
 def unpack_packed(packed, layout):

@@ -1,0 +1,68 @@
+"""The tcgen05 BF16 GEMM (msim_gemm_bf16) against a plain PyTorch FP32 reference of the same op."""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2603_29332_b300 import msim
+
+pytestmark = pytest.mark.gpu
+
+
+def _ref(A, B, bias, act):
+    z = A.float() @ B.float().T
+    if bias is not None:
+        z = z + bias
+    if act == 1:
+        return z * torch.sigmoid(z), z
+    if act == 2:
+        return torch.sigmoid(z), z
+    return z, z
+
+
+@pytest.mark.parametrize("M,N,K,act,bias", [
+    (128, 128, 64, 0, False),      # one tile, one K slice
+    (300, 200, 90, 1, True),       # ragged rows, columns and K (TMA zero fill)
+    (64, 48, 16, 2, True),         # smaller than a tile
+    (1000, 512, 512, 1, True),     # hidden layer shape
+    (4096, 2800, 512, 0, True),    # surrogate output layer (256-wide tiles)
+    (257, 1024, 2184, 1, True),    # long K (policy input layer)
+])
+def test_gemm_matches_fp32_reference(M, N, K, act, bias):
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
+    Kp = (K + 7) // 8 * 8
+    A = torch.zeros((M, Kp), device="cuda", dtype=torch.bfloat16)
+    B = torch.zeros((N, Kp), device="cuda", dtype=torch.bfloat16)
+    A[:, :K] = (torch.randn((M, K), device="cuda", generator=g)).bfloat16()
+    B[:, :K] = (torch.randn((N, K), device="cuda", generator=g) / K ** 0.5).bfloat16()
+    b = torch.randn(N, device="cuda", generator=g) if bias else None
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = msim.gemm_bf16(A[:, :K], B[:, :K], b, act=act, err=err)
+    torch.cuda.synchronize()
+    ref, _ = _ref(A[:, :K], B[:, :K], b, act)
+    assert err.item() == 0
+    # FP32 accumulation of exact BF16 products: error ~ K * 2^-24 * sum |a b|
+    scale = (A[:, :K].float().abs() @ B[:, :K].float().abs().T) + 1.0
+    assert ((C - ref).abs() / scale).max().item() < 1e-5
+
+
+def test_gemm_bf16_output_and_preactivation():
+    M, N, K = 256, 384, 160
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn((M, K), device="cuda", generator=g).bfloat16()
+    B = (torch.randn((N, K), device="cuda", generator=g) / K ** 0.5).bfloat16()
+    b = torch.randn(N, device="cuda", generator=g)
+    Z = torch.empty((M, N), device="cuda", dtype=torch.bfloat16)
+    C = msim.gemm_bf16(A, B, b, act=1, out_bf16=True, Z=Z)
+    torch.cuda.synchronize()
+    ref, zref = _ref(A, B, b, 1)
+    assert C.dtype == torch.bfloat16
+    assert (C.float() - ref).abs().max().item() <= 1e-2 * ref.abs().max().item()
+    assert (Z.float() - zref).abs().max().item() <= 1e-2 * zref.abs().max().item()
+
+
+def test_gemm_rejects_unaligned_pitch():
+    A = torch.zeros((16, 20), device="cuda", dtype=torch.bfloat16)   # pitch 20 is not a multiple of 8
+    B = torch.zeros((16, 20), device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(msim.MsimError) as ei:
+        msim.gemm_bf16(A, B)
+    assert ei.value.code == 1
