@@ -62,7 +62,7 @@ typedef struct {
     int32_t n_models;
     const msim_model_desc* models;  /* host array [n_models] */
     const int32_t* envs_per_model;  /* host array [n_models], each >= 0, total >= 1 */
-    int32_t geometry_mode;          /* 0 = exact via-point geometry */
+    int32_t geometry_mode;          /* 0 = exact via-point geometry, 1 = learned (msim_set_geometry_mode) */
     float dt;                       /* substep length [s], > 0 */
     uint64_t seed;                  /* reserved for stochastic parts; 0 is fine */
     int32_t device;                 /* CUDA device ordinal */
@@ -176,10 +176,103 @@ MSIM_API msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_
  *   copy of the pre-activation (pitch ldz).  err (optional device uint32) gets bit 0 if a bounded
  *   wait inside the kernel expired.  Device pointers; asynchronous on `stream`.
  *   MSIM_ERR_ARG on bad sizes or alignment, MSIM_ERR_UNSUPPORTED if the driver lacks tensor maps.
- *   The paper has no GEMM of its own; its networks are 3-layer MLPs (Methods). */
+ *   The paper has no GEMM of its own; its networks are 3-layer MLPs (Methods, "Training hyperparameters"). */
 MSIM_API msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ldb, const float* bias, void* C,
                                     int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t c_bf16, int32_t act, void* Z,
                                     int32_t ldz, uint32_t* err, msim_stream_t stream);
+
+/* ---- 3-layer MLP on the tensor cores (the surrogate's and the policy's network) ----------
+ * A network x -> silu(W1 x + b1) -> silu(W2 h1 + b2) -> out(W3 h2 + b3), out = identity or
+ * sigmoid (the paper's networks are 3-layer MLPs, Methods, "Training hyperparameters").  BF16 weights and activations,
+ * FP32 accumulation, FP32 master weights, gradients and Adam moments (Kingma & Ba 2015), all in
+ * one flat FP32 layout (msim_mlp_layout).  Device work is asynchronous on `stream` unless noted. */
+typedef struct msim_mlp_* msim_mlp;
+
+/* msim_mlp_create -- allocate a network (in >= 1, hidden a multiple of 8, out >= 1) with scratch
+ *   for batches up to max_batch; out_act 0 = identity, 2 = sigmoid; weights Kaiming-uniform
+ *   (bound sqrt(6 / fan_in), output layer scaled by out_scale) from a Philox-4x32-10 stream keyed
+ *   by seed, biases zero.  Synchronous.  *net owned by the library until msim_mlp_destroy. */
+MSIM_API msim_status msim_mlp_create(int32_t in, int32_t hidden, int32_t out, int32_t out_act, int32_t max_batch,
+                                     uint64_t seed, float out_scale, msim_mlp* net);
+MSIM_API msim_status msim_mlp_destroy(msim_mlp m);
+/* msim_mlp_layout -- element offsets of W1 [hidden][in_pitch], b1, W2 [hidden][hidden], b2,
+ *   W3 [out_pitch][hidden], b3 in the flat buffers, their total length, and the pitches. */
+MSIM_API msim_status msim_mlp_layout(msim_mlp m, int64_t offsets[6], int64_t* n_params, int32_t* in_pitch,
+                                     int32_t* out_pitch);
+/* msim_mlp_get / msim_mlp_set -- synchronous copy of a flat buffer to / from HOST memory:
+ *   which 0 = parameters, 1 = gradients, 2 = Adam first moments, 3 = Adam second moments; n must be
+ *   the n_params of msim_mlp_layout.  Setting parameters refreshes the BF16 copies; setting the
+ *   moments also sets the Adam step counter to `adam_step` (ignored otherwise). */
+MSIM_API msim_status msim_mlp_get(msim_mlp m, int32_t which, float* host, int64_t n);
+MSIM_API msim_status msim_mlp_set(msim_mlp m, int32_t which, const float* host, int64_t n, int32_t adam_step);
+/* msim_mlp_forward -- Y [B][ldy] FP32 = network(X), X [B][ldx] BF16 (device; ldx >= in_pitch,
+ *   a multiple of 8), 1 <= B <= max_batch. */
+MSIM_API msim_status msim_mlp_forward(msim_mlp m, const void* X, int32_t ldx, int32_t B, float* Y, int32_t ldy,
+                                      msim_stream_t stream);
+/* msim_mlp_backward -- gradients of mean((y - t)^2) over the batch and outputs into the gradient
+ *   buffer (forward included); T [B][ldt] FP32 device.  If loss is non-NULL the call synchronises
+ *   the stream and writes the loss there (host). */
+MSIM_API msim_status msim_mlp_backward(msim_mlp m, const void* X, int32_t ldx, const float* T, int32_t ldt, int32_t B,
+                                       float* loss, msim_stream_t stream);
+/* msim_mlp_adam -- one Adam step from the gradient buffer (bias-corrected, step counter + 1). */
+MSIM_API msim_status msim_mlp_adam(msim_mlp m, float lr, float beta1, float beta2, float eps, msim_stream_t stream);
+
+/* ---- learned muscle geometry (surrogate) ---------------------------------------------------
+ * The equation of motion (Methods, "Musculoskeletal dynamics") needs the muscle lengths (for l_m,
+ * v_m of Eq. 1) and the moment-arm matrix J_m(q) of the muscle paths.  The paper computes them
+ * from the paths; a learned map q -> (lengths, moment arms) is this library's option, with no
+ * counterpart in the paper, judged against the exact path it replaces.  Single-model handles
+ * only (MSIM_ERR_UNSUPPORTED otherwise).  Outputs of
+ * msim_geometry / msim_surrogate_predict are rows [L (m, caller's muscle order) | R (nnz, the
+ * sparse order of msim_get_layout's muscle_dof)], FP32, pitch ld_out >= m + nnz.
+ *
+ * msim_surrogate_train -- synchronous.  Draws n_samples configurations uniformly in the training
+ * box (the joint-limit box widened by 5 % of each range; +-pi for a DoF without limits), labels
+ * them with the exact geometry kernel, normalises every output by its mean and standard deviation,
+ * and trains a 3-layer MLP (n -> 512 -> 512 -> m + nnz, SiLU, BF16 tensor-core GEMMs with FP32
+ * accumulation) for `epochs` passes of n_samples / batch minibatches with Adam (beta 0.9, 0.999,
+ * eps 1e-8; learning rate lr with cosine decay to lr / 100).  Randomness from the create seed.
+ * Needs about n_samples * (4 (m + nnz) + 2 n) bytes of device memory while it runs (MSIM_ERR_OOM
+ * otherwise).  1 <= batch <= 65536, batch <= n_samples, epochs >= 1, lr > 0. */
+MSIM_API msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epochs, int32_t batch, float lr,
+                                          msim_stream_t stream);
+/* msim_set_geometry_mode -- 0 exact via-point geometry, 1 learned.  In mode 1 each substep runs
+ * the network on every environment's q, then the step kernel uses its outputs except for
+ * environments whose q is outside the training box, or that a failed check has flagged (these
+ * use the exact geometry).  Each substep, a Philox-4x32-10 draw keyed by the create seed selects a
+ * fraction check_frac (default 0.01) of the other environments for a check: they compute both and
+ * use the exact one; an error above tol (default 1e-3, i.e. 1 mm for lengths and moment arms)
+ * flags the environment until its msim_reset.  Mode 1 before msim_surrogate_train: MSIM_ERR_STATE. */
+MSIM_API msim_status msim_set_geometry_mode(msim_handle h, int32_t mode);
+/* msim_surrogate_set_check -- check fraction in [0, 1] and tolerance > 0 (metres). */
+MSIM_API msim_status msim_surrogate_set_check(msim_handle h, float check_frac, float tol);
+
+typedef struct {
+    uint64_t env_substeps;      /* environment-substeps stepped in mode 1 */
+    uint64_t learned;           /* ... of which used the network's geometry */
+    uint64_t out_of_box;        /* ... of which had q outside the training box */
+    uint64_t flagged;           /* ... of which were flagged by an earlier failed check */
+    uint64_t checked;           /* ... of which were checked against the exact geometry */
+    uint64_t check_failed;      /* ... of which exceeded the tolerance */
+    float max_check_error;      /* largest |network - exact| seen by a check (metres) */
+    float train_loss;           /* mean squared normalised error, last training epoch */
+    int32_t flagged_envs;       /* environments flagged now */
+    int32_t trained;
+} msim_surrogate_info;
+/* msim_surrogate_stats -- synchronises; counters since training or the last reset_counters. */
+MSIM_API msim_status msim_surrogate_stats(msim_handle h, msim_surrogate_info* out, int32_t reset_counters);
+/* msim_surrogate_network -- the trained network (borrowed: owned by the handle, valid until the
+ * next msim_surrogate_train or msim_destroy; msim_mlp_destroy refuses it).  Its parameters can be
+ * read and replaced with msim_mlp_get / msim_mlp_set. */
+MSIM_API msim_status msim_surrogate_network(msim_handle h, struct msim_mlp_** net);
+/* msim_geometry -- exact geometry of model `model` at n_rows configurations q [n_rows][ldq]
+ * (device, ldq >= n_dofs) into out [n_rows][ld_out] (device).  Asynchronous. */
+MSIM_API msim_status msim_geometry(msim_handle h, int32_t model, const float* q, int32_t ldq, int32_t n_rows,
+                                   float* out, int32_t ld_out, msim_stream_t stream);
+/* msim_surrogate_predict -- the network's de-normalised geometry at n_rows configurations (same
+ * layout as msim_geometry).  Uses the handle's inference buffers: stream-ordered with msim_step. */
+MSIM_API msim_status msim_surrogate_predict(msim_handle h, const float* q, int32_t ldq, int32_t n_rows, float* out,
+                                            int32_t ld_out, msim_stream_t stream);
 
 /* msim_last_error -- text of the last failure on this handle (or of the last failed create
  *   when h is NULL).  Owned by the library, valid until the next call. */

@@ -1,5 +1,6 @@
 // kernels.h -- launch interface between the C ABI (msim_api.cu) and the device code.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,7 +31,20 @@ struct StepArgs {
     float dt;
     int envs_per_block;
     int wpe;                      // warps per environment: 1, 2 or 4
-    EvalPtrs ev;                  // used by the eval kernel only
+    EvalPtrs ev;                  // eval: per-stage outputs; geometry mode: ev.L = label rows
+                                  // [env][ev.nnz_pitch] (L then R), rows from env_begin
+    // surrogate step (one substep per launch)
+    const float* surr_Y;          // network output rows, row (e - env_begin), pitch surr_ld
+    int surr_ld;
+    const float* surr_mu;         // output de-normalisation
+    const float* surr_sd;
+    const float* box_c;           // training box: |q - box_c| <= box_s per DoF
+    const float* box_s;
+    uint8_t* fallback;            // per environment: 1 = exact geometry until reset
+    unsigned long long* surr_stats;
+    float check_frac, tol;
+    uint32_t surr_seed;
+    const uint32_t* step_ctr;     // substep counter of the check draw (advanced by the input kernel)
     unsigned long long* timers;   // per-phase cycle counters (profiling builds only)
 };
 
@@ -40,10 +54,17 @@ constexpr int kMaxEnvsPerBlock = 16;
 
 cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_geom(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_surr_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
+// network input rows X[r] = bf16((q[env_begin + r] - c) / sc), pad columns 0; advances *step_ctr
+// (optional) by one
+cudaError_t launch_surr_input(const float* q, int pitch_n, int env_begin, int n_envs, const float* c, const float* sc,
+                              int n, __nv_bfloat16* X, int ldx, uint32_t* step_ctr, cudaStream_t s);
 cudaError_t launch_set_l0(uint8_t* img, const float* L, int m, cudaStream_t s);
-cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, const float* q0, const float* qd0,
-                         const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m, int n_envs,
-                         cudaStream_t s);
+// fallback (optional): per-environment surrogate fallback flags, cleared with the state
+cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
+                         const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,
+                         int n_envs, cudaStream_t s);
 cudaError_t set_step_smem_limit(size_t bytes);
 int step_blocks_per_sm(int threads, size_t smem, int wpe);
 

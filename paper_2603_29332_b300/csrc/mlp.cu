@@ -1,0 +1,279 @@
+// mlp.cu -- forward / backward / Adam of the 3-layer MLP on the tcgen05 GEMM (see mlp.h).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "gemm_tc.h"
+#include "mlp.h"
+
+namespace msim {
+namespace {
+
+int pad8(int x) { return (x + 7) & ~7; }
+size_t pad8s(size_t x) { return (x + 7) & ~size_t(7); }
+
+// ---------------------------------------------------------------- elementwise kernels
+__global__ void k_init(float* P, size_t n, size_t oW1, int hid, int in, int inp, size_t oW2, size_t oW3, int outp_rows,
+                       float bound1, float bound2, float bound3, uint32_t k0, uint32_t k1) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {(uint32_t)i, (uint32_t)(i >> 32), 0x5eedu, 0u};
+        philox4x32_10(c, k0, k1);
+        const float u = 2.f * u01_from_bits(c[0]) - 1.f;
+        float v = 0.f;
+        if (i >= oW1 && i < oW1 + (size_t)hid * inp) {
+            const int col = (int)((i - oW1) % inp);
+            v = col < in ? bound1 * u : 0.f;
+        } else if (i >= oW2 && i < oW2 + (size_t)hid * hid) {
+            v = bound2 * u;
+        } else if (i >= oW3 && i < oW3 + (size_t)outp_rows * hid) {
+            v = bound3 * u;
+        }
+        P[i] = v;
+    }
+}
+
+__global__ void k_to_bf16(const float* P, __nv_bfloat16* Ph, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        Ph[i] = __float2bfloat16_rn(P[i]);
+}
+
+// dst[c][r] = bf16(src[r][c]) for an R x C FP32 matrix (weights)
+__global__ void k_transpose_f32_to_bf16(const float* src, int R, int C, int lds, __nv_bfloat16* dst, int ldd) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        tile[j][threadIdx.x] = (r < R && c < C) ? src[(size_t)r * lds + c] : 0.f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (c < C && r < R) dst[(size_t)c * ldd + r] = __float2bfloat16_rn(tile[threadIdx.x][j]);
+    }
+}
+
+// dst[c][r] = src[r][c] for an R x C BF16 matrix
+__global__ void k_transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds, __nv_bfloat16* dst, int ldd) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int r = r0 + j, c = c0 + threadIdx.x;
+        tile[j][threadIdx.x] = (r < R && c < C) ? src[(size_t)r * lds + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int c = c0 + j, r = r0 + threadIdx.x;
+        if (c < C && r < R) dst[(size_t)c * ldd + r] = tile[threadIdx.x][j];
+    }
+}
+
+// dY = d mean((y - t)^2) / dy (times y (1 - y) for a sigmoid output), as BF16; loss sum
+__global__ void k_loss_grad(const float* Y, int ldy, const float* T, int ldt, int B, int N, float scale, int sig,
+                            __nv_bfloat16* dY, int ldd, float* loss_acc) {
+    float acc = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)B * N; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / N), c = (int)(i % N);
+        const float y = Y[(size_t)r * ldy + c];
+        const float d = y - T[(size_t)r * ldt + c];
+        acc += d * d;
+        float g = scale * d;
+        if (sig) g *= y * (1.f - y);
+        dY[(size_t)r * ldd + c] = __float2bfloat16_rn(g);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, acc);
+}
+
+// dZ = dH * silu'(Z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)
+__global__ void k_dsilu(const float* dH, const __nv_bfloat16* Z, int B, int N, int ld, __nv_bfloat16* dZ) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)B * N; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / N), c = (int)(i % N);
+        const size_t o = (size_t)r * ld + c;
+        const float z = __bfloat162float(Z[o]);
+        const float sgm = 1.f / (1.f + expf(-z));
+        dZ[o] = __float2bfloat16_rn(dH[o] * sgm * (1.f + z * (1.f - sgm)));
+    }
+}
+
+// db[c] = sum over rows of src[r][c]
+__global__ void k_colsum(const __nv_bfloat16* src, int B, int N, int ld, float* db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    float s = 0.f;
+    for (int r = 0; r < B; ++r) s += __bfloat162float(src[(size_t)r * ld + c]);
+    db[c] = s;
+}
+
+__global__ void k_adam(float* P, const float* G, float* Am, float* Av, size_t n, float lr, float b1, float b2,
+                       float eps, float bc1, float bc2, __nv_bfloat16* Ph) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float g = G[i];
+        const float m = b1 * Am[i] + (1.f - b1) * g;
+        const float v = b2 * Av[i] + (1.f - b2) * g * g;
+        Am[i] = m;
+        Av[i] = v;
+        const float p = P[i] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+        P[i] = p;
+        Ph[i] = __float2bfloat16_rn(p);
+    }
+}
+
+int nblocks(size_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
+
+cudaError_t transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds, __nv_bfloat16* dst, int ldd,
+                           cudaStream_t s) {
+    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+    k_transpose_bf16<<<grid, block, 0, s>>>(src, R, C, lds, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, void* C, int ldc, int c_bf16,
+                 const float* bias, int act, void* Z, int ldz, uint32_t* err, cudaStream_t s) {
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc; g.c_bf16 = c_bf16; g.bias = bias; g.act = act;
+    g.Z = Z; g.ldz = ldz; g.err = err;
+    return gemm_bf16_tc(A, lda, B, ldb, g, s);
+}
+
+#define CK(x)                                  \
+    do {                                       \
+        const cudaError_t e_ = (x);            \
+        if (e_ != cudaSuccess) return e_;      \
+    } while (0)
+
+}  // namespace
+
+cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp** out_mlp) {
+    *out_mlp = nullptr;
+    if (in < 1 || hid < 8 || (hid % 8) || out < 1 || max_batch < 1) return cudaErrorInvalidValue;
+    Mlp* m = new Mlp();
+    std::memset(m, 0, sizeof(Mlp));
+    m->in = in; m->inp = pad8(in); m->hid = hid; m->out = out; m->outp = pad8(out); m->out_act = out_act;
+    m->max_batch = max_batch; m->bp = pad8(max_batch);
+    size_t o = 0;
+    m->oW1 = o; o = pad8s(o + (size_t)hid * m->inp);
+    m->ob1 = o; o = pad8s(o + hid);
+    m->oW2 = o; o = pad8s(o + (size_t)hid * hid);
+    m->ob2 = o; o = pad8s(o + hid);
+    m->oW3 = o; o = pad8s(o + (size_t)m->outp * hid);
+    m->ob3 = o; o = pad8s(o + m->outp);
+    m->n_params = o;
+    const size_t np = m->n_params, B = (size_t)max_batch;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+    };
+    A((void**)&m->P, np * 4); A((void**)&m->G, np * 4); A((void**)&m->Am, np * 4); A((void**)&m->Av, np * 4);
+    A((void**)&m->Ph, np * 2);
+    A((void**)&m->W2t, (size_t)hid * hid * 2); A((void**)&m->W3t, (size_t)hid * m->outp * 2);
+    A((void**)&m->H1, B * hid * 2); A((void**)&m->Z1, B * hid * 2); A((void**)&m->H2, B * hid * 2);
+    A((void**)&m->Z2, B * hid * 2); A((void**)&m->dY, B * m->outp * 2); A((void**)&m->dZ1, B * hid * 2);
+    A((void**)&m->dZ2, B * hid * 2);
+    A((void**)&m->Xt, (size_t)m->inp * m->bp * 2); A((void**)&m->H1t, (size_t)hid * m->bp * 2);
+    A((void**)&m->H2t, (size_t)hid * m->bp * 2); A((void**)&m->dYt, (size_t)m->outp * m->bp * 2);
+    A((void**)&m->dZ1t, (size_t)hid * m->bp * 2); A((void**)&m->dZ2t, (size_t)hid * m->bp * 2);
+    A((void**)&m->Y, B * m->outp * 4); A((void**)&m->dH, B * hid * 4);
+    A((void**)&m->loss_acc, 8); A((void**)&m->err, 8);
+    if (e != cudaSuccess) {
+        mlp_destroy(m);
+        return e;
+    }
+    *out_mlp = m;
+    return cudaSuccess;
+}
+
+void mlp_destroy(Mlp* m) {
+    if (!m) return;
+    void* ptrs[] = {m->P, m->G, m->Am, m->Av, m->Ph, m->W2t, m->W3t, m->H1, m->Z1, m->H2, m->Z2, m->dY, m->dZ1,
+                    m->dZ2, m->Xt, m->H1t, m->H2t, m->dYt, m->dZ1t, m->dZ2t, m->Y, m->dH, m->loss_acc, m->err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete m;
+}
+
+cudaError_t mlp_sync_bf16(Mlp* m, cudaStream_t s) {
+    k_to_bf16<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->Ph, m->n_params);
+    CK(cudaGetLastError());
+    dim3 block(32, 8);
+    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->hid + 31) / 32), block, 0, s>>>(
+        m->P + m->oW2, m->hid, m->hid, m->hid, m->W2t, m->hid);
+    CK(cudaGetLastError());
+    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->outp + 31) / 32), block, 0, s>>>(
+        m->P + m->oW3, m->outp, m->hid, m->hid, m->W3t, m->outp);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_init(Mlp* m, uint64_t seed, float out_scale, cudaStream_t s) {
+    const float b1 = sqrtf(6.f / m->in), b2 = sqrtf(6.f / m->hid), b3 = out_scale * sqrtf(6.f / m->hid);
+    k_init<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->n_params, m->oW1, m->hid, m->in, m->inp, m->oW2, m->oW3,
+                                                 m->out, b1, b2, b3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(m->Am, 0, m->n_params * 4, s));
+    CK(cudaMemsetAsync(m->Av, 0, m->n_params * 4, s));
+    m->adam_t = 0;
+    return mlp_sync_bf16(m, s);
+}
+
+cudaError_t mlp_forward(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s) {
+    if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;
+    const int h = m->hid;
+    CK(gemm(X, ldx, m->Ph + m->oW1, m->inp, B, h, m->in, m->H1, h, 1, m->P + m->ob1, 1, m->Z1, h, m->err, s));
+    CK(gemm(m->H1, h, m->Ph + m->oW2, h, B, h, h, m->H2, h, 1, m->P + m->ob2, 1, m->Z2, h, m->err, s));
+    return gemm(m->H2, h, m->Ph + m->oW3, h, B, m->out, h, Y, ldy, 0, m->P + m->ob3, m->out_act, nullptr, 0, m->err, s);
+}
+
+cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T, int ldt, int B, cudaStream_t s) {
+    if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;
+    const int h = m->hid, bp = pad8(B);
+    CK(mlp_forward(m, X, ldx, B, m->Y, m->outp, s));
+    CK(cudaMemsetAsync(m->loss_acc, 0, 4, s));
+    const size_t nY = (size_t)B * m->out;
+    k_loss_grad<<<nblocks(nY), 256, 0, s>>>(m->Y, m->outp, T, ldt, B, m->out, 2.f / (float)nY, m->out_act == 2, m->dY,
+                                             m->outp, m->loss_acc);
+    CK(cudaGetLastError());
+    // layer 3
+    CK(transpose_bf16(m->dY, B, m->out, m->outp, m->dYt, bp, s));
+    CK(transpose_bf16(m->H2, B, h, h, m->H2t, bp, s));
+    CK(gemm(m->dYt, bp, m->H2t, bp, m->out, h, B, m->G + m->oW3, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    k_colsum<<<(m->out + 255) / 256, 256, 0, s>>>(m->dY, B, m->out, m->outp, m->G + m->ob3);
+    CK(cudaGetLastError());
+    CK(gemm(m->dY, m->outp, m->W3t, m->outp, B, h, m->out, m->dH, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z2, B, h, h, m->dZ2);
+    CK(cudaGetLastError());
+    // layer 2
+    CK(transpose_bf16(m->dZ2, B, h, h, m->dZ2t, bp, s));
+    CK(transpose_bf16(m->H1, B, h, h, m->H1t, bp, s));
+    CK(gemm(m->dZ2t, bp, m->H1t, bp, h, h, B, m->G + m->oW2, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    k_colsum<<<(h + 255) / 256, 256, 0, s>>>(m->dZ2, B, h, h, m->G + m->ob2);
+    CK(cudaGetLastError());
+    CK(gemm(m->dZ2, h, m->W2t, h, B, h, h, m->dH, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z1, B, h, h, m->dZ1);
+    CK(cudaGetLastError());
+    // layer 1
+    CK(transpose_bf16(m->dZ1, B, h, h, m->dZ1t, bp, s));
+    CK(transpose_bf16(X, B, m->inp, ldx, m->Xt, bp, s));
+    CK(gemm(m->dZ1t, bp, m->Xt, bp, h, m->in, B, m->G + m->oW1, m->inp, 0, nullptr, 0, nullptr, 0, m->err, s));
+    k_colsum<<<(h + 255) / 256, 256, 0, s>>>(m->dZ1, B, h, h, m->G + m->ob1);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(Mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t s) {
+    m->adam_t += 1;
+    const float bc1 = 1.f - powf(beta1, (float)m->adam_t), bc2 = 1.f - powf(beta2, (float)m->adam_t);
+    k_adam<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->G, m->Am, m->Av, m->n_params, lr, beta1, beta2, eps, bc1,
+                                                  bc2, m->Ph);
+    CK(cudaGetLastError());
+    dim3 block(32, 8);
+    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->hid + 31) / 32), block, 0, s>>>(
+        m->P + m->oW2, m->hid, m->hid, m->hid, m->W2t, m->hid);
+    CK(cudaGetLastError());
+    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->outp + 31) / 32), block, 0, s>>>(
+        m->P + m->oW3, m->outp, m->hid, m->hid, m->W3t, m->outp);
+    return cudaGetLastError();
+}
+
+}  // namespace msim

@@ -10,12 +10,15 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <numeric>
 #include <string>
 #include <vector>
 
 #include "../../include/msim.h"
 #include "gemm_tc.h"
+#include "mlp.h"
 #include "image.h"
+#include "surrogate.h"
 #include "kernels.h"
 
 using namespace msim;
@@ -378,8 +381,17 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
 
 }  // namespace
 
+struct msim_mlp_ {
+    Mlp* m = nullptr;
+    bool borrowed = false;   // owned by a simulator handle (its surrogate network)
+};
+
 struct msim_handle_ {
     int device = 0;
+    int geometry_mode = 0;
+    uint32_t seed = 0;
+    Surrogate* sur = nullptr;
+    msim_mlp_ sur_view;
     int n_models = 0, n_envs = 0, pitch_n = 0, pitch_m = 0;
     float dt = 0.f;
     int num_sms = 0;
@@ -413,7 +425,18 @@ msim_status arg_fail(msim_handle h, const char* what) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+void surr_free(Surrogate* s) {
+    if (!s) return;
+    if (s->net) mlp_destroy(s->net);
+    cudaFree(s->mu); cudaFree(s->sd); cudaFree(s->box_c); cudaFree(s->box_s);
+    cudaFree(s->X); cudaFree(s->Y); cudaFree(s->fallback); cudaFree(s->stats); cudaFree(s->step_ctr);
+    cudaFree(s->out_tmp);
+    delete s;
+}
+
 void free_all(msim_handle h) {
+    surr_free(h->sur);
+    h->sur = nullptr;
     for (int i = 0; i < kMaxModels; ++i)
         if (h->d_img[i]) cudaFree(h->d_img[i]);
     cudaFree(h->q); cudaFree(h->qd); cudaFree(h->act); cudaFree(h->qdd); cudaFree(h->force);
@@ -470,6 +493,59 @@ void auto_launch(msim_handle h, int i) {
     else { h->pts_smem[i] = 0; h->epb[i] = e_out; }
 }
 
+// geometry-mode launch of model i over rows [0, n_rows) of q (pitch ldq) into out (pitch ldo)
+cudaError_t geometry_launch(msim_handle h, int i, const float* q, int ldq, int n_rows, float* out, int ldo,
+                            cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    StepArgs a = base_args(h, i);
+    const int wpe = h->wpe[i] == 1 ? 1 : 2;
+    int epb = h->epb[i];
+    if (wpe != h->wpe[i]) epb = std::max(1, std::min(max_epb(h, i, h->pts_smem[i] != 0, wpe), 8));
+    a.wpe = wpe;
+    a.envs_per_block = epb;
+    a.env_begin = 0;
+    a.env_end = n_rows;
+    a.q = const_cast<float*>(q);
+    a.qd = const_cast<float*>(q);
+    a.pitch_n = ldq;
+    a.act = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr;
+    a.ev.L = out;
+    a.ev.nnz_pitch = ldo;
+    const size_t smem = step_smem_bytes(h->models[i].hdr, epb, h->pts_smem[i], wpe);
+    const int groups = (n_rows + epb - 1) / epb;
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe));
+    return launch_geom(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
+}
+
+msim_status surrogate_step(msim_handle h, const float* exc, int n_sub, cudaStream_t s) {
+    Surrogate* S = h->sur;
+    if (!S || !S->trained) {
+        h->err = "msim_step: learned geometry selected but no surrogate has been trained";
+        return MSIM_ERR_STATE;
+    }
+    const Mlp* net = S->net;
+    for (int k = 0; k < n_sub; ++k) {
+        cudaError_t e = launch_surr_input(h->q, h->pitch_n, 0, h->n_envs, S->box_c, S->box_s, S->n, S->X, net->inp,
+                                          S->step_ctr, s);
+        if (e == cudaSuccess) e = mlp_forward(S->net, S->X, net->inp, h->n_envs, S->Y, net->outp, s);
+        if (e == cudaSuccess) {
+            StepArgs a = base_args(h, 0);
+            a.exc = exc;
+            a.n_sub = 1;
+            a.surr_Y = S->Y; a.surr_ld = net->outp;
+            a.surr_mu = S->mu; a.surr_sd = S->sd;
+            a.box_c = S->box_c; a.box_s = S->box_s;
+            a.fallback = S->fallback; a.surr_stats = S->stats;
+            a.check_frac = S->check_frac; a.tol = S->tol;
+            a.surr_seed = S->seed; a.step_ctr = S->step_ctr;
+            e = launch_surr_step(a, model_grid(h, 0),
+                                 step_smem_bytes(h->models[0].hdr, h->epb[0], h->pts_smem[0], h->wpe[0]), s);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "msim_step (learned geometry)");
+    }
+    return MSIM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -485,12 +561,15 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
     if (args->n_models < 1 || args->n_models > kMaxModels) return arg_fail(nullptr, "n_models must be 1..8");
     if (!args->models || !args->envs_per_model) return arg_fail(nullptr, "models / envs_per_model is NULL");
     if (!(args->dt > 0.f) || !std::isfinite(args->dt)) return arg_fail(nullptr, "dt must be > 0");
-    if (args->geometry_mode != 0) {
-        g_create_error = "geometry_mode: only 0 (exact via-point geometry) is provided by this entry point";
+    if (args->geometry_mode != 0 && args->geometry_mode != 1) return arg_fail(nullptr, "geometry_mode must be 0 or 1");
+    if (args->geometry_mode == 1 && args->n_models != 1) {
+        g_create_error = "geometry_mode 1 (learned geometry) needs a single-model handle";
         return MSIM_ERR_UNSUPPORTED;
     }
     msim_handle h = new msim_handle_();
     h->device = args->device;
+    h->geometry_mode = args->geometry_mode;
+    h->seed = (uint32_t)(args->seed ^ (args->seed >> 32));
     h->n_models = args->n_models;
     h->dt = args->dt;
     int total = 0, nmax = 0, mmax = 0;
@@ -672,8 +751,8 @@ msim_status msim_reset(msim_handle h, const float* q0, const float* qd0, const f
     if (!aligned16(q0) || !aligned16(qd0) || !aligned16(act0)) return arg_fail(h, "msim_reset: unaligned pointer");
     const int rows = env_ids ? n_ids : h->n_envs;
     cudaSetDevice(h->device);
-    cudaError_t e = launch_reset(h->q, h->qd, h->act, h->env_status, q0, qd0, act0, env_ids, rows, h->pitch_n,
-                                 h->pitch_m, h->n_envs, (cudaStream_t)stream);
+    cudaError_t e = launch_reset(h->q, h->qd, h->act, h->env_status, h->sur ? h->sur->fallback : nullptr, q0, qd0,
+                                 act0, env_ids, rows, h->pitch_n, h->pitch_m, h->n_envs, (cudaStream_t)stream);
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_reset");
 }
 
@@ -682,6 +761,7 @@ msim_status msim_step(msim_handle h, const float* excitations, int32_t n_substep
     if (n_substeps < 1 || n_substeps > 100000) return arg_fail(h, "msim_step: n_substeps must be 1..100000");
     if (!aligned16(excitations)) return arg_fail(h, "msim_step: excitations not 16-byte aligned");
     cudaSetDevice(h->device);
+    if (h->geometry_mode == 1) return surrogate_step(h, excitations, n_substeps, (cudaStream_t)stream);
     for (int i = 0; i < h->n_models; ++i) {
         if (h->env_begin[i + 1] == h->env_begin[i]) continue;
         StepArgs a = base_args(h, i);
@@ -814,6 +894,314 @@ msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ld
     }
     if (e == cudaErrorInvalidValue) return arg_fail(nullptr, "msim_gemm_bf16: pitch or alignment not supported");
     return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_gemm_bf16");
+}
+
+msim_status msim_mlp_create(int32_t in, int32_t hidden, int32_t out, int32_t out_act, int32_t max_batch, uint64_t seed,
+                            float out_scale, msim_mlp* outp) {
+    if (!outp || in < 1 || hidden < 8 || hidden % 8 || out < 1 || max_batch < 1 || (out_act != 0 && out_act != 2))
+        return arg_fail(nullptr, "msim_mlp_create: bad argument");
+    *outp = nullptr;
+    Mlp* m = nullptr;
+    cudaError_t e = mlp_create(in, hidden, out, out_act, max_batch, &m);
+    if (e == cudaSuccess) e = mlp_init(m, seed, out_scale, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        mlp_destroy(m);
+        return cuda_fail(nullptr, e, "msim_mlp_create");
+    }
+    msim_mlp h = new msim_mlp_();
+    h->m = m;
+    *outp = h;
+    return MSIM_OK;
+}
+
+msim_status msim_mlp_destroy(msim_mlp h) {
+    if (!h) return MSIM_OK;
+    if (h->borrowed) return arg_fail(nullptr, "msim_mlp_destroy: network owned by a simulator handle");
+    cudaDeviceSynchronize();
+    mlp_destroy(h->m);
+    delete h;
+    return MSIM_OK;
+}
+
+msim_status msim_mlp_layout(msim_mlp h, int64_t offsets[6], int64_t* n_params, int32_t* in_pitch, int32_t* out_pitch) {
+    if (!h) return arg_fail(nullptr, "msim_mlp_layout: NULL network");
+    const Mlp* m = h->m;
+    if (offsets) {
+        offsets[0] = (int64_t)m->oW1; offsets[1] = (int64_t)m->ob1; offsets[2] = (int64_t)m->oW2;
+        offsets[3] = (int64_t)m->ob2; offsets[4] = (int64_t)m->oW3; offsets[5] = (int64_t)m->ob3;
+    }
+    if (n_params) *n_params = (int64_t)m->n_params;
+    if (in_pitch) *in_pitch = m->inp;
+    if (out_pitch) *out_pitch = m->outp;
+    return MSIM_OK;
+}
+
+static float* mlp_buffer(Mlp* m, int which) {
+    return which == 0 ? m->P : which == 1 ? m->G : which == 2 ? m->Am : which == 3 ? m->Av : nullptr;
+}
+
+msim_status msim_mlp_get(msim_mlp h, int32_t which, float* host, int64_t n) {
+    if (!h || !host || n != (int64_t)h->m->n_params || !mlp_buffer(h->m, which))
+        return arg_fail(nullptr, "msim_mlp_get: bad argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, mlp_buffer(h->m, which), n * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_mlp_get");
+}
+
+msim_status msim_mlp_set(msim_mlp h, int32_t which, const float* host, int64_t n, int32_t adam_step) {
+    if (!h || !host || n != (int64_t)h->m->n_params || !mlp_buffer(h->m, which))
+        return arg_fail(nullptr, "msim_mlp_set: bad argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(mlp_buffer(h->m, which), host, n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && which == 0) e = mlp_sync_bf16(h->m, 0);
+    if (which >= 2) h->m->adam_t = adam_step;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_mlp_set");
+}
+
+msim_status msim_mlp_forward(msim_mlp h, const void* X, int32_t ldx, int32_t B, float* Y, int32_t ldy,
+                             msim_stream_t stream) {
+    if (!h || !X || !Y || B < 1 || B > h->m->max_batch || ldx < h->m->inp || ldx % 8 || ldy < h->m->out)
+        return arg_fail(nullptr, "msim_mlp_forward: bad argument");
+    const cudaError_t e = mlp_forward(h->m, (const __nv_bfloat16*)X, ldx, B, Y, ldy, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_mlp_forward");
+}
+
+msim_status msim_mlp_backward(msim_mlp h, const void* X, int32_t ldx, const float* T, int32_t ldt, int32_t B,
+                              float* loss, msim_stream_t stream) {
+    if (!h || !X || !T || B < 1 || B > h->m->max_batch || ldx < h->m->inp || ldx % 8 || ldt < h->m->out)
+        return arg_fail(nullptr, "msim_mlp_backward: bad argument");
+    cudaError_t e = mlp_backward(h->m, (const __nv_bfloat16*)X, ldx, T, ldt, B, (cudaStream_t)stream);
+    if (e == cudaSuccess && loss) {
+        float sum = 0.f;
+        e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaMemcpy(&sum, h->m->loss_acc, 4, cudaMemcpyDeviceToHost);
+        *loss = sum / ((float)B * (float)h->m->out);
+    }
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_mlp_backward");
+}
+
+msim_status msim_mlp_adam(msim_mlp h, float lr, float beta1, float beta2, float eps, msim_stream_t stream) {
+    if (!h || !(lr > 0.f)) return arg_fail(nullptr, "msim_mlp_adam: bad argument");
+    const cudaError_t e = mlp_adam(h->m, lr, beta1, beta2, eps, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_mlp_adam");
+}
+
+
+// ------------------------------------------------------------------ learned geometry
+msim_status msim_geometry(msim_handle h, int32_t model, const float* q, int32_t ldq, int32_t n_rows, float* out,
+                          int32_t ld_out, msim_stream_t stream) {
+    if (!h || model < 0 || model >= h->n_models || !q || !out || n_rows < 0)
+        return arg_fail(h, "msim_geometry: bad argument");
+    const ImgHeader& hd = h->models[model].hdr;
+    if (ldq < hd.n || ld_out < hd.m + hd.nnz) return arg_fail(h, "msim_geometry: pitch too small");
+    cudaSetDevice(h->device);
+    const cudaError_t e = geometry_launch(h, model, q, ldq, n_rows, out, ld_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_geometry");
+}
+
+msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epochs, int32_t batch, float lr,
+                                 msim_stream_t stream) {
+    if (!h) return arg_fail(h, "msim_surrogate_train: NULL handle");
+    if (h->n_models != 1) {
+        h->err = "msim_surrogate_train: single-model handles only";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    if (batch < 1 || batch > 65536 || n_samples < batch || n_samples > (int64_t)1 << 30 || epochs < 1 ||
+        !(lr > 0.f) || !std::isfinite(lr))
+        return arg_fail(h, "msim_surrogate_train: bad argument");
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const ImgHeader& hd = h->models[0].hdr;
+    const int n = hd.n, m = hd.m, nnz = hd.nnz, out = m + nnz;
+    if (m < 1) return arg_fail(h, "msim_surrogate_train: model has no muscles");
+    const int inp = (n + 7) & ~7, outp = (out + 7) & ~7;
+    const int64_t N = n_samples;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t need = (size_t)N * ((size_t)outp * 4 + (size_t)inp * 2) + ((size_t)64 << 20);
+    if (need > free_b) {
+        h->err = "msim_surrogate_train: not enough device memory for the labels";
+        return MSIM_ERR_OOM;
+    }
+    surr_free(h->sur);
+    h->sur = nullptr;
+    Surrogate* S = new Surrogate();
+    S->n = n; S->m = m; S->nnz = nnz; S->out = out;
+    S->seed = h->seed;
+    cudaError_t e = mlp_create(n, kSurrHidden, out, 0, std::max(batch, h->n_envs), &S->net);
+    if (e == cudaSuccess) e = mlp_init(S->net, (uint64_t)h->seed * 2654435761ull + 17u, 1.f, s);
+    auto A = [&](void** p, size_t b) {
+        if (e == cudaSuccess) e = cudaMalloc(p, b);
+    };
+    A((void**)&S->mu, outp * 4); A((void**)&S->sd, outp * 4);
+    A((void**)&S->box_c, h->pitch_n * 4); A((void**)&S->box_s, h->pitch_n * 4);
+    A((void**)&S->X, (size_t)h->n_envs * inp * 2); A((void**)&S->Y, (size_t)h->n_envs * outp * 4);
+    A((void**)&S->out_tmp, (size_t)h->n_envs * outp * 4);
+    A((void**)&S->fallback, h->n_envs); A((void**)&S->stats, 8 * 8); A((void**)&S->step_ctr, 4);
+    __nv_bfloat16* Xall = nullptr;
+    float *T = nullptr, *qc = nullptr;
+    double* acc = nullptr;
+    const int chunk = 65536;
+    A((void**)&Xall, (size_t)N * inp * 2); A((void**)&T, (size_t)N * outp * 4);
+    A((void**)&qc, (size_t)chunk * h->pitch_n * 4); A((void**)&acc, (size_t)outp * 16);
+    if (e == cudaSuccess) {
+        // training box: joint limits widened by 5 % of the range; +-pi without limits
+        std::vector<float> c(h->pitch_n, 0.f), sc(h->pitch_n, 1.f);
+        const DofRec* D = reinterpret_cast<const DofRec*>(h->models[0].blob.data() + hd.o_dof);
+        for (int d = 0; d < n; ++d) {
+            if (D[d].lo < D[d].hi) {
+                c[d] = 0.5f * (D[d].lo + D[d].hi);
+                sc[d] = 0.5f * (D[d].hi - D[d].lo) * 1.05f;
+            } else {
+                c[d] = 0.f;
+                sc[d] = 3.14159265f;
+            }
+        }
+        e = cudaMemcpyAsync(S->box_c, c.data(), h->pitch_n * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(S->box_s, sc.data(), h->pitch_n * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors go out of scope
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->fallback, 0, h->n_envs, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->stats, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->step_ctr, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (size_t)outp * 16, s);
+    // labels from the exact geometry kernel, chunk by chunk
+    for (int64_t r0 = 0; r0 < N && e == cudaSuccess; r0 += chunk) {
+        const int rows = (int)std::min<int64_t>(chunk, N - r0);
+        e = surr_sample(qc, h->pitch_n, Xall + (size_t)r0 * inp, inp, rows, n, S->box_c, S->box_s, S->seed,
+                        (uint64_t)r0, s);
+        if (e == cudaSuccess) e = geometry_launch(h, 0, qc, h->pitch_n, rows, T + (size_t)r0 * outp, outp, s);
+        if (e == cudaSuccess) e = surr_col_stats(T + (size_t)r0 * outp, outp, rows, out, acc, s);
+    }
+    if (e == cudaSuccess) e = surr_finalize(acc, out, outp, (double)N, 1e-4f, S->mu, S->sd, s);
+    if (e == cudaSuccess) e = surr_normalize(T, outp, N, out, S->mu, S->sd, s);
+    // minibatches: contiguous blocks of the i.i.d. samples, visited in an affine-permuted order
+    // per epoch; cosine learning-rate decay from lr to lr / 100
+    const int64_t nb = N / batch;
+    const int64_t total_it = nb * epochs;
+    int64_t it = 0;
+    float last = 0.f;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+        uint32_t ctr[4] = {(uint32_t)ep, 0x7e57u, 0u, 0u};
+        philox4x32_10(ctr, S->seed, 0x51ed270bu);
+        int64_t mult = 1 + 2 * (int64_t)(ctr[0] % 1024);
+        while (std::gcd(mult, nb) != 1) mult += 2;
+        const int64_t off = (int64_t)(ctr[1] % (uint32_t)nb);
+        for (int64_t k = 0; k < nb && e == cudaSuccess; ++k, ++it) {
+            const int64_t b = (mult * k + off) % nb;
+            const double frac = (double)it / (double)std::max<int64_t>(total_it - 1, 1);
+            const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))));
+            e = mlp_backward(S->net, Xall + (size_t)b * batch * inp, inp, T + (size_t)b * batch * outp, outp, batch, s);
+            if (e == cudaSuccess) e = mlp_adam(S->net, lr_t, 0.9f, 0.999f, 1e-8f, s);
+        }
+        if (e == cudaSuccess && ep == epochs - 1) {
+            float sum = 0.f;
+            e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) e = cudaMemcpy(&sum, S->net->loss_acc, 4, cudaMemcpyDeviceToHost);
+            last = sum / ((float)batch * (float)out);
+        }
+    }
+    uint32_t gemm_err = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&gemm_err, S->net->err, 4, cudaMemcpyDeviceToHost);
+    cudaFree(Xall); cudaFree(T); cudaFree(qc); cudaFree(acc);
+    if (e != cudaSuccess || gemm_err) {
+        const msim_status st = e != cudaSuccess ? cuda_fail(h, e, "msim_surrogate_train") : MSIM_ERR_TIMEOUT;
+        if (gemm_err) h->err = "msim_surrogate_train: a GEMM wait ran out";
+        surr_free(S);
+        return st;
+    }
+    S->loss = last;
+    S->trained = 1;
+    h->sur = S;
+    h->sur_view.m = S->net;
+    h->sur_view.borrowed = true;
+    return MSIM_OK;
+}
+
+msim_status msim_set_geometry_mode(msim_handle h, int32_t mode) {
+    if (!h || (mode != 0 && mode != 1)) return arg_fail(h, "msim_set_geometry_mode: mode must be 0 or 1");
+    if (mode == 1 && h->n_models != 1) {
+        h->err = "msim_set_geometry_mode: learned geometry needs a single-model handle";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    if (mode == 1 && (!h->sur || !h->sur->trained)) {
+        h->err = "msim_set_geometry_mode: no trained surrogate (msim_surrogate_train)";
+        return MSIM_ERR_STATE;
+    }
+    h->geometry_mode = mode;
+    return MSIM_OK;
+}
+
+msim_status msim_surrogate_set_check(msim_handle h, float check_frac, float tol) {
+    if (!h || !(check_frac >= 0.f && check_frac <= 1.f) || !(tol > 0.f) || !std::isfinite(tol))
+        return arg_fail(h, "msim_surrogate_set_check: check_frac in [0, 1], tol > 0");
+    if (!h->sur) {
+        h->err = "msim_surrogate_set_check: no trained surrogate";
+        return MSIM_ERR_STATE;
+    }
+    h->sur->check_frac = check_frac;
+    h->sur->tol = tol;
+    return MSIM_OK;
+}
+
+msim_status msim_surrogate_stats(msim_handle h, msim_surrogate_info* out, int32_t reset_counters) {
+    if (!h || !out) return arg_fail(h, "msim_surrogate_stats: NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    if (!h->sur) return MSIM_OK;
+    cudaSetDevice(h->device);
+    unsigned long long c[8] = {};
+    std::vector<uint8_t> fb(h->n_envs);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c, h->sur->stats, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(fb.data(), h->sur->fallback, h->n_envs, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset_counters) e = cudaMemset(h->sur->stats, 0, sizeof(c));
+    if (e != cudaSuccess) return cuda_fail(h, e, "msim_surrogate_stats");
+    out->env_substeps = c[0]; out->learned = c[1]; out->out_of_box = c[2];
+    out->flagged = c[3]; out->checked = c[4]; out->check_failed = c[5];
+    uint32_t bits = (uint32_t)c[6];
+    std::memcpy(&out->max_check_error, &bits, 4);
+    out->train_loss = h->sur->loss;
+    int nf = 0;
+    for (uint8_t v : fb) nf += v != 0;
+    out->flagged_envs = nf;
+    out->trained = h->sur->trained;
+    return MSIM_OK;
+}
+
+msim_status msim_surrogate_network(msim_handle h, msim_mlp* net) {
+    if (!h || !net) return arg_fail(h, "msim_surrogate_network: NULL argument");
+    *net = nullptr;
+    if (!h->sur || !h->sur->trained) {
+        h->err = "msim_surrogate_network: no trained surrogate";
+        return MSIM_ERR_STATE;
+    }
+    *net = &h->sur_view;
+    return MSIM_OK;
+}
+
+msim_status msim_surrogate_predict(msim_handle h, const float* q, int32_t ldq, int32_t n_rows, float* out,
+                                   int32_t ld_out, msim_stream_t stream) {
+    if (!h || !q || !out || n_rows < 0) return arg_fail(h, "msim_surrogate_predict: bad argument");
+    Surrogate* S = h->sur;
+    if (!S || !S->trained) {
+        h->err = "msim_surrogate_predict: no trained surrogate";
+        return MSIM_ERR_STATE;
+    }
+    if (ldq < S->n || ld_out < S->out) return arg_fail(h, "msim_surrogate_predict: pitch too small");
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (int r0 = 0; r0 < n_rows && e == cudaSuccess; r0 += h->n_envs) {
+        const int rows = std::min(h->n_envs, n_rows - r0);
+        e = launch_surr_input(q, ldq, r0, rows, S->box_c, S->box_s, S->n, S->X, S->net->inp, nullptr, s);
+        if (e == cudaSuccess) e = mlp_forward(S->net, S->X, S->net->inp, rows, S->out_tmp, S->net->outp, s);
+        if (e == cudaSuccess)
+            e = surr_denorm(S->out_tmp, S->net->outp, rows, S->out, S->mu, S->sd, out + (size_t)r0 * ld_out, ld_out, s);
+    }
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_surrogate_predict");
 }
 
 #ifdef MSIM_PHASE_TIMERS

@@ -31,10 +31,15 @@
 #include "dfloat.cuh"
 #include "image.h"
 #include "kernels.h"
+#include "mlp.h"
 
 namespace msim {
 
 namespace {
+
+// kernel modes: one substep loop, one-substep evaluation with every intermediate, muscle
+// geometry only (surrogate training labels), surrogate step (geometry from the learned model)
+constexpr int kModeStep = 0, kModeEval = 1, kModeGeom = 2, kModeSurr = 3;
 
 constexpr uint32_t kEnvNonFinite = 0x1u;
 constexpr uint32_t kEnvNotSpd = 0x2u;
@@ -498,12 +503,29 @@ __device__ __forceinline__ float hill_dfv(float v) {
     return 0.032f / (den * den);
 }
 
+// Per-environment context of a surrogate step: the network's normalised output row and its
+// de-normalisation, whether this environment must use the exact geometry (outside the training
+// box, or flagged), whether this substep cross-checks the two, and the check's tolerance.
+struct SurrCtx {
+    const float* Y;
+    const float* mu;
+    const float* sd;
+    bool use_exact;
+    bool check;
+    float tol;
+    unsigned int* max_err_bits;   // global running maximum of the check error (float bits)
+};
+
 // ------------------------------------------------------------------ phase 4: muscles
+#pragma nv_diag_suppress 128
 // One lane per muscle.  act: this environment's activation row in global memory (read;
-// written unless EVAL).  Returns true if a force was not finite.
-template <bool EVAL, int WPE>
-__device__ bool phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc, float* act,
-                              float* force_out, const EvalPtrs* ev) {
+// written unless MODE == kModeEval).
+// Returns bit 0: a force was not finite; bit 1 (surrogate step): the cross-check exceeded the
+// tolerance.  Geometry mode writes L to ev->L[k] and the moment arms to ev->R and stops there.
+// (The statements after its `continue` are unreachable in that mode only: warning 128 is off.)
+template <int MODE, int WPE>
+__device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc,
+                                  float* act, float* force_out, const EvalPtrs* ev, const SurrCtx* sc) {
     const ImgHeader& H = *T.H;
     const float* qd = ws + H.w_qd;
     const float* frame = ws + H.w_frame;
@@ -512,47 +534,79 @@ __device__ bool phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, flo
     int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
     float* rk = ws + H.w_rk;                                  // [kMaxCross][N]
     bool bad = false;
+    uint32_t flags = 0;
     SUB_T0();
     for (int r = g.lane; r < H.m; r += g.N) {
         const MuscleRec M = T.mus[r];
         const int k = M.orig;
-        const float a = act[k];
-        const float u = fminf(fmaxf(exc[k], 0.f), 1.f);
-        PointRec P = T.pt[M.p0];
-        int b = P.body_cross & 0xff;
-        int cprev = P.body_cross >> 8;
-        const float* fb = frame + 12 * b;
-        float x0[3];
-        rot3(fb, P.pos, x0);
-        x0[0] += fb[9]; x0[1] += fb[10]; x0[2] += fb[11];
+        const float a = MODE == kModeGeom ? 0.f : act[k];
+        const float u = MODE == kModeGeom ? 0.f : fminf(fmaxf(exc[k], 0.f), 1.f);
+        const bool learned = (MODE == kModeSurr) && !sc->use_exact;   // geometry from the network
         float L = 0.f, ldot = 0.f;
-        for (int j = 1; j < M.np; ++j) {
-            P = T.pt[M.p0 + j];
-            b = P.body_cross & 0xff;
-            const int c = P.body_cross >> 8;
-            fb = frame + 12 * b;
-            float x1[3];
-            rot3(fb, P.pos, x1);
-            x1[0] += fb[9]; x1[1] += fb[10]; x1[2] += fb[11];
-            const float dv[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
-            const float len2 = dot3(dv, dv);
-            const float inv = rsqrtf(len2);
-            L += len2 * inv;
-            const float uu[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
-            for (int i = cprev; i < c; ++i) {
-                const uint32_t ce = T.cross[M.x0 + i];
-                const int d = cross_dof(ce);
-                const float* Sd = S + 6 * d;
-                const float* o = frame + 12 * cross_body(ce) + 9;
-                const float rr[3] = {x1[0] - o[0], x1[1] - o[1], x1[2] - o[2]};
-                float rxu[3];
-                cross3(rr, uu, rxu);
-                const float Rv = -(Sd[0] * rxu[0] + Sd[1] * rxu[1] + Sd[2] * rxu[2]);   // R = -dL/dq
-                rk[i * g.N + g.lane] = Rv;
-                ldot -= Rv * qd[d];
+        if (!learned || sc->check) {
+            // exact via-point geometry: L = sum |x_{j+1} - x_j|, R = -dL/dq of the crossed DoFs
+            PointRec P = T.pt[M.p0];
+            int b = P.body_cross & 0xff;
+            int cprev = P.body_cross >> 8;
+            const float* fb = frame + 12 * b;
+            float x0[3];
+            rot3(fb, P.pos, x0);
+            x0[0] += fb[9]; x0[1] += fb[10]; x0[2] += fb[11];
+            for (int j = 1; j < M.np; ++j) {
+                P = T.pt[M.p0 + j];
+                b = P.body_cross & 0xff;
+                const int c = P.body_cross >> 8;
+                fb = frame + 12 * b;
+                float x1[3];
+                rot3(fb, P.pos, x1);
+                x1[0] += fb[9]; x1[1] += fb[10]; x1[2] += fb[11];
+                const float dv[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
+                const float len2 = dot3(dv, dv);
+                const float inv = rsqrtf(len2);
+                L += len2 * inv;
+                const float uu[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+                for (int i = cprev; i < c; ++i) {
+                    const uint32_t ce = T.cross[M.x0 + i];
+                    const int d = cross_dof(ce);
+                    const float* Sd = S + 6 * d;
+                    const float* o = frame + 12 * cross_body(ce) + 9;
+                    const float rr[3] = {x1[0] - o[0], x1[1] - o[1], x1[2] - o[2]};
+                    float rxu[3];
+                    cross3(rr, uu, rxu);
+                    const float Rv = -(Sd[0] * rxu[0] + Sd[1] * rxu[1] + Sd[2] * rxu[2]);   // R = -dL/dq
+                    rk[i * g.N + g.lane] = Rv;
+                    ldot -= Rv * qd[d];
+                }
+                x0[0] = x1[0]; x0[1] = x1[1]; x0[2] = x1[2];
+                cprev = c;
             }
-            x0[0] = x1[0]; x0[1] = x1[1]; x0[2] = x1[2];
-            cprev = c;
+        }
+        if (MODE == kModeSurr && learned) {
+            // learned geometry: de-normalised network outputs (L first, then R in sparse order)
+            const int mm = H.m;
+            const float Ls = sc->Y[k] * sc->sd[k] + sc->mu[k];
+            if (sc->check) {
+                float e = fabsf(Ls - L);
+                for (int i = 0; i < M.nx; ++i) {
+                    const int o = mm + M.x0 + i;
+                    e = fmaxf(e, fabsf(sc->Y[o] * sc->sd[o] + sc->mu[o] - rk[i * g.N + g.lane]));
+                }
+                if (e > sc->tol) flags |= 2u;
+                if (e > 0.f) atomicMax(sc->max_err_bits, __float_as_uint(e));
+            } else {
+                L = Ls;
+                for (int i = 0; i < M.nx; ++i) {
+                    const int o = mm + M.x0 + i;
+                    const float Rv = sc->Y[o] * sc->sd[o] + sc->mu[o];
+                    rk[i * g.N + g.lane] = Rv;
+                    ldot -= Rv * qd[cross_dof(T.cross[M.x0 + i])];
+                }
+            }
+        }
+        if (MODE == kModeGeom) {
+            ev->L[k] = L;
+            for (int i = 0; i < M.nx; ++i) ev->R[M.x0 + i] = rk[i * g.N + g.lane];
+            continue;
         }
         SUB_MARK(8);
         const float lm = 1.f + (L - M.L0) * M.inv_lopt;
@@ -562,7 +616,7 @@ __device__ bool phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, flo
         const float dFdl = M.fmax * a * fl * hill_dfv(vm) * M.inv_vmax;
         const float tau = (u > a) ? H.tau_act * (0.5f + 1.5f * a) : H.tau_deact / (0.5f + 1.5f * a);
         const float an = fminf(fmaxf(a + dt * (u - a) / tau, 0.f), 1.f);
-        if (!EVAL) act[k] = an;
+        if (MODE != kModeEval) act[k] = an;
         if (force_out) force_out[k] = F;
         SUB_MARK(9);
         // rhs += R^T F; A += dt R^T (dF/dLdot) R as g g^T with g = sqrt(dt dF/dLdot) R.  All
@@ -580,7 +634,7 @@ __device__ bool phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, flo
         for (int i = 0; i < kMaxCross; ++i) {
             if (i < M.nx) {
                 fx_red(&racc[2 * cross_dof(cr[i])], Rr[i] * F);
-                if (EVAL && ev->tau_m) atomicAdd(&ev->tau_m[cross_dof(cr[i])], Rr[i] * F);
+                if ((MODE == kModeEval) && ev->tau_m) atomicAdd(&ev->tau_m[cross_dof(cr[i])], Rr[i] * F);
                 if (sq != 0.f) {
                     const float gi = sq * Rr[i];
                     const int base = cross_row(cr[i]) + M.dep0;
@@ -589,7 +643,7 @@ __device__ bool phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, flo
                 }
             }
         }
-        if (EVAL) {
+        if ((MODE == kModeEval)) {
             if (ev->L) ev->L[k] = L;
             if (ev->lm) ev->lm[k] = lm;
             if (ev->vm) ev->vm[k] = vm;
@@ -600,11 +654,13 @@ __device__ bool phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, flo
         }
         SUB_MARK(10);
     }
-    return g.any(bad);   // also orders the reductions before the next phase
+    // also orders the reductions before the next phase
+    const bool fail = g.any((flags & 2u) != 0);
+    return (g.any(bad) ? 1u : 0u) | (fail ? 2u : 0u);
 }
 
 // ------------------------------------------------------------------ phase 5: contact
-template <bool EVAL, int WPE>
+template <int MODE, int WPE>
 __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const EvalPtrs* ev) {
     const ImgHeader& H = *T.H;
     if (H.ns == 0) return;
@@ -682,7 +738,7 @@ __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, flo
                 fx_red(&Ai[2 * tgt[u]], val[u]);
                 if (diag[u]) {
                     fx_red(&racc[2 * dd[u]], tdiag[u]);
-                    if (EVAL && ev->tau_c) atomicAdd(&ev->tau_c[dd[u]], tdiag[u]);
+                    if ((MODE == kModeEval) && ev->tau_c) atomicAdd(&ev->tau_c[dd[u]], tdiag[u]);
                 }
             }
         }
@@ -691,7 +747,7 @@ __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, flo
 }
 
 // ------------------------------------------------------------------ phase 6: limits, damping
-template <bool EVAL, int WPE>
+template <int MODE, int WPE>
 __device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const EvalPtrs* ev) {
     const ImgHeader& H = *T.H;
     const float* q = ws + H.w_q;
@@ -711,7 +767,7 @@ __device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, floa
         }
         rhs[d] += t;
         A[D.row + D.depth] = df_add_f(A[D.row + D.depth], dt * dd);
-        if (EVAL && ev->tau_l) ev->tau_l[d] = t;
+        if ((MODE == kModeEval) && ev->tau_l) ev->tau_l[d] = t;
     }
     g.sync();
 }
@@ -835,10 +891,16 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
     } while (0)
 #endif
 
-template <bool EVAL, int WPE>
+// Returns the environment status bits; in a surrogate step bit 8 reports a failed cross-check.
+template <int MODE, int WPE>
 __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc, float* act,
-                            float* force_out, const EvalPtrs* ev, unsigned long long* timers) {
+                            float* force_out, const EvalPtrs* ev, const SurrCtx* sc, unsigned long long* timers) {
     const ImgHeader& H = *T.H;
+    if (MODE == kModeGeom) {
+        phase_kinematics(T, ws, g);
+        phase_muscles<kModeGeom>(T, ws, g, dt, exc, act, nullptr, ev, nullptr);
+        return 0u;
+    }
 #ifdef MSIM_PHASE_TIMERS
     long long t0_ = clock64();
 #else
@@ -855,21 +917,22 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
         int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
         for (int t = g.lane; t < 2 * H.n; t += g.N) racc[t] = 0;
     }
-    if (EVAL) {
+    if ((MODE == kModeEval)) {
         for (int d = g.lane; d < H.n; d += g.N)
             if (ev->bias) ev->bias[d] = -ws[H.w_rhs + d];
     }
     g.sync();
-    const bool bad = phase_muscles<EVAL>(T, ws, g, dt, exc, act, force_out, ev);
+    const uint32_t mflags = phase_muscles<MODE>(T, ws, g, dt, exc, act, force_out, ev, sc);
+    const bool bad = (mflags & 1u) != 0;
     PHASE_MARK(3);
-    phase_contact<EVAL>(T, ws, g, dt, ev);
+    phase_contact<MODE>(T, ws, g, dt, ev);
     PHASE_MARK(4);
-    phase_crba(T, ws, g, EVAL ? ev->M : nullptr);
+    phase_crba(T, ws, g, (MODE == kModeEval) ? ev->M : nullptr);
     PHASE_MARK(2);
-    phase_limits<EVAL>(T, ws, g, dt, ev);
+    phase_limits<MODE>(T, ws, g, dt, ev);
     PHASE_MARK(5);
     const df* A = reinterpret_cast<const df*>(ws + H.w_A);
-    if (EVAL) {
+    if ((MODE == kModeEval)) {
         for (int t = g.lane; t < H.n_packed; t += g.N)
             if (ev->A) ev->A[t] = A[t].hi + A[t].lo;
         const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
@@ -881,9 +944,9 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     }
     const bool ok = phase_factor_solve(T, ws, g);
     PHASE_MARK(6);
-    uint32_t st = (ok ? 0u : kEnvNotSpd) | (bad ? kEnvNonFinite : 0u);
+    uint32_t st = (ok ? 0u : kEnvNotSpd) | (bad ? kEnvNonFinite : 0u) | ((mflags & 2u) ? 0x100u : 0u);
     const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
-    if (!EVAL) {
+    if (!(MODE == kModeEval)) {
         float* q = ws + H.w_q;
         float* qd = ws + H.w_qd;
         for (int d = g.lane; d < H.n; d += g.N) {
@@ -899,7 +962,7 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
 }
 
 // ------------------------------------------------------------------ kernels
-template <bool EVAL, int WPE>
+template <int MODE, int WPE>
 __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -934,7 +997,7 @@ __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
         }
         g.sync();
         uint32_t st = 0;
-        if (EVAL) {
+        if ((MODE == kModeEval)) {
             EvalPtrs ev = a.ev;
             auto off = [&](float* p, size_t pitch) { return p ? p + (size_t)e * pitch : p; };
             ev.L = off(ev.L, a.pitch_m); ev.lm = off(ev.lm, a.pitch_m); ev.vm = off(ev.vm, a.pitch_m);
@@ -950,12 +1013,51 @@ __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
                 if (ev.tau_l) ev.tau_l[d] = 0.f;
             }
             g.sync();
-            st |= substep<true>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, a.timers);
+            st |= substep<kModeEval>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, nullptr, a.timers);
+        } else if (MODE == kModeGeom) {
+            EvalPtrs ev = a.ev;
+            ev.L = a.ev.L + (size_t)(e - a.env_begin) * ev.nnz_pitch;   // label row: L then R
+            ev.R = ev.L + H.m;
+            substep<kModeGeom>(T, ws, g, a.dt, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
         } else {
-            for (int s = 0; s < a.n_sub; ++s) {
-                const bool last = (s == a.n_sub - 1);
-                st |= substep<false>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
-                                     (last && a.force_out) ? a.force_out + rm : nullptr, nullptr, a.timers);
+            if (MODE == kModeSurr) {
+                // one substep with the learned geometry (the host loops over substeps)
+                bool oob = false;
+                for (int d = g.lane; d < H.n; d += g.N) oob |= fabsf(ws[H.w_q + d] - a.box_c[d]) > a.box_s[d];
+                oob = g.any(oob);
+                const bool flagged = a.fallback[e] != 0;
+                uint32_t c[4] = {(uint32_t)e, *a.step_ctr, 0x73u, 0x75u};
+                philox4x32_10(c, a.surr_seed, 0x9e3779b9u);
+                SurrCtx sc;
+                sc.Y = a.surr_Y + (size_t)(e - a.env_begin) * a.surr_ld;
+                sc.mu = a.surr_mu;
+                sc.sd = a.surr_sd;
+                sc.use_exact = oob || flagged;
+                sc.check = !sc.use_exact && u01_from_bits(c[0]) < a.check_frac;
+                sc.tol = a.tol;
+                sc.max_err_bits = reinterpret_cast<unsigned int*>(a.surr_stats + 6);
+                const uint32_t s1 = substep<kModeSurr>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+                                                       a.force_out ? a.force_out + rm : nullptr, nullptr, &sc, a.timers);
+                st |= s1 & 0xffu;
+                if (g.lane == 0) {
+                    unsigned long long* cs = a.surr_stats;   // see msim_surrogate_stats
+                    atomicAdd(&cs[0], 1ull);
+                    if (!sc.use_exact && !sc.check) atomicAdd(&cs[1], 1ull);
+                    if (oob) atomicAdd(&cs[2], 1ull);
+                    if (flagged) atomicAdd(&cs[3], 1ull);
+                    if (sc.check) atomicAdd(&cs[4], 1ull);
+                    if (s1 & 0x100u) {
+                        atomicAdd(&cs[5], 1ull);
+                        a.fallback[e] = 1;   // exact geometry for this environment until its reset
+                    }
+                }
+            } else {
+                for (int s = 0; s < a.n_sub; ++s) {
+                    const bool last = (s == a.n_sub - 1);
+                    st |= substep<kModeStep>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+                                             (last && a.force_out) ? a.force_out + rm : nullptr, nullptr, nullptr,
+                                             a.timers);
+                }
             }
             bool bad = false;
             const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
@@ -983,8 +1085,9 @@ __global__ void k_set_l0(uint8_t* img, const float* L, int m) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) mus[r].L0 = L[mus[r].orig];
 }
 
-__global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, const float* q0, const float* qd0,
-                        const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m, int n_envs) {
+__global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
+                        const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,
+                        int n_envs) {
     const int r = blockIdx.x;
     if (r >= n_rows) return;
     const int e = ids ? ids[r] : r;
@@ -995,7 +1098,10 @@ __global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, const
     }
     for (int i = threadIdx.x; i < pitch_m; i += blockDim.x)
         act[(size_t)e * pitch_m + i] = act0 ? act0[(size_t)r * pitch_m + i] : 0.f;
-    if (threadIdx.x == 0) status[e] = 0u;
+    if (threadIdx.x == 0) {
+        status[e] = 0u;
+        if (fallback) fallback[e] = 0;
+    }
 }
 
 }  // namespace
@@ -1008,36 +1114,74 @@ size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem, int wpe
 int step_blocks_per_sm(int threads, size_t smem, int wpe) {
     int n = 0;
     cudaError_t e;
-    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, 4>, threads, smem);
-    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, 2>, threads, smem);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false, 1>, threads, smem);
+    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<kModeStep, 4>, threads, smem);
+    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<kModeStep, 2>, threads, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<kModeStep, 1>, threads, smem);
     return e == cudaSuccess ? n : 1;
 }
 
 cudaError_t set_step_smem_limit(size_t bytes) {
     const int b = (int)bytes;
-    cudaError_t e = cudaFuncSetAttribute(k_step<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    return e;
+    const void* fns[] = {(const void*)k_step<kModeStep, 1>, (const void*)k_step<kModeStep, 2>,
+                         (const void*)k_step<kModeStep, 4>, (const void*)k_step<kModeEval, 1>,
+                         (const void*)k_step<kModeEval, 2>, (const void*)k_step<kModeEval, 4>,
+                         (const void*)k_step<kModeGeom, 1>, (const void*)k_step<kModeGeom, 2>,
+                         (const void*)k_step<kModeSurr, 1>, (const void*)k_step<kModeSurr, 2>,
+                         (const void*)k_step<kModeSurr, 4>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
     const int threads = 32 * a.wpe * a.envs_per_block;
-    if (a.wpe == 4) k_step<false, 4><<<grid, threads, smem, s>>>(a);
-    else if (a.wpe == 2) k_step<false, 2><<<grid, threads, smem, s>>>(a);
-    else k_step<false, 1><<<grid, threads, smem, s>>>(a);
+    if (a.wpe == 4) k_step<kModeStep, 4><<<grid, threads, smem, s>>>(a);
+    else if (a.wpe == 2) k_step<kModeStep, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<kModeStep, 1><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
     const int threads = 32 * a.wpe * a.envs_per_block;
-    if (a.wpe == 4) k_step<true, 4><<<grid, threads, smem, s>>>(a);
-    else if (a.wpe == 2) k_step<true, 2><<<grid, threads, smem, s>>>(a);
-    else k_step<true, 1><<<grid, threads, smem, s>>>(a);
+    if (a.wpe == 4) k_step<kModeEval, 4><<<grid, threads, smem, s>>>(a);
+    else if (a.wpe == 2) k_step<kModeEval, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<kModeEval, 1><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geom(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
+    const int threads = 32 * a.wpe * a.envs_per_block;
+    if (a.wpe == 2) k_step<kModeGeom, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<kModeGeom, 1><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surr_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
+    const int threads = 32 * a.wpe * a.envs_per_block;
+    if (a.wpe == 4) k_step<kModeSurr, 4><<<grid, threads, smem, s>>>(a);
+    else if (a.wpe == 2) k_step<kModeSurr, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<kModeSurr, 1><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_surr_input(const float* q, int pitch_n, int env_begin, int n_envs, const float* c, const float* sc,
+                             int n, __nv_bfloat16* X, int ldx, uint32_t* step_ctr) {
+    if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1u;   // read by the next step kernel
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_envs * ldx;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ldx), j = (int)(i % ldx);
+        const float v = j < n ? (q[(size_t)(env_begin + r) * pitch_n + j] - c[j]) / sc[j] : 0.f;
+        X[(size_t)r * ldx + j] = __float2bfloat16_rn(v);
+    }
+}
+
+cudaError_t launch_surr_input(const float* q, int pitch_n, int env_begin, int n_envs, const float* c, const float* sc,
+                              int n, __nv_bfloat16* X, int ldx, uint32_t* step_ctr, cudaStream_t s) {
+    const size_t tot = (size_t)n_envs * ldx;
+    const int blocks = (int)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
+    k_surr_input<<<blocks, 256, 0, s>>>(q, pitch_n, env_begin, n_envs, c, sc, n, X, ldx, step_ctr);
     return cudaGetLastError();
 }
 
@@ -1046,11 +1190,11 @@ cudaError_t launch_set_l0(uint8_t* img, const float* L, int m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, const float* q0, const float* qd0,
-                         const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m, int n_envs,
-                         cudaStream_t s) {
+cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
+                         const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,
+                         int n_envs, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
-    k_reset<<<n_rows, 128, 0, s>>>(q, qd, act, status, q0, qd0, act0, ids, n_rows, pitch_n, pitch_m, n_envs);
+    k_reset<<<n_rows, 128, 0, s>>>(q, qd, act, status, fallback, q0, qd0, act0, ids, n_rows, pitch_n, pitch_m, n_envs);
     return cudaGetLastError();
 }
 

@@ -56,13 +56,27 @@ class Dims(C.Structure):
 _EVAL_FIELDS = ("L", "lm", "vm", "force", "act_next", "R", "tau_m", "tau_c", "tau_l", "bias", "rhs", "qdd", "M", "A")
 
 
+class SurrogateInfo(C.Structure):
+    _fields_ = [("env_substeps", C.c_uint64), ("learned", C.c_uint64), ("out_of_box", C.c_uint64),
+                ("flagged", C.c_uint64), ("checked", C.c_uint64), ("check_failed", C.c_uint64),
+                ("max_check_error", C.c_float), ("train_loss", C.c_float), ("flagged_envs", C.c_int32),
+                ("trained", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class EvalOut(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in _EVAL_FIELDS] + [("nnz_pitch", C.c_int32), ("packed_pitch", C.c_int32)]
 
 
 EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_step", "msim_step_host",
            "msim_get_state", "msim_get_status", "msim_clear_status", "msim_eval", "msim_get_layout",
-           "msim_set_launch", "msim_gemm_bf16", "msim_last_error", "msim_version")
+           "msim_set_launch", "msim_gemm_bf16", "msim_mlp_create", "msim_mlp_destroy", "msim_mlp_layout",
+           "msim_mlp_get", "msim_mlp_set", "msim_mlp_forward", "msim_mlp_backward", "msim_mlp_adam",
+           "msim_surrogate_train", "msim_set_geometry_mode", "msim_surrogate_set_check", "msim_surrogate_stats",
+           "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict",
+           "msim_last_error", "msim_version")
 
 _lib = None
 
@@ -90,6 +104,23 @@ def load_library(path=LIB_PATH):
     lib.msim_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     lib.msim_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                    C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
+    lib.msim_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_float,
+                                    C.POINTER(vp)]
+    lib.msim_mlp_destroy.argtypes = [vp]
+    lib.msim_mlp_layout.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32)]
+    lib.msim_mlp_get.argtypes = [vp, C.c_int32, vp, C.c_int64]
+    lib.msim_mlp_set.argtypes = [vp, C.c_int32, vp, C.c_int64, C.c_int32]
+    lib.msim_mlp_forward.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
+    lib.msim_mlp_backward.argtypes = [vp, vp, C.c_int32, vp, C.c_int32, C.c_int32, C.POINTER(C.c_float), vp]
+    lib.msim_mlp_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]
+    lib.msim_surrogate_train.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_float, vp]
+    lib.msim_set_geometry_mode.argtypes = [vp, C.c_int32]
+    lib.msim_surrogate_set_check.argtypes = [vp, C.c_float, C.c_float]
+    lib.msim_surrogate_stats.argtypes = [vp, C.POINTER(SurrogateInfo), C.c_int32]
+    lib.msim_surrogate_network.argtypes = [vp, C.POINTER(vp)]
+    lib.msim_geometry.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
+    lib.msim_surrogate_predict.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
     lib.msim_last_error.argtypes = [vp]
     lib.msim_last_error.restype = C.c_char_p
     lib.msim_version.restype = C.c_int32
@@ -146,7 +177,7 @@ def model_desc(model):
 class Sim:
     """A batch of environments of one or more models on one CUDA device (``msim_create``)."""
 
-    def __init__(self, models, envs_per_model, dt=1e-3, device=0, geometry_mode=0):
+    def __init__(self, models, envs_per_model, dt=1e-3, device=0, geometry_mode=0, seed=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2603_29332_b300.Sim needs a CUDA device (no CPU fallback)")
@@ -163,7 +194,7 @@ class Sim:
             self._keep.append(k)
         arr = (ModelDesc * len(descs))(*descs)
         epm = np.ascontiguousarray(envs_per_model, dtype=np.int32)
-        args = CreateArgs(len(descs), arr, epm.ctypes.data_as(_i32p), geometry_mode, float(dt), 0, device)
+        args = CreateArgs(len(descs), arr, epm.ctypes.data_as(_i32p), geometry_mode, float(dt), seed, device)
         h = C.c_void_p()
         st = self.lib.msim_create(C.byref(args), C.byref(h))
         if st != MSIM_OK:
@@ -272,6 +303,49 @@ class Sim:
         return a
 
 
+    # ------------------------------------------------------------------ learned geometry
+    def geometry(self, q, model=0, stream=None):
+        """Exact geometry rows [L | R (sparse order)] at configurations q [rows, >= n] (CUDA FP32)."""
+        import torch
+        q = q.contiguous()
+        nm = self.dims.n_muscles[model] + self.dims.nnz[model]
+        out = torch.zeros((q.shape[0], nm), device=self.device)
+        self._check(self.lib.msim_geometry(self.h, model, q.data_ptr(), q.stride(0), q.shape[0], out.data_ptr(),
+                                           out.stride(0), _stream_ptr(stream)))
+        return out
+
+    def train_surrogate(self, n_samples, epochs, batch=4096, lr=1e-3, stream=None):
+        self._check(self.lib.msim_surrogate_train(self.h, int(n_samples), int(epochs), int(batch), float(lr),
+                                                  _stream_ptr(stream)))
+
+    def set_geometry_mode(self, mode):
+        self._check(self.lib.msim_set_geometry_mode(self.h, int(mode)))
+
+    def surrogate_set_check(self, check_frac, tol=1e-3):
+        self._check(self.lib.msim_surrogate_set_check(self.h, float(check_frac), float(tol)))
+
+    def surrogate_stats(self, reset=False):
+        info = SurrogateInfo()
+        self._check(self.lib.msim_surrogate_stats(self.h, C.byref(info), 1 if reset else 0))
+        return info.as_dict()
+
+    def surrogate_predict(self, q, stream=None):
+        import torch
+        q = q.contiguous()
+        nm = self.dims.n_muscles[0] + self.dims.nnz[0]
+        out = torch.zeros((q.shape[0], nm), device=self.device)
+        self._check(self.lib.msim_surrogate_predict(self.h, q.data_ptr(), q.stride(0), q.shape[0], out.data_ptr(),
+                                                    out.stride(0), _stream_ptr(stream)))
+        return out
+
+    def surrogate_network(self):
+        """The trained network as a borrowed MLP (parameters readable and replaceable)."""
+        h = C.c_void_p()
+        self._check(self.lib.msim_surrogate_network(self.h, C.byref(h)))
+        d_in = self.dims.n_dofs[0]
+        return MLP.borrowed(h, d_in, 512, self.dims.n_muscles[0] + self.dims.nnz[0])
+
+
 def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=None):
     """C = act(A B^T + bias) on the tensor cores (msim_gemm_bf16).  A [M, K], B [N, K]: BF16 CUDA
     tensors with unit column stride and row pitches multiple of 8."""
@@ -288,6 +362,113 @@ def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=N
     if st != MSIM_OK:
         raise MsimError(st, lib.msim_last_error(None).decode())
     return C
+
+
+class MLP:
+    """3-layer MLP on the tensor cores (msim_mlp_*): BF16 weights/activations, FP32 accumulation."""
+
+    def __init__(self, d_in, hidden, d_out, out_sigmoid=False, max_batch=4096, seed=0, out_scale=1.0):
+        self.lib = load_library()
+        h = C.c_void_p()
+        st = self.lib.msim_mlp_create(d_in, hidden, d_out, 2 if out_sigmoid else 0, max_batch, seed, out_scale,
+                                      C.byref(h))
+        if st != MSIM_OK:
+            raise MsimError(st, self.lib.msim_last_error(None).decode())
+        self.h = h
+        self._layout(d_in, hidden, d_out, max_batch)
+
+    @classmethod
+    def borrowed(cls, h, d_in, hidden, d_out):
+        """A view of a network owned elsewhere (a simulator's surrogate); close() leaves it alone."""
+        self = cls.__new__(cls)
+        self.lib = load_library()
+        self.h = h
+        self._borrowed = True
+        self._layout(d_in, hidden, d_out, 0)
+        return self
+
+    def _layout(self, d_in, hidden, d_out, max_batch):
+        off = (C.c_int64 * 6)()
+        n = C.c_int64()
+        ip, op = C.c_int32(), C.c_int32()
+        self.lib.msim_mlp_layout(self.h, off, C.byref(n), C.byref(ip), C.byref(op))
+        self.offsets = list(off)
+        self.n_params = n.value
+        self.in_pitch, self.out_pitch = ip.value, op.value
+        self.d_in, self.hidden, self.d_out, self.max_batch = d_in, hidden, d_out, max_batch
+
+    def _check(self, st):
+        if st != MSIM_OK:
+            raise MsimError(st, self.lib.msim_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "h", None) and not getattr(self, "_borrowed", False):
+            self.lib.msim_mlp_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # flat <-> (W1, b1, W2, b2, W3, b3)
+    def unflatten(self, flat):
+        o, h = self.offsets, self.hidden
+        W1 = flat[o[0]:o[0] + h * self.in_pitch].reshape(h, self.in_pitch)[:, : self.d_in]
+        W3 = flat[o[4]:o[4] + self.out_pitch * h].reshape(self.out_pitch, h)[: self.d_out]
+        return [W1, flat[o[1]:o[1] + h], flat[o[2]:o[2] + h * h].reshape(h, h), flat[o[3]:o[3] + h], W3,
+                flat[o[5]:o[5] + self.d_out]]
+
+    def flatten(self, params):
+        flat = np.zeros(self.n_params, np.float32)
+        o, h = self.offsets, self.hidden
+        W1 = np.zeros((h, self.in_pitch), np.float32)
+        W1[:, : self.d_in] = params[0]
+        flat[o[0]:o[0] + W1.size] = W1.ravel()
+        flat[o[1]:o[1] + h] = params[1]
+        flat[o[2]:o[2] + h * h] = np.asarray(params[2], np.float32).ravel()
+        flat[o[3]:o[3] + h] = params[3]
+        W3 = np.zeros((self.out_pitch, h), np.float32)
+        W3[: self.d_out] = params[4]
+        flat[o[4]:o[4] + W3.size] = W3.ravel()
+        flat[o[5]:o[5] + self.d_out] = params[5]
+        return flat
+
+    def get(self, which=0):
+        flat = np.zeros(self.n_params, np.float32)
+        self._check(self.lib.msim_mlp_get(self.h, which, flat.ctypes.data, self.n_params))
+        return flat
+
+    def set(self, flat, which=0, adam_step=0):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self.lib.msim_mlp_set(self.h, which, flat.ctypes.data, self.n_params, adam_step))
+
+    def pad_input(self, X):
+        """[B, d_in] -> BF16 CUDA tensor [B, in_pitch]."""
+        import torch
+        X = torch.as_tensor(X).float()
+        out = torch.zeros((X.shape[0], self.in_pitch), dtype=torch.bfloat16, device="cuda")
+        out[:, : self.d_in] = X.cuda().bfloat16()
+        return out
+
+    def forward(self, Xb, Y=None, stream=None):
+        import torch
+        B = Xb.shape[0]
+        if Y is None:
+            Y = torch.empty((B, self.out_pitch), dtype=torch.float32, device="cuda")
+        self._check(self.lib.msim_mlp_forward(self.h, Xb.data_ptr(), Xb.stride(0), B, Y.data_ptr(), Y.stride(0),
+                                              _stream_ptr(stream)))
+        return Y
+
+    def backward(self, Xb, T, stream=None):
+        loss = C.c_float()
+        self._check(self.lib.msim_mlp_backward(self.h, Xb.data_ptr(), Xb.stride(0), T.data_ptr(), T.stride(0),
+                                               Xb.shape[0], C.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._check(self.lib.msim_mlp_adam(self.h, lr, beta1, beta2, eps, _stream_ptr(stream)))
 
 
 def unpack_packed(packed, layout):
