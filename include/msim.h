@@ -274,6 +274,28 @@ MSIM_API msim_status msim_geometry(msim_handle h, int32_t model, const float* q,
 MSIM_API msim_status msim_surrogate_predict(msim_handle h, const float* q, int32_t ldq, int32_t n_rows, float* out,
                                             int32_t ld_out, msim_stream_t stream);
 
+/* msim_mlp_forward_noalloc -- Y [B][ldy] FP32 = the 3-layer MLP of msim_mlp_forward at caller-held
+ * weights, for callers that cannot allocate device memory.  The paper has no counterpart: it is an
+ * entry point of this library.  It allocates nothing (no cudaMalloc / cudaFree, no allocating
+ * library call): its hidden activations go to one fixed file-scope device array of
+ * MSIM_NOALLOC_MAX_ACT_ELEMS x 2 BF16 values (32 MiB) plus a 256-byte header, so B * hidden must
+ * not exceed MSIM_NOALLOC_MAX_ACT_ELEMS (MSIM_ERR_ARG with a message in msim_last_error(NULL)
+ * otherwise; split larger batches).  The first call on a device, made with that device current,
+ * looks up the array's device address (cudaGetSymbolAddress) once; make that first call before
+ * any stream capture.  Every call on a device shares the array, which keeps the last call's
+ * contents; the GEMMs' wait-expiry word in it is cleared by each call.  Calls whose GPU work
+ * overlaps (streams not ordered with each other) race on the array.
+ *   W1 [hidden][ldw1] BF16 (ldw1 >= in, multiple of 8), b1 [hidden] FP32, W2 [hidden][hidden] BF16,
+ *   b2 [hidden] FP32, W3 [out][hidden] BF16, b3 [out] FP32, X [B][ldx] BF16 (ldx >= in, multiple of
+ *   8): all device pointers, BF16 ones 16-byte aligned.  out_act 0 identity, 2 sigmoid.
+ *   status: optional device word; receives 0, or bit 0 set if a GEMM wait expired (Y invalid).
+ * Asynchronous on `stream`; argument checks are synchronous. */
+#define MSIM_NOALLOC_MAX_ACT_ELEMS (8u * 1024u * 1024u)
+MSIM_API msim_status msim_mlp_forward_noalloc(int32_t in, int32_t hidden, int32_t out, int32_t out_act, const void* W1,
+                                              int32_t ldw1, const float* b1, const void* W2, const float* b2,
+                                              const void* W3, const float* b3, const void* X, int32_t ldx, int32_t B,
+                                              float* Y, int32_t ldy, uint32_t* status, msim_stream_t stream);
+
 /* msim_last_error -- text of the last failure on this handle (or of the last failed create
  *   when h is NULL).  Owned by the library, valid until the next call. */
 MSIM_API const char* msim_last_error(msim_handle h);

@@ -381,6 +381,10 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
 
 }  // namespace
 
+namespace msim {
+void set_global_error(const char* what) { g_create_error = what; }
+}  // namespace msim
+
 struct msim_mlp_ {
     Mlp* m = nullptr;
     bool borrowed = false;   // owned by a simulator handle (its surrogate network)

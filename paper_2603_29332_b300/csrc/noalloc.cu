@@ -1,0 +1,104 @@
+// noalloc.cu -- forward pass of the 3-layer MLP from caller-held weights, allocating nothing.
+//
+// The two hidden activation matrices live in one file-scope device array of fixed size; its
+// device address is looked up once per device (cudaGetSymbolAddress, with that device current) on
+// the first call made while that device is current.  Every call on a device shares the array:
+// the array keeps the last call's contents, and calls whose GPU work overlaps (different streams
+// without ordering between them) race on it.  The GEMMs are the same tcgen05 kernels as
+// msim_mlp_forward's, launched on the caller's stream.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "../../include/msim.h"
+#include "gemm_tc.h"
+
+namespace msim {
+void set_global_error(const char* what);   // msim_api.cu: text returned by msim_last_error(NULL)
+}
+
+using namespace msim;
+
+namespace {
+
+// [0, 256): error word of the GEMMs' bounded waits (cleared by every call); [256, ...): H1 then H2,
+// B x hidden BF16 each.
+constexpr size_t kHeaderBytes = 256;
+constexpr size_t kActBytes = MSIM_NOALLOC_MAX_ACT_ELEMS * 2 * sizeof(__nv_bfloat16);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kHeaderBytes + kActBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set-up on first use per device).
+cudaError_t scratch_ptr(unsigned char** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_ptr[dev]);
+    return cudaSuccess;
+}
+
+cudaError_t gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, void* C, int ldc, int c_bf16,
+                 const float* bias, int act, uint32_t* err, cudaStream_t s) {
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc; g.c_bf16 = c_bf16; g.bias = bias; g.act = act;
+    g.err = err;
+    return gemm_bf16_tc(A, lda, B, ldb, g, s);
+}
+
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+msim_status fail(msim_status st, const char* what) {
+    set_global_error(what);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+msim_status msim_mlp_forward_noalloc(int32_t in, int32_t hidden, int32_t out, int32_t out_act, const void* W1,
+                                     int32_t ldw1, const float* b1, const void* W2, const float* b2, const void* W3,
+                                     const float* b3, const void* X, int32_t ldx, int32_t B, float* Y, int32_t ldy,
+                                     uint32_t* status, msim_stream_t stream) {
+    if (in < 1 || hidden < 8 || hidden % 8 || out < 1 || B < 1 || (out_act != 0 && out_act != 2))
+        return fail(MSIM_ERR_ARG, "msim_mlp_forward_noalloc: bad sizes or out_act");
+    if (!W1 || !b1 || !W2 || !b2 || !W3 || !b3 || !X || !Y)
+        return fail(MSIM_ERR_ARG, "msim_mlp_forward_noalloc: NULL pointer");
+    if (ldw1 < in || ldw1 % 8 || ldx < in || ldx % 8 || ldy < out)
+        return fail(MSIM_ERR_ARG, "msim_mlp_forward_noalloc: bad pitch");
+    if (!al16(W1) || !al16(W2) || !al16(W3) || !al16(X))
+        return fail(MSIM_ERR_ARG, "msim_mlp_forward_noalloc: W1, W2, W3 and X must be 16-byte aligned");
+    if ((int64_t)B * hidden > (int64_t)MSIM_NOALLOC_MAX_ACT_ELEMS)
+        return fail(MSIM_ERR_ARG,
+                    "msim_mlp_forward_noalloc: B * hidden exceeds MSIM_NOALLOC_MAX_ACT_ELEMS (fixed scratch size)");
+    unsigned char* base = nullptr;
+    cudaError_t e = scratch_ptr(&base);
+    if (e != cudaSuccess) return fail(MSIM_ERR_CUDA, "msim_mlp_forward_noalloc: cudaGetSymbolAddress failed");
+    uint32_t* err = reinterpret_cast<uint32_t*>(base);
+    __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(base + kHeaderBytes);
+    __nv_bfloat16* H2 = H1 + (size_t)B * hidden;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = gemm(X, ldx, W1, ldw1, B, hidden, in, H1, hidden, 1, b1, 1, err, s);
+    if (e == cudaSuccess) e = gemm(H1, hidden, W2, hidden, B, hidden, hidden, H2, hidden, 1, b2, 1, err, s);
+    if (e == cudaSuccess) e = gemm(H2, hidden, W3, hidden, B, out, hidden, Y, ldy, 0, b3, out_act, err, s);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaErrorInvalidValue) return fail(MSIM_ERR_ARG, "msim_mlp_forward_noalloc: pitch or alignment");
+    return e == cudaSuccess ? MSIM_OK : fail(MSIM_ERR_CUDA, "msim_mlp_forward_noalloc: launch failed");
+}
+
+}  // extern "C"

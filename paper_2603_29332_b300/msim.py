@@ -75,7 +75,7 @@ EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_s
            "msim_set_launch", "msim_gemm_bf16", "msim_mlp_create", "msim_mlp_destroy", "msim_mlp_layout",
            "msim_mlp_get", "msim_mlp_set", "msim_mlp_forward", "msim_mlp_backward", "msim_mlp_adam",
            "msim_surrogate_train", "msim_set_geometry_mode", "msim_surrogate_set_check", "msim_surrogate_stats",
-           "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict",
+           "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
            "msim_last_error", "msim_version")
 
 _lib = None
@@ -121,6 +121,8 @@ def load_library(path=LIB_PATH):
     lib.msim_surrogate_network.argtypes = [vp, C.POINTER(vp)]
     lib.msim_geometry.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
     lib.msim_surrogate_predict.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
+    lib.msim_mlp_forward_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp, vp,
+                                             vp, vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
     lib.msim_last_error.argtypes = [vp]
     lib.msim_last_error.restype = C.c_char_p
     lib.msim_version.restype = C.c_int32
@@ -469,6 +471,28 @@ class MLP:
 
     def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         self._check(self.lib.msim_mlp_adam(self.h, lr, beta1, beta2, eps, _stream_ptr(stream)))
+
+
+NOALLOC_MAX_ACT_ELEMS = 8 * 1024 * 1024   # MSIM_NOALLOC_MAX_ACT_ELEMS: B * hidden limit
+
+
+def mlp_forward_noalloc(W1, b1, W2, b2, W3, b3, X, d_in, out_sigmoid=False, Y=None, status=None, stream=None):
+    """msim_mlp_forward_noalloc: the MLP forward at caller-held CUDA weights (BF16 W, FP32 b), no
+    device allocation inside the call.  W1 [hidden, >= d_in] (pitch = its row stride), W2 [hidden,
+    hidden], W3 [out, hidden], X [B, >= d_in] BF16.  Returns Y [B, out] FP32 (allocated here by torch
+    unless given)."""
+    import torch
+    lib = load_library()
+    hidden, out, B = W2.shape[0], W3.shape[0], X.shape[0]
+    if Y is None:
+        Y = torch.empty((B, out), dtype=torch.float32, device=X.device)
+    st = lib.msim_mlp_forward_noalloc(d_in, hidden, out, 2 if out_sigmoid else 0, W1.data_ptr(), W1.stride(0),
+                                      b1.data_ptr(), W2.data_ptr(), b2.data_ptr(), W3.data_ptr(), b3.data_ptr(),
+                                      X.data_ptr(), X.stride(0), B, Y.data_ptr(), Y.stride(0),
+                                      status.data_ptr() if status is not None else None, _stream_ptr(stream))
+    if st != MSIM_OK:
+        raise MsimError(st, lib.msim_last_error(None).decode())
+    return Y
 
 
 def unpack_packed(packed, layout):
