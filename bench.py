@@ -10,6 +10,15 @@ Metric: env-steps/s = environments x substeps / device time.
 Under torchrun (N > 1) every rank steps its own 4096 environments (weak scaling, no data-path
 collective); the max over ranks of the timed region is used.  `--impl reference` times the
 FP64 CPU oracle on the host cores instead (rank 0 only).
+
+Beside the exact path, the default run (rank 0, N = 1) trains the learned-geometry surrogate
+(2M configurations, 50 epochs) and times the same rollout with it ("surrogate" in the line).
+Two more workloads print their own line:
+  --workload c2_mixed   three skeletons in one handle (8192 envs, 10 x 0.5 ms substeps per call,
+                        captured in a CUDA graph): per-model launches vs the autotuned mixed launch;
+  --workload c4_policy  16384 whole-body envs with a policy MLP in the loop (one inference per
+                        2 substeps, CUDA graphs), exact vs learned geometry;
+  --workload c3_mlp     the surrogate network's forward pass alone (tensor-core GEMMs).
 """
 import argparse
 import json
@@ -173,6 +182,7 @@ def run_gpu(args, rank, world, local_rank):
     excs = [sim.pad_m(excs_h[t]) for t in range(n_buf)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    tune = sim.autotune(None, n_sub=sub) if args.autotune else None   # launch shape (state restored)
     stream = torch.cuda.current_stream()
     for t in range(args.warmup):
         sim.step(excs[t % n_buf], sub)
@@ -231,12 +241,239 @@ def run_gpu(args, rank, world, local_rank):
            "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(args),
            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+           "launch_shape": {"warps_per_env": sim.dims.warps_per_env[0], "envs_per_block": sim.dims.envs_per_block[0],
+                            "points_in_smem": sim.dims.points_in_smem[0],
+                            "autotuned": tune is not None},
            "status_flags": flags,
            "precision_note": "FP32 throughout except the mass-matrix entries and their L^T L factorisation, "
                              "which use float-float pairs on the FP32 pipes"}
+    if args.surrogate and world == 1:
+        out["surrogate"] = run_surrogate(args, sim, model, excs, flush, value)
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model)
     return out
+
+
+def _mlp_flops(sizes):
+    return sum(2 * a * b for a, b in zip(sizes[:-1], sizes[1:]))
+
+
+def run_surrogate(args, sim, model, excs, flush, exact_value):
+    """Same rollout with the learned geometry: train, then time K steps (1 % checks, fallback)."""
+    import torch
+    E, sub = args.envs, args.substeps
+    n_buf = len(excs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # accuracy on fresh configurations in the training box
+    lo, hi = model.dof_limit[:, 0].astype(np.float64), model.dof_limit[:, 1].astype(np.float64)
+    c, hw = 0.5 * (lo + hi), 0.5 * (hi - lo) * 1.05
+    rng = np.random.default_rng(99)
+    qs = (c + hw * rng.uniform(-1, 1, (4096, model.n_dofs))).astype(np.float32)
+    qg = torch.zeros((4096, sim.pitch_n), device="cuda")
+    qg[:, : model.n_dofs] = torch.from_numpy(qs).cuda()
+    err = (sim.surrogate_predict(qg) - sim.geometry(qg)).abs()
+    m = model.n_muscles
+    eR = err[:, m:].flatten()[::5].float()
+    q0, qd0, a0 = mg.initial_state(model, E, seed=1)
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    sim.set_geometry_mode(1)
+    for t in range(args.warmup):
+        sim.step(excs[t % n_buf], sub)
+    torch.cuda.synchronize()
+    sim.surrogate_stats(reset=True)
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for t in range(args.steps):
+        flush.fill_(float(t))
+        starts[t].record(stream)
+        sim.step(excs[(args.warmup + t) % n_buf], sub)
+        ends[t].record(stream)
+    torch.cuda.synchronize()
+    total_ms = float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
+    st = sim.surrogate_stats()
+    status, flags = sim.status()
+    nonfinite = int((sim.state()["status"] & 1).count_nonzero())
+    sim.set_geometry_mode(0)
+    # the network alone at this batch, for its tensor-pipe fraction
+    net = sim.surrogate_network()
+    X = torch.zeros((E, net.in_pitch), dtype=torch.bfloat16, device="cuda")
+    Y = torch.empty((E, net.out_pitch), device="cuda")
+    for _ in range(3):
+        net.forward(X, Y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(20):
+        net.forward(X, Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mlp_ms = e0.elapsed_time(e1) / 20
+    mlp_tf = _mlp_flops([model.n_dofs, 512, 512, net.d_out]) * E / (mlp_ms * 1e-3) / 1e12
+    peaks = _peaks()
+    pk = peaks.get("bf16_tflops_sustained") or 1400.0
+    n = max(st["env_substeps"], 1)
+    value = E * sub * args.steps / (total_ms * 1e-3)
+    return {"value": value, "unit": UNIT, "ms_per_step": total_ms / args.steps, "vs_exact": value / exact_value,
+            "train_s": train_s, "train_samples": args.surr_samples, "train_epochs": args.surr_epochs,
+            "train_loss_normalised_mse": st["train_loss"],
+            "fraction_learned": st["learned"] / n, "fraction_out_of_box": st["out_of_box"] / n,
+            "fraction_flagged": st["flagged"] / n, "fraction_checked": st["checked"] / n,
+            "checks_failed": st["check_failed"], "max_check_error_m": st["max_check_error"],
+            "moment_arm_abs_err_m": {"median": float(eR.median()), "p99": float(eR.quantile(0.99)),
+                                     "max": float(err[:, m:].max())},
+            "length_abs_err_m": {"median": float(err[:, :m].median()), "max": float(err[:, :m].max())},
+            "mlp_forward": {"ms": mlp_ms, "tflops": mlp_tf, "peak_tflops": pk, "frac": mlp_tf / pk,
+                            "peak_note": "bf16_tflops_sustained of measured"},
+            "envs_non_finite": nonfinite, "status_flags": flags,
+            "box": "joint limits widened by 5 % of each range", "check": "1 % of envs per substep, 1 mm"}
+
+
+def run_mlp(args):
+    """The surrogate network's forward pass alone (90 -> 512 -> 512 -> m + nnz, random init) at
+    the whole-body batch: the tensor-core kernels of the learned geometry, for profiling."""
+    import torch
+    from paper_2603_29332_b300 import msim
+    model = mg.config_model(MODEL)
+    sim = msim.Sim(model, 8, dt=DT)
+    E = args.envs
+    net = msim.MLP(model.n_dofs, 512, model.n_muscles + sim.dims.nnz[0], max_batch=E, seed=3)
+    X = net.pad_input(np.random.default_rng(3).uniform(-1, 1, (E, model.n_dofs)))
+    Y = torch.empty((E, net.out_pitch), device="cuda")
+    for _ in range(args.warmup):
+        net.forward(X, Y)
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for _ in range(args.steps):
+        net.forward(X, Y)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    fl = _mlp_flops([model.n_dofs, 512, 512, net.d_out]) * E
+    pk = _peaks().get("bf16_tflops") or 1800.0
+    return {"metric": "MLP forward TFLOP/s (surrogate network, batch %d)" % E, "value": fl / (ms * 1e-3) / 1e12,
+            "unit": "TFLOP/s", "ms_per_step": ms, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "roofline": {"bound": "tensor", "achieved": fl / (ms * 1e-3) / 1e12, "peak": pk,
+                         "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / pk,
+                         "peak_note": "bf16_tflops (burst) of measured"}}
+
+
+def run_mixed(args):
+    """Three skeletons in one handle: per-model launches vs the autotuned mixed launch (graphs)."""
+    import torch
+    from paper_2603_29332_b300 import msim
+    names = ("c2_upper", "c2_lower", "c1_whole")
+    counts = (2458, 2458, 3276)
+    dt, sub = 5e-4, 10
+    models = [mg.config_model(nm) for nm in names]
+    sim = msim.Sim(models, list(counts), dt=dt)
+    qs, qds, acts, ex = [], [], [], []
+    for i, (mdl, E) in enumerate(zip(models, counts)):
+        q, qd, a = mg.initial_state(mdl, E, seed=2 + i)
+        qs.append(sim._pad(q, sim.pitch_n)); qds.append(sim._pad(qd, sim.pitch_n)); acts.append(sim._pad(a, sim.pitch_m))
+        ex.append(sim._pad(mg.smooth_excitations(mdl, E, 1, seed=2 + i)[0], sim.pitch_m))
+    q0, qd0, a0, exc = torch.cat(qs), torch.cat(qds), torch.cat(acts), torch.cat(ex)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def timed(label):
+        sim.reset(q0, qd0, a0)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            sim.step(exc, sub)
+        torch.cuda.synchronize()
+        sim.reset(q0, qd0, a0)
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        cur = torch.cuda.current_stream()
+        for t in range(args.steps):
+            flush.fill_(float(t))
+            starts[t].record(cur)
+            g.replay()
+            ends[t].record(cur)
+        torch.cuda.synchronize()
+        ms = float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))) / args.steps
+        return sum(counts) * sub / (ms * 1e-3), ms
+
+    base_value, base_ms = timed("per-model default")
+    tune = sim.autotune(None, n_sub=sub)
+    sim.set_mixed_launch(False)
+    permodel_value, permodel_ms = timed("per-model tuned")
+    sim.set_mixed_launch(True, tune["mixed_warps_per_env"], tune["mixed_slots"], tune["mixed_stage_points_mask"])
+    with ClockSampler(0) as clk:
+        mixed_value, mixed_ms = timed("mixed tuned")
+    st, flags = sim.status()
+    return {"metric": "env-steps/s, mixed batch of 3 skeletons x 8192 envs, one persistent launch",
+            "value": mixed_value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": mixed_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2458 upper-body (30 DoF, 250 muscles) + 2458 lower-limb (40 DoF, 300 muscles, "
+                                   "contact) + 3276 whole-body envs; 10 substeps x 0.5 ms per CUDA-graph replay",
+                       "l2": "flushed (256 MB write) between timed replays"},
+            "per_model_launches": {"default_shapes": base_value, "tuned_shapes": permodel_value,
+                                   "tuned_ms_per_step": permodel_ms},
+            "mixed_vs_per_model_tuned": mixed_value / permodel_value, "autotune": tune,
+            "clocks": clk.summary(), "status_flags": flags}
+
+
+def run_policy(args):
+    """16384 whole-body envs with a policy MLP in the loop, exact vs learned geometry (graphs)."""
+    import torch
+    from paper_2603_29332_b300 import msim
+    model = mg.config_model(MODEL)
+    E, per_act, acts_per_graph = args.policy_envs, 2, 50
+    sim = msim.Sim(model, E, dt=DT, seed=4)
+    pol = msim.MLP(2182, 1024, model.n_muscles, out_sigmoid=True, max_batch=E, seed=4)
+    sim.policy_attach(pol)
+    q0, qd0, a0 = mg.initial_state(model, E, seed=4)
+    stream = torch.cuda.Stream()
+    res = {}
+    for mode in ("exact", "learned"):
+        if mode == "learned":
+            sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=1e-3)
+            sim.set_geometry_mode(1)
+        sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            sim.policy_step(per_act, acts_per_graph)
+        torch.cuda.synchronize()
+        sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+        g.replay()
+        torch.cuda.synchronize()
+        replays = max(1, args.policy_steps // (per_act * acts_per_graph))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        e0.record(cur)
+        for _ in range(replays):
+            g.replay()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        steps = replays * per_act * acts_per_graph
+        res[mode] = {"value": E * steps / (ms * 1e-3), "ms_per_substep": ms / steps, "steps": steps,
+                     "status": sim.status()}
+        if mode == "learned":
+            res[mode]["surrogate_stats"] = sim.surrogate_stats()
+    return {"metric": "env-steps/s, closed loop with policy MLP, whole body x %d envs" % E,
+            "value": res["exact"]["value"], "unit": UNIT, "n_gpus": 1, "steps": res["exact"]["steps"],
+            "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16",
+            "data": "synthetic, random-init policy",
+            "config": {"workload": "whole body, %d envs, policy 2182 -> 1024 -> 1024 -> 700 sigmoid every 2 "
+                                   "substeps of 1 ms, %d acts per CUDA graph" % (E, acts_per_graph)},
+            "exact": res["exact"], "learned_geometry": res["learned"],
+            "learned_vs_exact": res["learned"]["value"] / res["exact"]["value"]}
 
 
 def main():
@@ -249,6 +486,13 @@ def main():
     ap.add_argument("--substeps", type=int, default=10)
     ap.add_argument("--ref-envs", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-surrogate", dest="surrogate", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--surr-samples", type=int, default=2097152)
+    ap.add_argument("--surr-epochs", type=int, default=50)
+    ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp"])
+    ap.add_argument("--policy-envs", type=int, default=16384)
+    ap.add_argument("--policy-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -257,6 +501,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         out = run_reference(args, rank)
+    elif args.workload == "c2_mixed":
+        out = run_mixed(args)
+    elif args.workload == "c4_policy":
+        out = run_policy(args)
+    elif args.workload == "c3_mlp":
+        out = run_mlp(args)
     else:
         if world > 1:
             import torch

@@ -168,6 +168,38 @@ MSIM_API msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_
 MSIM_API msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_per_block, int32_t stage_points,
                                      int32_t warps_per_env);
 
+/* ---- batching environments of different skeletons ------------------------------------------
+ * The paper runs thousands of environments of one model per GPU (Methods, "GPU-accelerated
+ * simulation framework"); a handle may hold up to 8 models.  By default msim_step issues one
+ * launch per model.  A mixed launch steps every model in ONE persistent launch: blocks take work
+ * items (a group of environments of one model for the whole call) from a queue ordered by cost
+ * per environment, re-staging a model image only when the next item belongs to another model.
+ * Results are identical to the per-model launches for the same warps_per_env.
+ *
+ * msim_set_mixed_launch -- enable (1) or disable (0).  warps_per_env 1, 2 or 4 (0: 2);
+ * slots_per_block = environments per block (0: the largest <= 8 that fits); stage_points_mask bit
+ * i = stage model i's via points in shared memory (-1: as in the per-model setting).
+ * MSIM_ERR_ARG if the shape does not fit (threads <= 512, shared memory). */
+MSIM_API msim_status msim_set_mixed_launch(msim_handle h, int32_t enable, int32_t warps_per_env,
+                                           int32_t slots_per_block, int32_t stage_points_mask);
+typedef struct {
+    int32_t mixed;                   /* 1: msim_step uses the mixed launch */
+    int32_t mixed_warps_per_env, mixed_slots, mixed_stage_points_mask;
+    int32_t warps_per_env[8], envs_per_block[8], stage_points[8];   /* per-model launches */
+    float ms_per_model;              /* best per-model launches, back to back, one call */
+    float ms_mixed;                  /* best mixed launch, one call (0: none fits) */
+    int32_t candidates;              /* configurations timed */
+    int32_t from_cache;              /* 1: taken from cache_path without timing */
+} msim_tune_result;
+/* msim_autotune -- synchronous.  Times, on the handle's own environments with n_substeps
+ * substeps per call (excitation 0), every per-model launch shape (warps per environment 1/2/4 x
+ * environments per block x via points in shared memory or not) and every mixed-launch shape,
+ * applies the fastest (per-model shapes always; the mixed launch if it beats the per-model
+ * launches back to back), and restores the state.  cache_path (may be NULL): a text file; a line
+ * whose key (models, environment counts, device, n_substeps, library version) matches is applied
+ * without timing; otherwise the result is appended.  The result goes to *out (may be NULL). */
+MSIM_API msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_substeps, msim_tune_result* out);
+
 /* msim_gemm_bf16 -- the tensor-core building block of the learned parts (surrogate, policy):
  *   C = act(A B^T + bias), A [M][K] BF16 with row pitch lda, B [N][K] BF16 with row pitch ldb
  *   (both K-contiguous; pitches multiples of 8 elements, bases 16-byte aligned), accumulated in
@@ -227,7 +259,8 @@ MSIM_API msim_status msim_mlp_adam(msim_mlp m, float lr, float beta1, float beta
  * sparse order of msim_get_layout's muscle_dof)], FP32, pitch ld_out >= m + nnz.
  *
  * msim_surrogate_train -- synchronous.  Draws n_samples configurations uniformly in the training
- * box (the joint-limit box widened by 5 % of each range; +-pi for a DoF without limits), labels
+ * box (each DoF's limit range widened by `margin` half-ranges on both sides, margin 0.05 unless
+ * msim_surrogate_set_box says otherwise; +-pi for a DoF without limits), labels
  * them with the exact geometry kernel, normalises every output by its mean and standard deviation,
  * and trains a 3-layer MLP (n -> 512 -> 512 -> m + nnz, SiLU, BF16 tensor-core GEMMs with FP32
  * accumulation) for `epochs` passes of n_samples / batch minibatches with Adam (beta 0.9, 0.999,
@@ -244,6 +277,10 @@ MSIM_API msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int3
  * use the exact one; an error above tol (default 1e-3, i.e. 1 mm for lengths and moment arms)
  * flags the environment until its msim_reset.  Mode 1 before msim_surrogate_train: MSIM_ERR_STATE. */
 MSIM_API msim_status msim_set_geometry_mode(msim_handle h, int32_t mode);
+/* msim_surrogate_set_box -- training-box margin in half-ranges, 0 <= margin <= 10, for the next
+ * msim_surrogate_train (the penalty joint limits let states pass the limits, so a box wider than
+ * the limits keeps more environments on the network). */
+MSIM_API msim_status msim_surrogate_set_box(msim_handle h, float margin);
 /* msim_surrogate_set_check -- check fraction in [0, 1] and tolerance > 0 (metres). */
 MSIM_API msim_status msim_surrogate_set_check(msim_handle h, float check_frac, float tol);
 
@@ -295,6 +332,28 @@ MSIM_API msim_status msim_mlp_forward_noalloc(int32_t in, int32_t hidden, int32_
                                               int32_t ldw1, const float* b1, const void* W2, const float* b2,
                                               const void* W3, const float* b3, const void* X, int32_t ldx, int32_t B,
                                               float* Y, int32_t ldy, uint32_t* status, msim_stream_t stream);
+
+/* ---- policy in the loop ----------------------------------------------------------------------
+ * The paper's training loop queries the control policy every 10 simulation substeps and keeps
+ * simulation and network inference on the GPU with no host round trips (Methods, "GPU-accelerated
+ * simulation framework", "Simulation parameters"); its networks are 3-layer MLPs (Methods,
+ * "Training hyperparameters").  Single-model handles.
+ *
+ * msim_policy_attach -- bind a policy network (msim_mlp_create with in >= 2 n + 2 m, out = m,
+ * sigmoid output for excitations in [0, 1], max_batch >= the handle's environments; NULL
+ * detaches).  Allocates the observation and excitation buffers (synchronous), so that
+ * msim_policy_step allocates nothing.  The network stays owned by the caller and must outlive
+ * the binding.
+ * msim_policy_step -- n_acts control steps: per step, the observation of every environment,
+ * [q (n) | qd (n) | act (m) | F / F_max (m) | 0 ...] in BF16, goes through the policy (BF16 tensor
+ * cores, FP32 accumulation) to the excitations, then msim_step advances n_substeps_per_act
+ * substeps (exact or learned geometry, per msim_set_geometry_mode).  Asynchronous: a whole
+ * rollout can be captured in a CUDA graph.
+ * msim_policy_excitations -- copy the last excitations [n_envs][pitch_m] (device pointer). */
+MSIM_API msim_status msim_policy_attach(msim_handle h, msim_mlp policy);
+MSIM_API msim_status msim_policy_step(msim_handle h, int32_t n_substeps_per_act, int32_t n_acts,
+                                      msim_stream_t stream);
+MSIM_API msim_status msim_policy_excitations(msim_handle h, float* out, msim_stream_t stream);
 
 /* msim_last_error -- text of the last failure on this handle (or of the last failed create
  *   when h is NULL).  Owned by the library, valid until the next call. */

@@ -2,14 +2,17 @@
 //
 //   C[m][n] = act( sum_k A[m][k] B[n][k] + bias[n] )      (both operands K-contiguous)
 //
-// One 128 x BN output tile per block, 192 threads in three roles:
+// One 128 x BN output tile per block (two blocks per SM, so one block's epilogue overlaps the
+// other's main loop), 192 threads in three roles:
 //   warp 0   TMA producer: 2-D tiled bulk copies (128-byte swizzle) of A and B K-slices into a
 //            ring of STAGES shared-memory slots, completion counted on the slot's `full` mbarrier;
 //   warp 1   allocates BN TMEM columns for the FP32 accumulator; one elected thread issues
 //            tcgen05.mma (kind::f16, M = 128, N = BN, K = 16 per instruction, 4 per 64-wide slice)
 //            and tcgen05.commit to release each slot (`empty`) and, at the end, the accumulator;
-//   warps 2-5 epilogue: tcgen05.ld of their 32 TMEM lanes, bias, activation, stores (FP32 or BF16,
-//            optionally also the pre-activation in BF16).
+//   warps 2-5 epilogue: tcgen05.ld of their 32 TMEM lanes (32 rows) x 32 columns at a time, bias,
+//            activation, then through a padded shared-memory block (the drained operand ring) so
+//            that the global stores run along rows, coalesced (FP32 or BF16 output, optionally
+//            also the pre-activation in BF16).
 // Every wait on an mbarrier is bounded; on expiry the block records an error code, skips its
 // stores and still frees its TMEM.  Out-of-range rows / columns of A and B read as zero (TMA
 // fill), so M, N and K need not be multiples of the tile; only the row pitches must be multiples
@@ -22,12 +25,20 @@
 
 #include "gemm_tc.h"
 
+// operand-ring depth per tile width (compile-time tuning constants)
+#ifndef MSIM_GEMM_STAGES_256
+#define MSIM_GEMM_STAGES_256 2
+#endif
+#ifndef MSIM_GEMM_STAGES_128
+#define MSIM_GEMM_STAGES_128 3
+#endif
+
 namespace msim {
 namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;                 // 64 BF16 = 128 bytes = one swizzle row
-constexpr int kStages = 3;
+constexpr int kStage = 36;              // epilogue staging row pitch (floats): 16-byte rows, no bank conflicts
 constexpr long long kSpinLimit = 1LL << 24;
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -76,14 +87,67 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// exponent clamped so that 1 + e^-x stays below 2^126, the range of the fast divide
 __device__ __forceinline__ float act_fn(float x, int act) {
-    if (act == 1) return x / (1.f + __expf(-x));     // SiLU
-    if (act == 2) return 1.f / (1.f + __expf(-x));   // sigmoid
+    if (act == 1) return __fdividef(x, 1.f + __expf(fminf(-x, 80.f)));     // SiLU
+    if (act == 2) return __fdividef(1.f, 1.f + __expf(fminf(-x, 80.f)));   // sigmoid
     return x;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(192, 1)
+// One warp's 32 rows x 32 columns of values (row = lane) from registers to global memory through
+// shared memory: written by rows, read back so that consecutive lanes store consecutive columns.
+// FP32: 8 lanes x 16 bytes per row; BF16: 4 lanes x 16 bytes per row.  Columns >= N and rows >= M
+// are not stored.
+__device__ __forceinline__ void store_block(float* stg, const float (&v)[32], int lane, void* out, int ld, bool bf16,
+                                            int row0, int col0, int M, int N, bool vec) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(&stg[lane * kStage + j]) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    __syncwarp();
+    if (!bf16) {
+        const int rs = lane >> 3, cs = (lane & 7) * 4;
+        float* C = reinterpret_cast<float*>(out);
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+            const int r = it * 4 + rs, row = row0 + r, col = col0 + cs;
+            if (row >= M) continue;
+            const float4 w = *reinterpret_cast<const float4*>(&stg[r * kStage + cs]);
+            float* dst = C + (size_t)row * ld + col;
+            if (vec && col + 4 <= N) {
+                *reinterpret_cast<float4*>(dst) = w;
+            } else {
+                const float a[4] = {w.x, w.y, w.z, w.w};
+                for (int j = 0; j < 4 && col + j < N; ++j) dst[j] = a[j];
+            }
+        }
+    } else {
+        const int rs = lane >> 2, cs = (lane & 3) * 8;
+        __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(out);
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int r = it * 8 + rs, row = row0 + r, col = col0 + cs;
+            if (row >= M) continue;
+            const float4 a = *reinterpret_cast<const float4*>(&stg[r * kStage + cs]);
+            const float4 b = *reinterpret_cast<const float4*>(&stg[r * kStage + cs + 4]);
+            __nv_bfloat16* dst = C + (size_t)row * ld + col;
+            if (vec && col + 8 <= N) {
+                uint4 w;
+                __nv_bfloat162 h0 = __floats2bfloat162_rn(a.x, a.y), h1 = __floats2bfloat162_rn(a.z, a.w);
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(b.x, b.y), h3 = __floats2bfloat162_rn(b.z, b.w);
+                w.x = *reinterpret_cast<uint32_t*>(&h0); w.y = *reinterpret_cast<uint32_t*>(&h1);
+                w.z = *reinterpret_cast<uint32_t*>(&h2); w.w = *reinterpret_cast<uint32_t*>(&h3);
+                *reinterpret_cast<uint4*>(dst) = w;
+            } else {
+                const float f[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                for (int j = 0; j < 8 && col + j < N; ++j) dst[j] = __float2bfloat16_rn(f[j]);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <int BN, int kStages>
+__global__ void __launch_bounds__(192, 2)
     k_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -162,64 +226,41 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(done))
                      : "memory");
     } else if (warp >= 2) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. output rows of that quarter
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. output rows of that quarter;
+        // once `done` fired every MMA has completed, so the operand ring is free for staging
         const bool ok = mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int quarter = warp & 3;
-        const int row = m0 + quarter * 32 + lane;
-        const bool store = ok && (*reinterpret_cast<volatile int*>(failed) == 0);
+        const int row0 = m0 + quarter * 32;
         if (!ok) atomicExch(failed, 1);
+        // warp-uniform: store_block synchronises the warp
+        const bool store = __all_sync(0xffffffffu, ok && (*reinterpret_cast<volatile int*>(failed) == 0));
+        float* stg = reinterpret_cast<float*>(smem) + quarter * 32 * kStage;
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
-            uint32_t r[16];
+        for (int c = 0; c < BN; c += 32) {
+            uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c;
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];"
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                 : "r"(taddr)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (!store || row >= p.M) continue;
+            if (!store || n0 + c >= p.N) continue;
             const int cn = n0 + c;
-            float v[16], z[16];
+            float v[32], z[32];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 32; ++j) {
                 z[j] = __uint_as_float(r[j]) + ((p.bias && cn + j < p.N) ? p.bias[cn + j] : 0.f);
                 v[j] = act_fn(z[j], p.act);
             }
-            const bool full_chunk = (cn + 16 <= p.N) && p.vec_ok;
-            if (p.c_bf16) {
-                __nv_bfloat16* C = reinterpret_cast<__nv_bfloat16*>(p.C) + (size_t)row * p.ldc + cn;
-                if (full_chunk) {
-                    uint4 w[2];
-                    uint32_t* wp = reinterpret_cast<uint32_t*>(w);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        wp[j] = *reinterpret_cast<uint32_t*>(&h2);
-                    }
-                    reinterpret_cast<uint4*>(C)[0] = w[0];
-                    reinterpret_cast<uint4*>(C)[1] = w[1];
-                } else {
-                    for (int j = 0; j < 16 && cn + j < p.N; ++j) C[j] = __float2bfloat16_rn(v[j]);
-                }
-            } else {
-                float* C = reinterpret_cast<float*>(p.C) + (size_t)row * p.ldc + cn;
-                if (full_chunk) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        reinterpret_cast<float4*>(C)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                } else {
-                    for (int j = 0; j < 16 && cn + j < p.N; ++j) C[j] = v[j];
-                }
-            }
-            if (p.Z) {
-                __nv_bfloat16* Zp = reinterpret_cast<__nv_bfloat16*>(p.Z) + (size_t)row * p.ldz + cn;
-                for (int j = 0; j < 16 && cn + j < p.N; ++j) Zp[j] = __float2bfloat16_rn(z[j]);
-            }
+            store_block(stg, v, lane, p.C, p.ldc, p.c_bf16 != 0, row0, cn, p.M, p.N, p.vec_ok != 0);
+            if (p.Z) store_block(stg, z, lane, p.Z, p.ldz, true, row0, cn, p.M, p.N, p.z_vec_ok != 0);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -256,23 +297,26 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int 
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int kStages>
 constexpr size_t gemm_smem() {
     return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
 }
+// the epilogue staging (4 warps x 32 rows x kStage floats) reuses the operand ring
+static_assert(4 * 32 * kStage * 4 <= 2 * (kBM * kBK * 2 + 128 * kBK * 2), "staging must fit in the ring");
 
-template <int BN>
+template <int BN, int kStages>
 cudaError_t launch_bn(const GemmArgs& a, const void* A, int lda, const void* B, int ldb, cudaStream_t s) {
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, a.M, a.K, lda, kBM) || !make_map(&mb, B, a.N, a.K, ldb, BN)) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem<BN>());
+        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gemm_smem<BN, kStages>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((a.N + BN - 1) / BN, (a.M + kBM - 1) / kBM);
-    k_gemm<BN><<<grid, 192, gemm_smem<BN>(), s>>>(ma, mb, a);
+    k_gemm<BN, kStages><<<grid, 192, gemm_smem<BN, kStages>(), s>>>(ma, mb, a);
     return cudaGetLastError();
 }
 
@@ -285,8 +329,10 @@ cudaError_t gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, GemmArg
         return cudaErrorInvalidValue;
     const int vec_align = args.c_bf16 ? 8 : 4;
     args.vec_ok = (args.ldc % vec_align == 0) && ((reinterpret_cast<uintptr_t>(args.C) & 15) == 0);
-    if (args.N > 128) return launch_bn<256>(args, A, lda, B, ldb, s);
-    return launch_bn<128>(args, A, lda, B, ldb, s);
+    args.z_vec_ok = args.Z && (args.ldz % 8 == 0) && ((reinterpret_cast<uintptr_t>(args.Z) & 15) == 0);
+    // two blocks per SM (<= 113 KB of shared memory and <= 256 TMEM columns each)
+    if (args.N > 128) return launch_bn<256, MSIM_GEMM_STAGES_256>(args, A, lda, B, ldb, s);
+    return launch_bn<128, MSIM_GEMM_STAGES_128>(args, A, lda, B, ldb, s);
 }
 
 }  // namespace msim

@@ -16,6 +16,7 @@ struct GemmArgs {
     int ldz;
     uint32_t* err;        // optional device word: bit 0 set if a bounded wait expired
     int vec_ok;           // set by gemm_bf16_tc
+    int z_vec_ok;         // set by gemm_bf16_tc
 };
 
 // C = act(A B^T + bias): A [M][K] BF16 (pitch lda), B [N][K] BF16 (pitch ldb), pitches multiples

@@ -54,6 +54,28 @@ constexpr int kMaxEnvsPerBlock = 16;
 
 cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
+// One model of a mixed launch, in queue order.
+struct MixedModel {
+    const uint8_t* img;
+    int staged_bytes;             // bytes of the image staged to shared memory (multiple of 16)
+    int points_in_smem;
+    int env_begin, env_end;
+    int epb;                      // environments per work item (<= slots)
+    int item_begin;               // first work item of this model
+};
+// All models in one persistent launch: a.q ... a.gflags, a.n_sub, a.dt and a.wpe are shared;
+// a.img / env range / envs_per_block are unused.
+struct MixedArgs {
+    StepArgs a;
+    int n_models;
+    MixedModel mdl[kMaxModels];
+    int n_items;
+    int slots;                    // environment slots per block (threads = 32 wpe slots)
+    int img_region;               // shared bytes reserved for the image (max over models, 128-aligned)
+    uint32_t* queue;              // work counter (zeroed by launch_mixed before the kernel)
+};
+cudaError_t launch_mixed(const MixedArgs& m, int grid, size_t smem, cudaStream_t s);
+int mixed_blocks_per_sm(int threads, size_t smem, int wpe);
 cudaError_t launch_geom(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_surr_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 // network input rows X[r] = bf16((q[env_begin + r] - c) / sc), pad columns 0; advances *step_ctr
@@ -61,6 +83,9 @@ cudaError_t launch_surr_step(const StepArgs& a, int grid, size_t smem, cudaStrea
 cudaError_t launch_surr_input(const float* q, int pitch_n, int env_begin, int n_envs, const float* c, const float* sc,
                               int n, __nv_bfloat16* X, int ldx, uint32_t* step_ctr, cudaStream_t s);
 cudaError_t launch_set_l0(uint8_t* img, const float* L, int m, cudaStream_t s);
+// policy observation rows [q | qd | act | force * inv_fmax | 0], BF16, pitch ldx (policy.cu)
+cudaError_t launch_obs(const float* q, const float* qd, const float* act, const float* force, const float* inv_fmax,
+                       int pitch_n, int pitch_m, int n, int m, int n_envs, __nv_bfloat16* X, int ldx, cudaStream_t s);
 // fallback (optional): per-environment surrogate fallback flags, cleared with the state
 cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
                          const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,

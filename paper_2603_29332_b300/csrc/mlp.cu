@@ -226,6 +226,14 @@ cudaError_t mlp_forward(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y
     return gemm(m->H2, h, m->Ph + m->oW3, h, B, m->out, h, Y, ldy, 0, m->P + m->ob3, m->out_act, nullptr, 0, m->err, s);
 }
 
+cudaError_t mlp_infer(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s) {
+    if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;
+    const int h = m->hid;
+    CK(gemm(X, ldx, m->Ph + m->oW1, m->inp, B, h, m->in, m->H1, h, 1, m->P + m->ob1, 1, nullptr, 0, m->err, s));
+    CK(gemm(m->H1, h, m->Ph + m->oW2, h, B, h, h, m->H2, h, 1, m->P + m->ob2, 1, nullptr, 0, m->err, s));
+    return gemm(m->H2, h, m->Ph + m->oW3, h, B, m->out, h, Y, ldy, 0, m->P + m->ob3, m->out_act, nullptr, 0, m->err, s);
+}
+
 cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T, int ldt, int B, cudaStream_t s) {
     if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;
     const int h = m->hid, bp = pad8(B);

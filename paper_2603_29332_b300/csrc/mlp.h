@@ -44,6 +44,8 @@ cudaError_t mlp_init(Mlp* m, uint64_t seed, float out_scale, cudaStream_t s);
 cudaError_t mlp_sync_bf16(Mlp* m, cudaStream_t s);
 // Y [B][ldy] = mlp(X), X [B][ldx] BF16 (ldx multiple of 8, columns >= in ignored)
 cudaError_t mlp_forward(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s);
+// the same without the pre-activation copies a later backward needs (inference)
+cudaError_t mlp_infer(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s);
 // gradients of mean((y - t)^2) into G (forward included); T [B][ldt] FP32
 cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T, int ldt, int B, cudaStream_t s);
 // one Adam step (Kingma & Ba 2015) on G, refreshes the BF16 copies

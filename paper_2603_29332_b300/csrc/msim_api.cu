@@ -19,6 +19,7 @@
 #include "mlp.h"
 #include "image.h"
 #include "surrogate.h"
+#include "handle.h"
 #include "kernels.h"
 
 using namespace msim;
@@ -26,12 +27,6 @@ using namespace msim;
 namespace {
 
 thread_local std::string g_create_error;
-
-struct ModelHost {
-    ImgHeader hdr;
-    std::vector<uint8_t> blob;
-    std::vector<int32_t> dof_parent, dof_depth, packed_row, mus_ptr, mus_dof;
-};
 
 int pad4(int x) { return (x + 3) & ~3; }
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -385,35 +380,8 @@ namespace msim {
 void set_global_error(const char* what) { g_create_error = what; }
 }  // namespace msim
 
-struct msim_mlp_ {
-    Mlp* m = nullptr;
-    bool borrowed = false;   // owned by a simulator handle (its surrogate network)
-};
-
-struct msim_handle_ {
-    int device = 0;
-    int geometry_mode = 0;
-    uint32_t seed = 0;
-    Surrogate* sur = nullptr;
-    msim_mlp_ sur_view;
-    int n_models = 0, n_envs = 0, pitch_n = 0, pitch_m = 0;
-    float dt = 0.f;
-    int num_sms = 0;
-    size_t smem_optin = 0;
-    ModelHost models[kMaxModels];
-    uint8_t* d_img[kMaxModels] = {};
-    int env_begin[kMaxModels + 1] = {};
-    int epb[kMaxModels] = {};
-    int pts_smem[kMaxModels] = {};
-    int wpe[kMaxModels] = {};
-    float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *exc_stage = nullptr;
-    uint32_t* env_status = nullptr;
-    uint32_t* gflags = nullptr;
-    unsigned long long* timers = nullptr;   // profiling builds (MSIM_PHASE_TIMERS) only
-    std::string err;
-};
-
-namespace {
+namespace msim {
+namespace host {
 
 msim_status cuda_fail(msim_handle h, cudaError_t e, const char* what) {
     char buf[256];
@@ -428,25 +396,6 @@ msim_status arg_fail(msim_handle h, const char* what) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-void surr_free(Surrogate* s) {
-    if (!s) return;
-    if (s->net) mlp_destroy(s->net);
-    cudaFree(s->mu); cudaFree(s->sd); cudaFree(s->box_c); cudaFree(s->box_s);
-    cudaFree(s->X); cudaFree(s->Y); cudaFree(s->fallback); cudaFree(s->stats); cudaFree(s->step_ctr);
-    cudaFree(s->out_tmp);
-    delete s;
-}
-
-void free_all(msim_handle h) {
-    surr_free(h->sur);
-    h->sur = nullptr;
-    for (int i = 0; i < kMaxModels; ++i)
-        if (h->d_img[i]) cudaFree(h->d_img[i]);
-    cudaFree(h->q); cudaFree(h->qd); cudaFree(h->act); cudaFree(h->qdd); cudaFree(h->force);
-    cudaFree(h->exc_stage); cudaFree(h->env_status); cudaFree(h->gflags);
-    if (h->timers) cudaFree(h->timers);
-}
 
 int model_grid(msim_handle h, int i) {
     const int ne = h->env_begin[i + 1] - h->env_begin[i];
@@ -497,6 +446,33 @@ void auto_launch(msim_handle h, int i) {
     else { h->pts_smem[i] = 0; h->epb[i] = e_out; }
 }
 
+}  // namespace host
+}  // namespace msim
+
+using namespace msim::host;
+
+namespace {
+
+void surr_free(Surrogate* s) {
+    if (!s) return;
+    if (s->net) mlp_destroy(s->net);
+    cudaFree(s->mu); cudaFree(s->sd); cudaFree(s->box_c); cudaFree(s->box_s);
+    cudaFree(s->X); cudaFree(s->Y); cudaFree(s->fallback); cudaFree(s->stats); cudaFree(s->step_ctr);
+    cudaFree(s->out_tmp);
+    delete s;
+}
+
+void free_all(msim_handle h) {
+    surr_free(h->sur);
+    h->sur = nullptr;
+    for (int i = 0; i < kMaxModels; ++i)
+        if (h->d_img[i]) cudaFree(h->d_img[i]);
+    cudaFree(h->q); cudaFree(h->qd); cudaFree(h->act); cudaFree(h->qdd); cudaFree(h->force);
+    cudaFree(h->exc_stage); cudaFree(h->env_status); cudaFree(h->gflags); cudaFree(h->queue);
+    cudaFree(h->obs); cudaFree(h->exc_policy); cudaFree(h->inv_fmax);
+    if (h->timers) cudaFree(h->timers);
+}
+
 // geometry-mode launch of model i over rows [0, n_rows) of q (pitch ldq) into out (pitch ldo)
 cudaError_t geometry_launch(msim_handle h, int i, const float* q, int ldq, int n_rows, float* out, int ldo,
                             cudaStream_t s) {
@@ -531,7 +507,7 @@ msim_status surrogate_step(msim_handle h, const float* exc, int n_sub, cudaStrea
     for (int k = 0; k < n_sub; ++k) {
         cudaError_t e = launch_surr_input(h->q, h->pitch_n, 0, h->n_envs, S->box_c, S->box_s, S->n, S->X, net->inp,
                                           S->step_ctr, s);
-        if (e == cudaSuccess) e = mlp_forward(S->net, S->X, net->inp, h->n_envs, S->Y, net->outp, s);
+        if (e == cudaSuccess) e = mlp_infer(S->net, S->X, net->inp, h->n_envs, S->Y, net->outp, s);
         if (e == cudaSuccess) {
             StepArgs a = base_args(h, 0);
             a.exc = exc;
@@ -627,6 +603,7 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
     ALLOC(h->act, rm); ALLOC(h->force, rm); ALLOC(h->exc_stage, rm);
     ALLOC(h->env_status, sizeof(uint32_t) * total);
     ALLOC(h->gflags, sizeof(uint32_t));
+    ALLOC(h->queue, sizeof(uint32_t));
 #ifdef MSIM_PHASE_TIMERS
     ALLOC(h->timers, sizeof(unsigned long long) * 16);
     cudaMemset(h->timers, 0, sizeof(unsigned long long) * 16);
@@ -766,17 +743,8 @@ msim_status msim_step(msim_handle h, const float* excitations, int32_t n_substep
     if (!aligned16(excitations)) return arg_fail(h, "msim_step: excitations not 16-byte aligned");
     cudaSetDevice(h->device);
     if (h->geometry_mode == 1) return surrogate_step(h, excitations, n_substeps, (cudaStream_t)stream);
-    for (int i = 0; i < h->n_models; ++i) {
-        if (h->env_begin[i + 1] == h->env_begin[i]) continue;
-        StepArgs a = base_args(h, i);
-        a.exc = excitations;
-        a.n_sub = n_substeps;
-        const cudaError_t e = launch_step(a, model_grid(h, i),
-                                          step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i], h->wpe[i]),
-                                          (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "msim_step launch");
-    }
-    return MSIM_OK;
+    const cudaError_t e = launch_all(h, excitations, n_substeps, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_step launch");
 }
 
 msim_status msim_step_host(msim_handle h, const float* excitations_host, int32_t n_substeps, float* q_host,
@@ -968,7 +936,7 @@ msim_status msim_mlp_forward(msim_mlp h, const void* X, int32_t ldx, int32_t B, 
                              msim_stream_t stream) {
     if (!h || !X || !Y || B < 1 || B > h->m->max_batch || ldx < h->m->inp || ldx % 8 || ldy < h->m->out)
         return arg_fail(nullptr, "msim_mlp_forward: bad argument");
-    const cudaError_t e = mlp_forward(h->m, (const __nv_bfloat16*)X, ldx, B, Y, ldy, (cudaStream_t)stream);
+    const cudaError_t e = mlp_infer(h->m, (const __nv_bfloat16*)X, ldx, B, Y, ldy, (cudaStream_t)stream);
     return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_mlp_forward");
 }
 
@@ -1029,11 +997,16 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
         h->err = "msim_surrogate_train: not enough device memory for the labels";
         return MSIM_ERR_OOM;
     }
+    const float margin = h->sur ? h->sur->box_margin : h->box_margin;
+    const float check_frac = h->sur ? h->sur->check_frac : 0.01f, tol = h->sur ? h->sur->tol : 1e-3f;
     surr_free(h->sur);
     h->sur = nullptr;
     Surrogate* S = new Surrogate();
     S->n = n; S->m = m; S->nnz = nnz; S->out = out;
     S->seed = h->seed;
+    S->box_margin = margin;
+    S->check_frac = check_frac;
+    S->tol = tol;
     cudaError_t e = mlp_create(n, kSurrHidden, out, 0, std::max(batch, h->n_envs), &S->net);
     if (e == cudaSuccess) e = mlp_init(S->net, (uint64_t)h->seed * 2654435761ull + 17u, 1.f, s);
     auto A = [&](void** p, size_t b) {
@@ -1051,13 +1024,13 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
     A((void**)&Xall, (size_t)N * inp * 2); A((void**)&T, (size_t)N * outp * 4);
     A((void**)&qc, (size_t)chunk * h->pitch_n * 4); A((void**)&acc, (size_t)outp * 16);
     if (e == cudaSuccess) {
-        // training box: joint limits widened by 5 % of the range; +-pi without limits
+        // training box: joint limits widened by box_margin half-ranges on each side; +-pi without limits
         std::vector<float> c(h->pitch_n, 0.f), sc(h->pitch_n, 1.f);
         const DofRec* D = reinterpret_cast<const DofRec*>(h->models[0].blob.data() + hd.o_dof);
         for (int d = 0; d < n; ++d) {
             if (D[d].lo < D[d].hi) {
                 c[d] = 0.5f * (D[d].lo + D[d].hi);
-                sc[d] = 0.5f * (D[d].hi - D[d].lo) * 1.05f;
+                sc[d] = 0.5f * (D[d].hi - D[d].lo) * (1.f + margin);
             } else {
                 c[d] = 0.f;
                 sc[d] = 3.14159265f;
@@ -1139,6 +1112,13 @@ msim_status msim_set_geometry_mode(msim_handle h, int32_t mode) {
     return MSIM_OK;
 }
 
+msim_status msim_surrogate_set_box(msim_handle h, float margin) {
+    if (!h || !(margin >= 0.f && margin <= 10.f)) return arg_fail(h, "msim_surrogate_set_box: margin in [0, 10]");
+    h->box_margin = margin;
+    if (h->sur) h->sur->box_margin = margin;   // takes effect at the next msim_surrogate_train
+    return MSIM_OK;
+}
+
 msim_status msim_surrogate_set_check(msim_handle h, float check_frac, float tol) {
     if (!h || !(check_frac >= 0.f && check_frac <= 1.f) || !(tol > 0.f) || !std::isfinite(tol))
         return arg_fail(h, "msim_surrogate_set_check: check_frac in [0, 1], tol > 0");
@@ -1201,11 +1181,79 @@ msim_status msim_surrogate_predict(msim_handle h, const float* q, int32_t ldq, i
     for (int r0 = 0; r0 < n_rows && e == cudaSuccess; r0 += h->n_envs) {
         const int rows = std::min(h->n_envs, n_rows - r0);
         e = launch_surr_input(q, ldq, r0, rows, S->box_c, S->box_s, S->n, S->X, S->net->inp, nullptr, s);
-        if (e == cudaSuccess) e = mlp_forward(S->net, S->X, S->net->inp, rows, S->out_tmp, S->net->outp, s);
+        if (e == cudaSuccess) e = mlp_infer(S->net, S->X, S->net->inp, rows, S->out_tmp, S->net->outp, s);
         if (e == cudaSuccess)
             e = surr_denorm(S->out_tmp, S->net->outp, rows, S->out, S->mu, S->sd, out + (size_t)r0 * ld_out, ld_out, s);
     }
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_surrogate_predict");
+}
+
+// ------------------------------------------------------------------ policy in the loop
+msim_status msim_policy_attach(msim_handle h, msim_mlp policy) {
+    if (!h) return arg_fail(h, "msim_policy_attach: NULL handle");
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->obs); cudaFree(h->exc_policy); cudaFree(h->inv_fmax);
+    h->obs = nullptr; h->exc_policy = nullptr; h->inv_fmax = nullptr; h->policy = nullptr;
+    if (!policy) return MSIM_OK;   // detach
+    if (h->n_models != 1) {
+        h->err = "msim_policy_attach: single-model handles only";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    const ImgHeader& hd = h->models[0].hdr;
+    Mlp* p = policy->m;
+    if (p->in < 2 * hd.n + 2 * hd.m || p->out != hd.m || p->max_batch < h->n_envs)
+        return arg_fail(h, "msim_policy_attach: policy needs in >= 2 n + 2 m, out = m, max_batch >= n_envs");
+    std::vector<float> inv(h->pitch_m, 0.f);
+    const MuscleRec* M = reinterpret_cast<const MuscleRec*>(h->models[0].blob.data() + hd.o_muscle);
+    for (int r = 0; r < hd.m; ++r) inv[M[r].orig] = 1.f / M[r].fmax;
+    cudaError_t e = cudaMalloc(&h->obs, (size_t)h->n_envs * p->inp * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&h->exc_policy, (size_t)h->n_envs * h->pitch_m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->inv_fmax, (size_t)h->pitch_m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(h->inv_fmax, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->exc_policy, 0, (size_t)h->n_envs * h->pitch_m * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(h->obs); cudaFree(h->exc_policy); cudaFree(h->inv_fmax);
+        h->obs = nullptr; h->exc_policy = nullptr; h->inv_fmax = nullptr;
+        return cuda_fail(h, e, "msim_policy_attach");
+    }
+    h->policy = p;
+    return MSIM_OK;
+}
+
+msim_status msim_policy_step(msim_handle h, int32_t n_substeps_per_act, int32_t n_acts, msim_stream_t stream) {
+    if (!h) return arg_fail(h, "msim_policy_step: NULL handle");
+    if (!h->policy) {
+        h->err = "msim_policy_step: no policy attached (msim_policy_attach)";
+        return MSIM_ERR_STATE;
+    }
+    if (n_substeps_per_act < 1 || n_substeps_per_act > 100000 || n_acts < 0)
+        return arg_fail(h, "msim_policy_step: n_substeps_per_act 1..100000, n_acts >= 0");
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const ImgHeader& hd = h->models[0].hdr;
+    Mlp* p = h->policy;
+    for (int k = 0; k < n_acts; ++k) {
+        cudaError_t e = launch_obs(h->q, h->qd, h->act, h->force, h->inv_fmax, h->pitch_n, h->pitch_m, hd.n, hd.m,
+                                   h->n_envs, h->obs, p->inp, s);
+        if (e == cudaSuccess) e = mlp_infer(p, h->obs, p->inp, h->n_envs, h->exc_policy, h->pitch_m, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "msim_policy_step (policy)");
+        const msim_status st = msim_step(h, h->exc_policy, n_substeps_per_act, stream);
+        if (st != MSIM_OK) return st;
+    }
+    return MSIM_OK;
+}
+
+msim_status msim_policy_excitations(msim_handle h, float* out, msim_stream_t stream) {
+    if (!h || !out) return arg_fail(h, "msim_policy_excitations: NULL argument");
+    if (!h->exc_policy) {
+        h->err = "msim_policy_excitations: no policy attached";
+        return MSIM_ERR_STATE;
+    }
+    cudaSetDevice(h->device);
+    const cudaError_t e = cudaMemcpyAsync(out, h->exc_policy, (size_t)h->n_envs * h->pitch_m * sizeof(float),
+                                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_policy_excitations");
 }
 
 #ifdef MSIM_PHASE_TIMERS

@@ -230,7 +230,7 @@ __device__ bool stage_image(uint8_t* dst, const uint8_t* src, int bytes, uint64_
         if (threadIdx.x == 0) atomicOr(gflags, kFlagTimeout);
         mbar_wait(mb, 0);   // give copies still in flight a second bounded chance to land
     }
-    return ok;
+    return __syncthreads_and(ok) != 0;   // one outcome for the whole block
 }
 
 // ------------------------------------------------------------------ phase 1: kinematics
@@ -591,7 +591,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                     const int o = mm + M.x0 + i;
                     e = fmaxf(e, fabsf(sc->Y[o] * sc->sd[o] + sc->mu[o] - rk[i * g.N + g.lane]));
                 }
-                if (e > sc->tol) flags |= 2u;
+                if (!(e <= sc->tol)) flags |= 2u;   // a non-finite state or output fails too
                 if (e > 0.f) atomicMax(sc->max_err_bits, __float_as_uint(e));
             } else {
                 L = Ls;
@@ -961,6 +961,101 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     return st;
 }
 
+// One environment e through one call (n_sub substeps, or one eval / geometry / learned-geometry
+// substep): state row from global memory into the group's workspace, the substeps, state and
+// status back.  Every lane of the group calls it.
+template <int MODE, int WPE>
+__device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, float* ws, const Grp<WPE>& g, int e) {
+    const ImgHeader& H = *T.H;
+    const size_t rn = (size_t)e * a.pitch_n, rm = (size_t)e * a.pitch_m;
+    for (int i = g.lane; i < H.n; i += g.N) {
+        ws[H.w_q + i] = a.q[rn + i];
+        ws[H.w_qd + i] = a.qd[rn + i];
+    }
+    g.sync();
+    uint32_t st = 0;
+    if ((MODE == kModeEval)) {
+        EvalPtrs ev = a.ev;
+        auto off = [&](float* p, size_t pitch) { return p ? p + (size_t)e * pitch : p; };
+        ev.L = off(ev.L, a.pitch_m); ev.lm = off(ev.lm, a.pitch_m); ev.vm = off(ev.vm, a.pitch_m);
+        ev.force = off(ev.force, a.pitch_m); ev.act_next = off(ev.act_next, a.pitch_m);
+        ev.R = off(ev.R, ev.nnz_pitch);
+        ev.tau_m = off(ev.tau_m, a.pitch_n); ev.tau_c = off(ev.tau_c, a.pitch_n);
+        ev.tau_l = off(ev.tau_l, a.pitch_n); ev.bias = off(ev.bias, a.pitch_n); ev.rhs = off(ev.rhs, a.pitch_n);
+        ev.qdd = off(ev.qdd, a.pitch_n);
+        ev.M = off(ev.M, ev.packed_pitch); ev.A = off(ev.A, ev.packed_pitch);
+        for (int d = g.lane; d < H.n; d += g.N) {
+            if (ev.tau_m) ev.tau_m[d] = 0.f;
+            if (ev.tau_c) ev.tau_c[d] = 0.f;
+            if (ev.tau_l) ev.tau_l[d] = 0.f;
+        }
+        g.sync();
+        st |= substep<kModeEval>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, nullptr, a.timers);
+    } else if (MODE == kModeGeom) {
+        EvalPtrs ev = a.ev;
+        ev.L = a.ev.L + (size_t)(e - a.env_begin) * ev.nnz_pitch;   // label row: L then R
+        ev.R = ev.L + H.m;
+        substep<kModeGeom>(T, ws, g, a.dt, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
+    } else {
+        if (MODE == kModeSurr) {
+            // one substep with the learned geometry (the host loops over substeps)
+            bool oob = false;
+            for (int d = g.lane; d < H.n; d += g.N)   // a non-finite q counts as outside
+                oob |= !(fabsf(ws[H.w_q + d] - a.box_c[d]) <= a.box_s[d]);
+            oob = g.any(oob);
+            const bool flagged = a.fallback[e] != 0;
+            uint32_t c[4] = {(uint32_t)e, *a.step_ctr, 0x73u, 0x75u};
+            philox4x32_10(c, a.surr_seed, 0x9e3779b9u);
+            SurrCtx sc;
+            sc.Y = a.surr_Y + (size_t)(e - a.env_begin) * a.surr_ld;
+            sc.mu = a.surr_mu;
+            sc.sd = a.surr_sd;
+            sc.use_exact = oob || flagged;
+            sc.check = !sc.use_exact && u01_from_bits(c[0]) < a.check_frac;
+            sc.tol = a.tol;
+            sc.max_err_bits = reinterpret_cast<unsigned int*>(a.surr_stats + 6);
+            const uint32_t s1 = substep<kModeSurr>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+                                                   a.force_out ? a.force_out + rm : nullptr, nullptr, &sc, a.timers);
+            st |= s1 & 0xffu;
+            if (g.lane == 0) {
+                unsigned long long* cs = a.surr_stats;   // see msim_surrogate_stats
+                atomicAdd(&cs[0], 1ull);
+                if (!sc.use_exact && !sc.check) atomicAdd(&cs[1], 1ull);
+                if (oob) atomicAdd(&cs[2], 1ull);
+                if (flagged) atomicAdd(&cs[3], 1ull);
+                if (sc.check) atomicAdd(&cs[4], 1ull);
+                if (s1 & 0x100u) {
+                    atomicAdd(&cs[5], 1ull);
+                    a.fallback[e] = 1;   // exact geometry for this environment until its reset
+                }
+            }
+        } else {
+            for (int s = 0; s < a.n_sub; ++s) {
+                const bool last = (s == a.n_sub - 1);
+                st |= substep<kModeStep>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+                                         (last && a.force_out) ? a.force_out + rm : nullptr, nullptr, nullptr,
+                                         a.timers);
+            }
+        }
+        bool bad = false;
+        const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
+        for (int d = g.lane; d < H.n; d += g.N) {
+            const float v0 = ws[H.w_q + d], v1 = ws[H.w_qd + d];
+            bad |= !(isfinite(v0) && isfinite(v1));
+            a.q[rn + d] = v0;
+            a.qd[rn + d] = v1;
+            if (a.qdd_out) a.qdd_out[rn + d] = Y[d].hi + Y[d].lo;
+        }
+        for (int k = g.lane; k < H.m; k += g.N) bad |= !isfinite(a.act[rm + k]);
+        if (g.any(bad)) st |= kEnvNonFinite;
+    }
+    if (st && g.lane == 0) {
+        atomicOr(&a.env_status[e], st);
+        atomicOr(a.gflags, st);
+    }
+    g.sync();
+}
+
 // ------------------------------------------------------------------ kernels
 template <int MODE, int WPE>
 __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
@@ -990,92 +1085,79 @@ __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
     for (int gi = blockIdx.x; gi < n_groups; gi += gridDim.x) {
         const int e = a.env_begin + gi * a.envs_per_block + slot;
         if (e >= a.env_end) continue;
-        const size_t rn = (size_t)e * a.pitch_n, rm = (size_t)e * a.pitch_m;
-        for (int i = g.lane; i < H.n; i += g.N) {
-            ws[H.w_q + i] = a.q[rn + i];
-            ws[H.w_qd + i] = a.qd[rn + i];
-        }
-        g.sync();
-        uint32_t st = 0;
-        if ((MODE == kModeEval)) {
-            EvalPtrs ev = a.ev;
-            auto off = [&](float* p, size_t pitch) { return p ? p + (size_t)e * pitch : p; };
-            ev.L = off(ev.L, a.pitch_m); ev.lm = off(ev.lm, a.pitch_m); ev.vm = off(ev.vm, a.pitch_m);
-            ev.force = off(ev.force, a.pitch_m); ev.act_next = off(ev.act_next, a.pitch_m);
-            ev.R = off(ev.R, ev.nnz_pitch);
-            ev.tau_m = off(ev.tau_m, a.pitch_n); ev.tau_c = off(ev.tau_c, a.pitch_n);
-            ev.tau_l = off(ev.tau_l, a.pitch_n); ev.bias = off(ev.bias, a.pitch_n); ev.rhs = off(ev.rhs, a.pitch_n);
-            ev.qdd = off(ev.qdd, a.pitch_n);
-            ev.M = off(ev.M, ev.packed_pitch); ev.A = off(ev.A, ev.packed_pitch);
-            for (int d = g.lane; d < H.n; d += g.N) {
-                if (ev.tau_m) ev.tau_m[d] = 0.f;
-                if (ev.tau_c) ev.tau_c[d] = 0.f;
-                if (ev.tau_l) ev.tau_l[d] = 0.f;
-            }
-            g.sync();
-            st |= substep<kModeEval>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, nullptr, a.timers);
-        } else if (MODE == kModeGeom) {
-            EvalPtrs ev = a.ev;
-            ev.L = a.ev.L + (size_t)(e - a.env_begin) * ev.nnz_pitch;   // label row: L then R
-            ev.R = ev.L + H.m;
-            substep<kModeGeom>(T, ws, g, a.dt, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
-        } else {
-            if (MODE == kModeSurr) {
-                // one substep with the learned geometry (the host loops over substeps)
-                bool oob = false;
-                for (int d = g.lane; d < H.n; d += g.N) oob |= fabsf(ws[H.w_q + d] - a.box_c[d]) > a.box_s[d];
-                oob = g.any(oob);
-                const bool flagged = a.fallback[e] != 0;
-                uint32_t c[4] = {(uint32_t)e, *a.step_ctr, 0x73u, 0x75u};
-                philox4x32_10(c, a.surr_seed, 0x9e3779b9u);
-                SurrCtx sc;
-                sc.Y = a.surr_Y + (size_t)(e - a.env_begin) * a.surr_ld;
-                sc.mu = a.surr_mu;
-                sc.sd = a.surr_sd;
-                sc.use_exact = oob || flagged;
-                sc.check = !sc.use_exact && u01_from_bits(c[0]) < a.check_frac;
-                sc.tol = a.tol;
-                sc.max_err_bits = reinterpret_cast<unsigned int*>(a.surr_stats + 6);
-                const uint32_t s1 = substep<kModeSurr>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
-                                                       a.force_out ? a.force_out + rm : nullptr, nullptr, &sc, a.timers);
-                st |= s1 & 0xffu;
-                if (g.lane == 0) {
-                    unsigned long long* cs = a.surr_stats;   // see msim_surrogate_stats
-                    atomicAdd(&cs[0], 1ull);
-                    if (!sc.use_exact && !sc.check) atomicAdd(&cs[1], 1ull);
-                    if (oob) atomicAdd(&cs[2], 1ull);
-                    if (flagged) atomicAdd(&cs[3], 1ull);
-                    if (sc.check) atomicAdd(&cs[4], 1ull);
-                    if (s1 & 0x100u) {
-                        atomicAdd(&cs[5], 1ull);
-                        a.fallback[e] = 1;   // exact geometry for this environment until its reset
-                    }
-                }
-            } else {
-                for (int s = 0; s < a.n_sub; ++s) {
-                    const bool last = (s == a.n_sub - 1);
-                    st |= substep<kModeStep>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
-                                             (last && a.force_out) ? a.force_out + rm : nullptr, nullptr, nullptr,
-                                             a.timers);
+        run_env<MODE, WPE>(a, T, ws, g, e);
+    }
+}
+
+// ------------------------------------------------------------------ mixed-model persistent kernel
+// All models of a handle in one launch.  Work items (one group of up to `epb` environments of one
+// model, n_sub substeps) are taken from a global counter in queue order (models ordered by cost
+// per environment, most expensive first, so the cheap items fill the tail).  A block re-stages
+// the model image only when its next item belongs to another model.
+template <int WPE>
+__global__ void __launch_bounds__(512, 1) k_step_mixed(MixedArgs ma) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    int* s_item = reinterpret_cast<int*>(smem + 8);
+    uint8_t* img = smem + 16;
+    const uint32_t mb = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const int slot = warp / WPE;
+    Grp<WPE> g;
+    g.wl = threadIdx.x & 31;
+    g.wi = warp % WPE;
+    g.lane = g.wi * 32 + g.wl;
+    g.bar = 1 + slot;
+    float* ws_all = reinterpret_cast<float*>(img + ma.img_region);
+    uint32_t phase = 0;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) *s_item = (int)atomicAdd(ma.queue, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();   // every thread has read the item (and left the previous one's image)
+        if (item >= ma.n_items) break;
+        int i = 0;
+        while (i + 1 < ma.n_models && item >= ma.mdl[i + 1].item_begin) ++i;
+        const MixedModel& M = ma.mdl[i];
+        if (i != cur) {
+            if (threadIdx.x == 0) {
+                // the generic-proxy reads of the previous image are ordered before the async copies
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(M.staged_bytes)
+                             : "memory");
+                const uint32_t d = smem_u32(img);
+                constexpr int kChunk = 32768;
+                for (int off = 0; off < M.staged_bytes; off += kChunk) {
+                    const int sz = (M.staged_bytes - off) < kChunk ? (M.staged_bytes - off) : kChunk;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            d + off),
+                        "l"(M.img + off), "r"(sz), "r"(mb)
+                        : "memory");
                 }
             }
-            bool bad = false;
-            const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
-            for (int d = g.lane; d < H.n; d += g.N) {
-                const float v0 = ws[H.w_q + d], v1 = ws[H.w_qd + d];
-                bad |= !(isfinite(v0) && isfinite(v1));
-                a.q[rn + d] = v0;
-                a.qd[rn + d] = v1;
-                if (a.qdd_out) a.qdd_out[rn + d] = Y[d].hi + Y[d].lo;
+            bool ok = mbar_wait(mb, phase & 1u);
+            if (!ok) {
+                if (threadIdx.x == 0) atomicOr(ma.a.gflags, kFlagTimeout);
+                mbar_wait(mb, phase & 1u);   // a second bounded chance for copies in flight
             }
-            for (int k = g.lane; k < H.m; k += g.N) bad |= !isfinite(a.act[rm + k]);
-            if (g.any(bad)) st |= kEnvNonFinite;
+            ++phase;
+            if (!__syncthreads_and(ok)) return;
+            cur = i;
         }
-        if (st && g.lane == 0) {
-            atomicOr(&a.env_status[e], st);
-            atomicOr(a.gflags, st);
+        Tables T = make_tables(img);
+        if (!M.points_in_smem) T.pt = reinterpret_cast<const PointRec*>(M.img + T.H->o_point);
+        float* ws = ws_all + (size_t)slot * ws_floats(*T.H, WPE);
+        if (slot < M.epb) {
+            const int e = M.env_begin + (item - M.item_begin) * M.epb + slot;
+            if (e < M.env_end) run_env<kModeStep, WPE>(ma.a, T, ws, g, e);
         }
-        g.sync();
     }
 }
 
@@ -1127,7 +1209,8 @@ cudaError_t set_step_smem_limit(size_t bytes) {
                          (const void*)k_step<kModeEval, 2>, (const void*)k_step<kModeEval, 4>,
                          (const void*)k_step<kModeGeom, 1>, (const void*)k_step<kModeGeom, 2>,
                          (const void*)k_step<kModeSurr, 1>, (const void*)k_step<kModeSurr, 2>,
-                         (const void*)k_step<kModeSurr, 4>};
+                         (const void*)k_step<kModeSurr, 4>, (const void*)k_step_mixed<1>,
+                         (const void*)k_step_mixed<2>, (const void*)k_step_mixed<4>};
     for (const void* f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         if (e != cudaSuccess) return e;
@@ -1141,6 +1224,25 @@ cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s
     else if (a.wpe == 2) k_step<kModeStep, 2><<<grid, threads, smem, s>>>(a);
     else k_step<kModeStep, 1><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mixed(const MixedArgs& m, int grid, size_t smem, cudaStream_t s) {
+    const int threads = 32 * m.a.wpe * m.slots;
+    cudaError_t e = cudaMemsetAsync(m.queue, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    if (m.a.wpe == 4) k_step_mixed<4><<<grid, threads, smem, s>>>(m);
+    else if (m.a.wpe == 2) k_step_mixed<2><<<grid, threads, smem, s>>>(m);
+    else k_step_mixed<1><<<grid, threads, smem, s>>>(m);
+    return cudaGetLastError();
+}
+
+int mixed_blocks_per_sm(int threads, size_t smem, int wpe) {
+    int n = 0;
+    cudaError_t e;
+    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<4>, threads, smem);
+    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<2>, threads, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<1>, threads, smem);
+    return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {

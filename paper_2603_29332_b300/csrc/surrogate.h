@@ -32,6 +32,7 @@ struct Surrogate {
     float* out_tmp = nullptr;             // [n_envs][outp] network output for msim_surrogate_predict
     uint32_t seed = 0;
     float check_frac = 0.01f, tol = 1e-3f;
+    float box_margin = 0.05f;             // box half-width = (1 + margin) x half the limit range
     int trained = 0;
     float loss = 0.f;                     // mean squared normalised error of the last epoch
 };

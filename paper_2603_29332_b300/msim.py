@@ -66,6 +66,20 @@ class SurrogateInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("mixed", C.c_int32), ("mixed_warps_per_env", C.c_int32), ("mixed_slots", C.c_int32),
+                ("mixed_stage_points_mask", C.c_int32), ("warps_per_env", C.c_int32 * 8),
+                ("envs_per_block", C.c_int32 * 8), ("stage_points", C.c_int32 * 8), ("ms_per_model", C.c_float),
+                ("ms_mixed", C.c_float), ("candidates", C.c_int32), ("from_cache", C.c_int32)]
+
+    def as_dict(self):
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if isinstance(v, C.Array) else v
+        return out
+
+
 class EvalOut(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in _EVAL_FIELDS] + [("nnz_pitch", C.c_int32), ("packed_pitch", C.c_int32)]
 
@@ -76,6 +90,8 @@ EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_s
            "msim_mlp_get", "msim_mlp_set", "msim_mlp_forward", "msim_mlp_backward", "msim_mlp_adam",
            "msim_surrogate_train", "msim_set_geometry_mode", "msim_surrogate_set_check", "msim_surrogate_stats",
            "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
+           "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_policy_attach",
+           "msim_policy_step", "msim_policy_excitations",
            "msim_last_error", "msim_version")
 
 _lib = None
@@ -117,12 +133,18 @@ def load_library(path=LIB_PATH):
     lib.msim_surrogate_train.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_float, vp]
     lib.msim_set_geometry_mode.argtypes = [vp, C.c_int32]
     lib.msim_surrogate_set_check.argtypes = [vp, C.c_float, C.c_float]
+    lib.msim_surrogate_set_box.argtypes = [vp, C.c_float]
     lib.msim_surrogate_stats.argtypes = [vp, C.POINTER(SurrogateInfo), C.c_int32]
     lib.msim_surrogate_network.argtypes = [vp, C.POINTER(vp)]
     lib.msim_geometry.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
     lib.msim_surrogate_predict.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
     lib.msim_mlp_forward_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp, vp,
                                              vp, vp, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
+    lib.msim_set_mixed_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    lib.msim_autotune.argtypes = [vp, C.c_char_p, C.c_int32, C.POINTER(TuneResult)]
+    lib.msim_policy_attach.argtypes = [vp, vp]
+    lib.msim_policy_step.argtypes = [vp, C.c_int32, C.c_int32, vp]
+    lib.msim_policy_excitations.argtypes = [vp, vp, vp]
     lib.msim_last_error.argtypes = [vp]
     lib.msim_last_error.restype = C.c_char_p
     lib.msim_version.restype = C.c_int32
@@ -305,6 +327,33 @@ class Sim:
         return a
 
 
+    def set_mixed_launch(self, enable=True, warps_per_env=0, slots_per_block=0, stage_points_mask=-1):
+        """One persistent launch for all models (msim_set_mixed_launch)."""
+        self._check(self.lib.msim_set_mixed_launch(self.h, 1 if enable else 0, warps_per_env, slots_per_block,
+                                                   stage_points_mask))
+
+    def autotune(self, cache_path=None, n_sub=10):
+        """Launch-shape autotuner (msim_autotune); returns the chosen shapes and timings."""
+        r = TuneResult()
+        path = cache_path.encode() if cache_path else None
+        self._check(self.lib.msim_autotune(self.h, path, int(n_sub), C.byref(r)))
+        self._check(self.lib.msim_get_dims(self.h, C.byref(self.dims)))
+        return r.as_dict()
+
+    # ------------------------------------------------------------------ policy in the loop
+    def policy_attach(self, net):
+        """Bind an MLP (in >= 2n + 2m, out = m, sigmoid) as the policy; None detaches."""
+        self._policy = net
+        self._check(self.lib.msim_policy_attach(self.h, net.h if net is not None else None))
+
+    def policy_step(self, n_sub_per_act=2, n_acts=1, stream=None):
+        self._check(self.lib.msim_policy_step(self.h, int(n_sub_per_act), int(n_acts), _stream_ptr(stream)))
+
+    def policy_excitations(self, stream=None):
+        out = self.zeros(self.pitch_m)
+        self._check(self.lib.msim_policy_excitations(self.h, _ptr(out), _stream_ptr(stream)))
+        return out
+
     # ------------------------------------------------------------------ learned geometry
     def geometry(self, q, model=0, stream=None):
         """Exact geometry rows [L | R (sparse order)] at configurations q [rows, >= n] (CUDA FP32)."""
@@ -319,6 +368,9 @@ class Sim:
     def train_surrogate(self, n_samples, epochs, batch=4096, lr=1e-3, stream=None):
         self._check(self.lib.msim_surrogate_train(self.h, int(n_samples), int(epochs), int(batch), float(lr),
                                                   _stream_ptr(stream)))
+
+    def surrogate_set_box(self, margin):
+        self._check(self.lib.msim_surrogate_set_box(self.h, float(margin)))
 
     def set_geometry_mode(self, mode):
         self._check(self.lib.msim_set_geometry_mode(self.h, int(mode)))
