@@ -111,7 +111,7 @@ def measured_traffic(envs):
     try:
         from paper_2603_29332_b300 import build
         d = json.load(open(os.path.join(ROOT, "profiles", "k_step_traffic.json")))
-        if d.get("source_digest") != build._digest():
+        if d.get("source_digest") != build.step_digest():
             return None
         return d["dram_bytes_per_env_per_launch"] * envs
     except Exception:
@@ -462,8 +462,10 @@ def run_policy(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         steps = replays * per_act * acts_per_graph
+        est = sim.state()["status"]
         res[mode] = {"value": E * steps / (ms * 1e-3), "ms_per_substep": ms / steps, "steps": steps,
-                     "status": sim.status()}
+                     "status": sim.status(), "envs_non_finite": int((est & 1).count_nonzero()),
+                     "envs_not_spd": int((est & 2).count_nonzero())}
         if mode == "learned":
             res[mode]["surrogate_stats"] = sim.surrogate_stats()
     return {"metric": "env-steps/s, closed loop with policy MLP, whole body x %d envs" % E,

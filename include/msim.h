@@ -194,8 +194,9 @@ typedef struct {
 /* msim_autotune -- synchronous.  Times, on the handle's own environments with n_substeps
  * substeps per call (excitation 0), every per-model launch shape (warps per environment 1/2/4 x
  * environments per block x via points in shared memory or not) and every mixed-launch shape,
- * applies the fastest (per-model shapes always; the mixed launch if it beats the per-model
- * launches back to back), and restores the state.  cache_path (may be NULL): a text file; a line
+ * applies the fastest (per-model shapes always; the mixed launch, timed only when two or more
+ * models have environments, if it beats the per-model launches back to back), and restores the
+ * state.  cache_path (may be NULL): a text file; a line
  * whose key (models, environment counts, device, n_substeps, library version) matches is applied
  * without timing; otherwise the result is appended.  The result goes to *out (may be NULL). */
 MSIM_API msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_substeps, msim_tune_result* out);

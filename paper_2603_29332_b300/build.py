@@ -19,14 +19,26 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-X
          "-Xcompiler", "-Wall", "--expt-relaxed-constexpr"]
 
 
-def _digest():
+# the files that decide the step kernel's code and memory traffic (model image, launch shape)
+STEP_FILES = ["step_kernels.cu", "kernels.h", "image.h", "dfloat.cuh", "msim_api.cu"]
+
+
+def _digest(files=None):
+    """SHA-256 of the given csrc files and the compiler flags; by default of all sources and
+    headers plus the public headers (the build stamp)."""
     h = hashlib.sha256()
-    for f in SOURCES + HEADERS:
+    for f in (SOURCES + HEADERS if files is None else files):
         h.update(open(os.path.join(CSRC, f), "rb").read())
-    for f in ("msim.h", "msim_model.h"):
-        h.update(open(os.path.join(ROOT, "include", f), "rb").read())
+    if files is None:
+        for f in ("msim.h", "msim_model.h"):
+            h.update(open(os.path.join(ROOT, "include", f), "rb").read())
     h.update(" ".join(ARCH + FLAGS).encode())
     return h.hexdigest()
+
+
+def step_digest():
+    """Digest of the step kernel's sources (keys the committed DRAM-traffic figure)."""
+    return _digest(STEP_FILES)
 
 
 def build(force=False, verbose=False):

@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(192, 2)
     uint64_t* done = empty + kStages;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     int* failed = reinterpret_cast<int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>(tmem_slot + 4);   // BN floats
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
@@ -227,7 +228,10 @@ __global__ void __launch_bounds__(192, 2)
                      : "memory");
     } else if (warp >= 2) {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. output rows of that quarter;
-        // once `done` fired every MMA has completed, so the operand ring is free for staging
+        // once `done` fired every MMA has completed, so the operand ring is free for staging.
+        // The tile's bias goes to shared memory while the main loop runs.
+        for (int j = threadIdx.x - 64; j < BN; j += 128) sbias[j] = (p.bias && n0 + j < p.N) ? p.bias[n0 + j] : 0.f;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
         const bool ok = mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int quarter = warp & 3;
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(192, 2)
             float v[32], z[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                z[j] = __uint_as_float(r[j]) + ((p.bias && cn + j < p.N) ? p.bias[cn + j] : 0.f);
+                z[j] = __uint_as_float(r[j]) + sbias[c + j];
                 v[j] = act_fn(z[j], p.act);
             }
             store_block(stg, v, lane, p.C, p.ldc, p.c_bf16 != 0, row0, cn, p.M, p.N, p.vec_ok != 0);
@@ -299,7 +303,7 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int 
 
 template <int BN, int kStages>
 constexpr size_t gemm_smem() {
-    return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16;
+    return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16 + BN * 4;
 }
 // the epilogue staging (4 warps x 32 rows x kStage floats) reuses the operand ring
 static_assert(4 * 32 * kStage * 4 <= 2 * (kBM * kBK * 2 + 128 * kBK * 2), "staging must fit in the ring");
@@ -330,8 +334,20 @@ cudaError_t gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, GemmArg
     const int vec_align = args.c_bf16 ? 8 : 4;
     args.vec_ok = (args.ldc % vec_align == 0) && ((reinterpret_cast<uintptr_t>(args.C) & 15) == 0);
     args.z_vec_ok = args.Z && (args.ldz % 8 == 0) && ((reinterpret_cast<uintptr_t>(args.Z) & 15) == 0);
-    // two blocks per SM (<= 113 KB of shared memory and <= 256 TMEM columns each)
-    if (args.N > 128) return launch_bn<256, MSIM_GEMM_STAGES_256>(args, A, lda, B, ldb, s);
+    // two blocks per SM (<= 113 KB of shared memory and <= 256 TMEM columns each).  Tile width:
+    // fewest waves of tiles over the 2 x SMs block slots, a 128-wide tile costing half a 256-wide
+    // one; ties go to 256 (more reuse of each A tile)
+    static int slots = 0;
+    if (!slots) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        slots = 2 * sms;
+    }
+    const long long mt = (args.M + kBM - 1) / kBM;
+    const long long w256 = (mt * ((args.N + 255) / 256) + slots - 1) / slots;
+    const long long w128 = (mt * ((args.N + 127) / 128) + slots - 1) / slots;
+    if (args.N > 128 && 2 * w256 <= w128) return launch_bn<256, MSIM_GEMM_STAGES_256>(args, A, lda, B, ldb, s);
     return launch_bn<128, MSIM_GEMM_STAGES_128>(args, A, lda, B, ldb, s);
 }
 

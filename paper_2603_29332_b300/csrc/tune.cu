@@ -357,12 +357,16 @@ msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_subst
     // 2. the per-model launches back to back, as msim_step issues them
     h->mixed = 0;
     if (e == cudaSuccess) r.ms_per_model = timed([&]() { return launch_all(h, h->exc_stage, n_substeps, s); });
-    // 3. one mixed launch
+    // 3. one mixed launch (only with environments of two or more models)
     float best_mixed = 1e30f;
     int best_w = 0, best_sl = 0, best_mask = 0;
-    int mask_best = 0;
-    for (int i = 0; i < h->n_models; ++i) mask_best |= (r.stage_points[i] ? 1 : 0) << i;
+    int mask_best = 0, populated = 0;
+    for (int i = 0; i < h->n_models; ++i) {
+        mask_best |= (r.stage_points[i] ? 1 : 0) << i;
+        populated += h->env_begin[i + 1] > h->env_begin[i];
+    }
     for (int w : {1, 2, 4}) {
+        if (populated < 2) break;
         for (int sl = 1; sl <= slots_limit(w); ++sl) {
             for (int mask : {mask_best, 0}) {
                 if (e != cudaSuccess) break;
