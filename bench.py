@@ -105,6 +105,22 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, world, device="cpu"):
+    """The largest value over the ranks (a timed region's duration); the value itself on one rank.
+    Environments are independent, so this is the only collective of a multi-GPU run."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(envs_per_rank, substeps, steps, world, seconds):
+    """Whole-job env-steps/s: every rank steps its own environments (weak scaling)."""
+    return world * envs_per_rank * substeps * steps / seconds
+
+
 def measured_traffic(envs):
     """DRAM bytes per step launch from the committed ncu summary, or None if the kernel sources
     changed since those counters were taken."""
@@ -202,11 +218,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(ms), world, "cuda")
     st, flags = sim.status()
     # end-to-end through the C ABI with host buffers: H2D excitations, step, D2H q and qd
     k_e2e = min(args.steps, 20)
@@ -216,15 +228,17 @@ def run_gpu(args, rank, world, local_rank):
     qd_out = torch.empty((E, sim.pitch_n), dtype=torch.float32).pin_memory()
     sim.step_host(pinned[0], sub, q_out, qd_out)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for t in range(k_e2e):
         sim.step_host(pinned[t % len(pinned)], sub, q_out, qd_out)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * E * sub * k_e2e / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e = {"value": job_rate(E, sub, k_e2e, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": E * sim.pitch_m * 4, "d2h_bytes_per_step": 2 * E * sim.pitch_n * 4}
     if rank != 0:
         return None
-    value = world * E * sub * args.steps / (total_ms * 1e-3)
+    value = job_rate(E, sub, args.steps, world, total_ms * 1e-3)
     fl = FL.flops_per_env_substep(model)["total"]
     launch_ms = total_ms / args.steps
     achieved = fl * E * sub / (launch_ms * 1e-3) / 1e12
