@@ -78,3 +78,26 @@ def adam_step(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         out_m.append(mi)
         out_v.append(vi)
     return out_p, out_m, out_v
+
+
+def flow_refine(a0, velocity, n_steps, dt):
+    """Action refinement by the flow ODE da/dt = psi(t, s, a) from t = 0 (Methods, "Reinforcement
+    learning with flow-based exploration"), integrated with n_steps explicit Euler steps of size
+    dt ("Training hyperparameters": 20 steps of 0.05): a_{k+1} = a_k + dt psi(k dt, a_k).
+    `velocity(t, a)` returns psi for the whole batch (the observation is bound inside it)."""
+    a = np.array(a0, dtype=np.float64)
+    for k in range(n_steps):
+        a = a + dt * velocity(k * dt, a)
+    return a
+
+
+def mlp_velocity(params, obs, in_round=None):
+    """psi(t, s, a) of a 3-layer MLP reading [obs | a | t]; `in_round` (optional) rounds the
+    network input as the device stores it."""
+    def v(t, a):
+        x = np.concatenate([obs, a, np.full((a.shape[0], 1), t)], axis=1)
+        if in_round is not None:
+            x = in_round(x)
+        y, _ = forward(params, x)
+        return y
+    return v

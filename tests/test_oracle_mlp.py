@@ -63,3 +63,40 @@ def test_training_reduces_loss():
         g, _ = mo.backward(p, x, t)
         p, m, v = mo.adam_step(p, g, m, v, step, 1e-2)
     assert mo.loss(p, x, t) < 0.2 * l0
+
+
+def test_flow_refine_constant_field_is_exact():
+    a0 = np.array([[0.1, -0.2, 0.3]])
+    a = mo.flow_refine(a0, lambda t, a: np.full_like(a, 0.7), 20, 0.05)
+    np.testing.assert_allclose(a, a0 + 20 * 0.05 * 0.7, rtol=0, atol=1e-14)
+
+
+def test_flow_refine_linear_decay_matches_the_euler_closed_form():
+    # da/dt = -a: explicit Euler gives a0 (1 - dt)^N, which tends to a0 e^{-1} as dt -> 0
+    a0 = np.array([[1.0, -2.0]])
+    a = mo.flow_refine(a0, lambda t, a: -a, 20, 0.05)
+    np.testing.assert_allclose(a, a0 * (1 - 0.05) ** 20, rtol=1e-14)
+    fine = mo.flow_refine(a0, lambda t, a: -a, 20000, 1.0 / 20000)
+    np.testing.assert_allclose(fine, a0 * np.exp(-1.0), rtol=1e-4)
+
+
+def test_flow_refine_time_field_is_the_left_riemann_sum():
+    # da/dt = t from t = 0: sum_k dt (k dt) = dt^2 N (N - 1) / 2 (-> 1/2 as dt -> 0)
+    a = mo.flow_refine(np.zeros((1, 1)), lambda t, a: np.full_like(a, t), 20, 0.05)
+    np.testing.assert_allclose(a, 0.05 ** 2 * 20 * 19 / 2, rtol=1e-14)
+
+
+def test_mlp_velocity_reads_obs_action_and_time_in_that_order():
+    rng = np.random.default_rng(3)
+    d_obs, m, hid = 3, 2, 4
+    W1 = np.zeros((hid, d_obs + m + 1))
+    W1[0, d_obs + m] = 1.0          # unit 0 sees t only
+    W1[1, d_obs] = 1.0              # unit 1 sees a[0] only
+    params = [W1, np.zeros(hid), np.eye(hid), np.zeros(hid), np.zeros((m, hid)), np.zeros(m)]
+    params[4][0, 0] = 1.0           # output 0 = silu(silu(t))
+    params[4][1, 1] = 1.0           # output 1 = silu(silu(a[0]))
+    obs = rng.normal(size=(5, d_obs))
+    a = rng.normal(size=(5, m))
+    y = mo.mlp_velocity(params, obs)(0.3, a)
+    np.testing.assert_allclose(y[:, 0], mo.silu(mo.silu(0.3)), rtol=1e-14)
+    np.testing.assert_allclose(y[:, 1], mo.silu(mo.silu(a[:, 0])), rtol=1e-14)
