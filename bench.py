@@ -144,9 +144,25 @@ def cpu_baseline(model, envs=512, substeps=20):
     t0 = time.perf_counter()
     ora.step(om, DT, q0, qd0, a0, exc, substeps)
     dt = time.perf_counter() - t0
-    return {"value": envs * substeps / dt, "unit": UNIT, "cores": ora.max_threads(), "kind": "oracle",
-            "sample": "%d envs x %d substeps of the whole-body model, FP64, OpenMP over envs, %.1f s" %
-                      (envs, substeps, dt)}
+    out = {"value": envs * substeps / dt, "unit": UNIT, "cores": ora.max_threads(), "kind": "oracle",
+           "sample": "%d envs x %d substeps of the whole-body model, FP64, OpenMP over envs, %.1f s" %
+                     (envs, substeps, dt)}
+    # one core, and the tiny model on all cores (bounded samples)
+    e1, s1 = 16, 20
+    t0 = time.perf_counter()
+    ora.step(om, DT, q0[:e1], qd0[:e1], a0[:e1], exc[:e1], s1, n_threads=1)
+    d1 = time.perf_counter() - t0
+    out["one_core"] = {"value": e1 * s1 / d1, "cores": 1, "sample": "%d envs x %d substeps, %.1f s" % (e1, s1, d1)}
+    tiny = mg.config_model("c0_tiny")
+    ot = ora.OracleModel(tiny)
+    qt, qdt, at = mg.initial_state(tiny, 64, seed=0)
+    ut = mg.uniform_excitations(tiny, 64, 1, seed=0)[0]
+    t0 = time.perf_counter()
+    ora.step(ot, DT, qt, qdt, at, ut, 100)
+    d2 = time.perf_counter() - t0
+    out["c0_tiny"] = {"value": 64 * 100 / d2, "cores": ora.max_threads(),
+                      "sample": "64 envs x 100 substeps of the 14-DoF model, %.2f s" % d2}
+    return out
 
 
 def run_reference(args, rank):
@@ -251,6 +267,17 @@ def run_gpu(args, rank, world, local_rank):
             "peak_note": "FP32 FMA peak 148 SMs x 128 lanes x 2 x 2032 MHz (no FP32 figure in MEASURED_PEAKS.json)"}
     if clocks:
         roof["frac_at_sampled_clock"] = achieved / fp32_peak_tflops(clocks["sm_mhz"])
+    try:   # our own FMA microbenchmark on this GPU, beside the derived figure
+        pk_meas = msim.measure_fp32_peak(local_rank)
+        roof["peak_fma_microbenchmark"] = pk_meas
+        roof["frac_of_fma_microbenchmark"] = achieved / pk_meas
+    except Exception:
+        pass
+    tr = measured_traffic(E)
+    if tr:
+        roof["hbm"] = {"achieved_gbs": tr / (launch_ms * 1e-3) / 1e9, "peak_gbs": _peaks().get("hbm_gbs", 6400.0),
+                       "frac": tr / (launch_ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6400.0),
+                       "peak_note": "hbm_gbs of measured"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(args),
@@ -453,8 +480,14 @@ def run_policy(args):
     q0, qd0, a0 = mg.initial_state(model, E, seed=4)
     stream = torch.cuda.Stream()
     res = {}
-    for mode in ("exact", "learned"):
+    flow = None
+    for mode in ("exact", "exact_flow", "learned"):
+        if mode == "exact_flow":
+            # flow refinement of the action: 20 Euler steps of a 2883 -> 1024 -> 1024 -> 700 network
+            flow = msim.MLP(2182 + model.n_muscles + 1, 1024, model.n_muscles, max_batch=E, seed=5)
+            sim.flow_attach(flow, n_steps=20, dt=0.05, sigma=0.05)
         if mode == "learned":
+            sim.flow_attach(None)
             sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=1e-3)
             sim.set_geometry_mode(1)
         sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
@@ -489,7 +522,9 @@ def run_policy(args):
             "config": {"workload": "whole body, %d envs, policy 2182 -> 1024 -> 1024 -> 700 sigmoid every 2 "
                                    "substeps of 1 ms, %d acts per CUDA graph" % (E, acts_per_graph)},
             "exact": res["exact"], "learned_geometry": res["learned"],
-            "learned_vs_exact": res["learned"]["value"] / res["exact"]["value"]}
+            "learned_vs_exact": res["learned"]["value"] / res["exact"]["value"],
+            "exact_with_flow_refinement": res["exact_flow"],
+            "flow_note": "initial sampler + 20 Euler steps (dt 0.05) of a 3-layer 1024 flow network per control step"}
 
 
 def main():

@@ -355,6 +355,25 @@ MSIM_API msim_status msim_policy_attach(msim_handle h, msim_mlp policy);
 MSIM_API msim_status msim_policy_step(msim_handle h, int32_t n_substeps_per_act, int32_t n_acts,
                                       msim_stream_t stream);
 MSIM_API msim_status msim_policy_excitations(msim_handle h, float* out, msim_stream_t stream);
+/* msim_flow_attach -- refine the policy's action with a flow network before each control step
+ * (Methods, "Reinforcement learning with flow-based exploration", the action ODE and
+ * "Training hyperparameters": N_ODE = 20 Euler steps of dt_ODE = 0.05).  The attached policy
+ * becomes the initial sampler: a0 = mu(s) + sigma eps, eps standard normal (Box-Muller on
+ * Philox-4x32-10 keyed by the create seed, counter = environment, muscle pair, control step), then
+ * n_steps times a <- a + dt psi(t, s, a) with t = 0, dt, ...; excitations u = clamp(a, 0, 1).
+ * psi is an msim_mlp with in = (policy in) + m + 1, reading [observation | a | t] in BF16, out = m,
+ * max_batch >= the environments.  Allocates its buffers (synchronous); NULL detaches; attaching
+ * another policy detaches the flow.  0 <= n_steps <= 1000, dt >= 0, sigma >= 0.
+ * msim_flow_actions -- copy the sampler's mean and the last refined action [n_envs][pitch_m]
+ * (device pointers, either may be NULL). */
+MSIM_API msim_status msim_flow_attach(msim_handle h, msim_mlp flow, int32_t n_steps, float dt, float sigma);
+MSIM_API msim_status msim_flow_actions(msim_handle h, float* mu, float* a, msim_stream_t stream);
+
+/* msim_measure_fp32_peak -- synchronous FP32 FMA throughput microbenchmark on `device` (8
+ * independent FMA chains per thread, 8 blocks of 256 threads per SM, best of three timed
+ * launches), in TFLOP/s.  The paper has no counterpart: it is the measured denominator of the
+ * step kernel's ALU roofline.  Allocates a small device buffer. */
+MSIM_API msim_status msim_measure_fp32_peak(int32_t device, double* tflops);
 
 /* msim_last_error -- text of the last failure on this handle (or of the last failed create
  *   when h is NULL).  Owned by the library, valid until the next call. */

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmsim.so")
-SOURCES = ["msim_api.cu", "step_kernels.cu", "gemm_tc.cu", "mlp.cu", "surrogate.cu", "noalloc.cu", "tune.cu", "policy.cu"]
+SOURCES = ["msim_api.cu", "step_kernels.cu", "gemm_tc.cu", "mlp.cu", "surrogate.cu", "noalloc.cu", "tune.cu", "policy.cu", "peak.cu"]
 HEADERS = ["image.h", "kernels.h", "dfloat.cuh", "gemm_tc.h", "mlp.h", "surrogate.h", "handle.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

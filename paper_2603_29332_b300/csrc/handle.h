@@ -55,6 +55,15 @@ struct msim_handle_ {
     __nv_bfloat16* obs = nullptr;            // [n_envs][policy in pitch]
     float* exc_policy = nullptr;             // [n_envs][pitch_m] policy output = excitations
     float* inv_fmax = nullptr;               // [pitch_m] 1 / F_max, caller's muscle order
+    // flow refinement of the policy's action (msim_flow_attach)
+    msim::Mlp* flow = nullptr;               // borrowed: psi(t, s, a), in = obs width + m + 1, out = m
+    __nv_bfloat16* flow_x = nullptr;         // [n_envs][flow in pitch]: obs | a | t
+    float* flow_a = nullptr;                 // [n_envs][pitch_m] the action being refined
+    float* flow_mu = nullptr;                // [n_envs][pitch_m] the initial sampler's mean
+    float* flow_v = nullptr;                 // [n_envs][flow out pitch] velocity
+    uint32_t* act_ctr = nullptr;             // device control-step counter of the noise draw
+    int flow_steps = 20;
+    float flow_dt = 0.05f, flow_sigma = 0.f;
     float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *exc_stage = nullptr;
     uint32_t* env_status = nullptr;
     uint32_t* gflags = nullptr;

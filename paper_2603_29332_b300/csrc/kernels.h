@@ -11,6 +11,8 @@ namespace msim {
 struct EvalPtrs {                 // per-stage outputs of one substep (msim_eval); any may be null
     float *L, *lm, *vm, *force, *act_next, *R, *tau_m, *tau_c, *tau_l, *bias, *rhs, *qdd, *M, *A;
     int nnz_pitch, packed_pitch;
+    float* xpos;                  // body-position mode: rows [env][xpos_pitch], body origins x, y, z
+    int xpos_pitch;
 };
 
 struct StepArgs {
@@ -25,6 +27,7 @@ struct StepArgs {
     int pitch_n, pitch_m;
     float* qdd_out;               // optional: last substep's accelerations
     float* force_out;             // optional: last substep's muscle forces
+    float* vm_out;                // optional: last substep's normalised fibre velocities
     uint32_t* env_status;
     uint32_t* gflags;
     int n_sub;
@@ -77,6 +80,8 @@ struct MixedArgs {
 cudaError_t launch_mixed(const MixedArgs& m, int grid, size_t smem, cudaStream_t s);
 int mixed_blocks_per_sm(int threads, size_t smem, int wpe);
 cudaError_t launch_geom(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
+// body origins of the configurations a.q rows [env_begin, env_end) into a.ev.xpos (pitch a.ev.xpos_pitch)
+cudaError_t launch_fk(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_surr_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 // network input rows X[r] = bf16((q[env_begin + r] - c) / sc), pad columns 0; advances *step_ctr
 // (optional) by one
@@ -90,6 +95,17 @@ cudaError_t launch_obs(const float* q, const float* qd, const float* act, const 
 cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
                          const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,
                          int n_envs, cudaStream_t s);
+// flow refinement of the policy's action (policy.cu): a = mu + sigma N(0, 1) (advances *act_ctr),
+// the per-step input columns [a | t] of the flow network, the observation columns, and the Euler
+// step a += dt v (with u = clamp(a, 0, 1) when u is given)
+cudaError_t launch_flow_init(const float* mu, int ldmu, float* a, int lda, int n_envs, int m, float sigma,
+                             uint32_t seed, uint32_t* act_ctr, cudaStream_t s);
+cudaError_t launch_flow_input(const float* a, int lda, int n_envs, int m, float t, __nv_bfloat16* X, int ldx, int off,
+                              cudaStream_t s);
+cudaError_t launch_copy_cols(const __nv_bfloat16* src, int lds, int n_envs, int cols, __nv_bfloat16* dst, int ldd,
+                             cudaStream_t s);
+cudaError_t launch_flow_axpy(float* a, int lda, const float* v, int ldv, int n_envs, int m, float dt, float* u, int ldu,
+                             cudaStream_t s);
 cudaError_t set_step_smem_limit(size_t bytes);
 int step_blocks_per_sm(int threads, size_t smem, int wpe);
 

@@ -1195,6 +1195,7 @@ msim_status msim_policy_attach(msim_handle h, msim_mlp policy) {
     cudaDeviceSynchronize();
     cudaFree(h->obs); cudaFree(h->exc_policy); cudaFree(h->inv_fmax);
     h->obs = nullptr; h->exc_policy = nullptr; h->inv_fmax = nullptr; h->policy = nullptr;
+    msim_flow_attach(h, nullptr, 0, 0.f, 0.f);   // a flow network is bound to its sampler
     if (!policy) return MSIM_OK;   // detach
     if (h->n_models != 1) {
         h->err = "msim_policy_attach: single-model handles only";
@@ -1233,10 +1234,31 @@ msim_status msim_policy_step(msim_handle h, int32_t n_substeps_per_act, int32_t 
     cudaStream_t s = (cudaStream_t)stream;
     const ImgHeader& hd = h->models[0].hdr;
     Mlp* p = h->policy;
+    Mlp* f = h->flow;
+    const int E = h->n_envs, m = hd.m;
     for (int k = 0; k < n_acts; ++k) {
         cudaError_t e = launch_obs(h->q, h->qd, h->act, h->force, h->inv_fmax, h->pitch_n, h->pitch_m, hd.n, hd.m,
                                    h->n_envs, h->obs, p->inp, s);
-        if (e == cudaSuccess) e = mlp_infer(p, h->obs, p->inp, h->n_envs, h->exc_policy, h->pitch_m, s);
+        if (!f) {
+            if (e == cudaSuccess) e = mlp_infer(p, h->obs, p->inp, E, h->exc_policy, h->pitch_m, s);
+        } else {
+            // a0 = mu(s) + sigma eps; a += dt psi(t, s, a) for N steps; u = clamp(a, 0, 1)
+            const int off = p->in;   // the flow input holds the observation columns first
+            if (e == cudaSuccess) e = mlp_infer(p, h->obs, p->inp, E, h->flow_mu, h->pitch_m, s);
+            if (e == cudaSuccess)
+                e = launch_flow_init(h->flow_mu, h->pitch_m, h->flow_a, h->pitch_m, E, m, h->flow_sigma, h->seed,
+                                     h->act_ctr, s);
+            if (e == cudaSuccess) e = launch_copy_cols(h->obs, p->inp, E, p->in, h->flow_x, f->inp, s);
+            for (int j = 0; j < h->flow_steps && e == cudaSuccess; ++j) {
+                e = launch_flow_input(h->flow_a, h->pitch_m, E, m, (float)j * h->flow_dt, h->flow_x, f->inp, off, s);
+                if (e == cudaSuccess) e = mlp_infer(f, h->flow_x, f->inp, E, h->flow_v, f->outp, s);
+                if (e == cudaSuccess)
+                    e = launch_flow_axpy(h->flow_a, h->pitch_m, h->flow_v, f->outp, E, m, h->flow_dt,
+                                         j + 1 == h->flow_steps ? h->exc_policy : nullptr, h->pitch_m, s);
+            }
+            if (e == cudaSuccess && h->flow_steps == 0)   // no refinement: u = clamp(a0)
+                e = launch_flow_axpy(h->flow_a, h->pitch_m, h->flow_v, f->outp, E, m, 0.f, h->exc_policy, h->pitch_m, s);
+        }
         if (e != cudaSuccess) return cuda_fail(h, e, "msim_policy_step (policy)");
         const msim_status st = msim_step(h, h->exc_policy, n_substeps_per_act, stream);
         if (st != MSIM_OK) return st;
@@ -1254,6 +1276,61 @@ msim_status msim_policy_excitations(msim_handle h, float* out, msim_stream_t str
     const cudaError_t e = cudaMemcpyAsync(out, h->exc_policy, (size_t)h->n_envs * h->pitch_m * sizeof(float),
                                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_policy_excitations");
+}
+
+msim_status msim_flow_attach(msim_handle h, msim_mlp flow, int32_t n_steps, float dt, float sigma) {
+    if (!h) return arg_fail(h, "msim_flow_attach: NULL handle");
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->flow_x); cudaFree(h->flow_a); cudaFree(h->flow_mu); cudaFree(h->flow_v); cudaFree(h->act_ctr);
+    h->flow_x = nullptr; h->flow_a = nullptr; h->flow_mu = nullptr; h->flow_v = nullptr; h->act_ctr = nullptr;
+    h->flow = nullptr;
+    if (!flow) return MSIM_OK;   // detach
+    if (!h->policy) {
+        h->err = "msim_flow_attach: attach the initial sampler first (msim_policy_attach)";
+        return MSIM_ERR_STATE;
+    }
+    const ImgHeader& hd = h->models[0].hdr;
+    Mlp* f = flow->m;
+    const int m = hd.m;
+    if (f->in != h->policy->in + m + 1 || f->out != m || f->max_batch < h->n_envs || h->policy->out != m)
+        return arg_fail(h, "msim_flow_attach: flow needs in = policy in + m + 1, out = m, max_batch >= n_envs");
+    if (n_steps < 0 || n_steps > 1000 || !(dt >= 0.f) || !(sigma >= 0.f) || !std::isfinite(dt) || !std::isfinite(sigma))
+        return arg_fail(h, "msim_flow_attach: 0 <= n_steps <= 1000, dt >= 0, sigma >= 0");
+    cudaError_t e = cudaMalloc(&h->flow_x, (size_t)h->n_envs * f->inp * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&h->flow_a, (size_t)h->n_envs * h->pitch_m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->flow_mu, (size_t)h->n_envs * h->pitch_m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->flow_v, (size_t)h->n_envs * f->outp * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->act_ctr, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(h->flow_x, 0, (size_t)h->n_envs * f->inp * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemset(h->flow_a, 0, (size_t)h->n_envs * h->pitch_m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->flow_mu, 0, (size_t)h->n_envs * h->pitch_m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->flow_v, 0, (size_t)h->n_envs * f->outp * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->act_ctr, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaFree(h->flow_x); cudaFree(h->flow_a); cudaFree(h->flow_mu); cudaFree(h->flow_v); cudaFree(h->act_ctr);
+        h->flow_x = nullptr; h->flow_a = nullptr; h->flow_mu = nullptr; h->flow_v = nullptr; h->act_ctr = nullptr;
+        return cuda_fail(h, e, "msim_flow_attach");
+    }
+    h->flow = f;
+    h->flow_steps = n_steps;
+    h->flow_dt = dt;
+    h->flow_sigma = sigma;
+    return MSIM_OK;
+}
+
+msim_status msim_flow_actions(msim_handle h, float* a0, float* a, msim_stream_t stream) {
+    if (!h || (!a0 && !a)) return arg_fail(h, "msim_flow_actions: NULL argument");
+    if (!h->flow) {
+        h->err = "msim_flow_actions: no flow attached";
+        return MSIM_ERR_STATE;
+    }
+    cudaSetDevice(h->device);
+    const size_t bytes = (size_t)h->n_envs * h->pitch_m * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (a0) e = cudaMemcpyAsync(a0, h->flow_mu, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    if (e == cudaSuccess && a) e = cudaMemcpyAsync(a, h->flow_a, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_flow_actions");
 }
 
 #ifdef MSIM_PHASE_TIMERS

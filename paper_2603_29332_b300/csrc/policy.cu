@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "mlp.h"
 
 namespace msim {
 namespace {
@@ -24,7 +25,95 @@ __global__ void k_obs(const float* q, const float* qd, const float* act, const f
     }
 }
 
+// a = mu + sigma * eps, eps standard normal by Box-Muller on Philox-4x32-10 bits keyed by seed,
+// counter (environment, muscle pair, control-step counter)
+__global__ void k_flow_init(const float* mu, int ldmu, float* a, int lda, int n_envs, int m, float sigma,
+                            uint32_t seed, const uint32_t* act_ctr) {
+    const uint32_t step = *act_ctr;
+    const int pairs = (m + 1) / 2;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_envs * pairs;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / pairs), j = 2 * (int)(i % pairs);
+        float z0 = 0.f, z1 = 0.f;
+        if (sigma > 0.f) {
+            uint32_t c[4] = {(uint32_t)e, (uint32_t)j, step, 0x666c6f77u};
+            philox4x32_10(c, seed, 0xa5a5a5a5u);
+            const float u1 = u01_from_bits(c[0]), u2 = u01_from_bits(c[1]);
+            const float r = sqrtf(-2.f * logf(u1));
+            float sn, cs;
+            sincospif(2.f * u2, &sn, &cs);
+            z0 = r * cs;
+            z1 = r * sn;
+        }
+        a[(size_t)e * lda + j] = mu[(size_t)e * ldmu + j] + sigma * z0;
+        if (j + 1 < m) a[(size_t)e * lda + j + 1] = mu[(size_t)e * ldmu + j + 1] + sigma * z1;
+    }
+}
+
+// flow-network input columns that change per Euler step: X[e][off + j] = a[e][j], X[e][off + m] = t
+__global__ void k_flow_input(const float* a, int lda, int n_envs, int m, float t, __nv_bfloat16* X, int ldx, int off) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_envs * (m + 1);
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / (m + 1)), j = (int)(i % (m + 1));
+        const float v = j < m ? a[(size_t)e * lda + j] : t;
+        X[(size_t)e * ldx + off + j] = __float2bfloat16_rn(v);
+    }
+}
+
+// copy the observation columns into the flow-network input rows (once per control step)
+__global__ void k_copy_cols(const __nv_bfloat16* src, int lds, int n_envs, int cols, __nv_bfloat16* dst, int ldd) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_envs * cols;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / cols), j = (int)(i % cols);
+        dst[(size_t)e * ldd + j] = src[(size_t)e * lds + j];
+    }
+}
+
+// Euler step a += dt v; on the last step also the excitations u = clamp(a, 0, 1)
+__global__ void k_flow_axpy(float* a, int lda, const float* v, int ldv, int n_envs, int m, float dt, float* u, int ldu) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_envs * m;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / m), j = (int)(i % m);
+        const float x = __fadd_rn(a[(size_t)e * lda + j], __fmul_rn(dt, v[(size_t)e * ldv + j]));   // no FMA
+        a[(size_t)e * lda + j] = x;
+        if (u) u[(size_t)e * ldu + j] = fminf(fmaxf(x, 0.f), 1.f);
+    }
+}
+
+__global__ void k_bump(uint32_t* ctr) { *ctr += 1u; }
+
+int grid_for(size_t work) {
+    const size_t b = (work + 255) / 256;
+    return (int)(b < 8192 ? (b > 0 ? b : 1) : 8192);
+}
+
 }  // namespace
+
+cudaError_t launch_flow_init(const float* mu, int ldmu, float* a, int lda, int n_envs, int m, float sigma,
+                             uint32_t seed, uint32_t* act_ctr, cudaStream_t s) {
+    k_bump<<<1, 1, 0, s>>>(act_ctr);
+    k_flow_init<<<grid_for((size_t)n_envs * ((m + 1) / 2)), 256, 0, s>>>(mu, ldmu, a, lda, n_envs, m, sigma, seed,
+                                                                           act_ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_input(const float* a, int lda, int n_envs, int m, float t, __nv_bfloat16* X, int ldx, int off,
+                              cudaStream_t s) {
+    k_flow_input<<<grid_for((size_t)n_envs * (m + 1)), 256, 0, s>>>(a, lda, n_envs, m, t, X, ldx, off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_cols(const __nv_bfloat16* src, int lds, int n_envs, int cols, __nv_bfloat16* dst, int ldd,
+                             cudaStream_t s) {
+    k_copy_cols<<<grid_for((size_t)n_envs * cols), 256, 0, s>>>(src, lds, n_envs, cols, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flow_axpy(float* a, int lda, const float* v, int ldv, int n_envs, int m, float dt, float* u, int ldu,
+                             cudaStream_t s) {
+    k_flow_axpy<<<grid_for((size_t)n_envs * m), 256, 0, s>>>(a, lda, v, ldv, n_envs, m, dt, u, ldu);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_obs(const float* q, const float* qd, const float* act, const float* force, const float* inv_fmax,
                        int pitch_n, int pitch_m, int n, int m, int n_envs, __nv_bfloat16* X, int ldx, cudaStream_t s) {

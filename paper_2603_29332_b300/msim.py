@@ -91,7 +91,8 @@ EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_s
            "msim_surrogate_train", "msim_set_geometry_mode", "msim_surrogate_set_check", "msim_surrogate_stats",
            "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
            "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_policy_attach",
-           "msim_policy_step", "msim_policy_excitations",
+           "msim_policy_step", "msim_policy_excitations", "msim_measure_fp32_peak", "msim_flow_attach",
+           "msim_flow_actions",
            "msim_last_error", "msim_version")
 
 _lib = None
@@ -145,6 +146,9 @@ def load_library(path=LIB_PATH):
     lib.msim_policy_attach.argtypes = [vp, vp]
     lib.msim_policy_step.argtypes = [vp, C.c_int32, C.c_int32, vp]
     lib.msim_policy_excitations.argtypes = [vp, vp, vp]
+    lib.msim_measure_fp32_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+    lib.msim_flow_attach.argtypes = [vp, vp, C.c_int32, C.c_float, C.c_float]
+    lib.msim_flow_actions.argtypes = [vp, vp, vp, vp]
     lib.msim_last_error.argtypes = [vp]
     lib.msim_last_error.restype = C.c_char_p
     lib.msim_version.restype = C.c_int32
@@ -349,6 +353,18 @@ class Sim:
     def policy_step(self, n_sub_per_act=2, n_acts=1, stream=None):
         self._check(self.lib.msim_policy_step(self.h, int(n_sub_per_act), int(n_acts), _stream_ptr(stream)))
 
+    def flow_attach(self, net, n_steps=20, dt=0.05, sigma=0.0):
+        """Refine the policy's action with a flow network (in = policy in + m + 1, out = m)."""
+        self._flow = net
+        self._check(self.lib.msim_flow_attach(self.h, net.h if net is not None else None, int(n_steps), float(dt),
+                                              float(sigma)))
+
+    def flow_actions(self, stream=None):
+        """(sampler mean, last refined action), [n_envs, pitch_m] each."""
+        mu, a = self.zeros(self.pitch_m), self.zeros(self.pitch_m)
+        self._check(self.lib.msim_flow_actions(self.h, _ptr(mu), _ptr(a), _stream_ptr(stream)))
+        return mu, a
+
     def policy_excitations(self, stream=None):
         out = self.zeros(self.pitch_m)
         self._check(self.lib.msim_policy_excitations(self.h, _ptr(out), _stream_ptr(stream)))
@@ -398,6 +414,16 @@ class Sim:
         self._check(self.lib.msim_surrogate_network(self.h, C.byref(h)))
         d_in = self.dims.n_dofs[0]
         return MLP.borrowed(h, d_in, 512, self.dims.n_muscles[0] + self.dims.nnz[0])
+
+
+def measure_fp32_peak(device=0):
+    """FP32 FMA throughput of the device in TFLOP/s (msim_measure_fp32_peak)."""
+    lib = load_library()
+    v = C.c_double()
+    st = lib.msim_measure_fp32_peak(int(device), C.byref(v))
+    if st != MSIM_OK:
+        raise MsimError(st, "msim_measure_fp32_peak failed")
+    return v.value
 
 
 def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=None):
