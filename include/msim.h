@@ -369,6 +369,29 @@ MSIM_API msim_status msim_policy_excitations(msim_handle h, float* out, msim_str
 MSIM_API msim_status msim_flow_attach(msim_handle h, msim_mlp flow, int32_t n_steps, float dt, float sigma);
 MSIM_API msim_status msim_flow_actions(msim_handle h, float* mu, float* a, msim_stream_t stream);
 
+/* ---- imitation reward -------------------------------------------------------------------------
+ * The paper's unified imitation environment (Methods, "Unified imitation environment") turns the
+ * tracking error Delta (joint angles and body positions against the reference motion) into the
+ * reward r = -log(1 - D(Delta)) with a discriminator D, and "Training regularization" adds the
+ * power penalty r_power = -(1/|A|) sum_i |F_m^(i) v_m^(i)| with weight w_power.  Single-model
+ * handles.  The discriminator is trained elsewhere; here it is only evaluated.
+ *
+ * msim_reward_attach -- bind D (msim_mlp with in = n + 3 nb, out = 1, sigmoid output, max_batch
+ * >= the environments; NULL detaches) and w_power.  Allocates its buffers (synchronous); from then
+ * on every step also stores the last substep's normalised fibre velocities v_m (Eq. 1).
+ * msim_reward -- for every environment: Delta = [q - q_ref (n) | x_b(q) - x_b(q_ref) (3 nb, body
+ * origins in the world frame, bodies in model order)], D(Delta) on the tensor cores (BF16 input,
+ * FP32 accumulation), r = -log(1 - min(D, 1 - 1e-7)) + w_power r_power with F and v_m of the last
+ * substep of the last step (0 before the first step).  q_ref: device [n_envs][pitch_n]; reward:
+ * device [n_envs]; parts (optional): device [n_envs][2] = (tracking, power) terms; delta
+ * (optional): device [n_envs][ld_delta] FP32.  Asynchronous.
+ * msim_body_positions -- body origins [n_rows][3 nb] (device) at configurations q [n_rows][ldq]. */
+MSIM_API msim_status msim_reward_attach(msim_handle h, msim_mlp disc, float w_power);
+MSIM_API msim_status msim_reward(msim_handle h, const float* q_ref, float* reward, float* parts, float* delta,
+                                 int32_t ld_delta, msim_stream_t stream);
+MSIM_API msim_status msim_body_positions(msim_handle h, const float* q, int32_t ldq, int32_t n_rows, float* xpos,
+                                         msim_stream_t stream);
+
 /* msim_measure_fp32_peak -- synchronous FP32 FMA throughput microbenchmark on `device` (8
  * independent FMA chains per thread, 8 blocks of 256 threads per SM, best of three timed
  * launches), in TFLOP/s.  The paper has no counterpart: it is the measured denominator of the

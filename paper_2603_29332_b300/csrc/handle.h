@@ -62,6 +62,14 @@ struct msim_handle_ {
     float* flow_mu = nullptr;                // [n_envs][pitch_m] the initial sampler's mean
     float* flow_v = nullptr;                 // [n_envs][flow out pitch] velocity
     uint32_t* act_ctr = nullptr;             // device control-step counter of the noise draw
+    // imitation reward (msim_reward_attach / msim_reward)
+    msim::Mlp* disc = nullptr;               // borrowed: D(Delta), in = n + 3 nb, out = 1, sigmoid
+    float* vm = nullptr;                     // [n_envs][pitch_m] last substep's fibre velocities
+    float* xpos_sim = nullptr;               // [n_envs][3 nb]
+    float* xpos_ref = nullptr;               // [n_envs][3 nb]
+    __nv_bfloat16* delta_x = nullptr;        // [n_envs][disc in pitch]
+    float* disc_out = nullptr;               // [n_envs][disc out pitch]
+    float w_power = 0.f;
     int flow_steps = 20;
     float flow_dt = 0.05f, flow_sigma = 0.f;
     float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *exc_stage = nullptr;

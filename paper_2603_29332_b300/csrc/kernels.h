@@ -106,6 +106,11 @@ cudaError_t launch_copy_cols(const __nv_bfloat16* src, int lds, int n_envs, int 
                              cudaStream_t s);
 cudaError_t launch_flow_axpy(float* a, int lda, const float* v, int ldv, int n_envs, int m, float dt, float* u, int ldu,
                              cudaStream_t s);
+// imitation reward (policy.cu): tracking-error rows of the discriminator, then the reward
+cudaError_t launch_delta(const float* q, const float* qr, int pitch_n, const float* xs, const float* xr, int n, int nb,
+                         int n_envs, __nv_bfloat16* X, int ldx, float* D, int ldd, cudaStream_t s);
+cudaError_t launch_reward(const float* Dout, int ldo, const float* F, const float* vm, int pitch_m, int m, int n_envs,
+                          float w_power, float* r, float* parts, cudaStream_t s);
 cudaError_t set_step_smem_limit(size_t bytes);
 int step_blocks_per_sm(int threads, size_t smem, int wpe);
 

@@ -415,7 +415,7 @@ StepArgs base_args(msim_handle h, int i) {
     a.env_end = h->env_begin[i + 1];
     a.q = h->q; a.qd = h->qd; a.act = h->act;
     a.pitch_n = h->pitch_n; a.pitch_m = h->pitch_m;
-    a.qdd_out = h->qdd; a.force_out = h->force;
+    a.qdd_out = h->qdd; a.force_out = h->force; a.vm_out = h->vm;
     a.env_status = h->env_status; a.gflags = h->gflags;
     a.dt = h->dt;
     a.envs_per_block = h->epb[i];
@@ -488,13 +488,36 @@ cudaError_t geometry_launch(msim_handle h, int i, const float* q, int ldq, int n
     a.q = const_cast<float*>(q);
     a.qd = const_cast<float*>(q);
     a.pitch_n = ldq;
-    a.act = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr;
+    a.act = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr; a.vm_out = nullptr;
     a.ev.L = out;
     a.ev.nnz_pitch = ldo;
     const size_t smem = step_smem_bytes(h->models[i].hdr, epb, h->pts_smem[i], wpe);
     const int groups = (n_rows + epb - 1) / epb;
     const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe));
     return launch_geom(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
+}
+
+// body-position launch of model i over rows [0, n_rows) of q (pitch ldq) into xpos [row][3 nb]
+cudaError_t fk_launch(msim_handle h, int i, const float* q, int ldq, int n_rows, float* xpos, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    StepArgs a = base_args(h, i);
+    const int wpe = h->wpe[i] == 1 ? 1 : 2;
+    int epb = h->epb[i];
+    if (wpe != h->wpe[i]) epb = std::max(1, std::min(max_epb(h, i, h->pts_smem[i] != 0, wpe), 8));
+    a.wpe = wpe;
+    a.envs_per_block = epb;
+    a.env_begin = 0;
+    a.env_end = n_rows;
+    a.q = const_cast<float*>(q);
+    a.qd = const_cast<float*>(q);
+    a.pitch_n = ldq;
+    a.act = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr; a.vm_out = nullptr;
+    a.ev.xpos = xpos;
+    a.ev.xpos_pitch = 3 * h->models[i].hdr.nb;
+    const size_t smem = step_smem_bytes(h->models[i].hdr, epb, h->pts_smem[i], wpe);
+    const int groups = (n_rows + epb - 1) / epb;
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe));
+    return launch_fk(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
 }
 
 msim_status surrogate_step(msim_handle h, const float* exc, int n_sub, cudaStream_t s) {
@@ -1331,6 +1354,79 @@ msim_status msim_flow_actions(msim_handle h, float* a0, float* a, msim_stream_t 
     if (a0) e = cudaMemcpyAsync(a0, h->flow_mu, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     if (e == cudaSuccess && a) e = cudaMemcpyAsync(a, h->flow_a, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_flow_actions");
+}
+
+// ------------------------------------------------------------------ imitation reward
+msim_status msim_reward_attach(msim_handle h, msim_mlp disc, float w_power) {
+    if (!h) return arg_fail(h, "msim_reward_attach: NULL handle");
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->vm); cudaFree(h->xpos_sim); cudaFree(h->xpos_ref); cudaFree(h->delta_x); cudaFree(h->disc_out);
+    h->vm = nullptr; h->xpos_sim = nullptr; h->xpos_ref = nullptr; h->delta_x = nullptr; h->disc_out = nullptr;
+    h->disc = nullptr;
+    if (!disc) return MSIM_OK;   // detach (the step stops writing fibre velocities)
+    if (h->n_models != 1) {
+        h->err = "msim_reward_attach: single-model handles only";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    const ImgHeader& hd = h->models[0].hdr;
+    Mlp* d = disc->m;
+    if (d->in != hd.n + 3 * hd.nb || d->out != 1 || d->out_act != 2 || d->max_batch < h->n_envs)
+        return arg_fail(h, "msim_reward_attach: discriminator needs in = n + 3 nb, out = 1 (sigmoid), "
+                           "max_batch >= n_envs");
+    if (!std::isfinite(w_power)) return arg_fail(h, "msim_reward_attach: w_power must be finite");
+    const size_t E = (size_t)h->n_envs;
+    cudaError_t e = cudaMalloc(&h->vm, E * h->pitch_m * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->xpos_sim, E * 3 * hd.nb * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->xpos_ref, E * 3 * hd.nb * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->delta_x, E * d->inp * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&h->disc_out, E * d->outp * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->vm, 0, E * h->pitch_m * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(h->vm); cudaFree(h->xpos_sim); cudaFree(h->xpos_ref); cudaFree(h->delta_x); cudaFree(h->disc_out);
+        h->vm = nullptr; h->xpos_sim = nullptr; h->xpos_ref = nullptr; h->delta_x = nullptr; h->disc_out = nullptr;
+        return cuda_fail(h, e, "msim_reward_attach");
+    }
+    h->disc = d;
+    h->w_power = w_power;
+    return MSIM_OK;
+}
+
+msim_status msim_reward(msim_handle h, const float* q_ref, float* reward, float* parts, float* delta, int32_t ld_delta,
+                        msim_stream_t stream) {
+    if (!h || !q_ref || !reward) return arg_fail(h, "msim_reward: NULL argument");
+    if (!h->disc) {
+        h->err = "msim_reward: no discriminator attached (msim_reward_attach)";
+        return MSIM_ERR_STATE;
+    }
+    const ImgHeader& hd = h->models[0].hdr;
+    if (delta && ld_delta < hd.n + 3 * hd.nb) return arg_fail(h, "msim_reward: ld_delta < n + 3 nb");
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Mlp* d = h->disc;
+    const int E = h->n_envs;
+    cudaError_t e = fk_launch(h, 0, h->q, h->pitch_n, E, h->xpos_sim, s);
+    if (e == cudaSuccess) e = fk_launch(h, 0, q_ref, h->pitch_n, E, h->xpos_ref, s);
+    if (e == cudaSuccess)
+        e = launch_delta(h->q, q_ref, h->pitch_n, h->xpos_sim, h->xpos_ref, hd.n, hd.nb, E, h->delta_x, d->inp, delta,
+                         ld_delta, s);
+    if (e == cudaSuccess) e = mlp_infer(d, h->delta_x, d->inp, E, h->disc_out, d->outp, s);
+    if (e == cudaSuccess)
+        e = launch_reward(h->disc_out, d->outp, h->force, h->vm, h->pitch_m, hd.m, E, h->w_power, reward, parts, s);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_reward");
+}
+
+msim_status msim_body_positions(msim_handle h, const float* q, int32_t ldq, int32_t n_rows, float* xpos,
+                                msim_stream_t stream) {
+    if (!h || !q || !xpos || n_rows < 0) return arg_fail(h, "msim_body_positions: bad argument");
+    if (h->n_models != 1) {
+        h->err = "msim_body_positions: single-model handles only";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    if (ldq < h->models[0].hdr.n) return arg_fail(h, "msim_body_positions: ldq < n");
+    cudaSetDevice(h->device);
+    const cudaError_t e = fk_launch(h, 0, q, ldq, n_rows, xpos, (cudaStream_t)stream);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_body_positions");
 }
 
 #ifdef MSIM_PHASE_TIMERS

@@ -82,6 +82,41 @@ __global__ void k_flow_axpy(float* a, int lda, const float* v, int ldv, int n_en
 
 __global__ void k_bump(uint32_t* ctr) { *ctr += 1u; }
 
+// tracking error Delta = [q - q_ref | x_body(q) - x_body(q_ref)]: BF16 network rows (pitch ldx,
+// pad columns 0) and, optionally, FP32 rows
+__global__ void k_delta(const float* q, const float* qr, int pitch_n, const float* xs, const float* xr, int n, int nb,
+                        int n_envs, __nv_bfloat16* X, int ldx, float* D, int ldd) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_envs * ldx;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i / ldx), j = (int)(i % ldx);
+        float v = 0.f;
+        if (j < n) v = q[(size_t)e * pitch_n + j] - qr[(size_t)e * pitch_n + j];
+        else if (j < n + 3 * nb) v = xs[(size_t)e * 3 * nb + j - n] - xr[(size_t)e * 3 * nb + j - n];
+        X[i] = __float2bfloat16_rn(v);
+        if (D && j < n + 3 * nb) D[(size_t)e * ldd + j] = v;
+    }
+}
+
+// r = -log(1 - D(Delta)) + w_power r_power, r_power = -(1/m) sum_k |F_k v_k|; one warp per env
+__global__ void k_reward(const float* Dout, int ldo, const float* F, const float* vm, int pitch_m, int m, int n_envs,
+                         float w_power, float* r, float* parts) {
+    const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (warp >= n_envs) return;
+    float s = 0.f;
+    for (int k = lane; k < m; k += 32) s += fabsf(F[(size_t)warp * pitch_m + k] * vm[(size_t)warp * pitch_m + k]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const float d = fminf(Dout[(size_t)warp * ldo], 1.f - 1e-7f);   // keeps the reward finite
+        const float rt = -log1pf(-d);
+        const float rp = -s / (float)m;
+        r[warp] = rt + w_power * rp;
+        if (parts) {
+            parts[2 * warp] = rt;
+            parts[2 * warp + 1] = rp;
+        }
+    }
+}
+
 int grid_for(size_t work) {
     const size_t b = (work + 255) / 256;
     return (int)(b < 8192 ? (b > 0 ? b : 1) : 8192);
@@ -112,6 +147,18 @@ cudaError_t launch_copy_cols(const __nv_bfloat16* src, int lds, int n_envs, int 
 cudaError_t launch_flow_axpy(float* a, int lda, const float* v, int ldv, int n_envs, int m, float dt, float* u, int ldu,
                              cudaStream_t s) {
     k_flow_axpy<<<grid_for((size_t)n_envs * m), 256, 0, s>>>(a, lda, v, ldv, n_envs, m, dt, u, ldu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_delta(const float* q, const float* qr, int pitch_n, const float* xs, const float* xr, int n, int nb,
+                         int n_envs, __nv_bfloat16* X, int ldx, float* D, int ldd, cudaStream_t s) {
+    k_delta<<<grid_for((size_t)n_envs * ldx), 256, 0, s>>>(q, qr, pitch_n, xs, xr, n, nb, n_envs, X, ldx, D, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reward(const float* Dout, int ldo, const float* F, const float* vm, int pitch_m, int m, int n_envs,
+                          float w_power, float* r, float* parts, cudaStream_t s) {
+    k_reward<<<(n_envs + 7) / 8, 256, 0, s>>>(Dout, ldo, F, vm, pitch_m, m, n_envs, w_power, r, parts);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,7 @@ namespace {
 
 // kernel modes: one substep loop, one-substep evaluation with every intermediate, muscle
 // geometry only (surrogate training labels), surrogate step (geometry from the learned model)
-constexpr int kModeStep = 0, kModeEval = 1, kModeGeom = 2, kModeSurr = 3;
+constexpr int kModeStep = 0, kModeEval = 1, kModeGeom = 2, kModeSurr = 3, kModeFk = 4;
 
 constexpr uint32_t kEnvNonFinite = 0x1u;
 constexpr uint32_t kEnvNotSpd = 0x2u;
@@ -525,7 +525,7 @@ struct SurrCtx {
 // (The statements after its `continue` are unreachable in that mode only: warning 128 is off.)
 template <int MODE, int WPE>
 __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc,
-                                  float* act, float* force_out, const EvalPtrs* ev, const SurrCtx* sc) {
+                                  float* act, float* force_out, float* vm_out, const EvalPtrs* ev, const SurrCtx* sc) {
     const ImgHeader& H = *T.H;
     const float* qd = ws + H.w_qd;
     const float* frame = ws + H.w_frame;
@@ -618,6 +618,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
         const float an = fminf(fmaxf(a + dt * (u - a) / tau, 0.f), 1.f);
         if (MODE != kModeEval) act[k] = an;
         if (force_out) force_out[k] = F;
+        if (vm_out) vm_out[k] = vm;
         SUB_MARK(9);
         // rhs += R^T F; A += dt R^T (dF/dLdot) R as g g^T with g = sqrt(dt dF/dLdot) R.  All
         // operands are loaded first, then the reductions issue back to back.
@@ -894,11 +895,18 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
 // Returns the environment status bits; in a surrogate step bit 8 reports a failed cross-check.
 template <int MODE, int WPE>
 __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc, float* act,
-                            float* force_out, const EvalPtrs* ev, const SurrCtx* sc, unsigned long long* timers) {
+                            float* force_out, float* vm_out, const EvalPtrs* ev, const SurrCtx* sc,
+                            unsigned long long* timers) {
     const ImgHeader& H = *T.H;
     if (MODE == kModeGeom) {
         phase_kinematics(T, ws, g);
-        phase_muscles<kModeGeom>(T, ws, g, dt, exc, act, nullptr, ev, nullptr);
+        phase_muscles<kModeGeom>(T, ws, g, dt, exc, act, nullptr, nullptr, ev, nullptr);
+        return 0u;
+    }
+    if (MODE == kModeFk) {   // body origins only
+        phase_kinematics(T, ws, g);
+        const float* frame = ws + H.w_frame;
+        for (int i = g.lane; i < 3 * H.nb; i += g.N) ev->xpos[i] = frame[12 * (i / 3) + 9 + i % 3];
         return 0u;
     }
 #ifdef MSIM_PHASE_TIMERS
@@ -922,7 +930,7 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
             if (ev->bias) ev->bias[d] = -ws[H.w_rhs + d];
     }
     g.sync();
-    const uint32_t mflags = phase_muscles<MODE>(T, ws, g, dt, exc, act, force_out, ev, sc);
+    const uint32_t mflags = phase_muscles<MODE>(T, ws, g, dt, exc, act, force_out, vm_out, ev, sc);
     const bool bad = (mflags & 1u) != 0;
     PHASE_MARK(3);
     phase_contact<MODE>(T, ws, g, dt, ev);
@@ -990,12 +998,16 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             if (ev.tau_l) ev.tau_l[d] = 0.f;
         }
         g.sync();
-        st |= substep<kModeEval>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, &ev, nullptr, a.timers);
+        st |= substep<kModeEval>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, nullptr, &ev, nullptr, a.timers);
     } else if (MODE == kModeGeom) {
         EvalPtrs ev = a.ev;
         ev.L = a.ev.L + (size_t)(e - a.env_begin) * ev.nnz_pitch;   // label row: L then R
         ev.R = ev.L + H.m;
-        substep<kModeGeom>(T, ws, g, a.dt, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
+        substep<kModeGeom>(T, ws, g, a.dt, nullptr, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
+    } else if (MODE == kModeFk) {
+        EvalPtrs ev = a.ev;
+        ev.xpos = a.ev.xpos + (size_t)(e - a.env_begin) * ev.xpos_pitch;
+        substep<kModeFk>(T, ws, g, a.dt, nullptr, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
     } else {
         if (MODE == kModeSurr) {
             // one substep with the learned geometry (the host loops over substeps)
@@ -1015,7 +1027,8 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             sc.tol = a.tol;
             sc.max_err_bits = reinterpret_cast<unsigned int*>(a.surr_stats + 6);
             const uint32_t s1 = substep<kModeSurr>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
-                                                   a.force_out ? a.force_out + rm : nullptr, nullptr, &sc, a.timers);
+                                                   a.force_out ? a.force_out + rm : nullptr,
+                                                   a.vm_out ? a.vm_out + rm : nullptr, nullptr, &sc, a.timers);
             st |= s1 & 0xffu;
             if (g.lane == 0) {
                 unsigned long long* cs = a.surr_stats;   // see msim_surrogate_stats
@@ -1033,7 +1046,8 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             for (int s = 0; s < a.n_sub; ++s) {
                 const bool last = (s == a.n_sub - 1);
                 st |= substep<kModeStep>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
-                                         (last && a.force_out) ? a.force_out + rm : nullptr, nullptr, nullptr,
+                                         (last && a.force_out) ? a.force_out + rm : nullptr,
+                                         (last && a.vm_out) ? a.vm_out + rm : nullptr, nullptr, nullptr,
                                          a.timers);
             }
         }
@@ -1208,6 +1222,7 @@ cudaError_t set_step_smem_limit(size_t bytes) {
                          (const void*)k_step<kModeStep, 4>, (const void*)k_step<kModeEval, 1>,
                          (const void*)k_step<kModeEval, 2>, (const void*)k_step<kModeEval, 4>,
                          (const void*)k_step<kModeGeom, 1>, (const void*)k_step<kModeGeom, 2>,
+                         (const void*)k_step<kModeFk, 1>, (const void*)k_step<kModeFk, 2>,
                          (const void*)k_step<kModeSurr, 1>, (const void*)k_step<kModeSurr, 2>,
                          (const void*)k_step<kModeSurr, 4>, (const void*)k_step_mixed<1>,
                          (const void*)k_step_mixed<2>, (const void*)k_step_mixed<4>};
@@ -1257,6 +1272,13 @@ cudaError_t launch_geom(const StepArgs& a, int grid, size_t smem, cudaStream_t s
     const int threads = 32 * a.wpe * a.envs_per_block;
     if (a.wpe == 2) k_step<kModeGeom, 2><<<grid, threads, smem, s>>>(a);
     else k_step<kModeGeom, 1><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fk(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
+    const int threads = 32 * a.wpe * a.envs_per_block;
+    if (a.wpe == 2) k_step<kModeFk, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<kModeFk, 1><<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -92,7 +92,7 @@ EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_s
            "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
            "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_policy_attach",
            "msim_policy_step", "msim_policy_excitations", "msim_measure_fp32_peak", "msim_flow_attach",
-           "msim_flow_actions",
+           "msim_flow_actions", "msim_reward_attach", "msim_reward", "msim_body_positions",
            "msim_last_error", "msim_version")
 
 _lib = None
@@ -149,6 +149,9 @@ def load_library(path=LIB_PATH):
     lib.msim_measure_fp32_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
     lib.msim_flow_attach.argtypes = [vp, vp, C.c_int32, C.c_float, C.c_float]
     lib.msim_flow_actions.argtypes = [vp, vp, vp, vp]
+    lib.msim_reward_attach.argtypes = [vp, vp, C.c_float]
+    lib.msim_reward.argtypes = [vp, vp, vp, vp, vp, C.c_int32, vp]
+    lib.msim_body_positions.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp]
     lib.msim_last_error.argtypes = [vp]
     lib.msim_last_error.restype = C.c_char_p
     lib.msim_version.restype = C.c_int32
@@ -364,6 +367,31 @@ class Sim:
         mu, a = self.zeros(self.pitch_m), self.zeros(self.pitch_m)
         self._check(self.lib.msim_flow_actions(self.h, _ptr(mu), _ptr(a), _stream_ptr(stream)))
         return mu, a
+
+    def reward_attach(self, disc, w_power=0.0):
+        """Bind the discriminator (in = n + 3 nb, out = 1, sigmoid) of the imitation reward."""
+        self._disc = disc
+        self._check(self.lib.msim_reward_attach(self.h, disc.h if disc is not None else None, float(w_power)))
+
+    def reward(self, q_ref, stream=None, with_parts=False, with_delta=False):
+        """Imitation reward of every environment against q_ref [n_envs, pitch_n] (CUDA)."""
+        import torch
+        r = torch.zeros(self.n_envs, device=self.device)
+        parts = torch.zeros((self.n_envs, 2), device=self.device) if with_parts else None
+        nd = self.dims.n_dofs[0] + 3 * self.dims.n_bodies[0]
+        delta = torch.zeros((self.n_envs, nd), device=self.device) if with_delta else None
+        self._check(self.lib.msim_reward(self.h, _ptr(q_ref), _ptr(r), _ptr(parts) if parts is not None else None,
+                                         _ptr(delta) if delta is not None else None, nd, _stream_ptr(stream)))
+        return r, parts, delta
+
+    def body_positions(self, q, stream=None):
+        """Body origins [rows, 3 nb] at configurations q [rows, >= n] (CUDA FP32)."""
+        import torch
+        q = q.contiguous()
+        out = torch.zeros((q.shape[0], 3 * self.dims.n_bodies[0]), device=self.device)
+        self._check(self.lib.msim_body_positions(self.h, q.data_ptr(), q.stride(0), q.shape[0], out.data_ptr(),
+                                                 _stream_ptr(stream)))
+        return out
 
     def policy_excitations(self, stream=None):
         out = self.zeros(self.pitch_m)
