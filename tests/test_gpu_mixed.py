@@ -117,3 +117,38 @@ def test_autotune_keeps_state_and_caches_its_choice():
         r2 = other.autotune(path, n_sub=10)
         assert r2["from_cache"] == 1 and r2["mixed"] == r["mixed"]
         assert r2["envs_per_block"] == r["envs_per_block"]
+
+
+def test_a_model_without_environments_is_skipped_by_both_launches():
+    models = [mg.config_model(n) for n in NAMES]
+    counts = [9, 0, 7]
+    a = msim.Sim(models, counts, dt=DT)
+    b = msim.Sim(models, counts, dt=DT)
+    b.set_mixed_launch(True)
+    qs, qds, acts, ex = [], [], [], []
+    for i, (m, E) in enumerate(zip(models, counts)):
+        if E == 0:
+            continue
+        q, qd, ac = mg.initial_state(m, E, seed=i)
+        qs.append(a._pad(q, a.pitch_n)); qds.append(a._pad(qd, a.pitch_n)); acts.append(a._pad(ac, a.pitch_m))
+        ex.append(a._pad(mg.uniform_excitations(m, E, 1, seed=i)[0], a.pitch_m))
+    for s in (a, b):
+        s.reset(torch.cat(qs), torch.cat(qds), torch.cat(acts))
+        s.step(torch.cat(ex), 10)
+    _same_state(a, b)
+
+
+def test_autotune_ignores_a_damaged_cache_line():
+    counts = (16, 16, 16)
+    sim, _, _ = _mixed_sim(counts, seed=8)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "tune.txt")
+        r = sim.autotune(path, n_sub=2)
+        line = open(path).read().split()
+        with open(path, "w") as f:   # same key, truncated fields: must be re-timed, not applied
+            f.write(" ".join(line[:6]) + "\n")
+        other, _, _ = _mixed_sim(counts, seed=9)
+        r2 = other.autotune(path, n_sub=2)
+        assert r2["from_cache"] == 0 and r2["candidates"] > 0
+        r3 = other.autotune(path, n_sub=2)
+        assert r3["from_cache"] == 1

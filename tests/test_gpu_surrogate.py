@@ -208,3 +208,36 @@ def test_surrogate_argument_and_state_errors():
     sim.train_surrogate(8192, 1, batch=1024)
     net = sim.surrogate_network()
     assert sim.lib.msim_mlp_destroy(net.h) == 1   # borrowed: refused (MSIM_ERR_ARG)
+
+
+def test_learned_geometry_steps_replay_from_a_cuda_graph(trained):
+    """Without checks the learned-geometry step is deterministic: a captured graph of it replays
+    bit for bit like the eager calls (input kernel, network, step kernel per substep)."""
+    model, sim = trained
+    q0, qd0, a0 = mg.initial_state(model, E, seed=13)
+    exc = sim.pad_m(mg.smooth_excitations(model, E, 1, seed=13)[0])
+    sim.set_geometry_mode(1)
+    sim.surrogate_set_check(0.0, 1e-3)
+    try:
+        sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+        for _ in range(3):
+            sim.step(exc, 2)
+        eager = sim.state()
+        stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            sim.step(exc, 2)
+        torch.cuda.synchronize()
+        sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+        sim.surrogate_stats(reset=True)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        replay = sim.state()
+        for k in ("q", "qd", "act"):
+            assert torch.equal(eager[k], replay[k]), k
+        assert sim.surrogate_stats()["env_substeps"] == 6 * E
+    finally:
+        sim.set_geometry_mode(0)
+        sim.surrogate_set_check(0.01, 1e-3)
