@@ -18,7 +18,8 @@ Two more workloads print their own line:
                         captured in a CUDA graph): per-model launches vs the autotuned mixed launch;
   --workload c4_policy  16384 whole-body envs with a policy MLP in the loop (one inference per
                         2 substeps, CUDA graphs), exact vs learned geometry;
-  --workload c3_mlp     the surrogate network's forward pass alone (tensor-core GEMMs).
+  --workload c3_mlp     the surrogate network's forward pass alone (tensor-core GEMMs);
+  --workload c3_width   the learned geometry's accuracy and cost against the network width.
 """
 import argparse
 import json
@@ -406,6 +407,57 @@ def run_mlp(args):
                          "peak_note": "bf16_tflops (burst) of measured"}}
 
 
+def run_width(args):
+    """Learned geometry: accuracy and network cost against the hidden width (2M samples, 50
+    epochs each, training box = limits + 5 %), on fresh configurations of the box."""
+    import torch
+    from paper_2603_29332_b300 import msim
+    model = mg.config_model(MODEL)
+    E = args.envs
+    sim = msim.Sim(model, E, dt=DT, seed=3)
+    m = model.n_muscles
+    lo, hi = model.dof_limit[:, 0].astype(np.float64), model.dof_limit[:, 1].astype(np.float64)
+    c, hw = 0.5 * (lo + hi), 0.5 * (hi - lo) * 1.05
+    qs = (c + hw * np.random.default_rng(99).uniform(-1, 1, (8192, model.n_dofs))).astype(np.float32)
+    qg = torch.zeros((8192, sim.pitch_n), device="cuda")
+    qg[:, : model.n_dofs] = torch.from_numpy(qs).cuda()
+    exact = sim.geometry(qg)
+    rows = []
+    for hidden in (512, 1024, 2048):
+        sim.surrogate_set_width(hidden)
+        t0 = time.perf_counter()
+        sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=1e-3)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        err = (sim.surrogate_predict(qg) - exact).abs()
+        eR = err[:, m:]
+        net = sim.surrogate_network()
+        X = torch.zeros((E, net.in_pitch), dtype=torch.bfloat16, device="cuda")
+        Y = torch.empty((E, net.out_pitch), device="cuda")
+        for _ in range(3):
+            net.forward(X, Y)
+        cur = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(cur)
+        for _ in range(20):
+            net.forward(X, Y)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        rows.append({"hidden": hidden, "train_s": train_s,
+                     "moment_arm_abs_err_m": {"median": float(eR.median()),
+                                              "p99": float(eR.flatten()[::3].quantile(0.99)),
+                                              "max": float(eR.max())},
+                     "length_abs_err_m_median": float(err[:, :m].median()),
+                     "env_rms_err_m_median": float(err.pow(2).mean(1).sqrt().median()),
+                     "envs_with_max_err_within_1mm": float((err.max(1).values <= 1e-3).float().mean()),
+                     "forward_us_at_batch": e0.elapsed_time(e1) / 20 * 1e3})
+    return {"metric": "learned geometry accuracy vs hidden width (whole body, %d samples x %d epochs)"
+                      % (args.surr_samples, args.surr_epochs),
+            "value": rows[0]["moment_arm_abs_err_m"]["median"], "unit": "m (median moment-arm error, width 512)",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "batch": E, "widths": rows}
+
+
 def run_mixed(args):
     """Three skeletons in one handle: per-model launches vs the autotuned mixed launch (graphs)."""
     import torch
@@ -541,7 +593,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
-    ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp"])
+    ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
     ap.add_argument("--policy-envs", type=int, default=16384)
     ap.add_argument("--policy-steps", type=int, default=2000)
     args = ap.parse_args()
@@ -558,6 +610,8 @@ def main():
         out = run_policy(args)
     elif args.workload == "c3_mlp":
         out = run_mlp(args)
+    elif args.workload == "c3_width":
+        out = run_width(args)
     else:
         if world > 1:
             import torch

@@ -263,7 +263,8 @@ MSIM_API msim_status msim_mlp_adam(msim_mlp m, float lr, float beta1, float beta
  * box (each DoF's limit range widened by `margin` half-ranges on both sides, margin 0.05 unless
  * msim_surrogate_set_box says otherwise; +-pi for a DoF without limits), labels
  * them with the exact geometry kernel, normalises every output by its mean and standard deviation,
- * and trains a 3-layer MLP (n -> 512 -> 512 -> m + nnz, SiLU, BF16 tensor-core GEMMs with FP32
+ * and trains a 3-layer MLP (n -> 512 -> 512 -> m + nnz by default, msim_surrogate_set_width; SiLU,
+ * BF16 tensor-core GEMMs with FP32
  * accumulation) for `epochs` passes of n_samples / batch minibatches with Adam (beta 0.9, 0.999,
  * eps 1e-8; learning rate lr with cosine decay to lr / 100).  Randomness from the create seed.
  * Needs about n_samples * (4 (m + nnz) + 2 n) bytes of device memory while it runs (MSIM_ERR_OOM
@@ -282,6 +283,9 @@ MSIM_API msim_status msim_set_geometry_mode(msim_handle h, int32_t mode);
  * msim_surrogate_train (the penalty joint limits let states pass the limits, so a box wider than
  * the limits keeps more environments on the network). */
 MSIM_API msim_status msim_surrogate_set_box(msim_handle h, float margin);
+/* msim_surrogate_set_width -- hidden width of the next msim_surrogate_train's network (default
+ * 512; a multiple of 64 in [64, 4096]): accuracy against cost. */
+MSIM_API msim_status msim_surrogate_set_width(msim_handle h, int32_t hidden);
 /* msim_surrogate_set_check -- check fraction in [0, 1] and tolerance > 0 (metres). */
 MSIM_API msim_status msim_surrogate_set_check(msim_handle h, float check_frac, float tol);
 

@@ -33,6 +33,7 @@ struct msim_handle_ {
     uint32_t seed = 0;
     msim::Surrogate* sur = nullptr;
     float box_margin = 0.05f;   // training box of the next msim_surrogate_train
+    int surr_hidden = msim::kSurrHidden;   // hidden width of the next msim_surrogate_train
     msim_mlp_ sur_view;
     int n_models = 0, n_envs = 0, pitch_n = 0, pitch_m = 0;
     float dt = 0.f;

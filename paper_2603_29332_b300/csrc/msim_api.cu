@@ -1030,7 +1030,7 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
     S->box_margin = margin;
     S->check_frac = check_frac;
     S->tol = tol;
-    cudaError_t e = mlp_create(n, kSurrHidden, out, 0, std::max(batch, h->n_envs), &S->net);
+    cudaError_t e = mlp_create(n, h->surr_hidden, out, 0, std::max(batch, h->n_envs), &S->net);
     if (e == cudaSuccess) e = mlp_init(S->net, (uint64_t)h->seed * 2654435761ull + 17u, 1.f, s);
     auto A = [&](void** p, size_t b) {
         if (e == cudaSuccess) e = cudaMalloc(p, b);
@@ -1139,6 +1139,13 @@ msim_status msim_surrogate_set_box(msim_handle h, float margin) {
     if (!h || !(margin >= 0.f && margin <= 10.f)) return arg_fail(h, "msim_surrogate_set_box: margin in [0, 10]");
     h->box_margin = margin;
     if (h->sur) h->sur->box_margin = margin;   // takes effect at the next msim_surrogate_train
+    return MSIM_OK;
+}
+
+msim_status msim_surrogate_set_width(msim_handle h, int32_t hidden) {
+    if (!h || hidden < 64 || hidden > 4096 || hidden % 64)
+        return arg_fail(h, "msim_surrogate_set_width: hidden must be a multiple of 64 in [64, 4096]");
+    h->surr_hidden = hidden;   // takes effect at the next msim_surrogate_train
     return MSIM_OK;
 }
 

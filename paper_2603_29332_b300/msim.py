@@ -90,7 +90,7 @@ EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_s
            "msim_mlp_get", "msim_mlp_set", "msim_mlp_forward", "msim_mlp_backward", "msim_mlp_adam",
            "msim_surrogate_train", "msim_set_geometry_mode", "msim_surrogate_set_check", "msim_surrogate_stats",
            "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
-           "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_policy_attach",
+           "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_surrogate_set_width", "msim_policy_attach",
            "msim_policy_step", "msim_policy_excitations", "msim_measure_fp32_peak", "msim_flow_attach",
            "msim_flow_actions", "msim_reward_attach", "msim_reward", "msim_body_positions",
            "msim_last_error", "msim_version")
@@ -135,6 +135,7 @@ def load_library(path=LIB_PATH):
     lib.msim_set_geometry_mode.argtypes = [vp, C.c_int32]
     lib.msim_surrogate_set_check.argtypes = [vp, C.c_float, C.c_float]
     lib.msim_surrogate_set_box.argtypes = [vp, C.c_float]
+    lib.msim_surrogate_set_width.argtypes = [vp, C.c_int32]
     lib.msim_surrogate_stats.argtypes = [vp, C.POINTER(SurrogateInfo), C.c_int32]
     lib.msim_surrogate_network.argtypes = [vp, C.POINTER(vp)]
     lib.msim_geometry.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
@@ -416,6 +417,9 @@ class Sim:
     def surrogate_set_box(self, margin):
         self._check(self.lib.msim_surrogate_set_box(self.h, float(margin)))
 
+    def surrogate_set_width(self, hidden):
+        self._check(self.lib.msim_surrogate_set_width(self.h, int(hidden)))
+
     def set_geometry_mode(self, mode):
         self._check(self.lib.msim_set_geometry_mode(self.h, int(mode)))
 
@@ -441,7 +445,11 @@ class Sim:
         h = C.c_void_p()
         self._check(self.lib.msim_surrogate_network(self.h, C.byref(h)))
         d_in = self.dims.n_dofs[0]
-        return MLP.borrowed(h, d_in, 512, self.dims.n_muscles[0] + self.dims.nnz[0])
+        off = (C.c_int64 * 6)()
+        ip = C.c_int32()
+        self.lib.msim_mlp_layout(h, off, None, C.byref(ip), None)
+        hidden = (off[1] - off[0]) // ip.value
+        return MLP.borrowed(h, d_in, hidden, self.dims.n_muscles[0] + self.dims.nnz[0])
 
 
 def measure_fp32_peak(device=0):
