@@ -104,9 +104,13 @@ struct alignas(16) ImgHeader {
 //   racc[n][2]                        R^T F + tau_c as fixed-point int32 pairs
 //   y[n][2]                           float-float solution of the two triangular solves
 //   sph[ns][12]                       per-sphere contact point, force, damping, flags
-//   rk[kMaxCross][32 wpe]             per-lane moment arms of the muscle being processed (last)
+//   rk[kMaxCross][32 wpe]             per-lane moment arms of the muscle being processed (last);
+//                                     sin, cos of the joint angles during the kinematics pass
 
 // floats per environment slot for a group of `wpe` warps per environment
-__host__ __device__ inline int ws_floats(const ImgHeader& h, int wpe) { return h.w_rk + kMaxCross * 32 * wpe; }
+// (the moment-arm region also holds the joint sines and cosines during the kinematics pass)
+__host__ __device__ inline int ws_floats(const ImgHeader& h, int wpe) {
+    return h.w_rk + (kMaxCross * 32 * wpe > 2 * h.n ? kMaxCross * 32 * wpe : 2 * h.n);
+}
 
 }  // namespace msim

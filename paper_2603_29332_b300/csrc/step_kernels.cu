@@ -244,6 +244,11 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
     float* FI = ws + H.w_fi;
     float* S = ws + H.w_S;
     float* Acc = ws + H.w_A;   // bias accelerations live in the A region during this pass
+    float* SC = ws + H.w_rk;   // sin, cos of every joint angle (the moment-arm scratch is free here)
+    // 1. joint-angle sines and cosines, all DoFs in parallel (off the level-by-level chain)
+    for (int d = g.lane; d < H.n; d += g.N) sincosf(q[d], &SC[2 * d], &SC[2 * d + 1]);
+    g.sync();
+    // 2. frames, velocities and bias accelerations, root first, the bodies of a level in parallel
     for (int l = 0; l < H.n_blevels; ++l) {
         const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
         for (int i = i0 + g.lane; i < i1; i += g.N) {
@@ -292,8 +297,7 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
                     vl[k] += sl[k];
                 }
                 // R <- R Rot(axis, q) = c R + s (rows x axis) + (1 - c) (R axis) axis^T
-                float sn, cs;
-                sincosf(q[d], &sn, &cs);
+                const float sn = SC[2 * d], cs = SC[2 * d + 1];
                 const float* ax = D.axis;
                 const float omc = 1.f - cs;
 #pragma unroll
@@ -315,73 +319,88 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
             float* Ab = Acc + 6 * b;
 #pragma unroll
             for (int k = 0; k < 3; ++k) { Vb[k] = w[k]; Vb[3 + k] = vl[k]; Ab[k] = aw[k]; Ab[3 + k] = al[k]; }
-            // spatial inertia about the world origin: m, h = m c, Ibar = R Ic R^T + m (|c|^2 1 - c c^T).
-            // R Ic R^T in FP32 (a consistent perturbation of the body's own inertia); the
-            // parallel-axis part, exact products of the FP32 COM, in float-float.
-            const float m = B.mass;
-            float c[3];
-            rot3(R, B.com, c);
-            c[0] += p[0]; c[1] += p[1]; c[2] += p[2];
-            const float I9[9] = {B.I[0], B.I[3], B.I[4], B.I[3], B.I[1], B.I[5], B.I[4], B.I[5], B.I[2]};
-            float TI[9];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc)
-                    TI[3 * r + cc] = R[3 * r] * I9[cc] + R[3 * r + 1] * I9[3 + cc] + R[3 * r + 2] * I9[6 + cc];
-            const df c00 = two_prod(c[0], c[0]), c11 = two_prod(c[1], c[1]), c22 = two_prod(c[2], c[2]);
-            const df cc2 = df_add(df_add(c00, c11), c22);
-            df Ibd[6];   // xx yy zz xy xz yz
-            {
-                const float rxx = TI[0] * R[0] + TI[1] * R[1] + TI[2] * R[2];
-                const float ryy = TI[3] * R[3] + TI[4] * R[4] + TI[5] * R[5];
-                const float rzz = TI[6] * R[6] + TI[7] * R[7] + TI[8] * R[8];
-                const float rxy = TI[0] * R[3] + TI[1] * R[4] + TI[2] * R[5];
-                const float rxz = TI[0] * R[6] + TI[1] * R[7] + TI[2] * R[8];
-                const float ryz = TI[3] * R[6] + TI[4] * R[7] + TI[5] * R[8];
-                Ibd[0] = df_add_f(df_mul_f(df_add(cc2, df_neg(c00)), m), rxx);
-                Ibd[1] = df_add_f(df_mul_f(df_add(cc2, df_neg(c11)), m), ryy);
-                Ibd[2] = df_add_f(df_mul_f(df_add(cc2, df_neg(c22)), m), rzz);
-                Ibd[3] = df_add_f(df_neg(df_mul_f(two_prod(c[0], c[1]), m)), rxy);
-                Ibd[4] = df_add_f(df_neg(df_mul_f(two_prod(c[0], c[2]), m)), rxz);
-                Ibd[5] = df_add_f(df_neg(df_mul_f(two_prod(c[1], c[2]), m)), ryz);
-            }
-            const df hd[3] = {two_prod(m, c[0]), two_prod(m, c[1]), two_prod(m, c[2])};
-            // FP32 body force from the rounded inertia: f = I a + v x* (I v)
-            const float h[3] = {hd[0].hi, hd[1].hi, hd[2].hi};
-            const float Ib[6] = {Ibd[0].hi, Ibd[1].hi, Ibd[2].hi, Ibd[3].hi, Ibd[4].hi, Ibd[5].hi};
-            auto imul = [&](const float xw[3], const float xl[3], float ow[3], float ol[3]) {
-                float t1[3], t2[3];
-                cross3(h, xl, t1);
-                cross3(h, xw, t2);
-                ow[0] = Ib[0] * xw[0] + Ib[3] * xw[1] + Ib[4] * xw[2] + t1[0];
-                ow[1] = Ib[3] * xw[0] + Ib[1] * xw[1] + Ib[5] * xw[2] + t1[1];
-                ow[2] = Ib[4] * xw[0] + Ib[5] * xw[1] + Ib[2] * xw[2] + t1[2];
-                ol[0] = m * xl[0] - t2[0];
-                ol[1] = m * xl[1] - t2[1];
-                ol[2] = m * xl[2] - t2[2];
-            };
-            float Ivw[3], Ivl[3], Iaw[3], Ial[3];
-            imul(w, vl, Ivw, Ivl);
-            imul(aw, al, Iaw, Ial);
-            float t1[3], t2[3], t3[3];
-            cross3(w, Ivw, t1);
-            cross3(vl, Ivl, t2);
-            cross3(w, Ivl, t3);
-            float* fi = FI + kFiStride * b;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                fi[k] = Iaw[k] + t1[k] + t2[k];
-                fi[3 + k] = Ial[k] + t3[k];
-            }
-            df* Id = reinterpret_cast<df*>(fi + 6);   // m, h[3], Ibar[6]
-            Id[0] = df_make(m);
-            Id[1] = hd[0]; Id[2] = hd[1]; Id[3] = hd[2];
-#pragma unroll
-            for (int e = 0; e < 6; ++e) Id[4 + e] = Ibd[e];
         }
         g.sync();
     }
+    // 3. spatial inertia and body force of every body, all bodies in parallel
+    for (int b = g.lane; b < H.nb; b += g.N) {
+        const BodyRec& B = T.body[b];
+        const float* Fb = frame + 12 * b;
+        const float* Vb = V + 6 * b;
+        const float* Ab = Acc + 6 * b;
+        float R[9], p[3], w[3], vl[3], aw[3], al[3];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = Fb[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            p[k] = Fb[9 + k]; w[k] = Vb[k]; vl[k] = Vb[3 + k]; aw[k] = Ab[k]; al[k] = Ab[3 + k];
+        }
+        // spatial inertia about the world origin: m, h = m c, Ibar = R Ic R^T + m (|c|^2 1 - c c^T).
+        // R Ic R^T in FP32 (a consistent perturbation of the body's own inertia); the
+        // parallel-axis part, exact products of the FP32 COM, in float-float.
+        const float m = B.mass;
+        float c[3];
+        rot3(R, B.com, c);
+        c[0] += p[0]; c[1] += p[1]; c[2] += p[2];
+        const float I9[9] = {B.I[0], B.I[3], B.I[4], B.I[3], B.I[1], B.I[5], B.I[4], B.I[5], B.I[2]};
+        float TI[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+                TI[3 * r + cc] = R[3 * r] * I9[cc] + R[3 * r + 1] * I9[3 + cc] + R[3 * r + 2] * I9[6 + cc];
+        const df c00 = two_prod(c[0], c[0]), c11 = two_prod(c[1], c[1]), c22 = two_prod(c[2], c[2]);
+        const df cc2 = df_add(df_add(c00, c11), c22);
+        df Ibd[6];   // xx yy zz xy xz yz
+        {
+            const float rxx = TI[0] * R[0] + TI[1] * R[1] + TI[2] * R[2];
+            const float ryy = TI[3] * R[3] + TI[4] * R[4] + TI[5] * R[5];
+            const float rzz = TI[6] * R[6] + TI[7] * R[7] + TI[8] * R[8];
+            const float rxy = TI[0] * R[3] + TI[1] * R[4] + TI[2] * R[5];
+            const float rxz = TI[0] * R[6] + TI[1] * R[7] + TI[2] * R[8];
+            const float ryz = TI[3] * R[6] + TI[4] * R[7] + TI[5] * R[8];
+            Ibd[0] = df_add_f(df_mul_f(df_add(cc2, df_neg(c00)), m), rxx);
+            Ibd[1] = df_add_f(df_mul_f(df_add(cc2, df_neg(c11)), m), ryy);
+            Ibd[2] = df_add_f(df_mul_f(df_add(cc2, df_neg(c22)), m), rzz);
+            Ibd[3] = df_add_f(df_neg(df_mul_f(two_prod(c[0], c[1]), m)), rxy);
+            Ibd[4] = df_add_f(df_neg(df_mul_f(two_prod(c[0], c[2]), m)), rxz);
+            Ibd[5] = df_add_f(df_neg(df_mul_f(two_prod(c[1], c[2]), m)), ryz);
+        }
+        const df hd[3] = {two_prod(m, c[0]), two_prod(m, c[1]), two_prod(m, c[2])};
+        // FP32 body force from the rounded inertia: f = I a + v x* (I v)
+        const float h[3] = {hd[0].hi, hd[1].hi, hd[2].hi};
+        const float Ib[6] = {Ibd[0].hi, Ibd[1].hi, Ibd[2].hi, Ibd[3].hi, Ibd[4].hi, Ibd[5].hi};
+        auto imul = [&](const float xw[3], const float xl[3], float ow[3], float ol[3]) {
+            float t1[3], t2[3];
+            cross3(h, xl, t1);
+            cross3(h, xw, t2);
+            ow[0] = Ib[0] * xw[0] + Ib[3] * xw[1] + Ib[4] * xw[2] + t1[0];
+            ow[1] = Ib[3] * xw[0] + Ib[1] * xw[1] + Ib[5] * xw[2] + t1[1];
+            ow[2] = Ib[4] * xw[0] + Ib[5] * xw[1] + Ib[2] * xw[2] + t1[2];
+            ol[0] = m * xl[0] - t2[0];
+            ol[1] = m * xl[1] - t2[1];
+            ol[2] = m * xl[2] - t2[2];
+        };
+        float Ivw[3], Ivl[3], Iaw[3], Ial[3];
+        imul(w, vl, Ivw, Ivl);
+        imul(aw, al, Iaw, Ial);
+        float t1[3], t2[3], t3[3];
+        cross3(w, Ivw, t1);
+        cross3(vl, Ivl, t2);
+        cross3(w, Ivl, t3);
+        float* fi = FI + kFiStride * b;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            fi[k] = Iaw[k] + t1[k] + t2[k];
+            fi[3 + k] = Ial[k] + t3[k];
+        }
+        df* Id = reinterpret_cast<df*>(fi + 6);   // m, h[3], Ibar[6]
+        Id[0] = df_make(m);
+        Id[1] = hd[0]; Id[2] = hd[1]; Id[3] = hd[2];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) Id[4 + e] = Ibd[e];
+    }
+    g.sync();
 }
 
 // ------------------------------------------------------------------ phase 2: subtree sums, bias
