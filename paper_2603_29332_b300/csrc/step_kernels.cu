@@ -410,40 +410,35 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     float* FI = ws + H.w_fi;
     const float* S = ws + H.w_S;
     float* rhs = ws + H.w_rhs;
+    // subtree sums leaves first; every body's 16 components (force 6, float-float inertia 10) go
+    // to their own lanes, so a level costs one chain of child additions per component
     for (int l = H.n_blevels - 1; l >= 0; --l) {
         const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
-        for (int i = i0 + g.lane; i < i1; i += g.N) {
-            const int b = T.border[i];
+        for (int t = g.lane; t < 16 * (i1 - i0); t += g.N) {
+            const int b = T.border[i0 + t / 16], comp = t % 16;
             const BodyRec& B = T.body[b];
             float* fi = FI + kFiStride * b;
-            float f[6];
-            df I[10];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) f[k] = fi[k];
-            const df* Ib = reinterpret_cast<const df*>(fi + 6);
-#pragma unroll
-            for (int k = 0; k < 10; ++k) I[k] = Ib[k];
-            for (int c = 0; c < B.nchild; ++c) {
-                const float* fc = FI + kFiStride * T.child[B.child0 + c];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) f[k] += fc[k];
-                const df* Ic = reinterpret_cast<const df*>(fc + 6);
-#pragma unroll
-                for (int k = 0; k < 10; ++k) I[k] = df_add(I[k], Ic[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) fi[k] = f[k];
-            df* Io = reinterpret_cast<df*>(fi + 6);
-#pragma unroll
-            for (int k = 0; k < 10; ++k) Io[k] = I[k];
-            for (int j = 0; j < B.ndof; ++j) {
-                const int d = B.dof0 + j;
-                const float* Sd = S + 6 * d;
-                rhs[d] = -(Sd[0] * f[0] + Sd[1] * f[1] + Sd[2] * f[2] + Sd[3] * f[3] + Sd[4] * f[4] + Sd[5] * f[5]);
+            if (comp < 6) {
+                float f = fi[comp];
+                for (int c = 0; c < B.nchild; ++c) f += FI[kFiStride * T.child[B.child0 + c] + comp];
+                fi[comp] = f;
+            } else {
+                df* Io = reinterpret_cast<df*>(fi + 6) + (comp - 6);
+                df I = *Io;
+                for (int c = 0; c < B.nchild; ++c)
+                    I = df_add(I, reinterpret_cast<const df*>(FI + kFiStride * T.child[B.child0 + c] + 6)[comp - 6]);
+                *Io = I;
             }
         }
         g.sync();
     }
+    // bias of every DoF from its body's subtree force, all DoFs in parallel: rhs = -S^T f
+    for (int d = g.lane; d < H.n; d += g.N) {
+        const float* Sd = S + 6 * d;
+        const float* f = FI + kFiStride * T.dof[d].body;
+        rhs[d] = -(Sd[0] * f[0] + Sd[1] * f[1] + Sd[2] * f[2] + Sd[3] * f[3] + Sd[4] * f[4] + Sd[5] * f[5]);
+    }
+    g.sync();
 }
 
 // ------------------------------------------------------------------ phase 3: CRBA (float-float)
