@@ -861,28 +861,24 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
         }
         SUB_MARK(13);
     }
-    // L x = y, root first (x overwrites y).  The nodes of a level are dealt round-robin to the
-    // group's warps; inside a warp each node gets a group of lanes that reduces its dot product
-    // over the ancestors with shuffles.
-    for (int l = 0; l < H.n_dlevels; ++l) {
-        const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
-        const int nkw = (i1 - i0 - g.wi + WPE - 1) / WPE;   // nodes handled by this warp
-        for (int c0 = 0; c0 < nkw; c0 += 32) {
-            const int nk = min(nkw - c0, 32);
-            int gs = 32;
-            while (gs > 1 && gs * nk > 32) gs >>= 1;          // lanes per node
-            const int grp = g.wl / gs, li = g.wl % gs;
-            const bool act = grp < nk;
-            const int k = T.dorder[i0 + g.wi + WPE * (c0 + (act ? grp : 0))];
+    // L x = y, root first (x overwrites y), by columns: once the nodes of depth l are final,
+    // every deeper node k subtracts L_{k,a} x_a for its ancestor a of depth l (exactly one per
+    // node and level, so the level's updates are independent); a node of depth l + 1 has then
+    // received all its terms and is scaled by 1 / L_kk in the same pass.
+    const int n_all = T.dlevel[H.n_dlevels];
+    for (int i = g.lane; i < T.dlevel[1]; i += g.N) {   // roots
+        const DofRec& D = T.dof[T.dorder[i]];
+        Y[T.dorder[i]] = df_mul(Y[T.dorder[i]], A[D.row + D.depth]);
+    }
+    g.sync();
+    for (int l = 0; l + 1 < H.n_dlevels; ++l) {
+        const int next_end = T.dlevel[l + 2];
+        for (int i = T.dlevel[l + 1] + g.lane; i < n_all; i += g.N) {
+            const int k = T.dorder[i];
             const DofRec& D = T.dof[k];
-            df part = df_make(0.f);
-            if (act)
-                for (int j = li; j < D.depth; j += gs) part = df_add(part, df_mul(A[D.row + j], Y[T.anc[D.row + j]]));
-            for (int o = gs >> 1; o > 0; o >>= 1) {
-                const df w = {__shfl_xor_sync(0xffffffffu, part.hi, o), __shfl_xor_sync(0xffffffffu, part.lo, o)};
-                part = df_add(part, w);
-            }
-            if (act && li == 0) Y[k] = df_mul(df_add(Y[k], df_neg(part)), A[D.row + D.depth]);
+            df y = df_fms(Y[k], A[D.row + l], Y[T.anc[D.row + l]]);
+            if (i < next_end) y = df_mul(y, A[D.row + D.depth]);   // depth l + 1: complete
+            Y[k] = y;
         }
         g.sync();
     }
