@@ -47,9 +47,14 @@ typedef struct {
     double contact_k, contact_c, contact_mu, contact_eps;
     double limit_k, limit_c, tau_act, tau_deact, vmax_per_lopt;
     int implicit_damping;
+    /* wrapping cylinders: at most one per muscle, on the segment that ends at the muscle's
+     * point number wrap_segment (1 .. points - 1), fixed to body wrap_body */
+    int nw;
+    const int *wrap_muscle, *wrap_segment, *wrap_body;
+    const double *wrap_center, *wrap_axis, *wrap_radius;
 } ora_model;
 
-int ora_abi_version(void) { return 3; }
+int ora_abi_version(void) { return 4; }
 
 /* ---------------------------------------------------------------- small 3-vector helpers */
 static void cross3(const double a[3], const double b[3], double c[3]) {
@@ -152,6 +157,53 @@ static void point_jac(const ora_model* M, const double* s, const double* o, int 
 
 /* ---------------------------------------------------------------- muscle geometry
  * L[k] = sum over segments of |x_{j+1} - x_j|; R[k][d] = -dL_k/dq_d (dense m x n, or NULL). */
+/* Shortest path from P to S around an infinite cylinder (centre c, unit axis a, radius r;
+ * world frame).  In the plane normal to the axis the path is the tangent from P, the arc, and
+ * the tangent to S, taken around the side with the shorter arc; along the axis the path is a
+ * straight line once the cylinder is unrolled, so the length is sqrt(l_plane^2 + dz^2).  The
+ * path wraps when both points lie outside the cylinder and the straight segment passes within
+ * r of the axis (in the normal plane); otherwise it is the straight segment (*active = 0).
+ * Q and T receive the two tangent points. */
+double ora_wrap_cylinder(const double P[3], const double S[3], const double c[3], const double a[3], double r,
+                            int* active, double Q[3], double T[3]) {
+    double e1[3], e2[3];
+    const double ref[3] = {fabs(a[0]) < 0.9 ? 1.0 : 0.0, fabs(a[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+    cross3(a, ref, e1);
+    double nrm = sqrt(dot3(e1, e1));
+    e1[0] /= nrm; e1[1] /= nrm; e1[2] /= nrm;
+    cross3(a, e1, e2);
+    double p[3] = {P[0] - c[0], P[1] - c[1], P[2] - c[2]}, q[3] = {S[0] - c[0], S[1] - c[1], S[2] - c[2]};
+    double px = dot3(p, e1), py = dot3(p, e2), pz = dot3(p, a);
+    double sx = dot3(q, e1), sy = dot3(q, e2), sz = dot3(q, a);
+    double rp = sqrt(px * px + py * py), rs = sqrt(sx * sx + sy * sy);
+    double dv[3] = {S[0] - P[0], S[1] - P[1], S[2] - P[2]};
+    double straight = sqrt(dot3(dv, dv));
+    *active = 0;
+    if (rp <= r || rs <= r) return straight;
+    double ex = sx - px, ey = sy - py, ee = ex * ex + ey * ey;
+    double t = ee > 0.0 ? -(px * ex + py * ey) / ee : 0.0;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    double cx = px + t * ex, cy = py + t * ey;
+    if (cx * cx + cy * cy >= r * r) return straight;
+    double thp = atan2(py, px), ths = atan2(sy, sx), alp = acos(r / rp), als = acos(r / rs);
+    const double two_pi = 6.283185307179586476925286766559;
+    double arc_ccw = fmod(fmod((ths - als) - (thp + alp), two_pi) + two_pi, two_pi);
+    double arc_cw = fmod(fmod((thp - alp) - (ths + als), two_pi) + two_pi, two_pi);
+    double phq, pht, arc;
+    if (arc_ccw <= arc_cw) { phq = thp + alp; pht = ths - als; arc = arc_ccw; }
+    else { phq = thp - alp; pht = ths + als; arc = arc_cw; }
+    double lp = sqrt(rp * rp - r * r), ls = sqrt(rs * rs - r * r);
+    double lplane = lp + r * arc + ls, dz = sz - pz;
+    double zq = pz + dz * lp / lplane, zt = pz + dz * (lp + r * arc) / lplane;
+    for (int i = 0; i < 3; ++i) {
+        Q[i] = c[i] + r * cos(phq) * e1[i] + r * sin(phq) * e2[i] + zq * a[i];
+        T[i] = c[i] + r * cos(pht) * e1[i] + r * sin(pht) * e2[i] + zt * a[i];
+    }
+    *active = 1;
+    return sqrt(lplane * lplane + dz * dz);
+}
+
 void ora_muscle_geometry(const ora_model* M, const double* Rb, const double* pb, const double* s,
                          const double* o, double* L, double* R) {
     for (int k = 0; k < M->m; ++k) {
@@ -159,6 +211,9 @@ void ora_muscle_geometry(const ora_model* M, const double* Rb, const double* pb,
         double len = 0.0;
         double* row = R ? R + (size_t)k * M->n : NULL;
         if (row) memset(row, 0, sizeof(double) * M->n);
+        int w = -1;
+        for (int i = 0; i < M->nw; ++i)
+            if (M->wrap_muscle[i] == k) w = i;
         double xprev[3];
         int bprev = -1;
         for (int j = p0; j < p1; ++j) {
@@ -166,7 +221,36 @@ void ora_muscle_geometry(const ora_model* M, const double* Rb, const double* pb,
             double x[3];
             matvec3(Rb + 9 * b, M->point_pos + 3 * j, x);
             x[0] += pb[3 * b]; x[1] += pb[3 * b + 1]; x[2] += pb[3 * b + 2];
-            if (j > p0) {
+            int wrapped = 0;
+            if (j > p0 && w >= 0 && j - p0 == M->wrap_segment[w]) {
+                /* the segment from the previous point to this one may wrap the cylinder: lengths
+                 * by wrap_cylinder, moment arms from the two straight parts with the tangent
+                 * points held fixed on the cylinder's body (they slide along the surface, which
+                 * changes the length only to second order) */
+                int bw = M->wrap_body[w];
+                double cw[3], aw[3], Q[3], T[3];
+                matvec3(Rb + 9 * bw, M->wrap_center + 3 * w, cw);
+                cw[0] += pb[3 * bw]; cw[1] += pb[3 * bw + 1]; cw[2] += pb[3 * bw + 2];
+                matvec3(Rb + 9 * bw, M->wrap_axis + 3 * w, aw);
+                double an = sqrt(dot3(aw, aw));
+                aw[0] /= an; aw[1] /= an; aw[2] /= an;
+                double lw = ora_wrap_cylinder(xprev, x, cw, aw, M->wrap_radius[w], &wrapped, Q, T);
+                if (wrapped) {
+                    len += lw;
+                    if (row) {
+                        double d1[3] = {Q[0] - xprev[0], Q[1] - xprev[1], Q[2] - xprev[2]};
+                        double d2[3] = {x[0] - T[0], x[1] - T[1], x[2] - T[2]};
+                        double l1 = sqrt(dot3(d1, d1)), l2 = sqrt(dot3(d2, d2));
+                        double u1[3] = {d1[0] / l1, d1[1] / l1, d1[2] / l1};
+                        double u2[3] = {d2[0] / l2, d2[1] / l2, d2[2] / l2};
+                        add_wJ(M, s, o, bw, Q, u1, -1.0, row);
+                        add_wJ(M, s, o, bprev, xprev, u1, +1.0, row);
+                        add_wJ(M, s, o, b, x, u2, -1.0, row);
+                        add_wJ(M, s, o, bw, T, u2, +1.0, row);
+                    }
+                }
+            }
+            if (j > p0 && !wrapped) {
                 double dv[3] = {x[0] - xprev[0], x[1] - xprev[1], x[2] - xprev[2]};
                 double sl = sqrt(dot3(dv, dv));
                 len += sl;

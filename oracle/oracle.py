@@ -38,7 +38,9 @@ class _OraModel(C.Structure):
                 ("contact_k", C.c_double), ("contact_c", C.c_double), ("contact_mu", C.c_double),
                 ("contact_eps", C.c_double), ("limit_k", C.c_double), ("limit_c", C.c_double),
                 ("tau_act", C.c_double), ("tau_deact", C.c_double), ("vmax_per_lopt", C.c_double),
-                ("implicit_damping", C.c_int)]
+                ("implicit_damping", C.c_int),
+                ("nw", C.c_int), ("wrap_muscle", _ip), ("wrap_segment", _ip), ("wrap_body", _ip),
+                ("wrap_center", _dp), ("wrap_axis", _dp), ("wrap_radius", _dp)]
 
 
 class _EvalOut(C.Structure):
@@ -69,6 +71,7 @@ def lib():
         _lib.ora_eval.restype = C.c_int
         _lib.ora_cholesky_solve.restype = C.c_int
         _lib.ora_max_threads.restype = C.c_int
+        _lib.ora_wrap_cylinder.restype = C.c_double
     return _lib
 
 
@@ -93,6 +96,14 @@ class OracleModel:
             sphere_body=i(model.sphere_body if model.n_spheres else np.zeros(1)),
             sphere_pos=f(model.sphere_pos if model.n_spheres else np.zeros((1, 3))),
             sphere_radius=f(model.sphere_radius if model.n_spheres else np.zeros(1)))
+        nw = int(np.asarray(model.wrap_muscle).shape[0])
+        self._keep.update(
+            wrap_muscle=i(model.wrap_muscle if nw else np.zeros(1)),
+            wrap_segment=i(model.wrap_segment if nw else np.zeros(1)),
+            wrap_body=i(model.wrap_body if nw else np.zeros(1)),
+            wrap_center=f(model.wrap_center if nw else np.zeros((1, 3))),
+            wrap_axis=f(model.wrap_axis if nw else np.zeros((1, 3))),
+            wrap_radius=f(model.wrap_radius if nw else np.zeros(1)))
         s = _OraModel()
         s.nb, s.n, s.m, s.np, s.ns = model.n_bodies, model.n_dofs, model.n_muscles, model.n_points, model.n_spheres
         for k, v in self._keep.items():
@@ -101,6 +112,7 @@ class OracleModel:
         for k, v in model.scalars().items():
             setattr(s, k, float(v))
         s.implicit_damping = 1 if implicit_damping else 0
+        s.nw = nw
         self.s = s
         self.n, self.m, self.nb = model.n_dofs, model.n_muscles, model.n_bodies
         self.L0 = np.zeros(self.m)
@@ -143,6 +155,16 @@ def fk(model, q):
     Rb = np.zeros((om.nb, 3, 3)); pb = np.zeros((om.nb, 3)); s = np.zeros((om.n, 3)); o = np.zeros((om.n, 3))
     lib().ora_fk(om.ref, _ptr(q), _ptr(Rb), _ptr(pb), _ptr(s), _ptr(o))
     return Rb, pb, s, o
+
+
+def wrap_cylinder(P, S, c, a, r):
+    """Shortest path P -> S around an infinite cylinder (centre c, unit axis a, radius r):
+    (length, wraps, tangent point Q, tangent point T)."""
+    P, S, c, a = (np.ascontiguousarray(v, dtype=np.float64) for v in (P, S, c, a))
+    Q, T = np.zeros(3), np.zeros(3)
+    act = C.c_int(0)
+    L = lib().ora_wrap_cylinder(_ptr(P), _ptr(S), _ptr(c), _ptr(a), C.c_double(r), C.byref(act), _ptr(Q), _ptr(T))
+    return L, bool(act.value), Q, T
 
 
 def muscle_geometry(model, q):

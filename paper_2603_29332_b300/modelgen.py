@@ -77,6 +77,14 @@ class Model:
     tau_act: float = TAU_ACT
     tau_deact: float = TAU_DEACT
     vmax_per_lopt: float = 10.0
+    # wrapping cylinders (at most one per muscle): the segment ending at the muscle's point
+    # number wrap_segment wraps around an infinite cylinder fixed to body wrap_body
+    wrap_muscle: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    wrap_segment: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    wrap_body: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    wrap_center: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))   # body frame
+    wrap_axis: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))     # unit, body frame
+    wrap_radius: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float32))
 
     def __post_init__(self):
         # scalar parameters are FP32 values too, like every array
@@ -84,6 +92,11 @@ class Model:
                   "tau_deact", "vmax_per_lopt"):
             setattr(self, k, float(np.float32(getattr(self, k))))
         self.gravity = _f32(self.gravity)
+        for k in ("wrap_muscle", "wrap_segment", "wrap_body"):
+            setattr(self, k, np.asarray(getattr(self, k), dtype=np.int32).reshape(-1))
+        self.wrap_center = _f32(np.asarray(self.wrap_center, dtype=np.float64).reshape(-1, 3))
+        self.wrap_axis = _f32(np.asarray(self.wrap_axis, dtype=np.float64).reshape(-1, 3))
+        self.wrap_radius = _f32(np.asarray(self.wrap_radius, dtype=np.float64).reshape(-1))
 
     @property
     def n_bodies(self):
@@ -120,6 +133,14 @@ class Model:
         assert np.allclose(np.linalg.norm(self.dof_axis, axis=1), 1.0, atol=1e-6)
         assert self.muscle_point_start[0] == 0 and self.muscle_point_start[-1] == self.n_points
         assert np.all(np.diff(self.muscle_point_start) >= 2)
+        W = self.wrap_muscle.shape[0]
+        assert all(a.shape[0] == W for a in (self.wrap_segment, self.wrap_body, self.wrap_center, self.wrap_axis,
+                                            self.wrap_radius))
+        assert len(set(self.wrap_muscle.tolist())) == W          # at most one cylinder per muscle
+        if W:
+            npts = np.diff(self.muscle_point_start)[self.wrap_muscle]
+            assert np.all((self.wrap_segment >= 1) & (self.wrap_segment < npts))
+            assert np.all(self.wrap_radius > 0)
         return self
 
 
@@ -175,11 +196,12 @@ def capsule_inertia(mass, length, radius, direction):
 
 def make_model(name, body_parent, body_ndof, body_offset, body_mass, body_com, body_inertia,
                dof_axis, muscle_points=(), muscle_fmax=(), muscle_lopt=(), muscle_lslack=None,
-               dof_limit=None, dof_damping=None, spheres=(), **scalars):
+               dof_limit=None, dof_damping=None, spheres=(), wraps=(), **scalars):
     """Assemble a :class:`Model` from explicit arrays (used for hand-built test models).
 
     ``muscle_points`` is a list (one entry per muscle) of lists of (body, (x, y, z)).
     ``spheres`` is a list of (body, (x, y, z), radius).
+    ``wraps`` is a list of (muscle, segment end point index, body, centre, axis, radius).
     """
     body_parent = np.asarray(body_parent, dtype=np.int32)
     body_ndof = np.asarray(body_ndof, dtype=np.int32)
@@ -219,6 +241,9 @@ def make_model(name, body_parent, body_ndof, body_offset, body_mass, body_com, b
         point_body=np.asarray(pbody, dtype=np.int32),
         point_pos=_f32(np.asarray(ppos, dtype=np.float64).reshape(-1, 3)),
         sphere_body=sb, sphere_pos=_f32(sp), sphere_radius=_f32(sr),
+        wrap_muscle=[w[0] for w in wraps], wrap_segment=[w[1] for w in wraps], wrap_body=[w[2] for w in wraps],
+        wrap_center=[w[3] for w in wraps], wrap_axis=[_unit(np.asarray(w[4], dtype=np.float64)) for w in wraps],
+        wrap_radius=[w[5] for w in wraps],
     )
     for k, v in scalars.items():
         if k == "gravity":
@@ -242,11 +267,14 @@ CONFIGS = {
                      contact=False, seed=21),
     "c2_lower": dict(n_bodies=27, n_dofs=40, n_muscles=300, max_points=6, max_span=3, limits=True,
                      contact=True, seed=22),
+    # the whole body with a quarter of its muscles wrapping a cylinder at a joint
+    "c1_wrap": dict(n_bodies=60, n_dofs=90, n_muscles=700, max_points=6, max_span=3, limits=True,
+                    contact=True, seed=1, wrap_frac=0.25),
 }
 
 
 def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, limits, contact, seed,
-             n_legs=2, spheres_per_foot=4, sphere_radius=0.03, max_dof_per_body=3):
+             n_legs=2, spheres_per_foot=4, sphere_radius=0.03, max_dof_per_body=3, wrap_frac=0.0):
     """Draw one synthetic skeleton + muscle model.
 
     Tree: a root body, then limb chains of U{3..8} bodies each, the parent of each chain drawn
@@ -400,8 +428,31 @@ def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, li
     else:
         lim = np.zeros((n_dofs, 2))
 
+    # wrapping cylinders (after every other draw, from their own stream, so the rest of the model
+    # does not depend on wrap_frac): on a fraction of the muscles, the first segment that crosses
+    # a joint wraps a cylinder at that joint, fixed to the distal body, its axis along the
+    # joint's first hinge, radius 0.7 x the nearer point's distance from that axis at q = 0
+    # (at most 5 cm)
+    wraps = []
+    if wrap_frac > 0:
+        wr = np.random.default_rng(seed + 5000)
+        starts = np.concatenate([[0], np.cumsum(ndof)[:-1]])
+        for k in np.flatnonzero(wr.uniform(size=n_muscles) < wrap_frac):
+            pts = muscle_points[k]
+            for j in range(1, len(pts)):
+                bp, bs = pts[j - 1][0], pts[j][0]
+                if bp == bs:
+                    continue
+                a = _unit(np.asarray(axes[starts[bs]], dtype=np.float64))
+                P = origin0[bp] + np.asarray(pts[j - 1][1])
+                S = origin0[bs] + np.asarray(pts[j][1])
+                dist = [np.linalg.norm((X - origin0[bs]) - ((X - origin0[bs]) @ a) * a) for X in (P, S)]
+                r = min(0.7 * min(dist), 0.05)
+                if r >= 0.005:
+                    wraps.append((int(k), j, int(bs), (0.0, 0.0, 0.0), a, r))
+                break
     return make_model(name or "synthetic", parent, ndof, offset, mass, com, inertia, axes,
-                      muscle_points, fmax, lopt, lslack, dof_limit=lim, spheres=spheres)
+                      muscle_points, fmax, lopt, lslack, dof_limit=lim, spheres=spheres, wraps=wraps)
 
 
 def config_model(name):
