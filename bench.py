@@ -169,7 +169,7 @@ def cpu_baseline(model, envs=512, substeps=20):
 def run_reference(args, rank):
     if rank != 0:
         return None
-    model = mg.config_model(MODEL)
+    model = mg.config_model(args.model)
     from oracle import oracle as ora
     om = ora.OracleModel(model)
     envs, sub = args.ref_envs, args.substeps
@@ -195,9 +195,10 @@ def run_reference(args, rank):
 
 
 def _config(args):
-    return {"workload": "whole-body synthetic model (60 bodies, 90 hinge DoF, 700 Hill muscles, 8 contact "
+    wrap = ", 188 of them wrapping a cylinder" if args.model == "c1_wrap" else ""
+    return {"workload": "whole-body synthetic model (60 bodies, 90 hinge DoF, 700 Hill muscles%s, 8 contact "
                         "spheres), %d envs, %d substeps x dt %.0e s per step, smooth excitations, exact geometry"
-                        % (args.envs, args.substeps, DT),
+                        % (wrap, args.envs, args.substeps, DT),
             "envs_per_gpu": args.envs, "substeps_per_step": args.substeps, "dt": DT, "geometry": "exact",
             "l2": "flushed (256 MB write) between timed steps; excitation inputs cycle over 32 distinct buffers"}
 
@@ -206,7 +207,7 @@ def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2603_29332_b300 import msim
     torch.cuda.set_device(local_rank)
-    model = mg.config_model(MODEL)
+    model = mg.config_model(args.model)
     E, sub = args.envs, args.substeps
     sim = msim.Sim([model], [E], dt=DT, device=local_rank)
     q0, qd0, a0 = mg.initial_state(model, E, seed=1 + rank)
@@ -594,6 +595,8 @@ def main():
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
     ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
+    ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap"],
+                    help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder)")
     ap.add_argument("--policy-envs", type=int, default=16384)
     ap.add_argument("--policy-steps", type=int, default=2000)
     args = ap.parse_args()

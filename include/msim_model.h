@@ -20,7 +20,8 @@
  *   - dof_limit[2d], dof_limit[2d+1] = lo, hi [rad]; lo >= hi disables the limit.
  *
  * Limits of this build: n_dofs <= 255, n_bodies <= 255, max DoF depth <= 63, points per
- * muscle <= 8, DoFs crossed per muscle <= 12, n_spheres <= 32, n_muscles <= 4096.
+ * muscle <= 8, DoFs crossed per muscle <= 12, n_spheres <= 32, n_muscles <= 4096,
+ * n_wraps <= 255.
  */
 #ifndef MSIM_MODEL_H
 #define MSIM_MODEL_H
@@ -57,6 +58,17 @@ typedef struct {
     float limit_k, limit_c;            /* joint-limit stiffness N m/rad, damping N m s/rad */
     float tau_act, tau_deact;          /* activation / deactivation time constants (Eq. 2) */
     float vmax_per_lopt;               /* maximum contraction velocity in l_opt per second */
+    /* wrapping cylinders (may be 0 / NULL): the segment of muscle wrap_muscle[w] that ends at
+     * its point number wrap_segment[w] (1 .. points - 1) takes the shortest way around an
+     * infinite cylinder fixed to body wrap_body[w] (on the muscle's chain between that segment's
+     * two bodies), centre and axis in that body's frame; at most one cylinder per muscle */
+    int32_t n_wraps;
+    const int32_t* wrap_muscle;        /* [n_wraps] */
+    const int32_t* wrap_segment;       /* [n_wraps] */
+    const int32_t* wrap_body;          /* [n_wraps] */
+    const float* wrap_center;          /* [n_wraps][3] */
+    const float* wrap_axis;            /* [n_wraps][3] (normalised by the library) */
+    const float* wrap_radius;          /* [n_wraps], > 0 */
 } msim_model_desc;
 
 #ifdef __cplusplus

@@ -35,8 +35,9 @@ struct alignas(16) DofRec {     // 32 B
     uint8_t body;
 };
 
-// Muscle records are sorted by (points, crossed DoFs) so that the 32 muscles a warp handles
-// together run the same loop trip counts; `orig` is the muscle's index in the caller's order.
+// Muscle records are sorted by (wrapped segment, points, crossed DoFs) so that the 32 muscles a
+// warp handles together run the same loop trip counts and take the wrapping branch together;
+// `orig` is the muscle's index in the caller's order.
 struct alignas(16) MuscleRec {  // 32 B
     float fmax;
     float inv_lopt;             // 1 / l_opt
@@ -45,7 +46,8 @@ struct alignas(16) MuscleRec {  // 32 B
     int32_t p0;                 // first path point
     int32_t x0;                 // first entry in the crossed-DoF table (== offset in sparse R)
     uint8_t np, nx;             // number of points, number of crossed DoFs
-    uint8_t dep0, pad0;         // depth of the first crossed DoF (the others follow it, +1 each)
+    uint8_t dep0;               // depth of the first crossed DoF (the others follow it, +1 each)
+    uint8_t wrap;               // 0: none; else 1 + index into the wrap table
     int32_t orig;
 };
 
@@ -59,6 +61,14 @@ __host__ __device__ inline int cross_row(uint32_t c) { return c >> 16; }
 struct alignas(16) PointRec {   // 16 B
     float pos[3];               // body frame
     int32_t body_cross;         // body | (crossed DoFs at or above this point's body) << 8
+};
+
+struct alignas(16) WrapRec {    // 32 B, a muscle's wrapping cylinder (MuscleRec::wrap = index + 1)
+    float center[3];            // body frame
+    float radius;
+    float axis[3];              // unit, body frame
+    int32_t body_cross;         // body | (crossed DoFs at or above this body) << 8, as PointRec,
+                                // | (number of the muscle point that ends the wrapped segment) << 16
 };
 
 struct alignas(16) SphereRec {  // 32 B
@@ -76,7 +86,7 @@ struct alignas(16) ImgHeader {
     int32_t n_blevels, n_dlevels, max_depth, n_tri, total_bytes;
     // byte offsets of the sections
     int32_t o_body, o_dof, o_muscle, o_sphere, o_cross, o_border, o_blevel, o_child, o_anc, o_dorder, o_dlevel,
-        o_tri, o_point, o_rowanc, o_crba, o_pad0;
+        o_tri, o_point, o_rowanc, o_crba, o_wrap;
     // per-environment workspace layout (float offsets inside the environment's slot)
     int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_racc, w_y, w_sph, w_rk, w_pad0, w_pad1, w_pad2,
         w_pad3;

@@ -171,6 +171,24 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     // ---- muscles
     std::vector<MuscleRec> mus(m);
     std::vector<PointRec> pts(np);
+    // wrapping cylinders
+    const int nw = d.n_wraps;
+    if (nw < 0 || nw > 255) FAIL("n_wraps must be 0..255");
+    if (nw > 0 && (!d.wrap_muscle || !d.wrap_segment || !d.wrap_body || !d.wrap_center || !d.wrap_axis ||
+                   !d.wrap_radius))
+        FAIL("wrap arrays are NULL");
+    std::vector<int> wrap_of(m, -1);
+    for (int w = 0; w < nw; ++w) {
+        const int k = d.wrap_muscle[w];
+        if (k < 0 || k >= m) FAIL("wrap %d: muscle out of range", w);
+        if (wrap_of[k] >= 0) FAIL("muscle %d has two wrapping cylinders", k);
+        wrap_of[k] = w;
+        if (!(d.wrap_radius[w] > 0.f) || !finite_all(d.wrap_center + 3 * w, 3) || !finite_all(d.wrap_axis + 3 * w, 3))
+            FAIL("wrap %d: radius must be > 0 and centre / axis finite", w);
+        const float* ax = d.wrap_axis + 3 * w;
+        if (!(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2] > 1e-12f)) FAIL("wrap %d: zero axis", w);
+    }
+    std::vector<WrapRec> wraps(nw);
     std::vector<uint32_t> cross;
     std::vector<int32_t> mus_ptr(m + 1, 0), mus_dof;
     if (m > 0) {
@@ -216,6 +234,23 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         }
         MuscleRec& M = mus[k];
         std::memset(&M, 0, sizeof(M));
+        if (wrap_of[k] >= 0) {
+            const int w = wrap_of[k], seg = d.wrap_segment[w], bw = d.wrap_body[w];
+            if (seg < 1 || seg >= cnt) FAIL("wrap %d: segment must be 1..points-1 of muscle %d", w, k);
+            const int tw = (bw >= 0 && bw < nb) ? pos_of(bw) : -1;
+            if (tw < pos_of(d.point_body[j0 + seg - 1]) || tw > pos_of(d.point_body[j0 + seg]))
+                FAIL("wrap %d: body must lie on the chain between the wrapped segment's bodies", w);
+            WrapRec& W = wraps[w];
+            const float* ax = d.wrap_axis + 3 * w;
+            const float an = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+            for (int c = 0; c < 3; ++c) {
+                W.center[c] = d.wrap_center[3 * w + c];
+                W.axis[c] = ax[c] / an;
+            }
+            W.radius = d.wrap_radius[w];
+            W.body_cross = bw | (ccount[tw] << 8) | (seg << 16);
+            M.wrap = (uint8_t)(w + 1);
+        }
         M.fmax = d.muscle_fmax[k];
         M.inv_lopt = 1.f / d.muscle_lopt[k];
         M.L0 = 0.f;
@@ -234,10 +269,23 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             }
         mus_ptr[k + 1] = (int32_t)cross.size();
     }
-    // records sorted by (points, crossed DoFs): a warp's 32 lanes then share loop trip counts
-    std::stable_sort(mus.begin(), mus.end(), [](const MuscleRec& a, const MuscleRec& b) {
-        return a.np != b.np ? a.np < b.np : a.nx < b.nx;
-    });
+    // records sorted by (wrapped segment, points, crossed DoFs): a warp's 32 lanes then share
+    // loop trip counts and take the wrapping branch together
+    std::vector<int> wseg(m, 0);
+    for (int k = 0; k < m; ++k)
+        if (mus[k].wrap) wseg[k] = d.wrap_segment[mus[k].wrap - 1];
+    {
+        std::vector<int> order(m);
+        for (int k = 0; k < m; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const MuscleRec &A = mus[a], &B = mus[b];
+            if (wseg[a] != wseg[b]) return wseg[a] < wseg[b];
+            return A.np != B.np ? A.np < B.np : A.nx < B.nx;
+        });
+        std::vector<MuscleRec> sorted(m);
+        for (int k = 0; k < m; ++k) sorted[k] = mus[order[k]];
+        mus.swap(sorted);
+    }
     if (!(d.vmax_per_lopt > 0.f) || !(d.tau_act > 0.f) || !(d.tau_deact > 0.f)) FAIL("time constants must be > 0");
 
     // ---- spheres
@@ -310,7 +358,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.o_tri = place(sizeof(uint16_t) * tri.size());
     h.o_rowanc = place(sizeof(uint16_t) * rowanc.size());
     h.o_crba = place(crba_order.size());
-    h.o_point = place(sizeof(PointRec) * np);   // last: may stay in global memory (staging split)
+    h.o_point = place(sizeof(PointRec) * np);   // with the wraps, may stay in global memory (staging split)
+    h.o_wrap = place(sizeof(WrapRec) * std::max(nw, 1));
     h.total_bytes = (int32_t)off;
     // per-environment workspace
     int w = 0;
@@ -353,6 +402,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     put(h.o_dof, dofs.data(), sizeof(DofRec) * n);
     put(h.o_muscle, mus.data(), sizeof(MuscleRec) * m);
     put(h.o_point, pts.data(), sizeof(PointRec) * np);
+    if (nw > 0) put(h.o_wrap, wraps.data(), sizeof(WrapRec) * nw);
     put(h.o_sphere, sph.data(), sizeof(SphereRec) * ns);
     put(h.o_cross, cross.data(), sizeof(uint32_t) * cross.size());
     put(h.o_border, border.data(), border.size());

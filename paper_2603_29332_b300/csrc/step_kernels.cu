@@ -52,6 +52,7 @@ struct Tables {
     const DofRec* dof;
     const MuscleRec* mus;
     const PointRec* pt;
+    const WrapRec* wrap;
     const SphereRec* sph;
     const uint32_t* cross;
     const uint8_t* border;
@@ -73,6 +74,7 @@ __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     t.dof = reinterpret_cast<const DofRec*>(img + h.o_dof);
     t.mus = reinterpret_cast<const MuscleRec*>(img + h.o_muscle);
     t.pt = reinterpret_cast<const PointRec*>(img + h.o_point);
+    t.wrap = reinterpret_cast<const WrapRec*>(img + h.o_wrap);
     t.sph = reinterpret_cast<const SphereRec*>(img + h.o_sphere);
     t.cross = reinterpret_cast<const uint32_t*>(img + h.o_cross);
     t.border = img + h.o_border;
@@ -530,6 +532,58 @@ struct SurrCtx {
     unsigned int* max_err_bits;   // global running maximum of the check error (float bits)
 };
 
+// Shortest path x0 -> x1 around an infinite cylinder (world centre c, unit axis a, radius r):
+// in the plane normal to the axis, tangent - arc - tangent on the side of the shorter arc;
+// along the axis a straight line once the cylinder is unrolled.  Wraps (returns true, with the
+// length, the tangent points Q, T and the unit directions u1 of x0 -> Q and u2 of T -> x1) when
+// both points are outside the cylinder and the straight segment passes within r of the axis.
+// With p, s the two points' in-plane offsets from the axis, the shorter arc is the one on the
+// side the chord passes (counter-clockwise about a when p x s >= 0): for an active wrap both
+// arcs are psi - alpha_p - alpha_s and 2 pi - psi - alpha_p - alpha_s, psi the angle from p to s
+// the short way round.  The tangent points come from the angle-sum identities
+// (cos alpha = r / rho, sin alpha = l / rho, l the tangent length), the arc from one atan2, the
+// directions from the circle's tangent at Q and T and the unrolled slope.
+__device__ bool wrap_path(const float x0[3], const float x1[3], const float c[3], const float a[3], float r,
+                          float& len, float Q[3], float T[3], float u1[3], float u2[3]) {
+    float e1[3];
+    const float ref[3] = {fabsf(a[0]) < 0.9f ? 1.f : 0.f, fabsf(a[0]) < 0.9f ? 0.f : 1.f, 0.f};
+    cross3(a, ref, e1);
+    const float in1 = rsqrtf(dot3(e1, e1));
+    e1[0] *= in1; e1[1] *= in1; e1[2] *= in1;
+    float e2[3];
+    cross3(a, e1, e2);
+    const float p[3] = {x0[0] - c[0], x0[1] - c[1], x0[2] - c[2]};
+    const float q[3] = {x1[0] - c[0], x1[1] - c[1], x1[2] - c[2]};
+    const float px = dot3(p, e1), py = dot3(p, e2), pz = dot3(p, a);
+    const float sx = dot3(q, e1), sy = dot3(q, e2), sz = dot3(q, a);
+    const float rp2 = px * px + py * py, rs2 = sx * sx + sy * sy, r2 = r * r;
+    if (!(rp2 > r2 && rs2 > r2)) return false;
+    const float ex = sx - px, ey = sy - py, ee = ex * ex + ey * ey;
+    float t = ee > 0.f ? -(px * ex + py * ey) / ee : 0.f;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const float cx = px + t * ex, cy = py + t * ey;
+    if (cx * cx + cy * cy >= r2) return false;
+    const float turn = (px * sy - py * sx >= 0.f) ? 1.f : -1.f;   // +1: counter-clockwise about a
+    const float lp = sqrtf(rp2 - r2), ls = sqrtf(rs2 - r2);
+    const float ip = 1.f / rp2, is = 1.f / rs2;
+    // Q at the angle of p advanced by alpha_p, T at the angle of s moved back by alpha_s
+    const float cq = (px * r - turn * py * lp) * ip, sq = (py * r + turn * px * lp) * ip;
+    const float ct = (sx * r + turn * sy * ls) * is, st = (sy * r - turn * sx * ls) * is;
+    const float arc = fmaxf(atan2f(turn * (cq * st - sq * ct), cq * ct + sq * st), 0.f);
+    const float lplane = lp + r * arc + ls, dz = sz - pz;
+    const float zq = pz + dz * lp / lplane, zt = pz + dz * (lp + r * arc) / lplane;
+    len = sqrtf(lplane * lplane + dz * dz);
+    const float il = 1.f / len, kp = lplane * il * turn, kz = dz * il;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Q[i] = c[i] + r * cq * e1[i] + r * sq * e2[i] + zq * a[i];
+        T[i] = c[i] + r * ct * e1[i] + r * st * e2[i] + zt * a[i];
+        u1[i] = kp * (cq * e2[i] - sq * e1[i]) + kz * a[i];   // direction of travel at Q
+        u2[i] = kp * (ct * e2[i] - st * e1[i]) + kz * a[i];   // and at T
+    }
+    return true;
+}
+
 // ------------------------------------------------------------------ phase 4: muscles
 #pragma nv_diag_suppress 128
 // One lane per muscle.  act: this environment's activation row in global memory (read;
@@ -566,6 +620,23 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             float x0[3];
             rot3(fb, P.pos, x0);
             x0[0] += fb[9]; x0[1] += fb[10]; x0[2] += fb[11];
+            // moment arms of the crossed DoFs [i0, i1) for a straight piece with unit direction
+            // uu whose distal end xd moves with them: R = -dL/dq = -s_d . ((xd - o_d) x uu)
+            auto arms = [&](int i0, int i1, const float xd[3], const float uu[3]) {
+                for (int i = i0; i < i1; ++i) {
+                    const uint32_t ce = T.cross[M.x0 + i];
+                    const int d = cross_dof(ce);
+                    const float* Sd = S + 6 * d;
+                    const float* o = frame + 12 * cross_body(ce) + 9;
+                    const float rr[3] = {xd[0] - o[0], xd[1] - o[1], xd[2] - o[2]};
+                    float rxu[3];
+                    cross3(rr, uu, rxu);
+                    const float Rv = -(Sd[0] * rxu[0] + Sd[1] * rxu[1] + Sd[2] * rxu[2]);
+                    rk[i * g.N + g.lane] = Rv;
+                    ldot -= Rv * qd[d];
+                }
+            };
+            const int wseg = M.wrap ? (T.wrap[M.wrap - 1].body_cross >> 16) : 0;
             for (int j = 1; j < M.np; ++j) {
                 P = T.pt[M.p0 + j];
                 b = P.body_cross & 0xff;
@@ -574,22 +645,30 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                 float x1[3];
                 rot3(fb, P.pos, x1);
                 x1[0] += fb[9]; x1[1] += fb[10]; x1[2] += fb[11];
-                const float dv[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
-                const float len2 = dot3(dv, dv);
-                const float inv = rsqrtf(len2);
-                L += len2 * inv;
-                const float uu[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
-                for (int i = cprev; i < c; ++i) {
-                    const uint32_t ce = T.cross[M.x0 + i];
-                    const int d = cross_dof(ce);
-                    const float* Sd = S + 6 * d;
-                    const float* o = frame + 12 * cross_body(ce) + 9;
-                    const float rr[3] = {x1[0] - o[0], x1[1] - o[1], x1[2] - o[2]};
-                    float rxu[3];
-                    cross3(rr, uu, rxu);
-                    const float Rv = -(Sd[0] * rxu[0] + Sd[1] * rxu[1] + Sd[2] * rxu[2]);   // R = -dL/dq
-                    rk[i * g.N + g.lane] = Rv;
-                    ldot -= Rv * qd[d];
+                bool wrapped = false;
+                if (j == wseg) {
+                    // the wrapped segment: tangent points held on the cylinder's body for the arms
+                    const WrapRec W = T.wrap[M.wrap - 1];
+                    const float* fw = frame + 12 * (W.body_cross & 0xff);
+                    float cw[3], aw[3], Q[3], Tp[3], u1[3], u2[3], lw;
+                    rot3(fw, W.center, cw);
+                    cw[0] += fw[9]; cw[1] += fw[10]; cw[2] += fw[11];
+                    rot3(fw, W.axis, aw);
+                    wrapped = wrap_path(x0, x1, cw, aw, W.radius, lw, Q, Tp, u1, u2);
+                    if (wrapped) {
+                        L += lw;
+                        const int cw_i = (W.body_cross >> 8) & 0xff;
+                        arms(cprev, cw_i, Q, u1);   // DoFs that move the cylinder with x1
+                        arms(cw_i, c, x1, u2);      // DoFs that move x1 alone
+                    }
+                }
+                if (!wrapped) {
+                    const float dv[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
+                    const float len2 = dot3(dv, dv);
+                    const float inv = rsqrtf(len2);
+                    L += len2 * inv;
+                    const float uu[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+                    arms(cprev, c, x1, uu);
                 }
                 x0[0] = x1[0]; x0[1] = x1[1]; x0[2] = x1[2];
                 cprev = c;
@@ -1092,7 +1171,10 @@ __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
     __syncthreads();
 #endif
     Tables T = make_tables(img);
-    if (!a.points_in_smem) T.pt = reinterpret_cast<const PointRec*>(a.img + T.H->o_point);
+    if (!a.points_in_smem) {
+        T.pt = reinterpret_cast<const PointRec*>(a.img + T.H->o_point);
+        T.wrap = reinterpret_cast<const WrapRec*>(a.img + T.H->o_wrap);
+    }
     const ImgHeader& H = *T.H;
     const int warp = threadIdx.x >> 5;
     const int slot = warp / WPE;
@@ -1176,7 +1258,10 @@ __global__ void __launch_bounds__(512, 1) k_step_mixed(MixedArgs ma) {
             cur = i;
         }
         Tables T = make_tables(img);
-        if (!M.points_in_smem) T.pt = reinterpret_cast<const PointRec*>(M.img + T.H->o_point);
+        if (!M.points_in_smem) {
+            T.pt = reinterpret_cast<const PointRec*>(M.img + T.H->o_point);
+            T.wrap = reinterpret_cast<const WrapRec*>(M.img + T.H->o_wrap);
+        }
         float* ws = ws_all + (size_t)slot * ws_floats(*T.H, WPE);
         if (slot < M.epb) {
             const int e = M.env_begin + (item - M.item_begin) * M.epb + slot;

@@ -36,7 +36,9 @@ class ModelDesc(C.Structure):
                 ("gravity", C.c_float * 3), ("contact_k", C.c_float), ("contact_c", C.c_float),
                 ("contact_mu", C.c_float), ("contact_eps", C.c_float), ("limit_k", C.c_float),
                 ("limit_c", C.c_float), ("tau_act", C.c_float), ("tau_deact", C.c_float),
-                ("vmax_per_lopt", C.c_float)]
+                ("vmax_per_lopt", C.c_float),
+                ("n_wraps", C.c_int32), ("wrap_muscle", _i32p), ("wrap_segment", _i32p), ("wrap_body", _i32p),
+                ("wrap_center", _f32p), ("wrap_axis", _f32p), ("wrap_radius", _f32p)]
 
 
 class CreateArgs(C.Structure):
@@ -194,10 +196,13 @@ def model_desc(model):
                 muscle_point_start=i(model.muscle_point_start), muscle_fmax=f(model.muscle_fmax),
                 muscle_lopt=f(model.muscle_lopt), muscle_lslack=f(model.muscle_lslack),
                 point_body=i(model.point_body), point_pos=f(model.point_pos), sphere_body=i(model.sphere_body),
-                sphere_pos=f(model.sphere_pos), sphere_radius=f(model.sphere_radius))
+                sphere_pos=f(model.sphere_pos), sphere_radius=f(model.sphere_radius),
+                wrap_muscle=i(model.wrap_muscle), wrap_segment=i(model.wrap_segment), wrap_body=i(model.wrap_body),
+                wrap_center=f(model.wrap_center), wrap_axis=f(model.wrap_axis), wrap_radius=f(model.wrap_radius))
     d = ModelDesc()
     d.n_bodies, d.n_dofs, d.n_muscles = model.n_bodies, model.n_dofs, model.n_muscles
     d.n_points, d.n_spheres = model.n_points, model.n_spheres
+    d.n_wraps = int(model.wrap_muscle.shape[0])
     for k, v in keep.items():
         setattr(d, k, v.ctypes.data_as(_i32p if v.dtype == np.int32 else _f32p) if v.size else None)
     d.gravity = (C.c_float * 3)(*[float(x) for x in model.gravity])
