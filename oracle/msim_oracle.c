@@ -21,6 +21,11 @@
  *      joint-limit penalty are taken linearly implicit: (M + dt D) q_dd = rhs
  *   9. semi-implicit Euler: qd += dt q_dd, q += dt qd, act = clamp(act + dt act_dot, 0, 1)
  *
+ * Free root (optional, the paper's skeleton has a floating pelvis): body 0 joined to the world
+ * by six DoFs.  DoFs 0-2 translate its origin along world x, y, z (q = position, qd = velocity);
+ * DoFs 3-5 turn it about world x, y, z through its origin (qd = world angular velocity, q = the
+ * rotation vector of its orientation, advanced by the exponential map: R <- exp(dt w) R).
+ *
  * The paper does not print f_l, f_v, f_p (it cites Millard 2013), the tendon model, the contact
  * solver details or the integrator; the readings used here are the named functions below and
  * are listed with their reasons in the design notes of the repository.
@@ -52,9 +57,15 @@ typedef struct {
     int nw;
     const int *wrap_muscle, *wrap_segment, *wrap_body;
     const double *wrap_center, *wrap_axis, *wrap_radius;
+    int free_root;   /* 1: body 0 has the six free DoFs 0-5 described above */
 } ora_model;
 
-int ora_abi_version(void) { return 4; }
+int ora_abi_version(void) { return 5; }
+
+/* DoF kinds: a translation of the free root (its point Jacobian is the axis itself), else a
+ * rotation about the axis s_d through o_d (point Jacobian s_d x (x - o_d)). */
+static int is_slide(const ora_model* M, int d) { return M->free_root && d < 3; }
+static int is_free_rot(const ora_model* M, int d) { return M->free_root && d >= 3 && d < 6; }
 
 /* ---------------------------------------------------------------- small 3-vector helpers */
 static void cross3(const double a[3], const double b[3], double c[3]) {
@@ -113,6 +124,21 @@ void ora_fk(const ora_model* M, const double* q, double* Rb, double* pb, double*
             matvec3(R, off, p);
             p[0] += pb[3 * pa]; p[1] += pb[3 * pa + 1]; p[2] += pb[3 * pa + 2];
         }
+        if (b == 0 && M->free_root) {
+            /* origin at offset + q[0..2]; orientation exp(q[3..5]); world axes x, y, z */
+            double th = sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+            if (th > 0.0) {
+                double a[3] = {q[3] / th, q[4] / th, q[5] / th};
+                rodrigues(a, th, R);
+            }
+            for (int i = 0; i < 3; ++i) p[i] += q[i];
+            for (int d = 0; d < 6; ++d) {
+                for (int i = 0; i < 3; ++i) { s[3 * d + i] = (i == d % 3) ? 1.0 : 0.0; o[3 * d + i] = p[i]; }
+            }
+            memcpy(Rb, R, sizeof(R));
+            memcpy(pb, p, sizeof(p));
+            continue;
+        }
         for (int j = 0; j < M->body_ndof[b]; ++j) {
             int d = M->body_dof_start[b] + j;
             const double* a = M->dof_axis + 3 * d;
@@ -135,7 +161,8 @@ static void add_wJ(const ora_model* M, const double* s, const double* o, int bod
         for (int j = 0; j < M->body_ndof[b]; ++j) {
             int d = M->body_dof_start[b] + j;
             double r[3] = {x[0] - o[3 * d], x[1] - o[3 * d + 1], x[2] - o[3 * d + 2]}, c[3];
-            cross3(s + 3 * d, r, c);
+            if (is_slide(M, d)) memcpy(c, s + 3 * d, sizeof(c));
+            else cross3(s + 3 * d, r, c);
             g[d] += scale * dot3(w, c);
         }
     }
@@ -149,7 +176,8 @@ static void point_jac(const ora_model* M, const double* s, const double* o, int 
         for (int j = 0; j < M->body_ndof[b]; ++j) {
             int d = M->body_dof_start[b] + j;
             double r[3] = {x[0] - o[3 * d], x[1] - o[3 * d + 1], x[2] - o[3 * d + 2]}, c[3];
-            cross3(s + 3 * d, r, c);
+            if (is_slide(M, d)) memcpy(c, s + 3 * d, sizeof(c));
+            else cross3(s + 3 * d, r, c);
             J[d] = c[0]; J[M->n + d] = c[1]; J[2 * M->n + d] = c[2];
         }
     }
@@ -332,8 +360,13 @@ void ora_rnea(const ora_model* M, const double* q, const double* qd, const doubl
         for (int j = 0; j < M->body_ndof[b]; ++j) {
             int d = M->body_dof_start[b] + j;
             const double* sd = s + 3 * d;
+            if (is_slide(M, d)) {          /* the origin's acceleration is q_dd itself */
+                for (int i = 0; i < 3; ++i) a[i] += sd[i] * qdd[d];
+                continue;
+            }
             double c[3];
             cross3(wv, sd, c);
+            if (is_free_rot(M, d)) c[0] = c[1] = c[2] = 0.0;   /* world-fixed axes */
             for (int i = 0; i < 3; ++i) dwv[i] += c[i] * qd[d] + sd[i] * qdd[d];
             for (int i = 0; i < 3; ++i) wv[i] += sd[i] * qd[d];
         }
@@ -363,7 +396,7 @@ void ora_rnea(const ora_model* M, const double* q, const double* qd, const doubl
     for (int b = nb - 1; b >= 0; --b) {
         for (int j = 0; j < M->body_ndof[b]; ++j) {
             int d = M->body_dof_start[b] + j;
-            tau[d] = dot3(s + 3 * d, nm + 3 * b);
+            tau[d] = dot3(s + 3 * d, is_slide(M, d) ? f + 3 * b : nm + 3 * b);   /* force or moment */
         }
         int pa = M->body_parent[b];
         if (pa >= 0) {
@@ -413,6 +446,7 @@ void ora_mass_matrix_jac(const ora_model* M, const double* q, double* Mout) {
         for (int a = b; a >= 0; a = M->body_parent[a])
             for (int j = 0; j < M->body_ndof[a]; ++j) {
                 int d = M->body_dof_start[a] + j;
+                if (is_slide(M, d)) continue;   /* translations do not turn the body */
                 Jw[d] = s[3 * d]; Jw[n + d] = s[3 * d + 1]; Jw[2 * n + d] = s[3 * d + 2];
             }
         world_inertia(Rb + 9 * b, M->body_inertia + 6 * b, Iw);
@@ -633,6 +667,32 @@ int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, c
     return bad;
 }
 
+/* Position update of semi-implicit Euler from the new velocities: q += dt qd, except the free
+ * root's rotation vector, which follows R <- exp(dt w) R (unit quaternions: the product of the
+ * step's rotation and the current one, returned as the rotation vector of angle in [0, pi]). */
+void ora_integrate_q(const ora_model* M, double dt, double* q, const double* qd) {
+    for (int d = 0; d < M->n; ++d)
+        if (!is_free_rot(M, d)) q[d] += dt * qd[d];
+    if (!M->free_root) return;
+    double qa[4], qb[4], qc[4];
+    double th = sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+    qa[0] = cos(0.5 * th);
+    for (int i = 0; i < 3; ++i) qa[1 + i] = th > 0.0 ? sin(0.5 * th) * q[3 + i] / th : 0.0;
+    double w[3] = {dt * qd[3], dt * qd[4], dt * qd[5]};
+    double ph = sqrt(dot3(w, w));
+    qb[0] = cos(0.5 * ph);
+    for (int i = 0; i < 3; ++i) qb[1 + i] = ph > 0.0 ? sin(0.5 * ph) * w[i] / ph : 0.0;
+    /* qc = qb * qa (Hamilton product) */
+    qc[0] = qb[0] * qa[0] - qb[1] * qa[1] - qb[2] * qa[2] - qb[3] * qa[3];
+    qc[1] = qb[0] * qa[1] + qb[1] * qa[0] + qb[2] * qa[3] - qb[3] * qa[2];
+    qc[2] = qb[0] * qa[2] - qb[1] * qa[3] + qb[2] * qa[0] + qb[3] * qa[1];
+    qc[3] = qb[0] * qa[3] + qb[1] * qa[2] - qb[2] * qa[1] + qb[3] * qa[0];
+    if (qc[0] < 0.0) for (int i = 0; i < 4; ++i) qc[i] = -qc[i];
+    double vn = sqrt(qc[1] * qc[1] + qc[2] * qc[2] + qc[3] * qc[3]);
+    double ang = 2.0 * atan2(vn, qc[0]);
+    for (int i = 0; i < 3; ++i) q[3 + i] = vn > 0.0 ? ang * qc[1 + i] / vn : 0.0;
+}
+
 /* n_sub substeps for each of n_envs environments, states updated in place (rows [E][n], [E][m]);
  * exc [E][m] is held over the substeps.  qdd_out / force_out (optional) receive the last substep's
  * accelerations and muscle forces.  status (optional, [E]) gets 1 where a solve failed.
@@ -658,10 +718,8 @@ void ora_step(const ora_model* M, const double* L0, double dt, int n_envs, int n
             memset(&out, 0, sizeof(out));
             out.qdd = qdd; out.force = F; out.act_next = anext;
             bad |= ora_eval(M, L0, dt, qe, qde, ae, ue, &out);
-            for (int d = 0; d < n; ++d) {
-                qde[d] += dt * qdd[d];
-                qe[d] += dt * qde[d];
-            }
+            for (int d = 0; d < n; ++d) qde[d] += dt * qdd[d];
+            ora_integrate_q(M, dt, qe, qde);
             memcpy(ae, anext, sizeof(double) * m);
         }
         if (qdd_out) memcpy(qdd_out + (size_t)e * n, qdd, sizeof(double) * n);

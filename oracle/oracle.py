@@ -40,7 +40,8 @@ class _OraModel(C.Structure):
                 ("tau_act", C.c_double), ("tau_deact", C.c_double), ("vmax_per_lopt", C.c_double),
                 ("implicit_damping", C.c_int),
                 ("nw", C.c_int), ("wrap_muscle", _ip), ("wrap_segment", _ip), ("wrap_body", _ip),
-                ("wrap_center", _dp), ("wrap_axis", _dp), ("wrap_radius", _dp)]
+                ("wrap_center", _dp), ("wrap_axis", _dp), ("wrap_radius", _dp),
+                ("free_root", C.c_int)]
 
 
 class _EvalOut(C.Structure):
@@ -63,6 +64,8 @@ def lib():
         build()
         _lib = C.CDLL(_LIB)
         _lib.ora_abi_version.restype = C.c_int
+        if _lib.ora_abi_version() != 5:
+            raise RuntimeError("stale oracle library: rebuild with oracle.build(force=True)")
         for name in ("ora_fl", "ora_fp", "ora_fv", "ora_dfv"):
             getattr(_lib, name).restype = C.c_double
             getattr(_lib, name).argtypes = [C.c_double]
@@ -113,6 +116,7 @@ class OracleModel:
             setattr(s, k, float(v))
         s.implicit_damping = 1 if implicit_damping else 0
         s.nw = nw
+        s.free_root = 1 if getattr(model, "free_root", False) else 0
         self.s = s
         self.n, self.m, self.nb = model.n_dofs, model.n_muscles, model.n_bodies
         self.L0 = np.zeros(self.m)
@@ -208,6 +212,16 @@ def contact(model, q, qd):
     tau = np.zeros(om.n); D = np.zeros((om.n, om.n)); fs = np.zeros((max(om.model.n_spheres, 1), 3))
     lib().ora_contact(om.ref, _ptr(Rb), _ptr(pb), _ptr(s), _ptr(o), _ptr(qd), _ptr(tau), _ptr(D), _ptr(fs))
     return tau, D, fs[: om.model.n_spheres]
+
+
+def integrate_q(model, dt, q, qd):
+    """Position update of semi-implicit Euler from the new velocities (a copy of q): q + dt qd,
+    except a free root's rotation vector, advanced by R <- exp(dt w) R."""
+    om = _as(model)
+    q = np.array(q, dtype=np.float64, order="C")
+    qd = np.ascontiguousarray(qd, dtype=np.float64)
+    lib().ora_integrate_q(om.ref, C.c_double(dt), _ptr(q), _ptr(qd))
+    return q
 
 
 def cholesky_solve(A, b):

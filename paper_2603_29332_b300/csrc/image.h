@@ -88,8 +88,9 @@ struct alignas(16) ImgHeader {
     int32_t o_body, o_dof, o_muscle, o_sphere, o_cross, o_border, o_blevel, o_child, o_anc, o_dorder, o_dlevel,
         o_tri, o_point, o_rowanc, o_crba, o_wrap;
     // per-environment workspace layout (float offsets inside the environment's slot)
-    int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_racc, w_y, w_sph, w_rk, w_pad0, w_pad1, w_pad2,
-        w_pad3;
+    int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_racc, w_y, w_sph, w_rk,
+        max_nx,                 // most DoFs one muscle crosses (rows of the moment-arm region)
+        w_pad1, w_pad2, w_pad3;
     float gravity[3];
     float contact_k, contact_c, contact_mu, contact_eps2;
     float limit_k, limit_c, tau_act, tau_deact;
@@ -114,13 +115,13 @@ struct alignas(16) ImgHeader {
 //   racc[n][2]                        R^T F + tau_c as fixed-point int32 pairs
 //   y[n][2]                           float-float solution of the two triangular solves
 //   sph[ns][12]                       per-sphere contact point, force, damping, flags
-//   rk[kMaxCross][32 wpe]             per-lane moment arms of the muscle being processed (last);
+//   rk[max_nx][32 wpe]                per-lane moment arms of the muscle being processed (last);
 //                                     sin, cos of the joint angles during the kinematics pass
 
 // floats per environment slot for a group of `wpe` warps per environment
 // (the moment-arm region also holds the joint sines and cosines during the kinematics pass)
 __host__ __device__ inline int ws_floats(const ImgHeader& h, int wpe) {
-    return h.w_rk + (kMaxCross * 32 * wpe > 2 * h.n ? kMaxCross * 32 * wpe : 2 * h.n);
+    return h.w_rk + (h.max_nx * 32 * wpe > 2 * h.n ? h.max_nx * 32 * wpe : 2 * h.n);
 }
 
 }  // namespace msim

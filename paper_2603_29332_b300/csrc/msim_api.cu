@@ -380,6 +380,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.w_y = slot(2 * n);
     h.w_sph = slot(12 * ns);
     h.w_rk = w;   // last: its size depends on the warps per environment (ws_floats)
+    h.max_nx = 1;
+    for (int k = 0; k < m; ++k) h.max_nx = std::max(h.max_nx, (int)mus[k].nx);
     for (int c = 0; c < 3; ++c) h.gravity[c] = d.gravity[c];
     h.contact_k = d.contact_k;
     h.contact_c = d.contact_c;

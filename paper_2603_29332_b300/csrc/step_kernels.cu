@@ -600,7 +600,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
     const float* S = ws + H.w_S;
     int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);   // damping sums, fixed point
     int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
-    float* rk = ws + H.w_rk;                                  // [kMaxCross][N]
+    float* rk = ws + H.w_rk;                                  // [max_nx][N]
     bool bad = false;
     uint32_t flags = 0;
     SUB_T0();

@@ -77,6 +77,10 @@ class Model:
     tau_act: float = TAU_ACT
     tau_deact: float = TAU_DEACT
     vmax_per_lopt: float = 10.0
+    # free root: body 0 joined to the world by six DoFs 0-5, translations of its origin along
+    # world x, y, z, then rotations about world x, y, z through it (q: position and rotation
+    # vector, qd: velocity and world angular velocity); dof_axis rows 0-5 are e_x e_y e_z e_x e_y e_z
+    free_root: bool = False
     # wrapping cylinders (at most one per muscle): the segment ending at the muscle's point
     # number wrap_segment wraps around an infinite cylinder fixed to body wrap_body
     wrap_muscle: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
@@ -126,7 +130,13 @@ class Model:
     def validate(self):
         B, n = self.n_bodies, self.n_dofs
         assert np.all(self.body_parent < np.arange(B))
-        assert np.all((self.body_ndof >= 1) & (self.body_ndof <= 3))
+        nd = self.body_ndof
+        if self.free_root:
+            assert self.body_parent[0] == -1 and nd[0] == 6
+            assert np.array_equal(self.dof_axis[:6], np.vstack([np.eye(3), np.eye(3)]))
+            assert np.all(self.dof_limit[:6, 0] >= self.dof_limit[:6, 1])   # no limits on the root
+            nd = nd[1:]
+        assert np.all((nd >= 1) & (nd <= 3))
         assert self.body_dof_start[0] == 0
         assert np.all(self.body_dof_start[1:] == np.cumsum(self.body_ndof)[:-1])
         assert int(self.body_ndof.sum()) == n
@@ -253,6 +263,24 @@ def make_model(name, body_parent, body_ndof, body_offset, body_mass, body_com, b
     return mdl.validate()
 
 
+def with_free_root(model, name=None):
+    """The same model with body 0 (a root) joined to the world by a free joint: its hinges are
+    replaced by the six free-root DoFs (no limits, no damping); everything else is unchanged."""
+    assert model.body_parent[0] == -1 and not model.free_root
+    k = int(model.body_ndof[0])
+    ndof = model.body_ndof.copy()
+    ndof[0] = 6
+    starts = np.zeros_like(ndof)
+    starts[1:] = np.cumsum(ndof)[:-1]
+    axis = np.vstack([np.eye(3), np.eye(3), model.dof_axis[k:]])
+    lim = np.vstack([np.zeros((6, 2)), model.dof_limit[k:]])
+    damp = np.concatenate([np.zeros(6), model.dof_damping[k:]])
+    kw = {f: getattr(model, f) for f in model.__dataclass_fields__}
+    kw.update(name=name or model.name + "_float", body_ndof=ndof.astype(np.int32), body_dof_start=starts.astype(np.int32),
+              dof_axis=_f32(axis), dof_limit=_f32(lim), dof_damping=_f32(damp), free_root=True)
+    return Model(**kw).validate()
+
+
 # ----------------------------------------------------------------------------------------------
 # synthetic whole-body-like models
 
@@ -270,11 +298,15 @@ CONFIGS = {
     # the whole body with a quarter of its muscles wrapping a cylinder at a joint
     "c1_wrap": dict(n_bodies=60, n_dofs=90, n_muscles=700, max_points=6, max_span=3, limits=True,
                     contact=True, seed=1, wrap_frac=0.25),
+    # the whole body on a free (floating) root instead of its root hinges
+    "c1_float": dict(n_bodies=60, n_dofs=90, n_muscles=700, max_points=6, max_span=3, limits=True,
+                     contact=True, seed=1, free_root=True),
 }
 
 
 def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, limits, contact, seed,
-             n_legs=2, spheres_per_foot=4, sphere_radius=0.03, max_dof_per_body=3, wrap_frac=0.0):
+             n_legs=2, spheres_per_foot=4, sphere_radius=0.03, max_dof_per_body=3, wrap_frac=0.0,
+             free_root=False):
     """Draw one synthetic skeleton + muscle model.
 
     Tree: a root body, then limb chains of U{3..8} bodies each, the parent of each chain drawn
@@ -451,8 +483,9 @@ def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, li
                 if r >= 0.005:
                     wraps.append((int(k), j, int(bs), (0.0, 0.0, 0.0), a, r))
                 break
-    return make_model(name or "synthetic", parent, ndof, offset, mass, com, inertia, axes,
-                      muscle_points, fmax, lopt, lslack, dof_limit=lim, spheres=spheres, wraps=wraps)
+    mdl = make_model(name or "synthetic", parent, ndof, offset, mass, com, inertia, axes,
+                     muscle_points, fmax, lopt, lslack, dof_limit=lim, spheres=spheres, wraps=wraps)
+    return with_free_root(mdl, name) if free_root else mdl
 
 
 def config_model(name):
@@ -485,13 +518,16 @@ def tree_stats(model):
 
 
 def initial_state(model, n_envs, seed):
-    """q0 ~ U(-0.3, 0.3) rad (clipped into enabled joint limits), qd0 = 0, act0 = 0."""
+    """q0 ~ U(-0.3, 0.3) rad (clipped into enabled joint limits), qd0 = 0, act0 = 0; a free
+    root starts at its model pose (q = 0: position offset, world-aligned)."""
     rng = np.random.default_rng(seed + 1000)
     n, m = model.n_dofs, model.n_muscles
     q = rng.uniform(-0.3, 0.3, size=(n_envs, n))
     lo, hi = model.dof_limit[:, 0], model.dof_limit[:, 1]
     on = lo < hi
     q[:, on] = np.clip(q[:, on], lo[on], hi[on])
+    if model.free_root:
+        q[:, :6] = 0.0
     return (q.astype(np.float32), np.zeros((n_envs, n), np.float32), np.zeros((n_envs, m), np.float32))
 
 
