@@ -196,9 +196,10 @@ def run_reference(args, rank):
 
 def _config(args):
     wrap = ", 188 of them wrapping a cylinder" if args.model == "c1_wrap" else ""
-    return {"workload": "whole-body synthetic model (60 bodies, 90 hinge DoF, 700 Hill muscles%s, 8 contact "
+    dofs = "a free root (6 DoF) and 89 hinge DoF" if args.model == "c1_float" else "90 hinge DoF"
+    return {"workload": "whole-body synthetic model (60 bodies, %s, 700 Hill muscles%s, 8 contact "
                         "spheres), %d envs, %d substeps x dt %.0e s per step, smooth excitations, exact geometry"
-                        % (wrap, args.envs, args.substeps, DT),
+                        % (dofs, wrap, args.envs, args.substeps, DT),
             "envs_per_gpu": args.envs, "substeps_per_step": args.substeps, "dt": DT, "geometry": "exact",
             "l2": "flushed (256 MB write) between timed steps; excitation inputs cycle over 32 distinct buffers"}
 
@@ -595,8 +596,8 @@ def main():
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
     ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
-    ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap"],
-                    help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder)")
+    ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_float"],
+                    help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; c1_float: a free root)")
     ap.add_argument("--policy-envs", type=int, default=16384)
     ap.add_argument("--policy-steps", type=int, default=2000)
     args = ap.parse_args()

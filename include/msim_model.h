@@ -8,7 +8,8 @@
  *
  * Geometry conventions:
  *   - Bodies are listed parents first: body_parent[b] < b, -1 = the fixed world.
- *   - Body b owns body_ndof[b] in {1,2,3} hinge DoFs, numbered consecutively in body order.
+ *   - Body b owns body_ndof[b] in {1,2,3} hinge DoFs, numbered consecutively in body order
+ *     (6 free DoFs for body 0 with free_root, below).
  *   - Frame of body b = frame of its parent * translate(body_offset[b]) * Rot(a_0, q_0) * ...
  *     * Rot(a_{k-1}, q_{k-1}), each axis a_j (dof_axis, unit) given in the frame just before
  *     its hinge.  The body origin is the joint origin.
@@ -69,6 +70,14 @@ typedef struct {
     const float* wrap_center;          /* [n_wraps][3] */
     const float* wrap_axis;            /* [n_wraps][3] (normalised by the library) */
     const float* wrap_radius;          /* [n_wraps], > 0 */
+    /* free (floating) root: 0 = every root body is fixed to the world.  1 = body 0 (a root) is
+     * joined to the world by six DoFs 0-5 (body_ndof[0] = 6; its dof_axis rows are ignored and
+     * its dof_limit rows must be disabled): DoFs 0-2 translate its origin along world x, y, z
+     * (q = position offset from body_offset[0] in m, qd = velocity), DoFs 3-5 turn it about
+     * world x, y, z through its origin (qd = angular velocity in the world frame, rad/s; q =
+     * the rotation vector of its orientation, rad, advanced by R <- exp(dt w) R each substep and
+     * kept at angle <= pi).  The paper's skeleton has such a root ("Observation space"). */
+    int32_t free_root;
 } msim_model_desc;
 
 #ifdef __cplusplus

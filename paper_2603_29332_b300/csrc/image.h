@@ -96,7 +96,8 @@ struct alignas(16) ImgHeader {
     float limit_k, limit_c, tau_act, tau_deact;
     float fp_den;               // exp(4) - 1 of the passive curve
     float fp_slope;             // slope of the passive curve's linear extension
-    float pad[3];
+    int32_t free_root;          // 1: body 0 has the six free DoFs 0-5 (msim_model.h)
+    float pad[2];
 };
 
 // Per environment workspace (floats), laid out by the host (msim_api.cu):

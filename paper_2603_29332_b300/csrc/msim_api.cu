@@ -69,7 +69,11 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         const int pb = d.body_parent[b];
         if (pb < -1 || pb >= b) FAIL("body_parent[%d] = %d must be in [-1, %d)", b, pb, b);
         const int k = d.body_ndof[b];
-        if (k < 1 || k > 3) FAIL("body_ndof[%d] = %d must be 1..3", b, k);
+        if (d.free_root && b == 0) {
+            if (pb != -1 || k != 6) FAIL("free root: body 0 must be a root with 6 DoFs");
+        } else if (k < 1 || k > 3) {
+            FAIL("body_ndof[%d] = %d must be 1..3", b, k);
+        }
         dof0[b] = acc;
         for (int j = 0; j < k; ++j) {
             const int dd = acc + j;
@@ -82,7 +86,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         bdepth[b] = pb < 0 ? 0 : bdepth[pb] + 1;
     }
     if (acc != n) FAIL("sum of body_ndof (%d) != n_dofs (%d)", acc, n);
-    for (int i = 0; i < n; ++i) {
+    if (d.free_root != 0 && d.free_root != 1) FAIL("free_root must be 0 or 1");
+    for (int i = d.free_root ? 6 : 0; i < n; ++i) {   // the free root's axes are implied
         const float* a = d.dof_axis + 3 * i;
         const double nrm = std::sqrt(double(a[0]) * a[0] + double(a[1]) * a[1] + double(a[2]) * a[2]);
         if (std::fabs(nrm - 1.0) > 1e-4) FAIL("dof_axis[%d] is not a unit vector", i);
@@ -322,6 +327,10 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         D.lo = d.dof_limit ? d.dof_limit[2 * i] : 0.f;
         D.hi = d.dof_limit ? d.dof_limit[2 * i + 1] : 0.f;
         D.damp = d.dof_damping ? d.dof_damping[i] : 0.f;
+        if (d.free_root && i < 6) {   // world axes x, y, z (translations, then rotations)
+            for (int c = 0; c < 3; ++c) D.axis[c] = (c == i % 3) ? 1.f : 0.f;
+            if (D.lo < D.hi) FAIL("free root: DoF %d must have no limit", i);
+        }
         D.row = row[i];
         D.parent = (int16_t)dpar[i];
         D.depth = (uint8_t)depth[i];
@@ -394,6 +403,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     const double e4 = std::exp(4.0);
     h.fp_den = (float)(e4 - 1.0);
     h.fp_slope = (float)((4.0 / 0.6) * e4 / (e4 - 1.0));
+    h.free_root = d.free_root;
 
     out.blob.assign(h.total_bytes, 0);
     auto put = [&](int32_t o, const void* src, size_t bytes) {
@@ -1053,6 +1063,10 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
     if (!h) return arg_fail(h, "msim_surrogate_train: NULL handle");
     if (h->n_models != 1) {
         h->err = "msim_surrogate_train: single-model handles only";
+        return MSIM_ERR_UNSUPPORTED;
+    }
+    if (h->models[0].hdr.free_root) {   // the training box spans joint limits; a free root has none
+        h->err = "msim_surrogate_train: models with a free root are not supported";
         return MSIM_ERR_UNSUPPORTED;
     }
     if (batch < 1 || batch > 65536 || n_samples < batch || n_samples > (int64_t)1 << 30 || epochs < 1 ||

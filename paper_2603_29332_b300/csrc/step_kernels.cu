@@ -276,7 +276,42 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
                     w[k] = Vp[k]; vl[k] = Vp[3 + k]; aw[k] = Ap[k]; al[k] = Ap[3 + k];
                 }
             }
-            for (int j = 0; j < B.ndof; ++j) {
+            if (b == 0 && H.free_root) {
+                // free root: origin at offset + q[0..2], orientation exp(q[3..5]) (Rodrigues:
+                // R = I + (sin t / t) K + ((1 - cos t) / t^2) K^2, K = [r]x, with 1 - cos t =
+                // 2 sin^2(t / 2)); axes world x, y, z: slides S = [0; e], turns S = [e; p x e]
+                const float r0 = q[3], r1 = q[4], r2 = q[5];
+                const float t2 = r0 * r0 + r1 * r1 + r2 * r2, t = sqrtf(t2);
+                float sh, ch;
+                sincosf(0.5f * t, &sh, &ch);
+                const float ka = t > 1e-20f ? 2.f * sh * ch / t : 1.f;
+                const float kb = t > 1e-20f ? 2.f * sh * sh / t2 : 0.5f;
+                const float rr[3] = {r0, r1, r2};
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) R[3 * i + k] = kb * rr[i] * rr[k] + (i == k ? 1.f - kb * t2 : 0.f);
+                R[1] -= ka * r2; R[2] += ka * r1; R[3] += ka * r2; R[5] -= ka * r0; R[6] -= ka * r1; R[7] += ka * r0;
+                p[0] += q[0]; p[1] += q[1]; p[2] += q[2];
+                const float om[3] = {qd[3], qd[4], qd[5]}, vp[3] = {qd[0], qd[1], qd[2]};
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    float* St = S + 6 * i;
+                    float* Sr = S + 6 * (3 + i);
+                    const float e[3] = {i == 0 ? 1.f : 0.f, i == 1 ? 1.f : 0.f, i == 2 ? 1.f : 0.f};
+                    float pe[3];
+                    cross3(p, e, pe);
+                    St[0] = St[1] = St[2] = 0.f; St[3] = e[0]; St[4] = e[1]; St[5] = e[2];
+                    Sr[0] = e[0]; Sr[1] = e[1]; Sr[2] = e[2]; Sr[3] = pe[0]; Sr[4] = pe[1]; Sr[5] = pe[2];
+                }
+                // velocity [w; v_p + p x w]; bias [0; v_p x w] (the turn axes move with the origin)
+                float pw[3], vw[3];
+                cross3(p, om, pw);
+                cross3(vp, om, vw);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { w[k] = om[k]; vl[k] = vp[k] + pw[k]; al[k] += vw[k]; }
+            }
+            for (int j = 0; j < B.ndof && !(b == 0 && H.free_root); ++j) {
                 const int d = B.dof0 + j;
                 const DofRec& D = T.dof[d];
                 float s[3], ps[3];
@@ -819,6 +854,10 @@ __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, flo
                 float Ja[3], Jb[3];
                 cross3(Sa, ra, Ja);
                 cross3(Sb, rb, Jb);
+                if (H.free_root) {   // a slide of the free root moves the point along its axis
+                    if (da < 3) { Ja[0] = Sa[3]; Ja[1] = Sa[4]; Ja[2] = Sa[5]; }
+                    if (db < 3) { Jb[0] = Sb[3]; Jb[1] = Sb[4]; Jb[2] = Sb[5]; }
+                }
                 val[u] = (o[6] * Ja[0]) * (o[6] * Jb[0]) + (o[7] * Ja[1]) * (o[7] * Jb[1]) +
                          (o[8] * Ja[2]) * (o[8] * Jb[2]);
                 tgt[u] = T.dof[da].row + ib;
@@ -965,6 +1004,30 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
     return g.all(ok);
 }
 
+// Free root: the rotation vector r of the orientation after a step with world angular velocity
+// w, R <- exp(dt w) R, by unit quaternions (product of the step's rotation and the current one,
+// sign chosen so that the angle stays in [0, pi]).
+__device__ void free_root_turn(float* r, const float* w, float dt) {
+    auto quat = [](float x, float y, float z, float o[4]) {
+        const float t = sqrtf(x * x + y * y + z * z);
+        float sh, ch;
+        sincosf(0.5f * t, &sh, &ch);
+        const float k = t > 1e-20f ? sh / t : 0.5f;
+        o[0] = ch; o[1] = k * x; o[2] = k * y; o[3] = k * z;
+    };
+    float a[4], b[4], c[4];
+    quat(r[0], r[1], r[2], a);
+    quat(dt * w[0], dt * w[1], dt * w[2], b);
+    c[0] = b[0] * a[0] - b[1] * a[1] - b[2] * a[2] - b[3] * a[3];
+    c[1] = b[0] * a[1] + b[1] * a[0] + b[2] * a[3] - b[3] * a[2];
+    c[2] = b[0] * a[2] - b[1] * a[3] + b[2] * a[0] + b[3] * a[1];
+    c[3] = b[0] * a[3] + b[1] * a[2] - b[2] * a[1] + b[3] * a[0];
+    const float sg = c[0] < 0.f ? -1.f : 1.f;
+    const float vn = sqrtf(c[1] * c[1] + c[2] * c[2] + c[3] * c[3]);
+    const float k = vn > 1e-30f ? 2.f * atan2f(vn, sg * c[0]) * sg / vn : 2.f * sg;
+    r[0] = k * c[1]; r[1] = k * c[2]; r[2] = k * c[3];
+}
+
 // ------------------------------------------------------------------ one substep
 // With MSIM_PHASE_TIMERS defined (profiling builds only), lane 0 of every group adds the
 // cycles spent in each phase to timers[0..7].
@@ -1049,9 +1112,13 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
         for (int d = g.lane; d < H.n; d += g.N) {
             const float v = qd[d] + dt * (Y[d].hi + Y[d].lo);
             qd[d] = v;
-            q[d] += dt * v;
+            if (!(H.free_root && d >= 3 && d < 6)) q[d] += dt * v;
         }
         g.sync();
+        if (H.free_root) {
+            if (g.lane == 0) free_root_turn(q + 3, qd + 3, dt);
+            g.sync();
+        }
     } else if (ev->qdd) {
         for (int d = g.lane; d < H.n; d += g.N) ev->qdd[d] = Y[d].hi + Y[d].lo;
     }

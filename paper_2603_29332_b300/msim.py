@@ -38,7 +38,7 @@ class ModelDesc(C.Structure):
                 ("limit_c", C.c_float), ("tau_act", C.c_float), ("tau_deact", C.c_float),
                 ("vmax_per_lopt", C.c_float),
                 ("n_wraps", C.c_int32), ("wrap_muscle", _i32p), ("wrap_segment", _i32p), ("wrap_body", _i32p),
-                ("wrap_center", _f32p), ("wrap_axis", _f32p), ("wrap_radius", _f32p)]
+                ("wrap_center", _f32p), ("wrap_axis", _f32p), ("wrap_radius", _f32p), ("free_root", C.c_int32)]
 
 
 class CreateArgs(C.Structure):
@@ -203,6 +203,7 @@ def model_desc(model):
     d.n_bodies, d.n_dofs, d.n_muscles = model.n_bodies, model.n_dofs, model.n_muscles
     d.n_points, d.n_spheres = model.n_points, model.n_spheres
     d.n_wraps = int(model.wrap_muscle.shape[0])
+    d.free_root = 1 if getattr(model, "free_root", False) else 0
     for k, v in keep.items():
         setattr(d, k, v.ctypes.data_as(_i32p if v.dtype == np.int32 else _f32p) if v.size else None)
     d.gravity = (C.c_float * 3)(*[float(x) for x in model.gravity])

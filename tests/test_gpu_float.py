@@ -1,0 +1,134 @@
+"""Free (floating) root on the device, through the C ABI, against the FP64 oracle.
+
+Body 0 joined to the world by six DoFs (translations of its origin along world x, y, z, then
+rotations about world x, y, z through it; q = position and rotation vector, qd = velocity and
+world angular velocity).  Checks: every stage of one substep of the floating whole body, a
+100-substep trajectory, the exact semi-implicit Euler free fall of a spinning sphere, a long
+spin that carries the rotation vector through angle pi, and the host's checks.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from scipy.spatial.transform import Rotation
+
+from oracle import oracle as ora
+from paper_2603_29332_b300 import modelgen as mg
+from paper_2603_29332_b300 import msim
+from tests.gpu_common import oracle_eval, qdd_rel_err, random_states, sample_envs
+
+pytestmark = pytest.mark.gpu
+
+DT = 1e-3
+
+
+def _sphere(omega_scale=1.0):
+    base = mg.make_model("ball", [-1], [1], [[0.0, 0.0, 1.0]], [2.0], [[0, 0, 0]], [[0.02, 0.02, 0.02, 0, 0, 0]],
+                         [[0, 0, 1]], muscle_points=[[(0, (0.0, 0.0, 0.1)), (0, (0.0, 0.1, 0.0))]],
+                         muscle_fmax=[10.0], muscle_lopt=[0.1])
+    return mg.with_free_root(base)
+
+
+def test_floating_body_stage_parity():
+    model = mg.config_model("c1_float")
+    om = ora.OracleModel(model)
+    E, n, m = 1024, model.n_dofs, model.n_muscles
+    sim = msim.Sim(model, E, dt=DT)
+    lay = sim.layout(0)
+    q, qd, act, exc = random_states(model, E, seed=31)
+    q[:, 2] = np.abs(q[:, 2]) * 0.1 - 0.02        # root height near the model pose: some feet touch
+    res = sim.eval(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act), sim.pad_m(exc))
+    g = {k: v.double().cpu().numpy() for k, v in res.items()}
+    worst, n_contact = 0.0, 0
+    for e in sample_envs(E, 24, seed=4):
+        r = oracle_eval(om, DT, q[e], qd[e], act[e], exc[e])
+        assert r["status"] == 0
+        np.testing.assert_allclose(g["L"][e, :m], r["L"], rtol=0, atol=2e-6)
+        np.testing.assert_allclose(msim.unpack_R(g["R"][e], lay, n), r["R"], rtol=0, atol=2e-6)
+        Mg = msim.unpack_packed(g["M"][e], lay)
+        np.testing.assert_allclose(Mg, r["M"], rtol=0, atol=2e-6 * np.abs(r["M"]).max())
+        sC = np.abs(r["bias"]).max() + 1.0
+        np.testing.assert_allclose(g["bias"][e, :n], r["bias"], rtol=0, atol=2e-5 * sC)
+        np.testing.assert_allclose(g["tau_c"][e, :n], r["tau_c"], rtol=0, atol=1e-3 * (np.abs(r["tau_c"]).max() + 1))
+        n_contact += int(np.abs(r["tau_c"]).max() > 0)
+        worst = max(worst, qdd_rel_err(g["qdd"][e, :n], r["qdd"]))
+    print("\nfloating root: worst qdd rel err %.2e, envs in contact %d" % (worst, n_contact))
+    assert worst <= 1e-4
+    assert n_contact > 0
+
+
+def test_floating_body_trajectory_100_steps():
+    model = mg.config_model("c1_float")
+    om = ora.OracleModel(model)
+    E, steps = 1024, 100
+    sim = msim.Sim(model, E, dt=DT)
+    q0, qd0, a0 = mg.initial_state(model, E, seed=9)
+    exc = mg.smooth_excitations(model, E, steps, seed=9)
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    for t in range(steps):
+        sim.step(sim.pad_m(exc[t]), 1)
+    qg = sim.state()["q"][:, :model.n_dofs].double().cpu().numpy()
+    idx = sample_envs(E, 12, seed=2)
+    q, qd, act = q0[idx].astype(np.float64), qd0[idx].astype(np.float64), a0[idx].astype(np.float64)
+    for t in range(steps):
+        q, qd, act, *_ = ora.step(om, DT, q, qd, act, exc[t][idx].astype(np.float64), 1)
+    err = np.abs(qg[idx] - q).max()
+    drop = np.abs(q[:, :6]).max()
+    print("\nfloating trajectory: max |q_gpu - q_oracle| %.2e (root moved up to %.3f)" % (err, drop))
+    assert err <= 1e-3
+    assert drop > 1e-3   # the root did move
+    assert sim.status() == (0, 0)
+
+
+def test_free_fall_of_a_spinning_sphere_is_exact_semi_implicit_euler():
+    model = _sphere()
+    E, N = 4, 200
+    sim = msim.Sim(model, E, dt=DT)
+    v0 = np.array([[0.3, -0.2, 1.5], [0, 0, 0], [1, 1, 1], [-2, 0.5, 0]], np.float32)
+    w0 = np.array([[0.4, 1.1, -0.7], [0, 0, 3.0], [0, 0, 0], [2, -1, 0.5]], np.float32)
+    q0 = np.zeros((E, 6), np.float32)
+    qd0 = np.concatenate([v0, w0], 1)
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(np.zeros((E, 1), np.float32)))
+    zero = sim.pad_m(np.zeros((E, 1), np.float32))
+    sim.step(zero, N)
+    st = sim.state()
+    q, qd = st["q"][:, :6].double().cpu().numpy(), st["qd"][:, :6].double().cpu().numpy()
+    g = model.gravity
+    for e in range(E):
+        np.testing.assert_allclose(qd[e, :3], v0[e] + N * DT * g, rtol=0, atol=2e-5)
+        np.testing.assert_allclose(q[e, :3], N * DT * v0[e] + DT * DT * g * N * (N + 1) / 2, rtol=0, atol=2e-5)
+        np.testing.assert_allclose(qd[e, 3:], w0[e], rtol=0, atol=1e-5)
+        np.testing.assert_allclose(q[e, 3:], N * DT * w0[e].astype(np.float64), rtol=0, atol=1e-4)
+
+
+def test_long_spin_carries_the_rotation_vector_through_pi():
+    model = _sphere()
+    E, N = 2, 1500
+    sim = msim.Sim(model, E, dt=DT)
+    w0 = np.array([[0.0, 0.0, 4.0], [2.0, -3.0, 1.0]], np.float32)   # 6 rad and 5.6 rad: past pi
+    qd0 = np.concatenate([np.zeros((E, 3), np.float32), w0], 1)
+    sim.reset(sim.pad_n(np.zeros((E, 6), np.float32)), sim.pad_n(qd0), sim.pad_m(np.zeros((E, 1), np.float32)))
+    sim.step(sim.pad_m(np.zeros((E, 1), np.float32)), N)
+    r = sim.state()["q"][:, 3:6].double().cpu().numpy()
+    for e in range(E):
+        want = Rotation.from_rotvec(N * DT * w0[e].astype(np.float64)).as_matrix()
+        np.testing.assert_allclose(Rotation.from_rotvec(r[e]).as_matrix(), want, rtol=0, atol=2e-4)
+        assert np.linalg.norm(r[e]) <= np.pi + 1e-5
+
+
+def test_free_root_checks():
+    model = mg.config_model("c1_float")
+    sim = msim.Sim(model, 8, dt=DT)
+    with pytest.raises(msim.MsimError, match="free root"):
+        sim.train_surrogate(n_samples=4096, epochs=1)
+    bad = copy.deepcopy(model)
+    bad.dof_limit[0] = [-1.0, 1.0]
+    with pytest.raises(msim.MsimError, match="no limit"):
+        msim.Sim(bad, 4, dt=DT)
+    bad = copy.deepcopy(model)
+    bad.free_root = False
+    with pytest.raises(msim.MsimError, match="body_ndof"):
+        msim.Sim(bad, 4, dt=DT)
