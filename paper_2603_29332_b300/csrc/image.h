@@ -97,7 +97,8 @@ struct alignas(16) ImgHeader {
     float fp_den;               // exp(4) - 1 of the passive curve
     float fp_slope;             // slope of the passive curve's linear extension
     int32_t free_root;          // 1: body 0 has the six free DoFs 0-5 (msim_model.h)
-    float pad[2];
+    int32_t n_wraps;            // wrapping cylinders (their records follow the via points)
+    float pad[1];
 };
 
 // Per environment workspace (floats), laid out by the host (msim_api.cu):

@@ -34,6 +34,8 @@ struct StepArgs {
     float dt;
     int envs_per_block;
     int wpe;                      // warps per environment: 1, 2 or 4
+    int wrap;                     // 1: the model has wrapping cylinders (step launches take the
+                                  // variant with the wrapping branch)
     EvalPtrs ev;                  // eval: per-stage outputs; geometry mode: ev.L = label rows
                                   // [env][ev.nnz_pitch] (L then R), rows from env_begin
     // surrogate step (one substep per launch)
@@ -76,9 +78,10 @@ struct MixedArgs {
     int slots;                    // environment slots per block (threads = 32 wpe slots)
     int img_region;               // shared bytes reserved for the image (max over models, 128-aligned)
     uint32_t* queue;              // work counter (zeroed by launch_mixed before the kernel)
+    int wrap;                     // 1: some model has wrapping cylinders
 };
 cudaError_t launch_mixed(const MixedArgs& m, int grid, size_t smem, cudaStream_t s);
-int mixed_blocks_per_sm(int threads, size_t smem, int wpe);
+int mixed_blocks_per_sm(int threads, size_t smem, int wpe, bool wrap);
 cudaError_t launch_geom(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
 // body origins of the configurations a.q rows [env_begin, env_end) into a.ev.xpos (pitch a.ev.xpos_pitch)
 cudaError_t launch_fk(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
@@ -112,6 +115,6 @@ cudaError_t launch_delta(const float* q, const float* qr, int pitch_n, const flo
 cudaError_t launch_reward(const float* Dout, int ldo, const float* F, const float* vm, int pitch_m, int m, int n_envs,
                           float w_power, float* r, float* parts, cudaStream_t s);
 cudaError_t set_step_smem_limit(size_t bytes);
-int step_blocks_per_sm(int threads, size_t smem, int wpe);
+int step_blocks_per_sm(int threads, size_t smem, int wpe, bool wrap);
 
 }  // namespace msim

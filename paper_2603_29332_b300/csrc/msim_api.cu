@@ -404,6 +404,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.fp_den = (float)(e4 - 1.0);
     h.fp_slope = (float)((4.0 / 0.6) * e4 / (e4 - 1.0));
     h.free_root = d.free_root;
+    h.n_wraps = nw;
 
     out.blob.assign(h.total_bytes, 0);
     auto put = [&](int32_t o, const void* src, size_t bytes) {
@@ -463,7 +464,8 @@ int model_grid(msim_handle h, int i) {
     const int ne = h->env_begin[i + 1] - h->env_begin[i];
     const int groups = (ne + h->epb[i] - 1) / h->epb[i];
     const size_t smem = step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i], h->wpe[i]);
-    const int per_sm = std::max(1, step_blocks_per_sm(32 * h->wpe[i] * h->epb[i], smem, h->wpe[i]));
+    const int per_sm =
+        std::max(1, step_blocks_per_sm(32 * h->wpe[i] * h->epb[i], smem, h->wpe[i], h->models[i].hdr.n_wraps > 0));
     return std::max(1, std::min(groups, h->num_sms * per_sm));
 }
 
@@ -471,6 +473,7 @@ StepArgs base_args(msim_handle h, int i) {
     StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.img = h->d_img[i];
+    a.wrap = h->models[i].hdr.n_wraps > 0 ? 1 : 0;
     a.points_in_smem = h->pts_smem[i];
     a.staged_bytes = h->pts_smem[i] ? h->models[i].hdr.total_bytes : h->models[i].hdr.o_point;
     a.env_begin = h->env_begin[i];
@@ -555,7 +558,7 @@ cudaError_t geometry_launch(msim_handle h, int i, const float* q, int ldq, int n
     a.ev.nnz_pitch = ldo;
     const size_t smem = step_smem_bytes(h->models[i].hdr, epb, h->pts_smem[i], wpe);
     const int groups = (n_rows + epb - 1) / epb;
-    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe));
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe, h->models[i].hdr.n_wraps > 0));
     return launch_geom(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
 }
 
@@ -578,7 +581,7 @@ cudaError_t fk_launch(msim_handle h, int i, const float* q, int ldq, int n_rows,
     a.ev.xpos_pitch = 3 * h->models[i].hdr.nb;
     const size_t smem = step_smem_bytes(h->models[i].hdr, epb, h->pts_smem[i], wpe);
     const int groups = (n_rows + epb - 1) / epb;
-    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe));
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe, h->models[i].hdr.n_wraps > 0));
     return launch_fk(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
 }
 

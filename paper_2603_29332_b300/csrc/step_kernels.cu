@@ -39,7 +39,14 @@ namespace {
 
 // kernel modes: one substep loop, one-substep evaluation with every intermediate, muscle
 // geometry only (surrogate training labels), surrogate step (geometry from the learned model)
-constexpr int kModeStep = 0, kModeEval = 1, kModeGeom = 2, kModeSurr = 3, kModeFk = 4;
+// kModeStepW / kModeSurrW: the step and the learned-geometry substep with the wrapping-cylinder
+// branch compiled in (models that have cylinders); kModeStep and kModeSurr leave it out (so that
+// the two stay alike instruction for instruction, their exact geometry agrees bit for bit); the
+// other modes always keep it.
+constexpr int kModeStep = 0, kModeEval = 1, kModeGeom = 2, kModeSurr = 3, kModeFk = 4, kModeStepW = 5,
+              kModeSurrW = 6;
+__host__ __device__ constexpr bool is_surr(int mode) { return mode == kModeSurr || mode == kModeSurrW; }
+__host__ __device__ constexpr bool has_wrap(int mode) { return mode != kModeStep && mode != kModeSurr; }
 
 constexpr uint32_t kEnvNonFinite = 0x1u;
 constexpr uint32_t kEnvNotSpd = 0x2u;
@@ -644,7 +651,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
         const int k = M.orig;
         const float a = MODE == kModeGeom ? 0.f : act[k];
         const float u = MODE == kModeGeom ? 0.f : fminf(fmaxf(exc[k], 0.f), 1.f);
-        const bool learned = (MODE == kModeSurr) && !sc->use_exact;   // geometry from the network
+        const bool learned = is_surr(MODE) && !sc->use_exact;   // geometry from the network
         float L = 0.f, ldot = 0.f;
         if (!learned || sc->check) {
             // exact via-point geometry: L = sum |x_{j+1} - x_j|, R = -dL/dq of the crossed DoFs
@@ -671,7 +678,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                     ldot -= Rv * qd[d];
                 }
             };
-            const int wseg = M.wrap ? (T.wrap[M.wrap - 1].body_cross >> 16) : 0;
+            const int wseg = (has_wrap(MODE) && M.wrap) ? (T.wrap[M.wrap - 1].body_cross >> 16) : 0;
             for (int j = 1; j < M.np; ++j) {
                 P = T.pt[M.p0 + j];
                 b = P.body_cross & 0xff;
@@ -681,7 +688,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                 rot3(fb, P.pos, x1);
                 x1[0] += fb[9]; x1[1] += fb[10]; x1[2] += fb[11];
                 bool wrapped = false;
-                if (j == wseg) {
+                if (has_wrap(MODE) && j == wseg) {
                     // the wrapped segment: tangent points held on the cylinder's body for the arms
                     const WrapRec W = T.wrap[M.wrap - 1];
                     const float* fw = frame + 12 * (W.body_cross & 0xff);
@@ -709,7 +716,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                 cprev = c;
             }
         }
-        if (MODE == kModeSurr && learned) {
+        if (is_surr(MODE) && learned) {
             // learned geometry: de-normalised network outputs (L first, then R in sparse order)
             const int mm = H.m;
             const float Ls = sc->Y[k] * sc->sd[k] + sc->mu[k];
@@ -1165,7 +1172,7 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
         ev.xpos = a.ev.xpos + (size_t)(e - a.env_begin) * ev.xpos_pitch;
         substep<kModeFk>(T, ws, g, a.dt, nullptr, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
     } else {
-        if (MODE == kModeSurr) {
+        if (is_surr(MODE)) {
             // one substep with the learned geometry (the host loops over substeps)
             bool oob = false;
             for (int d = g.lane; d < H.n; d += g.N)   // a non-finite q counts as outside
@@ -1182,7 +1189,7 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             sc.check = !sc.use_exact && u01_from_bits(c[0]) < a.check_frac;
             sc.tol = a.tol;
             sc.max_err_bits = reinterpret_cast<unsigned int*>(a.surr_stats + 6);
-            const uint32_t s1 = substep<kModeSurr>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+            const uint32_t s1 = substep<MODE>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
                                                    a.force_out ? a.force_out + rm : nullptr,
                                                    a.vm_out ? a.vm_out + rm : nullptr, nullptr, &sc, a.timers);
             st |= s1 & 0xffu;
@@ -1201,7 +1208,7 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
         } else {
             for (int s = 0; s < a.n_sub; ++s) {
                 const bool last = (s == a.n_sub - 1);
-                st |= substep<kModeStep>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+                st |= substep<MODE == kModeStepW ? kModeStepW : kModeStep>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
                                          (last && a.force_out) ? a.force_out + rm : nullptr,
                                          (last && a.vm_out) ? a.vm_out + rm : nullptr, nullptr, nullptr,
                                          a.timers);
@@ -1267,7 +1274,7 @@ __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
 // model, n_sub substeps) are taken from a global counter in queue order (models ordered by cost
 // per environment, most expensive first, so the cheap items fill the tail).  A block re-stages
 // the model image only when its next item belongs to another model.
-template <int WPE>
+template <int WPE, int MODE>
 __global__ void __launch_bounds__(512, 1) k_step_mixed(MixedArgs ma) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -1332,7 +1339,11 @@ __global__ void __launch_bounds__(512, 1) k_step_mixed(MixedArgs ma) {
         float* ws = ws_all + (size_t)slot * ws_floats(*T.H, WPE);
         if (slot < M.epb) {
             const int e = M.env_begin + (item - M.item_begin) * M.epb + slot;
-            if (e < M.env_end) run_env<kModeStep, WPE>(ma.a, T, ws, g, e);
+            // a model without cylinders takes the variant without them, as in its own launch
+            if (e < M.env_end) {
+                if (MODE == kModeStepW && T.H->n_wraps == 0) run_env<kModeStep, WPE>(ma.a, T, ws, g, e);
+                else run_env<MODE, WPE>(ma.a, T, ws, g, e);
+            }
         }
     }
 }
@@ -1369,25 +1380,35 @@ size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem, int wpe
     return 16 + ((staged + 127) & ~(size_t)127) + (size_t)epb * ws_floats(h, wpe) * sizeof(float);
 }
 
-int step_blocks_per_sm(int threads, size_t smem, int wpe) {
+template <int MODE>
+static int step_occ(int threads, size_t smem, int wpe) {
     int n = 0;
     cudaError_t e;
-    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<kModeStep, 4>, threads, smem);
-    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<kModeStep, 2>, threads, smem);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<kModeStep, 1>, threads, smem);
+    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<MODE, 4>, threads, smem);
+    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<MODE, 2>, threads, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<MODE, 1>, threads, smem);
     return e == cudaSuccess ? n : 1;
+}
+
+int step_blocks_per_sm(int threads, size_t smem, int wpe, bool wrap) {
+    return wrap ? step_occ<kModeStepW>(threads, smem, wpe) : step_occ<kModeStep>(threads, smem, wpe);
 }
 
 cudaError_t set_step_smem_limit(size_t bytes) {
     const int b = (int)bytes;
-    const void* fns[] = {(const void*)k_step<kModeStep, 1>, (const void*)k_step<kModeStep, 2>,
-                         (const void*)k_step<kModeStep, 4>, (const void*)k_step<kModeEval, 1>,
-                         (const void*)k_step<kModeEval, 2>, (const void*)k_step<kModeEval, 4>,
-                         (const void*)k_step<kModeGeom, 1>, (const void*)k_step<kModeGeom, 2>,
-                         (const void*)k_step<kModeFk, 1>, (const void*)k_step<kModeFk, 2>,
-                         (const void*)k_step<kModeSurr, 1>, (const void*)k_step<kModeSurr, 2>,
-                         (const void*)k_step<kModeSurr, 4>, (const void*)k_step_mixed<1>,
-                         (const void*)k_step_mixed<2>, (const void*)k_step_mixed<4>};
+    const void* fns[] = {(const void*)k_step<kModeStep, 1>,        (const void*)k_step<kModeStep, 2>,
+                         (const void*)k_step<kModeStep, 4>,        (const void*)k_step<kModeStepW, 1>,
+                         (const void*)k_step<kModeStepW, 2>,       (const void*)k_step<kModeStepW, 4>,
+                         (const void*)k_step<kModeEval, 1>,        (const void*)k_step<kModeEval, 2>,
+                         (const void*)k_step<kModeEval, 4>,        (const void*)k_step<kModeGeom, 1>,
+                         (const void*)k_step<kModeGeom, 2>,        (const void*)k_step<kModeFk, 1>,
+                         (const void*)k_step<kModeFk, 2>,          (const void*)k_step<kModeSurr, 1>,
+                         (const void*)k_step<kModeSurr, 2>,        (const void*)k_step<kModeSurr, 4>,
+                         (const void*)k_step<kModeSurrW, 1>,       (const void*)k_step<kModeSurrW, 2>,
+                         (const void*)k_step<kModeSurrW, 4>,
+                         (const void*)k_step_mixed<1, kModeStep>,  (const void*)k_step_mixed<2, kModeStep>,
+                         (const void*)k_step_mixed<4, kModeStep>,  (const void*)k_step_mixed<1, kModeStepW>,
+                         (const void*)k_step_mixed<2, kModeStepW>, (const void*)k_step_mixed<4, kModeStepW>};
     for (const void* f : fns) {
         const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         if (e != cudaSuccess) return e;
@@ -1395,31 +1416,48 @@ cudaError_t set_step_smem_limit(size_t bytes) {
     return cudaSuccess;
 }
 
-cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
+template <int MODE>
+static void step_launch(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
     const int threads = 32 * a.wpe * a.envs_per_block;
-    if (a.wpe == 4) k_step<kModeStep, 4><<<grid, threads, smem, s>>>(a);
-    else if (a.wpe == 2) k_step<kModeStep, 2><<<grid, threads, smem, s>>>(a);
-    else k_step<kModeStep, 1><<<grid, threads, smem, s>>>(a);
+    if (a.wpe == 4) k_step<MODE, 4><<<grid, threads, smem, s>>>(a);
+    else if (a.wpe == 2) k_step<MODE, 2><<<grid, threads, smem, s>>>(a);
+    else k_step<MODE, 1><<<grid, threads, smem, s>>>(a);
+}
+
+cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
+    if (a.wrap) step_launch<kModeStepW>(a, grid, smem, s);
+    else step_launch<kModeStep>(a, grid, smem, s);
     return cudaGetLastError();
+}
+
+template <int MODE>
+static void mixed_launch(const MixedArgs& m, int grid, size_t smem, cudaStream_t s) {
+    const int threads = 32 * m.a.wpe * m.slots;
+    if (m.a.wpe == 4) k_step_mixed<4, MODE><<<grid, threads, smem, s>>>(m);
+    else if (m.a.wpe == 2) k_step_mixed<2, MODE><<<grid, threads, smem, s>>>(m);
+    else k_step_mixed<1, MODE><<<grid, threads, smem, s>>>(m);
 }
 
 cudaError_t launch_mixed(const MixedArgs& m, int grid, size_t smem, cudaStream_t s) {
-    const int threads = 32 * m.a.wpe * m.slots;
     cudaError_t e = cudaMemsetAsync(m.queue, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if (m.a.wpe == 4) k_step_mixed<4><<<grid, threads, smem, s>>>(m);
-    else if (m.a.wpe == 2) k_step_mixed<2><<<grid, threads, smem, s>>>(m);
-    else k_step_mixed<1><<<grid, threads, smem, s>>>(m);
+    if (m.wrap) mixed_launch<kModeStepW>(m, grid, smem, s);
+    else mixed_launch<kModeStep>(m, grid, smem, s);
     return cudaGetLastError();
 }
 
-int mixed_blocks_per_sm(int threads, size_t smem, int wpe) {
+template <int MODE>
+static int mixed_occ(int threads, size_t smem, int wpe) {
     int n = 0;
     cudaError_t e;
-    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<4>, threads, smem);
-    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<2>, threads, smem);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<1>, threads, smem);
+    if (wpe == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<4, MODE>, threads, smem);
+    else if (wpe == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<2, MODE>, threads, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_mixed<1, MODE>, threads, smem);
     return e == cudaSuccess ? n : 0;
+}
+
+int mixed_blocks_per_sm(int threads, size_t smem, int wpe, bool wrap) {
+    return wrap ? mixed_occ<kModeStepW>(threads, smem, wpe) : mixed_occ<kModeStep>(threads, smem, wpe);
 }
 
 cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
@@ -1446,9 +1484,15 @@ cudaError_t launch_fk(const StepArgs& a, int grid, size_t smem, cudaStream_t s) 
 
 cudaError_t launch_surr_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s) {
     const int threads = 32 * a.wpe * a.envs_per_block;
-    if (a.wpe == 4) k_step<kModeSurr, 4><<<grid, threads, smem, s>>>(a);
-    else if (a.wpe == 2) k_step<kModeSurr, 2><<<grid, threads, smem, s>>>(a);
-    else k_step<kModeSurr, 1><<<grid, threads, smem, s>>>(a);
+    if (a.wrap) {
+        if (a.wpe == 4) k_step<kModeSurrW, 4><<<grid, threads, smem, s>>>(a);
+        else if (a.wpe == 2) k_step<kModeSurrW, 2><<<grid, threads, smem, s>>>(a);
+        else k_step<kModeSurrW, 1><<<grid, threads, smem, s>>>(a);
+    } else {
+        if (a.wpe == 4) k_step<kModeSurr, 4><<<grid, threads, smem, s>>>(a);
+        else if (a.wpe == 2) k_step<kModeSurr, 2><<<grid, threads, smem, s>>>(a);
+        else k_step<kModeSurr, 1><<<grid, threads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
