@@ -73,6 +73,8 @@ typedef struct {
     int32_t env_begin[9];           /* first env of each model (n_models + 1 entries used) */
     int32_t n_dofs[8], n_muscles[8], n_bodies[8], nnz[8], n_packed[8], envs_per_block[8];
     int32_t image_bytes[8], workspace_bytes_per_env[8], points_in_smem[8], warps_per_env[8];
+    /* points_in_smem: the staging level of msim_set_launch's stage_points (1 whole image in
+     * shared memory, 0 via points in global memory, 2 via points and muscle records there) */
 } msim_dims;
 
 /* msim_create -- build a simulator for one or more models (<= 8) on one device.
@@ -161,8 +163,9 @@ MSIM_API msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_
  *   warps_per_env in {1, 2, 4} (0 = keep): the warps that work on one environment together;
  *   envs_per_block in [1, 16] (0 = as many as shared memory holds, at most 8; at most 512
  *   threads and 15 environments per block when warps_per_env > 1); stage_points: 1 = copy the
- *   via-point table into shared memory with the rest of the model, 0 = leave it in global memory
- *   (read through the cache) to make room for more environments per block, -1 = keep.
+ *   whole model image into shared memory, 0 = leave the via points (and wrapping cylinders) in
+ *   global memory (read through the cache) to make room for more environments per block, 2 =
+ *   also leave the muscle records and the crossed-DoF table there, -1 = keep.
  *   (0, -1, 0) restores the default.  MSIM_ERR_ARG if shared memory or the thread limit do not
  *   fit.  Results do not depend on the launch shape. */
 MSIM_API msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_per_block, int32_t stage_points,

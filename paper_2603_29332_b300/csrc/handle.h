@@ -88,7 +88,7 @@ msim_status arg_fail(msim_handle h, const char* what);
 bool aligned16(const void* p);
 int model_grid(msim_handle h, int i);
 StepArgs base_args(msim_handle h, int i);
-int max_epb(msim_handle h, int i, bool pts, int wpe);
+int max_epb(msim_handle h, int i, int stage, int wpe);
 void auto_launch(msim_handle h, int i);
 // mixed launch of all models with the handle's mixed_* settings; false if they do not fit
 bool mixed_args(msim_handle h, int wpe, int slots, const int* pts, MixedArgs* out, size_t* smem, int* grid);

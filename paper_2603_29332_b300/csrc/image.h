@@ -120,6 +120,14 @@ struct alignas(16) ImgHeader {
 //   rk[max_nx][32 wpe]                per-lane moment arms of the muscle being processed (last);
 //                                     sin, cos of the joint angles during the kinematics pass
 
+// Bytes of the image a block copies to shared memory at staging level `stage`: 1 = all of it;
+// 0 = all but the via points and wrapping cylinders (read through the cache); 2 = also without
+// the muscle records and the crossed-DoF table (the image places these four sections last, in
+// this order: muscles, crossed DoFs, via points, cylinders).
+__host__ __device__ inline int staged_bytes(const ImgHeader& h, int stage) {
+    return stage == 1 ? h.total_bytes : (stage == 2 ? h.o_muscle : h.o_point);
+}
+
 // floats per environment slot for a group of `wpe` warps per environment
 // (the moment-arm region also holds the joint sines and cosines during the kinematics pass)
 __host__ __device__ inline int ws_floats(const ImgHeader& h, int wpe) {

@@ -17,8 +17,9 @@ struct EvalPtrs {                 // per-stage outputs of one substep (msim_eval
 
 struct StepArgs {
     const uint8_t* img;           // device image of the model (16-byte multiple)
-    int staged_bytes;             // prefix copied to shared memory (whole image, or all but the points)
-    int points_in_smem;           // 0: path points are read from the global image
+    int staged_bytes;             // prefix copied to shared memory (staged_bytes in image.h)
+    int stage;                    // staging level: 1 all, 0 all but via points / cylinders, 2 also
+                                  // without muscle records / crossed DoFs (read from the global image)
     int env_begin, env_end;       // environments of this model
     float* q;                     // state rows (pitch_n / pitch_m)
     float* qd;
@@ -54,7 +55,7 @@ struct StepArgs {
 };
 
 // dynamic shared memory of a launch with `epb` environments per block
-size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem, int wpe);
+size_t step_smem_bytes(const ImgHeader& h, int epb, int stage, int wpe);
 constexpr int kMaxEnvsPerBlock = 16;
 
 cudaError_t launch_step(const StepArgs& a, int grid, size_t smem, cudaStream_t s);
@@ -63,7 +64,7 @@ cudaError_t launch_eval(const StepArgs& a, int grid, size_t smem, cudaStream_t s
 struct MixedModel {
     const uint8_t* img;
     int staged_bytes;             // bytes of the image staged to shared memory (multiple of 16)
-    int points_in_smem;
+    int stage;                    // staging level (0 or 1 in a mixed launch)
     int env_begin, env_end;
     int epb;                      // environments per work item (<= slots)
     int item_begin;               // first work item of this model

@@ -355,9 +355,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     };
     h.o_body = place(sizeof(BodyRec) * nb);
     h.o_dof = place(sizeof(DofRec) * n);
-    h.o_muscle = place(sizeof(MuscleRec) * m);
     h.o_sphere = place(sizeof(SphereRec) * ns);
-    h.o_cross = place(sizeof(uint32_t) * cross.size());
     h.o_border = place(border.size());
     h.o_blevel = place(sizeof(int16_t) * blevel.size());
     h.o_child = place(child.size());
@@ -367,7 +365,10 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.o_tri = place(sizeof(uint16_t) * tri.size());
     h.o_rowanc = place(sizeof(uint16_t) * rowanc.size());
     h.o_crba = place(crba_order.size());
-    h.o_point = place(sizeof(PointRec) * np);   // with the wraps, may stay in global memory (staging split)
+    // last: the sections that may stay in global memory (staged_bytes in image.h)
+    h.o_muscle = place(sizeof(MuscleRec) * m);
+    h.o_cross = place(sizeof(uint32_t) * cross.size());
+    h.o_point = place(sizeof(PointRec) * np);
     h.o_wrap = place(sizeof(WrapRec) * std::max(nw, 1));
     h.total_bytes = (int32_t)off;
     // per-environment workspace
@@ -474,8 +475,8 @@ StepArgs base_args(msim_handle h, int i) {
     std::memset(&a, 0, sizeof(a));
     a.img = h->d_img[i];
     a.wrap = h->models[i].hdr.n_wraps > 0 ? 1 : 0;
-    a.points_in_smem = h->pts_smem[i];
-    a.staged_bytes = h->pts_smem[i] ? h->models[i].hdr.total_bytes : h->models[i].hdr.o_point;
+    a.stage = h->pts_smem[i];
+    a.staged_bytes = staged_bytes(h->models[i].hdr, h->pts_smem[i]);
     a.env_begin = h->env_begin[i];
     a.env_end = h->env_begin[i + 1];
     a.q = h->q; a.qd = h->qd; a.act = h->act;
@@ -489,9 +490,9 @@ StepArgs base_args(msim_handle h, int i) {
     return a;
 }
 
-int max_epb(msim_handle h, int i, bool pts, int wpe) {
+int max_epb(msim_handle h, int i, int stage, int wpe) {
     const ImgHeader& hd = h->models[i].hdr;
-    const size_t fixed = step_smem_bytes(hd, 0, pts, wpe);
+    const size_t fixed = step_smem_bytes(hd, 0, stage, wpe);
     const size_t per = (size_t)ws_floats(hd, wpe) * sizeof(float);
     if (fixed + per > h->smem_optin) return 0;
     const int lim = wpe == 1 ? kMaxEnvsPerBlock : std::min(15, 16 / wpe);   // 512 threads, 15 named barriers
@@ -499,16 +500,21 @@ int max_epb(msim_handle h, int i, bool pts, int wpe) {
 }
 
 // Default launch shape: two warps per environment, as many environments per block as shared
-// memory holds (<= 8, <= the model's environments); the path points are staged in shared memory
-// only when that costs no environment per block (otherwise they are read through the cache).
+// memory holds (<= 8, <= the model's environments); sections are left in global memory (via
+// points, then also the muscle records, staging levels 0 and 2) only when that gains an
+// environment per block.
 void auto_launch(msim_handle h, int i) {
     const int ne = h->env_begin[i + 1] - h->env_begin[i];
     const int w = 2;
-    int e_in = std::min(max_epb(h, i, true, w), 8), e_out = std::min(max_epb(h, i, false, w), 8);
-    if (ne > 0) { e_in = std::min(e_in, ne); e_out = std::min(e_out, ne); }
+    int best = -1, best_e = 0;
+    for (int stage : {1, 0, 2}) {
+        int e = std::min(max_epb(h, i, stage, w), 8);
+        if (ne > 0) e = std::min(e, ne);
+        if (e > best_e) { best = stage; best_e = e; }
+    }
     h->wpe[i] = w;
-    if (e_in >= 1 && e_in >= e_out) { h->pts_smem[i] = 1; h->epb[i] = e_in; }
-    else { h->pts_smem[i] = 0; h->epb[i] = e_out; }
+    h->pts_smem[i] = best < 0 ? 1 : best;
+    h->epb[i] = best_e;
 }
 
 }  // namespace host
@@ -545,7 +551,7 @@ cudaError_t geometry_launch(msim_handle h, int i, const float* q, int ldq, int n
     StepArgs a = base_args(h, i);
     const int wpe = h->wpe[i] == 1 ? 1 : 2;
     int epb = h->epb[i];
-    if (wpe != h->wpe[i]) epb = std::max(1, std::min(max_epb(h, i, h->pts_smem[i] != 0, wpe), 8));
+    if (wpe != h->wpe[i]) epb = std::max(1, std::min(max_epb(h, i, h->pts_smem[i], wpe), 8));
     a.wpe = wpe;
     a.envs_per_block = epb;
     a.env_begin = 0;
@@ -568,7 +574,7 @@ cudaError_t fk_launch(msim_handle h, int i, const float* q, int ldq, int n_rows,
     StepArgs a = base_args(h, i);
     const int wpe = h->wpe[i] == 1 ? 1 : 2;
     int epb = h->epb[i];
-    if (wpe != h->wpe[i]) epb = std::max(1, std::min(max_epb(h, i, h->pts_smem[i] != 0, wpe), 8));
+    if (wpe != h->wpe[i]) epb = std::max(1, std::min(max_epb(h, i, h->pts_smem[i], wpe), 8));
     a.wpe = wpe;
     a.envs_per_block = epb;
     a.env_begin = 0;
@@ -716,8 +722,8 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
             StepArgs a;
             std::memset(&a, 0, sizeof(a));
             a.img = h->d_img[i];
-            a.staged_bytes = M.hdr.o_point;
-            a.points_in_smem = 0;
+            a.stage = 0;
+            a.staged_bytes = staged_bytes(M.hdr, 0);
             a.env_begin = 0; a.env_end = 1;
             a.q = zq; a.qd = zq + h->pitch_n; a.act = zm; a.exc = zm + h->pitch_m;
             a.pitch_n = h->pitch_n; a.pitch_m = h->pitch_m;
@@ -794,21 +800,21 @@ msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_per_block
                             int32_t warps_per_env) {
     if (!h || model < 0 || model >= h->n_models) return arg_fail(h, "msim_set_launch: bad handle or model");
     if (envs_per_block < 0 || envs_per_block > kMaxEnvsPerBlock) return arg_fail(h, "envs_per_block must be 0..16");
-    if (stage_points < -1 || stage_points > 1) return arg_fail(h, "stage_points must be -1, 0 or 1");
+    if (stage_points < -1 || stage_points > 2) return arg_fail(h, "stage_points must be -1, 0, 1 or 2");
     if (warps_per_env != 0 && warps_per_env != 1 && warps_per_env != 2 && warps_per_env != 4)
         return arg_fail(h, "warps_per_env must be 0, 1, 2 or 4");
     if (envs_per_block == 0 && stage_points == -1 && warps_per_env == 0) {
         auto_launch(h, model);
         return MSIM_OK;
     }
-    const bool pts = stage_points == -1 ? (h->pts_smem[model] != 0) : (stage_points == 1);
+    const int pts = stage_points == -1 ? h->pts_smem[model] : stage_points;
     const int w = warps_per_env == 0 ? h->wpe[model] : warps_per_env;
     int e = envs_per_block;
     if (e == 0) e = std::min(max_epb(h, model, pts, w), 8);
     if (e < 1 || e > max_epb(h, model, pts, w) || step_smem_bytes(h->models[model].hdr, e, pts, w) > h->smem_optin)
         return arg_fail(h, "msim_set_launch: shared memory or thread limit exceeded");
     h->epb[model] = e;
-    h->pts_smem[model] = pts ? 1 : 0;
+    h->pts_smem[model] = pts;
     h->wpe[model] = w;
     return MSIM_OK;
 }

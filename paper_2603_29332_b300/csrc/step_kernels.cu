@@ -96,6 +96,17 @@ __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     return t;
 }
 
+// Sections left out of the staged prefix are read from the image in global memory.
+__device__ __forceinline__ void unstaged_tables(Tables& T, const uint8_t* gimg, int stage) {
+    if (stage == 1) return;
+    T.pt = reinterpret_cast<const PointRec*>(gimg + T.H->o_point);
+    T.wrap = reinterpret_cast<const WrapRec*>(gimg + T.H->o_wrap);
+    if (stage == 2) {
+        T.mus = reinterpret_cast<const MuscleRec*>(gimg + T.H->o_muscle);
+        T.cross = reinterpret_cast<const uint32_t*>(gimg + T.H->o_cross);
+    }
+}
+
 __device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
     c[0] = a[1] * b[2] - a[2] * b[1];
     c[1] = a[2] * b[0] - a[0] * b[2];
@@ -1245,10 +1256,7 @@ __global__ void __launch_bounds__(512, 1) k_step(StepArgs a) {
     __syncthreads();
 #endif
     Tables T = make_tables(img);
-    if (!a.points_in_smem) {
-        T.pt = reinterpret_cast<const PointRec*>(a.img + T.H->o_point);
-        T.wrap = reinterpret_cast<const WrapRec*>(a.img + T.H->o_wrap);
-    }
+    unstaged_tables(T, a.img, a.stage);
     const ImgHeader& H = *T.H;
     const int warp = threadIdx.x >> 5;
     const int slot = warp / WPE;
@@ -1332,10 +1340,7 @@ __global__ void __launch_bounds__(512, 1) k_step_mixed(MixedArgs ma) {
             cur = i;
         }
         Tables T = make_tables(img);
-        if (!M.points_in_smem) {
-            T.pt = reinterpret_cast<const PointRec*>(M.img + T.H->o_point);
-            T.wrap = reinterpret_cast<const WrapRec*>(M.img + T.H->o_wrap);
-        }
+        unstaged_tables(T, M.img, M.stage);
         float* ws = ws_all + (size_t)slot * ws_floats(*T.H, WPE);
         if (slot < M.epb) {
             const int e = M.env_begin + (item - M.item_begin) * M.epb + slot;
@@ -1375,8 +1380,8 @@ __global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, uint8
 
 }  // namespace
 
-size_t step_smem_bytes(const ImgHeader& h, int epb, bool points_in_smem, int wpe) {
-    const size_t staged = points_in_smem ? (size_t)h.total_bytes : (size_t)h.o_point;
+size_t step_smem_bytes(const ImgHeader& h, int epb, int stage, int wpe) {
+    const size_t staged = (size_t)staged_bytes(h, stage);
     return 16 + ((staged + 127) & ~(size_t)127) + (size_t)epb * ws_floats(h, wpe) * sizeof(float);
 }
 

@@ -74,7 +74,7 @@ bool mixed_args(msim_handle h, int wpe, int slots, const int* pts, MixedArgs* ou
     size_t region = 0;
     for (int k = 0; k < no; ++k) {
         const ImgHeader& hd = h->models[order[k]].hdr;
-        const size_t staged = pts[order[k]] ? (size_t)hd.total_bytes : (size_t)hd.o_point;
+        const size_t staged = (size_t)staged_bytes(hd, pts[order[k]] ? 1 : 0);
         region = std::max(region, (staged + 127) & ~(size_t)127);
     }
     if (16 + region >= h->smem_optin) return false;
@@ -90,8 +90,8 @@ bool mixed_args(msim_handle h, int wpe, int slots, const int* pts, MixedArgs* ou
         if (epb < 1) return false;
         MixedModel& M = m.mdl[k];
         M.img = h->d_img[i];
-        M.points_in_smem = pts[i] ? 1 : 0;
-        M.staged_bytes = pts[i] ? hd.total_bytes : hd.o_point;
+        M.stage = pts[i] ? 1 : 0;
+        M.staged_bytes = staged_bytes(hd, M.stage);
         M.env_begin = h->env_begin[i];
         M.env_end = h->env_begin[i + 1];
         M.epb = epb;
@@ -226,8 +226,8 @@ void write_cache(const char* path, uint64_t key, int n_models, const msim_tune_r
 bool apply(msim_handle h, const msim_tune_result& t) {
     for (int i = 0; i < h->n_models; ++i) {
         const int w = t.warps_per_env[i], e = t.envs_per_block[i];
-        const bool p = t.stage_points[i] != 0;
-        if ((w != 1 && w != 2 && w != 4) || e < 1 || e > max_epb(h, i, p, w)) return false;
+        const int p = t.stage_points[i];
+        if ((w != 1 && w != 2 && w != 4) || p < 0 || p > 2 || e < 1 || e > max_epb(h, i, p, w)) return false;
     }
     int pts[kMaxModels];
     for (int i = 0; i < kMaxModels; ++i) pts[i] = (t.mixed_stage_points_mask >> i) & 1;
@@ -240,7 +240,7 @@ bool apply(msim_handle h, const msim_tune_result& t) {
     for (int i = 0; i < h->n_models; ++i) {
         h->wpe[i] = t.warps_per_env[i];
         h->epb[i] = t.envs_per_block[i];
-        h->pts_smem[i] = t.stage_points[i] ? 1 : 0;
+        h->pts_smem[i] = t.stage_points[i];
     }
     h->mixed = t.mixed ? 1 : 0;
     h->mixed_wpe = t.mixed_warps_per_env;
@@ -263,7 +263,7 @@ msim_status msim_set_mixed_launch(msim_handle h, int32_t enable, int32_t warps_p
     const int w = warps_per_env == 0 ? 2 : warps_per_env;
     int pts[kMaxModels];
     for (int i = 0; i < kMaxModels; ++i)
-        pts[i] = stage_points_mask < 0 ? h->pts_smem[i] : ((stage_points_mask >> i) & 1);
+        pts[i] = stage_points_mask < 0 ? (h->pts_smem[i] == 1 ? 1 : 0) : ((stage_points_mask >> i) & 1);
     MixedArgs m;
     size_t sm;
     int grid;
@@ -325,7 +325,7 @@ msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_subst
         ++candidates;
         return best;
     };
-    const int epb_cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+    const int epb_cands[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16};
     // 1. per-model launches, each model on its own
     for (int i = 0; i < h->n_models && e == cudaSuccess; ++i) {
         const int ne = h->env_begin[i + 1] - h->env_begin[i];
@@ -335,8 +335,8 @@ msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_subst
         if (ne == 0) continue;
         float best = 1e30f;
         for (int w : {1, 2, 4}) {
-            for (int p = 0; p <= 1; ++p) {
-                const int emax = std::min(max_epb(h, i, p != 0, w), ne);
+            for (int p = 0; p <= 2; ++p) {
+                const int emax = std::min(max_epb(h, i, p, w), ne);
                 for (int ep : epb_cands) {
                     if (ep > emax || e != cudaSuccess) continue;
                     h->wpe[i] = w; h->epb[i] = ep; h->pts_smem[i] = p;
@@ -344,7 +344,7 @@ msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_subst
                     a.exc = h->exc_stage;
                     a.n_sub = n_substeps;
                     const int grid = model_grid(h, i);
-                    const size_t sm = step_smem_bytes(h->models[i].hdr, ep, p != 0, w);
+                    const size_t sm = step_smem_bytes(h->models[i].hdr, ep, p, w);
                     const float t = timed([&]() { return launch_step(a, grid, sm, s); });
                     if (t < best) {
                         best = t;
@@ -363,7 +363,7 @@ msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_subst
     int best_w = 0, best_sl = 0, best_mask = 0;
     int mask_best = 0, populated = 0;
     for (int i = 0; i < h->n_models; ++i) {
-        mask_best |= (r.stage_points[i] ? 1 : 0) << i;
+        mask_best |= (r.stage_points[i] == 1 ? 1 : 0) << i;
         populated += h->env_begin[i + 1] > h->env_begin[i];
     }
     for (int w : {1, 2, 4}) {

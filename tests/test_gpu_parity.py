@@ -167,15 +167,16 @@ def test_cuda_graph_replay_is_bitwise_equal_to_eager():
 
 
 def test_launch_shape_does_not_change_results():
-    """Warps per environment, environments per block and where the via points live change only
-    the speed: states after 20 substeps agree (bit-exact except the order of one float-float
+    """Warps per environment, environments per block and which image sections stay in global
+    memory (via points; also muscle records at staging level 2) change only the speed: states after 20 substeps agree (bit-exact except the order of one float-float
     dot product, so within 1e-6 relative)."""
     model = mg.config_model("c1_whole")
     E = 300
     q0, qd0, a0 = mg.initial_state(model, E, seed=6)
     exc = mg.smooth_excitations(model, E, 1, seed=6)[0]
     ref = None
-    for epb, pts, wpe in ((0, -1, 0), (0, 1, 1), (3, 0, 1), (0, 0, 2), (3, 1, 2), (0, 1, 4), (2, 0, 4)):
+    for epb, pts, wpe in ((0, -1, 0), (0, 1, 1), (3, 0, 1), (0, 0, 2), (3, 1, 2), (0, 1, 4), (2, 0, 4), (0, 2, 2),
+                          (5, 2, 1), (3, 2, 4)):
         sim = _sim(model, E)
         sim.set_launch(0, epb, pts, wpe)
         sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
