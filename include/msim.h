@@ -181,7 +181,9 @@ MSIM_API msim_status msim_set_launch(msim_handle h, int32_t model, int32_t envs_
  *
  * msim_set_mixed_launch -- enable (1) or disable (0).  warps_per_env 1, 2 or 4 (0: 2);
  * slots_per_block = environments per block (0: the largest <= 8 that fits); stage_points_mask bit
- * i = stage model i's via points in shared memory (-1: as in the per-model setting).
+ * i = stage model i's whole image in shared memory, else bit 8 + i = leave its muscle records as
+ * well as its via points in global memory (staging levels 1, 2, else 0 as in msim_set_launch;
+ * -1: as in the per-model setting).
  * MSIM_ERR_ARG if the shape does not fit (threads <= 512, shared memory). */
 MSIM_API msim_status msim_set_mixed_launch(msim_handle h, int32_t enable, int32_t warps_per_env,
                                            int32_t slots_per_block, int32_t stage_points_mask);

@@ -60,6 +60,17 @@ uint64_t tune_key(msim_handle h, int n_sub) {
 namespace msim {
 namespace host {
 
+// Staging levels of a mixed launch from a mask: bit i = model i fully staged (level 1); else
+// bit 8 + i = its muscle records also read through the cache (level 2); else level 0.
+void mask_levels(int32_t mask, int* lv) {
+    for (int i = 0; i < kMaxModels; ++i) lv[i] = ((mask >> i) & 1) ? 1 : (((mask >> (8 + i)) & 1) ? 2 : 0);
+}
+int32_t levels_mask(const int* lv, int n) {
+    int32_t m = 0;
+    for (int i = 0; i < n; ++i) m |= lv[i] == 1 ? (1 << i) : (lv[i] == 2 ? (1 << (8 + i)) : 0);
+    return m;
+}
+
 bool mixed_args(msim_handle h, int wpe, int slots, const int* pts, MixedArgs* out, size_t* smem, int* grid) {
     if (wpe != 1 && wpe != 2 && wpe != 4) return false;
     if (slots < 1 || slots > slots_limit(wpe)) return false;
@@ -74,7 +85,7 @@ bool mixed_args(msim_handle h, int wpe, int slots, const int* pts, MixedArgs* ou
     size_t region = 0;
     for (int k = 0; k < no; ++k) {
         const ImgHeader& hd = h->models[order[k]].hdr;
-        const size_t staged = (size_t)staged_bytes(hd, pts[order[k]] ? 1 : 0);
+        const size_t staged = (size_t)staged_bytes(hd, pts[order[k]]);
         region = std::max(region, (staged + 127) & ~(size_t)127);
     }
     if (16 + region >= h->smem_optin) return false;
@@ -90,7 +101,7 @@ bool mixed_args(msim_handle h, int wpe, int slots, const int* pts, MixedArgs* ou
         if (epb < 1) return false;
         MixedModel& M = m.mdl[k];
         M.img = h->d_img[i];
-        M.stage = pts[i] ? 1 : 0;
+        M.stage = pts[i];
         M.staged_bytes = staged_bytes(hd, M.stage);
         M.env_begin = h->env_begin[i];
         M.env_end = h->env_begin[i + 1];
@@ -230,7 +241,7 @@ bool apply(msim_handle h, const msim_tune_result& t) {
         if ((w != 1 && w != 2 && w != 4) || p < 0 || p > 2 || e < 1 || e > max_epb(h, i, p, w)) return false;
     }
     int pts[kMaxModels];
-    for (int i = 0; i < kMaxModels; ++i) pts[i] = (t.mixed_stage_points_mask >> i) & 1;
+    mask_levels(t.mixed_stage_points_mask, pts);
     if (t.mixed) {
         MixedArgs m;
         size_t sm;
@@ -262,8 +273,11 @@ msim_status msim_set_mixed_launch(msim_handle h, int32_t enable, int32_t warps_p
     }
     const int w = warps_per_env == 0 ? 2 : warps_per_env;
     int pts[kMaxModels];
-    for (int i = 0; i < kMaxModels; ++i)
-        pts[i] = stage_points_mask < 0 ? (h->pts_smem[i] == 1 ? 1 : 0) : ((stage_points_mask >> i) & 1);
+    if (stage_points_mask < 0) {
+        for (int i = 0; i < kMaxModels; ++i) pts[i] = h->pts_smem[i];
+    } else {
+        mask_levels(stage_points_mask, pts);
+    }
     MixedArgs m;
     size_t sm;
     int grid;
@@ -362,17 +376,19 @@ msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_subst
     float best_mixed = 1e30f;
     int best_w = 0, best_sl = 0, best_mask = 0;
     int mask_best = 0, populated = 0;
-    for (int i = 0; i < h->n_models; ++i) {
-        mask_best |= (r.stage_points[i] == 1 ? 1 : 0) << i;
-        populated += h->env_begin[i + 1] > h->env_begin[i];
-    }
+    for (int i = 0; i < h->n_models; ++i) populated += h->env_begin[i + 1] > h->env_begin[i];
+    mask_best = levels_mask(r.stage_points, h->n_models);
+    const int32_t all_cached = levels_mask(std::vector<int>(h->n_models, 2).data(), h->n_models);
     for (int w : {1, 2, 4}) {
         if (populated < 2) break;
         for (int sl = 1; sl <= slots_limit(w); ++sl) {
-            for (int mask : {mask_best, 0}) {
+            const int32_t masks[3] = {mask_best, 0, all_cached};
+            for (int mi = 0; mi < 3; ++mi) {
+                const int32_t mask = masks[mi];
                 if (e != cudaSuccess) break;
+                if ((mi == 1 && mask == mask_best) || (mi == 2 && (mask == mask_best || mask == 0))) continue;
                 int pts[kMaxModels];
-                for (int i = 0; i < kMaxModels; ++i) pts[i] = (mask >> i) & 1;
+                mask_levels(mask, pts);
                 MixedArgs m;
                 size_t sm;
                 int grid;
@@ -384,7 +400,6 @@ msim_status msim_autotune(msim_handle h, const char* cache_path, int32_t n_subst
                     best_mixed = t;
                     best_w = w; best_sl = sl; best_mask = mask;
                 }
-                if (mask_best == 0) break;   // both masks are the same
             }
         }
     }
