@@ -52,15 +52,16 @@ typedef struct {
     double contact_k, contact_c, contact_mu, contact_eps;
     double limit_k, limit_c, tau_act, tau_deact, vmax_per_lopt;
     int implicit_damping;
-    /* wrapping cylinders: at most one per muscle, on the segment that ends at the muscle's
-     * point number wrap_segment (1 .. points - 1), fixed to body wrap_body */
+    /* wrapping surfaces (cylinders or spheres): at most one per muscle, on the segment that ends
+     * at the muscle's point number wrap_segment (1 .. points - 1), fixed to body wrap_body */
     int nw;
     const int *wrap_muscle, *wrap_segment, *wrap_body;
     const double *wrap_center, *wrap_axis, *wrap_radius;
     int free_root;   /* 1: body 0 has the six free DoFs 0-5 described above */
+    const int* wrap_kind;   /* per wrap: 0 cylinder, 1 sphere (wrap_axis unused); NULL: cylinders */
 } ora_model;
 
-int ora_abi_version(void) { return 5; }
+int ora_abi_version(void) { return 6; }
 
 /* DoF kinds: a translation of the free root (its point Jacobian is the axis itself), else a
  * rotation about the axis s_d through o_d (point Jacobian s_d x (x - o_d)). */
@@ -232,6 +233,27 @@ double ora_wrap_cylinder(const double P[3], const double S[3], const double c[3]
     return sqrt(lplane * lplane + dz * dz);
 }
 
+/* Shortest path from P to S over a sphere (centre c, radius r): the great-circle route in the
+ * plane through P, S and c, i.e. the cylinder case with the axis normal to that plane (both
+ * points then have the same axial coordinate).  When P, c and S are collinear every plane
+ * through them is shortest; the one normal to a fixed vector perpendicular to S - P is taken. */
+double ora_wrap_sphere(const double P[3], const double S[3], const double c[3], double r, int* active, double Q[3],
+                       double T[3]) {
+    double p[3] = {P[0] - c[0], P[1] - c[1], P[2] - c[2]}, q[3] = {S[0] - c[0], S[1] - c[1], S[2] - c[2]}, n[3];
+    cross3(p, q, n);
+    double nn = sqrt(dot3(n, n));
+    if (!(nn > 1e-12 * sqrt(dot3(p, p) * dot3(q, q)))) {
+        double d[3] = {S[0] - P[0], S[1] - P[1], S[2] - P[2]};
+        const double ref[3] = {fabs(d[0]) <= fabs(d[1]) && fabs(d[0]) <= fabs(d[2]) ? 1.0 : 0.0,
+                               fabs(d[0]) > fabs(d[1]) && fabs(d[1]) <= fabs(d[2]) ? 1.0 : 0.0,
+                               fabs(d[2]) < fabs(d[0]) && fabs(d[2]) < fabs(d[1]) ? 1.0 : 0.0};
+        cross3(d, ref, n);
+        nn = sqrt(dot3(n, n));
+    }
+    n[0] /= nn; n[1] /= nn; n[2] /= nn;
+    return ora_wrap_cylinder(P, S, c, n, r, active, Q, T);
+}
+
 void ora_muscle_geometry(const ora_model* M, const double* Rb, const double* pb, const double* s,
                          const double* o, double* L, double* R) {
     for (int k = 0; k < M->m; ++k) {
@@ -259,10 +281,15 @@ void ora_muscle_geometry(const ora_model* M, const double* Rb, const double* pb,
                 double cw[3], aw[3], Q[3], T[3];
                 matvec3(Rb + 9 * bw, M->wrap_center + 3 * w, cw);
                 cw[0] += pb[3 * bw]; cw[1] += pb[3 * bw + 1]; cw[2] += pb[3 * bw + 2];
-                matvec3(Rb + 9 * bw, M->wrap_axis + 3 * w, aw);
-                double an = sqrt(dot3(aw, aw));
-                aw[0] /= an; aw[1] /= an; aw[2] /= an;
-                double lw = ora_wrap_cylinder(xprev, x, cw, aw, M->wrap_radius[w], &wrapped, Q, T);
+                double lw;
+                if (M->wrap_kind && M->wrap_kind[w] == 1) {
+                    lw = ora_wrap_sphere(xprev, x, cw, M->wrap_radius[w], &wrapped, Q, T);
+                } else {
+                    matvec3(Rb + 9 * bw, M->wrap_axis + 3 * w, aw);
+                    double an = sqrt(dot3(aw, aw));
+                    aw[0] /= an; aw[1] /= an; aw[2] /= an;
+                    lw = ora_wrap_cylinder(xprev, x, cw, aw, M->wrap_radius[w], &wrapped, Q, T);
+                }
                 if (wrapped) {
                     len += lw;
                     if (row) {

@@ -41,7 +41,7 @@ class _OraModel(C.Structure):
                 ("implicit_damping", C.c_int),
                 ("nw", C.c_int), ("wrap_muscle", _ip), ("wrap_segment", _ip), ("wrap_body", _ip),
                 ("wrap_center", _dp), ("wrap_axis", _dp), ("wrap_radius", _dp),
-                ("free_root", C.c_int)]
+                ("free_root", C.c_int), ("wrap_kind", _ip)]
 
 
 class _EvalOut(C.Structure):
@@ -64,7 +64,7 @@ def lib():
         build()
         _lib = C.CDLL(_LIB)
         _lib.ora_abi_version.restype = C.c_int
-        if _lib.ora_abi_version() != 5:
+        if _lib.ora_abi_version() != 6:
             raise RuntimeError("stale oracle library: rebuild with oracle.build(force=True)")
         for name in ("ora_fl", "ora_fp", "ora_fv", "ora_dfv"):
             getattr(_lib, name).restype = C.c_double
@@ -75,7 +75,14 @@ def lib():
         _lib.ora_cholesky_solve.restype = C.c_int
         _lib.ora_max_threads.restype = C.c_int
         _lib.ora_wrap_cylinder.restype = C.c_double
+        _lib.ora_wrap_sphere.restype = C.c_double
     return _lib
+
+
+def _wrap_kinds(model, nw):
+    """Per-wrap surface kind (0 cylinder, 1 sphere); a model without the field has cylinders."""
+    k = np.asarray(getattr(model, "wrap_kind", np.zeros(0)), dtype=np.int32).reshape(-1)
+    return k if (nw and k.shape[0] == nw) else np.zeros(max(nw, 1), np.int32)
 
 
 def _ptr(a, t=_dp):
@@ -106,7 +113,8 @@ class OracleModel:
             wrap_body=i(model.wrap_body if nw else np.zeros(1)),
             wrap_center=f(model.wrap_center if nw else np.zeros((1, 3))),
             wrap_axis=f(model.wrap_axis if nw else np.zeros((1, 3))),
-            wrap_radius=f(model.wrap_radius if nw else np.zeros(1)))
+            wrap_radius=f(model.wrap_radius if nw else np.zeros(1)),
+            wrap_kind=i(_wrap_kinds(model, nw)))
         s = _OraModel()
         s.nb, s.n, s.m, s.np, s.ns = model.n_bodies, model.n_dofs, model.n_muscles, model.n_points, model.n_spheres
         for k, v in self._keep.items():
@@ -168,6 +176,15 @@ def wrap_cylinder(P, S, c, a, r):
     Q, T = np.zeros(3), np.zeros(3)
     act = C.c_int(0)
     L = lib().ora_wrap_cylinder(_ptr(P), _ptr(S), _ptr(c), _ptr(a), C.c_double(r), C.byref(act), _ptr(Q), _ptr(T))
+    return L, bool(act.value), Q, T
+
+
+def wrap_sphere(P, S, c, r):
+    """Shortest path P -> S over a sphere (centre c, radius r): (length, wraps, Q, T)."""
+    P, S, c = (np.ascontiguousarray(v, dtype=np.float64) for v in (P, S, c))
+    Q, T = np.zeros(3), np.zeros(3)
+    act = C.c_int(0)
+    L = lib().ora_wrap_sphere(_ptr(P), _ptr(S), _ptr(c), C.c_double(r), C.byref(act), _ptr(Q), _ptr(T))
     return L, bool(act.value), Q, T
 
 

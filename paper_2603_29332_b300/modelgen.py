@@ -89,6 +89,7 @@ class Model:
     wrap_center: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))   # body frame
     wrap_axis: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))     # unit, body frame
     wrap_radius: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float32))
+    wrap_kind: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))   # 0 cylinder, 1 sphere
 
     def __post_init__(self):
         # scalar parameters are FP32 values too, like every array
@@ -96,8 +97,10 @@ class Model:
                   "tau_deact", "vmax_per_lopt"):
             setattr(self, k, float(np.float32(getattr(self, k))))
         self.gravity = _f32(self.gravity)
-        for k in ("wrap_muscle", "wrap_segment", "wrap_body"):
+        for k in ("wrap_muscle", "wrap_segment", "wrap_body", "wrap_kind"):
             setattr(self, k, np.asarray(getattr(self, k), dtype=np.int32).reshape(-1))
+        if self.wrap_kind.shape[0] == 0 and self.wrap_muscle.shape[0] > 0:
+            self.wrap_kind = np.zeros(self.wrap_muscle.shape[0], np.int32)   # cylinders
         self.wrap_center = _f32(np.asarray(self.wrap_center, dtype=np.float64).reshape(-1, 3))
         self.wrap_axis = _f32(np.asarray(self.wrap_axis, dtype=np.float64).reshape(-1, 3))
         self.wrap_radius = _f32(np.asarray(self.wrap_radius, dtype=np.float64).reshape(-1))
@@ -145,7 +148,8 @@ class Model:
         assert np.all(np.diff(self.muscle_point_start) >= 2)
         W = self.wrap_muscle.shape[0]
         assert all(a.shape[0] == W for a in (self.wrap_segment, self.wrap_body, self.wrap_center, self.wrap_axis,
-                                            self.wrap_radius))
+                                            self.wrap_radius, self.wrap_kind))
+        assert np.all((self.wrap_kind == 0) | (self.wrap_kind == 1))
         assert len(set(self.wrap_muscle.tolist())) == W          # at most one cylinder per muscle
         if W:
             npts = np.diff(self.muscle_point_start)[self.wrap_muscle]
@@ -211,7 +215,8 @@ def make_model(name, body_parent, body_ndof, body_offset, body_mass, body_com, b
 
     ``muscle_points`` is a list (one entry per muscle) of lists of (body, (x, y, z)).
     ``spheres`` is a list of (body, (x, y, z), radius).
-    ``wraps`` is a list of (muscle, segment end point index, body, centre, axis, radius).
+    ``wraps`` is a list of (muscle, segment end point index, body, centre, axis, radius[, kind]):
+    kind 0 = cylinder (default), 1 = sphere (the axis is then unused).
     """
     body_parent = np.asarray(body_parent, dtype=np.int32)
     body_ndof = np.asarray(body_ndof, dtype=np.int32)
@@ -253,7 +258,7 @@ def make_model(name, body_parent, body_ndof, body_offset, body_mass, body_com, b
         sphere_body=sb, sphere_pos=_f32(sp), sphere_radius=_f32(sr),
         wrap_muscle=[w[0] for w in wraps], wrap_segment=[w[1] for w in wraps], wrap_body=[w[2] for w in wraps],
         wrap_center=[w[3] for w in wraps], wrap_axis=[_unit(np.asarray(w[4], dtype=np.float64)) for w in wraps],
-        wrap_radius=[w[5] for w in wraps],
+        wrap_radius=[w[5] for w in wraps], wrap_kind=[w[6] if len(w) > 6 else 0 for w in wraps],
     )
     for k, v in scalars.items():
         if k == "gravity":
@@ -298,6 +303,9 @@ CONFIGS = {
     # the whole body with a quarter of its muscles wrapping a cylinder at a joint
     "c1_wrap": dict(n_bodies=60, n_dofs=90, n_muscles=700, max_points=6, max_span=3, limits=True,
                     contact=True, seed=1, wrap_frac=0.25),
+    # the wrapped body with half of its surfaces spheres instead of cylinders
+    "c1_wrap_mix": dict(n_bodies=60, n_dofs=90, n_muscles=700, max_points=6, max_span=3, limits=True,
+                        contact=True, seed=1, wrap_frac=0.25, sphere_frac=0.5),
     # the whole body on a free (floating) root instead of its root hinges
     "c1_float": dict(n_bodies=60, n_dofs=90, n_muscles=700, max_points=6, max_span=3, limits=True,
                      contact=True, seed=1, free_root=True),
@@ -306,7 +314,7 @@ CONFIGS = {
 
 def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, limits, contact, seed,
              n_legs=2, spheres_per_foot=4, sphere_radius=0.03, max_dof_per_body=3, wrap_frac=0.0,
-             free_root=False):
+             sphere_frac=0.0, free_root=False):
     """Draw one synthetic skeleton + muscle model.
 
     Tree: a root body, then limb chains of U{3..8} bodies each, the parent of each chain drawn
@@ -481,8 +489,13 @@ def generate(name=None, *, n_bodies, n_dofs, n_muscles, max_points, max_span, li
                 dist = [np.linalg.norm((X - origin0[bs]) - ((X - origin0[bs]) @ a) * a) for X in (P, S)]
                 r = min(0.7 * min(dist), 0.05)
                 if r >= 0.005:
-                    wraps.append((int(k), j, int(bs), (0.0, 0.0, 0.0), a, r))
+                    wraps.append((int(k), j, int(bs), (0.0, 0.0, 0.0), a, r, 0))
                 break
+        # a fraction of the surfaces become spheres centred at the joint, same radius (own
+        # stream, so the cylinders' parameters do not depend on sphere_frac)
+        sr = np.random.default_rng(seed + 6000)
+        kinds = (sr.uniform(size=len(wraps)) < sphere_frac).astype(int)
+        wraps = [w[:6] + (int(kd),) for w, kd in zip(wraps, kinds)]
     mdl = make_model(name or "synthetic", parent, ndof, offset, mass, com, inertia, axes,
                      muscle_points, fmax, lopt, lslack, dof_limit=lim, spheres=spheres, wraps=wraps)
     return with_free_root(mdl, name) if free_root else mdl

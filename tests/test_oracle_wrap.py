@@ -96,3 +96,86 @@ def test_wrapped_moment_arms_match_central_differences():
             # are rigid only to that level and L moves by ~1e-8 m/rad with DoFs no muscle crosses
             np.testing.assert_allclose(R[:, d], fd, rtol=0, atol=5e-8)
     assert hit > 0
+
+
+# ---------------------------------------------------------------- spheres
+def _plane_pts(rng, rho_p, rho_s, psi):
+    """P, S at distances rho_p, rho_s from the origin, psi apart, in a random plane."""
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    v = rng.normal(size=3)
+    v -= u * (u @ v)
+    v /= np.linalg.norm(v)
+    return rho_p * u, rho_s * (np.cos(psi) * u + np.sin(psi) * v), u, v
+
+
+@pytest.mark.parametrize("rho,psi,r", [(0.1, 2.8, 0.03), (0.08, 1.9, 0.05), (0.2, 3.0, 0.03)])
+def test_sphere_wrapped_length_closed_form_in_any_plane(rho, psi, r):
+    rng = np.random.default_rng(int(rho * 1000))
+    for _ in range(3):
+        P, S, u, v = _plane_pts(rng, rho, rho, psi)
+        c = rng.normal(size=3) * 0.5
+        L, wraps, Q, T = ora.wrap_sphere(P + c, S + c, c, r)
+        assert wraps
+        want = 2 * np.sqrt(rho ** 2 - r ** 2) + r * (psi - 2 * np.arccos(r / rho))
+        np.testing.assert_allclose(L, want, rtol=1e-12)
+        n = np.cross(u, v)
+        for X in (Q, T):      # tangent points on the sphere, in the plane of P, S and the centre
+            np.testing.assert_allclose(np.linalg.norm(X - c), r, rtol=1e-12)
+            assert abs((X - c) @ n) < 1e-13
+        L2, _, _, _ = ora.wrap_sphere(S + c, P + c, c, r)
+        np.testing.assert_allclose(L2, L, rtol=1e-13)
+
+
+def test_sphere_wrapped_length_against_brute_force_unequal_radii():
+    # minimise |P - X(a)| + r |b - a| + |X(b) - S| over the two contact angles on the great
+    # circle by brute force (the minimiser is tangent); P and S at different distances
+    rng = np.random.default_rng(7)
+    r = 0.04
+    for rho_p, rho_s, psi in ((0.09, 0.15, 2.6), (0.2, 0.06, 2.9), (0.07, 0.07, 3.1)):
+        P, S, u, v = _plane_pts(rng, rho_p, rho_s, psi)
+        L, wraps, _, _ = ora.wrap_sphere(P, S, np.zeros(3), r)
+        assert wraps
+        a = np.linspace(0.0, psi, 2001)
+        X = r * (np.cos(a)[:, None] * u + np.sin(a)[:, None] * v)
+        dP = np.linalg.norm(X - P, axis=1)
+        dS = np.linalg.norm(X - S, axis=1)
+        # contact from angle a_i to a_j >= a_i; a straight piece from P to X stays outside the
+        # ball when P lies on the outer side of the tangent plane at X: (P - X) . X >= 0
+        okP = ((P - X) * X).sum(1) >= 0
+        okS = ((S - X) * X).sum(1) >= 0
+        cost = dP[:, None] + r * (a[None, :] - a[:, None]) + dS[None, :]
+        valid = okP[:, None] & okS[None, :] & (a[None, :] >= a[:, None])
+        best = np.min(np.where(valid, cost, np.inf))
+        np.testing.assert_allclose(L, best, rtol=2e-6)
+
+
+def test_sphere_straight_when_the_chord_misses_or_a_point_is_inside():
+    rng = np.random.default_rng(3)
+    r = 0.03
+    P, S, _, _ = _plane_pts(rng, 0.1, 0.1, 0.9 * 2 * np.arccos(r / 0.1))
+    L, wraps, _, _ = ora.wrap_sphere(P, S, np.zeros(3), r)
+    assert not wraps and L == pytest.approx(np.linalg.norm(S - P), rel=1e-15)
+    P, S, _, _ = _plane_pts(rng, 0.02, 0.1, 2.5)
+    L, wraps, _, _ = ora.wrap_sphere(P, S, np.zeros(3), r)
+    assert not wraps and L == pytest.approx(np.linalg.norm(S - P), rel=1e-15)
+
+
+def test_sphere_wrapped_moment_arms_match_central_differences():
+    m = mg.config_model("c1_wrap_mix")
+    assert 0 < int(m.wrap_kind.sum()) < m.wrap_kind.shape[0]
+    rng = np.random.default_rng(8)
+    h = 1e-6
+    hit = 0
+    spheres = m.wrap_muscle[m.wrap_kind == 1]
+    for _ in range(3):
+        q = rng.uniform(-0.4, 0.4, m.n_dofs)
+        L, R = ora.muscle_geometry(m, q)
+        for d in rng.choice(m.n_dofs, 12, replace=False):
+            e = np.zeros(m.n_dofs)
+            e[d] = h
+            Lp, _ = ora.muscle_geometry(m, q + e)
+            Lm, _ = ora.muscle_geometry(m, q - e)
+            hit += int(np.count_nonzero(R[spheres, d]))
+            np.testing.assert_allclose(R[:, d], -(Lp - Lm) / (2 * h), rtol=0, atol=5e-8)
+    assert hit > 0
