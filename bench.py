@@ -195,7 +195,8 @@ def run_reference(args, rank):
 
 
 def _config(args):
-    wrap = ", 188 of them wrapping a cylinder" if args.model == "c1_wrap" else ""
+    wrap = {"c1_wrap": ", 188 of them wrapping a cylinder",
+            "c1_wrap_mix": ", 188 of them wrapping a cylinder (92) or a sphere (96)"}.get(args.model, "")
     dofs = "a free root (6 DoF) and 89 hinge DoF" if args.model == "c1_float" else "90 hinge DoF"
     return {"workload": "whole-body synthetic model (60 bodies, %s, 700 Hill muscles%s, 8 contact "
                         "spheres), %d envs, %d substeps x dt %.0e s per step, smooth excitations, exact geometry"
@@ -596,7 +597,7 @@ def main():
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
     ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
-    ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_float"],
+    ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_wrap_mix", "c1_float"],
                     help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; c1_float: a free root)")
     ap.add_argument("--policy-envs", type=int, default=16384)
     ap.add_argument("--policy-steps", type=int, default=2000)

@@ -59,9 +59,9 @@ typedef struct {
     float limit_k, limit_c;            /* joint-limit stiffness N m/rad, damping N m s/rad */
     float tau_act, tau_deact;          /* activation / deactivation time constants (Eq. 2) */
     float vmax_per_lopt;               /* maximum contraction velocity in l_opt per second */
-    /* wrapping cylinders (may be 0 / NULL): the segment of muscle wrap_muscle[w] that ends at
+    /* wrapping surfaces (may be 0 / NULL): the segment of muscle wrap_muscle[w] that ends at
      * its point number wrap_segment[w] (1 .. points - 1) takes the shortest way around an
-     * infinite cylinder fixed to body wrap_body[w] (on the muscle's chain between that segment's
+     * infinite cylinder (or a sphere, wrap_kind below) fixed to body wrap_body[w] (on the muscle's chain between that segment's
      * two bodies), centre and axis in that body's frame; at most one cylinder per muscle */
     int32_t n_wraps;
     const int32_t* wrap_muscle;        /* [n_wraps] */
@@ -78,6 +78,10 @@ typedef struct {
      * the rotation vector of its orientation, rad, advanced by R <- exp(dt w) R each substep and
      * kept at angle <= pi).  The paper's skeleton has such a root ("Observation space"). */
     int32_t free_root;
+    /* kind of each wrapping surface: 0 = cylinder, 1 = sphere (centre wrap_center, radius
+     * wrap_radius; wrap_axis unused): the wrapped segment follows the great circle in the plane
+     * through its two points and the centre.  NULL = all cylinders. */
+    const int32_t* wrap_kind;          /* [n_wraps] or NULL */
 } msim_model_desc;
 
 #ifdef __cplusplus

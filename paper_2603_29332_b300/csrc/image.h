@@ -63,12 +63,13 @@ struct alignas(16) PointRec {   // 16 B
     int32_t body_cross;         // body | (crossed DoFs at or above this point's body) << 8
 };
 
-struct alignas(16) WrapRec {    // 32 B, a muscle's wrapping cylinder (MuscleRec::wrap = index + 1)
+struct alignas(16) WrapRec {    // 32 B, a muscle's wrapping surface (MuscleRec::wrap = index + 1)
     float center[3];            // body frame
     float radius;
-    float axis[3];              // unit, body frame
+    float axis[3];              // unit, body frame (cylinders; zero for spheres)
     int32_t body_cross;         // body | (crossed DoFs at or above this body) << 8, as PointRec,
                                 // | (number of the muscle point that ends the wrapped segment) << 16
+                                // | kind << 24 (0 cylinder, 1 sphere)
 };
 
 struct alignas(16) SphereRec {  // 32 B

@@ -186,12 +186,17 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     for (int w = 0; w < nw; ++w) {
         const int k = d.wrap_muscle[w];
         if (k < 0 || k >= m) FAIL("wrap %d: muscle out of range", w);
-        if (wrap_of[k] >= 0) FAIL("muscle %d has two wrapping cylinders", k);
+        if (wrap_of[k] >= 0) FAIL("muscle %d has two wrapping surfaces", k);
         wrap_of[k] = w;
-        if (!(d.wrap_radius[w] > 0.f) || !finite_all(d.wrap_center + 3 * w, 3) || !finite_all(d.wrap_axis + 3 * w, 3))
-            FAIL("wrap %d: radius must be > 0 and centre / axis finite", w);
-        const float* ax = d.wrap_axis + 3 * w;
-        if (!(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2] > 1e-12f)) FAIL("wrap %d: zero axis", w);
+        const int kind = d.wrap_kind ? d.wrap_kind[w] : 0;
+        if (kind != 0 && kind != 1) FAIL("wrap %d: kind must be 0 (cylinder) or 1 (sphere)", w);
+        if (!(d.wrap_radius[w] > 0.f) || !finite_all(d.wrap_center + 3 * w, 3))
+            FAIL("wrap %d: radius must be > 0 and centre finite", w);
+        if (kind == 0) {
+            const float* ax = d.wrap_axis + 3 * w;
+            if (!finite_all(ax, 3) || !(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2] > 1e-12f))
+                FAIL("wrap %d: cylinder axis must be finite and non-zero", w);
+        }
     }
     std::vector<WrapRec> wraps(nw);
     std::vector<uint32_t> cross;
@@ -246,14 +251,15 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             if (tw < pos_of(d.point_body[j0 + seg - 1]) || tw > pos_of(d.point_body[j0 + seg]))
                 FAIL("wrap %d: body must lie on the chain between the wrapped segment's bodies", w);
             WrapRec& W = wraps[w];
+            const int kind = d.wrap_kind ? d.wrap_kind[w] : 0;
             const float* ax = d.wrap_axis + 3 * w;
-            const float an = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
+            const float an = kind ? 1.f : std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
             for (int c = 0; c < 3; ++c) {
                 W.center[c] = d.wrap_center[3 * w + c];
-                W.axis[c] = ax[c] / an;
+                W.axis[c] = kind ? 0.f : ax[c] / an;
             }
             W.radius = d.wrap_radius[w];
-            W.body_cross = bw | (ccount[tw] << 8) | (seg << 16);
+            W.body_cross = bw | (ccount[tw] << 8) | (seg << 16) | (kind << 24);
             M.wrap = (uint8_t)(w + 1);
         }
         M.fmax = d.muscle_fmax[k];

@@ -689,7 +689,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                     ldot -= Rv * qd[d];
                 }
             };
-            const int wseg = (has_wrap(MODE) && M.wrap) ? (T.wrap[M.wrap - 1].body_cross >> 16) : 0;
+            const int wseg = (has_wrap(MODE) && M.wrap) ? ((T.wrap[M.wrap - 1].body_cross >> 16) & 0xff) : 0;
             for (int j = 1; j < M.np; ++j) {
                 P = T.pt[M.p0 + j];
                 b = P.body_cross & 0xff;
@@ -706,7 +706,26 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                     float cw[3], aw[3], Q[3], Tp[3], u1[3], u2[3], lw;
                     rot3(fw, W.center, cw);
                     cw[0] += fw[9]; cw[1] += fw[10]; cw[2] += fw[11];
-                    rot3(fw, W.axis, aw);
+                    if (W.body_cross >> 24) {
+                        // sphere: the cylinder case about the normal of the plane through the
+                        // two points and the centre (a perpendicular to x1 - x0 if collinear)
+                        const float pp[3] = {x0[0] - cw[0], x0[1] - cw[1], x0[2] - cw[2]};
+                        const float qq[3] = {x1[0] - cw[0], x1[1] - cw[1], x1[2] - cw[2]};
+                        cross3(pp, qq, aw);
+                        float nn = dot3(aw, aw);
+                        if (!(nn > 1e-12f * dot3(pp, pp) * dot3(qq, qq))) {
+                            const float dd[3] = {x1[0] - x0[0], x1[1] - x0[1], x1[2] - x0[2]};
+                            const float a0 = fabsf(dd[0]), a1 = fabsf(dd[1]), a2 = fabsf(dd[2]);
+                            const float ref[3] = {a0 <= a1 && a0 <= a2 ? 1.f : 0.f, a0 > a1 && a1 <= a2 ? 1.f : 0.f,
+                                                  a2 < a0 && a2 < a1 ? 1.f : 0.f};
+                            cross3(dd, ref, aw);
+                            nn = dot3(aw, aw);
+                        }
+                        const float in = rsqrtf(nn);
+                        aw[0] *= in; aw[1] *= in; aw[2] *= in;
+                    } else {
+                        rot3(fw, W.axis, aw);
+                    }
                     wrapped = wrap_path(x0, x1, cw, aw, W.radius, lw, Q, Tp, u1, u2);
                     if (wrapped) {
                         L += lw;
@@ -1346,8 +1365,12 @@ __global__ void __launch_bounds__(512, 1) k_step_mixed(MixedArgs ma) {
             const int e = M.env_begin + (item - M.item_begin) * M.epb + slot;
             // a model without cylinders takes the variant without them, as in its own launch
             if (e < M.env_end) {
-                if (MODE == kModeStepW && T.H->n_wraps == 0) run_env<kModeStep, WPE>(ma.a, T, ws, g, e);
-                else run_env<MODE, WPE>(ma.a, T, ws, g, e);
+                if constexpr (MODE == kModeStepW) {
+                    if (T.H->n_wraps == 0) run_env<kModeStep, WPE>(ma.a, T, ws, g, e);
+                    else run_env<kModeStepW, WPE>(ma.a, T, ws, g, e);
+                } else {
+                    run_env<MODE, WPE>(ma.a, T, ws, g, e);
+                }
             }
         }
     }

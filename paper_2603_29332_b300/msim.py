@@ -38,7 +38,8 @@ class ModelDesc(C.Structure):
                 ("limit_c", C.c_float), ("tau_act", C.c_float), ("tau_deact", C.c_float),
                 ("vmax_per_lopt", C.c_float),
                 ("n_wraps", C.c_int32), ("wrap_muscle", _i32p), ("wrap_segment", _i32p), ("wrap_body", _i32p),
-                ("wrap_center", _f32p), ("wrap_axis", _f32p), ("wrap_radius", _f32p), ("free_root", C.c_int32)]
+                ("wrap_center", _f32p), ("wrap_axis", _f32p), ("wrap_radius", _f32p), ("free_root", C.c_int32),
+                ("wrap_kind", _i32p)]
 
 
 class CreateArgs(C.Structure):
@@ -198,7 +199,8 @@ def model_desc(model):
                 point_body=i(model.point_body), point_pos=f(model.point_pos), sphere_body=i(model.sphere_body),
                 sphere_pos=f(model.sphere_pos), sphere_radius=f(model.sphere_radius),
                 wrap_muscle=i(model.wrap_muscle), wrap_segment=i(model.wrap_segment), wrap_body=i(model.wrap_body),
-                wrap_center=f(model.wrap_center), wrap_axis=f(model.wrap_axis), wrap_radius=f(model.wrap_radius))
+                wrap_center=f(model.wrap_center), wrap_axis=f(model.wrap_axis), wrap_radius=f(model.wrap_radius),
+                wrap_kind=i(getattr(model, "wrap_kind", np.zeros(0))))
     d = ModelDesc()
     d.n_bodies, d.n_dofs, d.n_muscles = model.n_bodies, model.n_dofs, model.n_muscles
     d.n_points, d.n_spheres = model.n_points, model.n_spheres

@@ -1,11 +1,14 @@
-"""Muscle paths wrapping a cylinder, on the device, against the FP64 oracle (through the C ABI).
+"""Muscle paths wrapping a cylinder or a sphere, on the device, against the FP64 oracle (through
+the C ABI).
 
 The wrapped segment takes the shortest way around an infinite cylinder fixed to a body of the
 muscle's chain (tangent - arc - tangent in the plane normal to the axis, straight along the axis
-once unrolled).  Checks: lengths and moment arms of the whole-body model with a quarter of its
-muscles wrapping (with a count of the wraps that are active in the sample, so that the branch is
-exercised), the closed-form moment arm of a cylinder coaxial with a hinge, the accelerations and
-a 100-substep trajectory, the mixed launch, and the host's rejection of invalid wraps.
+once unrolled), or over a sphere (the great circle in the plane of the two points and the
+centre).  Checks: lengths and moment arms of the whole-body model with a quarter of its muscles
+wrapping, all cylinders or half spheres (with a count of the wraps that are active in the
+sample, so that the branches are exercised), the closed-form moment arm of a cylinder coaxial
+with a hinge, the accelerations and 100-substep trajectories, the mixed launch, and the host's
+rejection of invalid wraps.
 """
 import copy
 
@@ -32,11 +35,13 @@ def _unwrapped(model):
     m.wrap_center = np.zeros((0, 3), np.float32)
     m.wrap_axis = np.zeros((0, 3), np.float32)
     m.wrap_radius = np.zeros(0, np.float32)
+    m.wrap_kind = np.zeros(0, np.int32)
     return m
 
 
-def test_wrapped_geometry_and_accelerations_match_the_oracle():
-    model = mg.config_model("c1_wrap")
+@pytest.mark.parametrize("name", ["c1_wrap", "c1_wrap_mix"])
+def test_wrapped_geometry_and_accelerations_match_the_oracle(name):
+    model = mg.config_model(name)
     plain = _unwrapped(model)
     om = ora.OracleModel(model)
     E, n, m = 2048, model.n_dofs, model.n_muscles
@@ -45,12 +50,14 @@ def test_wrapped_geometry_and_accelerations_match_the_oracle():
     q, qd, act, exc = random_states(model, E, seed=21)
     res = sim.eval(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act), sim.pad_m(exc))
     g = {k: v.double().cpu().numpy() for k, v in res.items()}
-    active, worst_L, worst_R, worst_qdd = 0, 0.0, 0.0, 0.0
+    active, active_sph, worst_L, worst_R, worst_qdd = 0, 0, 0.0, 0.0, 0.0
     for e in sample_envs(E, 32, seed=3):
         r = oracle_eval(om, DT, q[e], qd[e], act[e], exc[e])
         assert r["status"] == 0
         L0, _ = ora.muscle_geometry(plain, q[e].astype(np.float64))
-        active += int(np.count_nonzero(np.abs(r["L"] - L0) > 1e-9))
+        moved = np.abs(r["L"] - L0) > 1e-9
+        active += int(np.count_nonzero(moved))
+        active_sph += int(np.count_nonzero(moved[model.wrap_muscle[model.wrap_kind == 1]]))
         Rg = msim.unpack_R(g["R"][e], lay, n)
         worst_L = max(worst_L, np.abs(g["L"][e, :m] - r["L"]).max())
         worst_R = max(worst_R, np.abs(Rg - r["R"]).max())
@@ -61,9 +68,11 @@ def test_wrapped_geometry_and_accelerations_match_the_oracle():
         st = np.abs(r["tau_m"]).max() + 1.0
         np.testing.assert_allclose(g["tau_m"][e, :n], r["tau_m"], rtol=0, atol=2e-3 * st)
         worst_qdd = max(worst_qdd, qdd_rel_err(g["qdd"][e, :n], r["qdd"]))
-    print("\nwrap: %d active wraps in the sample, worst |dL| %.2e m, |dR| %.2e m, qdd rel %.2e"
-          % (active, worst_L, worst_R, worst_qdd))
+    print("\n%s: %d active wraps in the sample, worst |dL| %.2e m, |dR| %.2e m, qdd rel %.2e"
+          % (name, active, worst_L, worst_R, worst_qdd))
     assert active >= 100, "too few active wraps in the sample to exercise the branch"
+    if model.wrap_kind.any():
+        assert active_sph >= 50, "too few active sphere wraps in the sample"
     assert worst_qdd <= 1e-4
 
 
@@ -86,8 +95,9 @@ def test_coaxial_cylinder_moment_arm_is_the_radius_on_the_device():
         np.testing.assert_allclose(Lg[e], L[0], rtol=0, atol=1e-7)
 
 
-def test_trajectory_parity_100_steps_with_wrapping():
-    model = mg.config_model("c1_wrap")
+@pytest.mark.parametrize("name", ["c1_wrap", "c1_wrap_mix"])
+def test_trajectory_parity_100_steps_with_wrapping(name):
+    model = mg.config_model(name)
     om = ora.OracleModel(model)
     E, steps = 1024, 100
     sim = msim.Sim(model, E, dt=DT)
@@ -102,7 +112,7 @@ def test_trajectory_parity_100_steps_with_wrapping():
     for t in range(steps):
         q, qd, act, *_ = ora.step(om, DT, q, qd, act, exc[t][idx].astype(np.float64), 1)
     err = np.abs(qg[idx] - q).max()
-    print("\nwrap trajectory: max |q_gpu - q_oracle| after %d substeps %.2e rad" % (steps, err))
+    print("\n%s trajectory: max |q_gpu - q_oracle| after %d substeps %.2e rad" % (name, steps, err))
     assert err <= 1e-3
     assert sim.status() == (0, 0)
 
@@ -133,6 +143,7 @@ def test_mixed_launch_with_wrapping_equals_per_model_launches_bitwise():
     (lambda m: m.wrap_segment.__setitem__(0, 0), "segment"),
     (lambda m: m.wrap_radius.__setitem__(0, -0.01), "radius"),
     (lambda m: m.wrap_body.__setitem__(0, m.n_bodies), "chain"),
+    (lambda m: m.wrap_kind.__setitem__(0, 2), "kind"),
 ])
 def test_invalid_wraps_are_rejected(edit, msg):
     model = copy.deepcopy(mg.config_model("c1_wrap"))
@@ -141,10 +152,10 @@ def test_invalid_wraps_are_rejected(edit, msg):
         msim.Sim(model, 4, dt=DT)
 
 
-def test_two_cylinders_on_one_muscle_are_rejected():
+def test_two_surfaces_on_one_muscle_are_rejected():
     model = copy.deepcopy(mg.config_model("c1_wrap"))
-    for k in ("wrap_muscle", "wrap_segment", "wrap_body", "wrap_center", "wrap_axis", "wrap_radius"):
+    for k in ("wrap_muscle", "wrap_segment", "wrap_body", "wrap_center", "wrap_axis", "wrap_radius", "wrap_kind"):
         a = getattr(model, k)
         setattr(model, k, np.concatenate([a, a[:1]]))
-    with pytest.raises(msim.MsimError, match="two wrapping cylinders"):
+    with pytest.raises(msim.MsimError, match="two wrapping surfaces"):
         msim.Sim(model, 4, dt=DT)
