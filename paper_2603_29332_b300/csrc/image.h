@@ -13,7 +13,7 @@ constexpr int kMaxCross = 12;   // DoFs crossed by one muscle
 constexpr int kMaxDepth = 63;   // DoF tree depth
 constexpr int kMaxModels = 8;
 constexpr int kMaxSpheres = 32;
-constexpr int kFiStride = 26;   // floats per body in the fi workspace
+constexpr int kFiStride = 20;   // floats per body in the fi workspace (float-float inertia)
 
 struct alignas(16) BodyRec {    // 64 B
     float off[3];               // joint origin in the parent frame (world for roots)
@@ -91,7 +91,8 @@ struct alignas(16) ImgHeader {
     // per-environment workspace layout (float offsets inside the environment's slot)
     int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_racc, w_y, w_sph, w_rk,
         max_nx,                 // most DoFs one muscle crosses (rows of the moment-arm region)
-        w_pad1, w_pad2, w_pad3;
+        w_f,                    // body forces (inside the A region, kinematics to subtree sums)
+        w_pad2, w_pad3;
     float gravity[3];
     float contact_k, contact_c, contact_mu, contact_eps2;
     float limit_k, limit_c, tau_act, tau_deact;
@@ -102,24 +103,27 @@ struct alignas(16) ImgHeader {
     float pad[1];
 };
 
-// Per environment workspace (floats), laid out by the host (msim_api.cu):
+// Per environment workspace (floats), laid out by the host (msim_api.cu).  Regions whose
+// lifetimes do not overlap share storage, so that more environments fit a block:
 //   q[n], qd[n]                       state, resident across substeps (act stays in global memory)
 //   frame[nb][12]                     body rotation (9, row-major) and origin (3), world
-//   v[nb][6]                          spatial velocity [w; v_O] (Plücker, world origin)
-//   fi[nb][26]                        body force [n; f] (6, FP32) and spatial inertia about the
-//                                     world origin (m, h, Ibar) as 10 float-float pairs (20),
-//                                     summed over subtrees in place
+//   fi[nb][20]                        spatial inertia about the world origin (m, h, Ibar) as 10
+//                                     float-float pairs, summed over subtrees in place
 //   S[n][6]                           joint motion axis [s; o x s]
-//   A[max(n_packed, 3 nb)][2]         packed M + dt D as float-float (hi, lo) pairs, factorised in
-//                                     place; holds the bias accelerations a[nb][6] (FP32) during
-//                                     the first pass, then the damping sums dt D as fixed-point
-//                                     int32 pairs (see fx_red) until the mass matrix is added
+//   A[max(n_packed, 9 nb)][2]         packed M + dt D as float-float (hi, lo) pairs, factorised in
+//                                     place.  Before that it holds, during the kinematics pass and
+//                                     the subtree sums, the bias accelerations a[nb][6], the
+//                                     spatial velocities v[nb][6] = [w; v_O] (w_v) and the body
+//                                     forces f[nb][6] = [n; f] (w_f, summed over subtrees), FP32;
+//                                     then the damping sums dt D as fixed-point int32 pairs (see
+//                                     fx_red) until the mass matrix is added
 //   rhs[n]                            tau_l - C (FP32)
-//   racc[n][2]                        R^T F + tau_c as fixed-point int32 pairs
-//   y[n][2]                           float-float solution of the two triangular solves
-//   sph[ns][12]                       per-sphere contact point, force, damping, flags
-//   rk[max_nx][32 wpe]                per-lane moment arms of the muscle being processed (last);
-//                                     sin, cos of the joint angles during the kinematics pass
+//   racc[n][2]                        R^T F + tau_c as fixed-point int32 pairs; the float-float
+//                                     solution y of the triangular solves replaces it (w_y)
+//   rk[max(max_nx 32 wpe, 2 n, 12 ns)] per-lane moment arms of the muscle being processed (last);
+//                                     sin, cos of the joint angles during the kinematics pass;
+//                                     per-sphere contact point, force, damping, flags during the
+//                                     contact pass (w_sph)
 
 // Bytes of the image a block copies to shared memory at staging level `stage`: 1 = all of it;
 // 0 = all but the via points and wrapping cylinders (read through the cache); 2 = also without
@@ -129,10 +133,13 @@ __host__ __device__ inline int staged_bytes(const ImgHeader& h, int stage) {
     return stage == 1 ? h.total_bytes : (stage == 2 ? h.o_muscle : h.o_point);
 }
 
-// floats per environment slot for a group of `wpe` warps per environment
-// (the moment-arm region also holds the joint sines and cosines during the kinematics pass)
+// floats per environment slot for a group of `wpe` warps per environment (the moment-arm
+// region also holds the joint sines and cosines, and the contact scratch)
 __host__ __device__ inline int ws_floats(const ImgHeader& h, int wpe) {
-    return h.w_rk + (h.max_nx * 32 * wpe > 2 * h.n ? h.max_nx * 32 * wpe : 2 * h.n);
+    int r = h.max_nx * 32 * wpe;
+    if (2 * h.n > r) r = 2 * h.n;
+    if (12 * h.ns > r) r = 12 * h.ns;
+    return h.w_rk + r;
 }
 
 }  // namespace msim

@@ -387,15 +387,16 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.w_q = slot(n);
     h.w_qd = slot(n);
     h.w_frame = slot(12 * nb);
-    h.w_v = slot(6 * nb);
     h.w_fi = slot(kFiStride * nb);
     h.w_S = slot(6 * n);
-    h.w_A = slot(2 * std::max(nM, 3 * nb));
+    h.w_A = slot(2 * std::max(nM, 9 * nb));
+    h.w_v = h.w_A + 6 * nb;    // inside A: velocities and body forces until the mass matrix
+    h.w_f = h.w_A + 12 * nb;
     h.w_rhs = slot(n);
     h.w_racc = slot(2 * n);
-    h.w_y = slot(2 * n);
-    h.w_sph = slot(12 * ns);
+    h.w_y = h.w_racc;          // the solution replaces the decoded accumulators
     h.w_rk = w;   // last: its size depends on the warps per environment (ws_floats)
+    h.w_sph = h.w_rk;          // contact scratch, after the muscles have used the region
     h.max_nx = 1;
     for (int k = 0; k < m; ++k) h.max_nx = std::max(h.max_nx, (int)mus[k].nx);
     for (int c = 0; c < 3; ++c) h.gravity[c] = d.gravity[c];

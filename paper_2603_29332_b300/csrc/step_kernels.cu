@@ -260,8 +260,9 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
     const float* q = ws + H.w_q;
     const float* qd = ws + H.w_qd;
     float* frame = ws + H.w_frame;
-    float* V = ws + H.w_v;
+    float* V = ws + H.w_v;     // in the A region during this pass (with Acc and FB)
     float* FI = ws + H.w_fi;
+    float* FB = ws + H.w_f;
     float* S = ws + H.w_S;
     float* Acc = ws + H.w_A;   // bias accelerations live in the A region during this pass
     float* SC = ws + H.w_rk;   // sin, cos of every joint angle (the moment-arm scratch is free here)
@@ -443,13 +444,13 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
         cross3(w, Ivw, t1);
         cross3(vl, Ivl, t2);
         cross3(w, Ivl, t3);
-        float* fi = FI + kFiStride * b;
+        float* fb = FB + 6 * b;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            fi[k] = Iaw[k] + t1[k] + t2[k];
-            fi[3 + k] = Ial[k] + t3[k];
+            fb[k] = Iaw[k] + t1[k] + t2[k];
+            fb[3 + k] = Ial[k] + t3[k];
         }
-        df* Id = reinterpret_cast<df*>(fi + 6);   // m, h[3], Ibar[6]
+        df* Id = reinterpret_cast<df*>(FI + kFiStride * b);   // m, h[3], Ibar[6]
         Id[0] = df_make(m);
         Id[1] = hd[0]; Id[2] = hd[1]; Id[3] = hd[2];
 #pragma unroll
@@ -463,6 +464,7 @@ template <int WPE>
 __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
     float* FI = ws + H.w_fi;
+    float* FB = ws + H.w_f;
     const float* S = ws + H.w_S;
     float* rhs = ws + H.w_rhs;
     // subtree sums leaves first; every body's 16 components (force 6, float-float inertia 10) go
@@ -472,16 +474,15 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
         for (int t = g.lane; t < 16 * (i1 - i0); t += g.N) {
             const int b = T.border[i0 + t / 16], comp = t % 16;
             const BodyRec& B = T.body[b];
-            float* fi = FI + kFiStride * b;
             if (comp < 6) {
-                float f = fi[comp];
-                for (int c = 0; c < B.nchild; ++c) f += FI[kFiStride * T.child[B.child0 + c] + comp];
-                fi[comp] = f;
+                float f = FB[6 * b + comp];
+                for (int c = 0; c < B.nchild; ++c) f += FB[6 * T.child[B.child0 + c] + comp];
+                FB[6 * b + comp] = f;
             } else {
-                df* Io = reinterpret_cast<df*>(fi + 6) + (comp - 6);
+                df* Io = reinterpret_cast<df*>(FI + kFiStride * b) + (comp - 6);
                 df I = *Io;
                 for (int c = 0; c < B.nchild; ++c)
-                    I = df_add(I, reinterpret_cast<const df*>(FI + kFiStride * T.child[B.child0 + c] + 6)[comp - 6]);
+                    I = df_add(I, reinterpret_cast<const df*>(FI + kFiStride * T.child[B.child0 + c])[comp - 6]);
                 *Io = I;
             }
         }
@@ -490,7 +491,7 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     // bias of every DoF from its body's subtree force, all DoFs in parallel: rhs = -S^T f
     for (int d = g.lane; d < H.n; d += g.N) {
         const float* Sd = S + 6 * d;
-        const float* f = FI + kFiStride * T.dof[d].body;
+        const float* f = FB + 6 * T.dof[d].body;
         rhs[d] = -(Sd[0] * f[0] + Sd[1] * f[1] + Sd[2] * f[2] + Sd[3] * f[3] + Sd[4] * f[4] + Sd[5] * f[5]);
     }
     g.sync();
@@ -509,7 +510,7 @@ __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float*
     for (int t = g.lane; t < H.n; t += g.N) {
         const int d = T.crba_order[t];
         const DofRec& D = T.dof[d];
-        const df* I = reinterpret_cast<const df*>(FI + kFiStride * D.body + 6);
+        const df* I = reinterpret_cast<const df*>(FI + kFiStride * D.body);
         const df m = I[0];
         const df h0 = I[1], h1 = I[2], h2 = I[3];
         const df* Ib = I + 4;   // xx yy zz xy xz yz
@@ -831,11 +832,11 @@ __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, flo
     const ImgHeader& H = *T.H;
     if (H.ns == 0) return;
     const float* frame = ws + H.w_frame;
-    const float* V = ws + H.w_v;
+    const float* qd = ws + H.w_qd;
     const float* S = ws + H.w_S;
     int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);
     int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
-    float* sph = ws + H.w_sph;
+    float* sph = ws + H.w_sph;   // the moment-arm region, free after the muscles
     for (int i = g.lane; i < H.ns; i += g.N) {
         const SphereRec& Sp = T.sph[i];
         const float* fr = frame + 12 * Sp.body;
@@ -844,7 +845,17 @@ __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, flo
         x[0] += fr[9]; x[1] += fr[10]; x[2] += fr[11];
         const float depth = Sp.radius - x[2];
         const float y[3] = {x[0], x[1], x[2] - Sp.radius};   // lowest point of the sphere
-        const float* Vb = V + 6 * Sp.body;
+        // spatial velocity of the sphere's body from the joint rates, sum of S_d qd_d over the
+        // DoFs that move it (root first, as the kinematics pass sums them)
+        const DofRec& Dl = T.dof[Sp.last_dof];
+        float Vb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int j = 0; j <= Dl.depth; ++j) {
+            const int d = T.anc[Dl.row + j];
+            const float* Sd = S + 6 * d;
+            const float qv = qd[d];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Vb[k] += Sd[k] * qv;
+        }
         float wy[3];
         cross3(Vb, y, wy);
         const float vy[3] = {Vb[3] + wy[0], Vb[4] + wy[1], Vb[5] + wy[2]};
