@@ -506,21 +506,44 @@ int max_epb(msim_handle h, int i, int stage, int wpe) {
     return std::min((int)((h->smem_optin - fixed) / per), lim);
 }
 
-// Default launch shape: two warps per environment, as many environments per block as shared
-// memory holds (<= 8, <= the model's environments); sections are left in global memory (via
-// points, then also the muscle records, staging levels 0 and 2) only when that gains an
-// environment per block.
+// Default launch shape: two warps per environment.  Among the environments per block (<= 8)
+// whose resident environments per SM (per block x blocks per SM) reach 85 % of the most any count
+// gives (the kernel is latency-bound: throughput follows residency), the one that gives the
+// busiest SM the fewest environments, ceil(blocks / block slots) x resident, the larger residency
+// on a tie.  Sections are left in global memory (via points, then also the muscle records,
+// staging levels 0 and 2) only when that is needed for the chosen count.
 void auto_launch(msim_handle h, int i) {
-    const int ne = h->env_begin[i + 1] - h->env_begin[i];
+    const int ne = std::max(1, h->env_begin[i + 1] - h->env_begin[i]);
     const int w = 2;
-    int best = -1, best_e = 0;
-    for (int stage : {1, 0, 2}) {
-        int e = std::min(max_epb(h, i, stage, w), 8);
-        if (ne > 0) e = std::min(e, ne);
-        if (e > best_e) { best = stage; best_e = e; }
+    int stage_of[9], per_sm_of[9], cmax = 0;
+    for (int e = 1; e <= 8; ++e) {
+        stage_of[e] = -1;
+        per_sm_of[e] = 0;
+        if (e > ne) continue;
+        for (int st : {1, 0, 2})
+            if (stage_of[e] < 0 && max_epb(h, i, st, w) >= e) stage_of[e] = st;
+        if (stage_of[e] < 0) continue;
+        const size_t smem = step_smem_bytes(h->models[i].hdr, e, stage_of[e], w);
+        per_sm_of[e] = std::max(1, step_blocks_per_sm(32 * w * e, smem, w, h->models[i].hdr.n_wraps > 0));
+        cmax = std::max(cmax, e * per_sm_of[e]);
+    }
+    int best_e = 1;
+    long best_load = -1, best_c = 0;
+    for (int e = 1; e <= 8; ++e) {
+        if (stage_of[e] < 0) continue;
+        const long c = (long)e * per_sm_of[e];
+        if (100 * c < 85L * cmax) continue;
+        const long blocks = (ne + e - 1) / e;
+        const long slots = (long)h->num_sms * per_sm_of[e];
+        const long load = (blocks + slots - 1) / slots * c;
+        if (best_load < 0 || load < best_load || (load == best_load && c > best_c)) {
+            best_load = load;
+            best_c = c;
+            best_e = e;
+        }
     }
     h->wpe[i] = w;
-    h->pts_smem[i] = best < 0 ? 1 : best;
+    h->pts_smem[i] = stage_of[best_e] < 0 ? 1 : stage_of[best_e];
     h->epb[i] = best_e;
 }
 
