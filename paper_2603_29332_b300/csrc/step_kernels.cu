@@ -959,6 +959,11 @@ __device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, floa
 // row + j; after the factorisation the diagonal slot holds 1 / L_kk.  The right-hand side is
 // carried as one more column, so L^T y = rhs is solved during the elimination; L qdd = y
 // follows root first, the nodes of a level in parallel.
+#ifndef MSIM_ELIM_UNROLL
+#define MSIM_ELIM_UNROLL 4
+#endif
+constexpr int kElimU = MSIM_ELIM_UNROLL;
+
 template <int WPE>
 __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
@@ -981,30 +986,42 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
         }
         g.sync();
         SUB_MARK(11);
-        // scale rows and rhs of the level's nodes: L_kj = A_kj / L_kk, y_k = b_k / L_kk
-        for (int i = i0; i < i1; ++i) {
-            const int k = T.dorder[i];
-            const DofRec& D = T.dof[k];
-            const df inv = A[D.row + D.depth];
-            for (int j = g.lane; j <= D.depth; j += g.N) {
-                if (j < D.depth) A[D.row + j] = df_mul(A[D.row + j], inv);
-                else Y[k] = df_mul(Y[k], inv);
+        // scale rows and rhs of the level's nodes: L_kj = A_kj / L_kk, y_k = b_k / L_kk; four
+        // nodes at a time, every load before the first store (entry j of each node per lane)
+        for (int c0 = i0; c0 < i1; c0 += 4) {
+            for (int j = g.lane; j <= kMaxDepth; j += g.N) {
+                df* ptr[4];
+                df val[4], inv[4];
+                bool on[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = c0 + u;
+                    const int k = T.dorder[i < i1 ? i : i0];
+                    const DofRec& D = T.dof[k];
+                    on[u] = i < i1 && j <= D.depth;
+                    ptr[u] = j < D.depth ? &A[D.row + j] : &Y[k];
+                    inv[u] = A[D.row + D.depth];
+                    val[u] = on[u] ? *ptr[u] : inv[u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (on[u]) *ptr[u] = df_mul(val[u], inv[u]);
             }
         }
         g.sync();
         SUB_MARK(12);
-        // eliminate node by node: A_ab -= L_ka L_kb for ancestors b <= a of k (four independent
+        // eliminate node by node: A_ab -= L_ka L_kb for ancestors b <= a of k (kElimU independent
         // updates per lane per iteration, loads first), then y_a -= L_ka y_k
         for (int i = i0; i < i1; ++i) {
             const int k = T.dorder[i];
             const DofRec& D = T.dof[k];
             const int np = D.depth * (D.depth + 1) / 2;
             const df* Lk = A + D.row;
-            for (int p0 = g.lane; p0 < np; p0 += 4 * g.N) {
-                df* tg[4];
-                df av[4], xv[4], yv[4];
+            for (int p0 = g.lane; p0 < np; p0 += kElimU * g.N) {
+                df* tg[kElimU];
+                df av[kElimU], xv[kElimU], yv[kElimU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kElimU; ++u) {
                     const int p = p0 + g.N * u;
                     const int tv = T.tri[p < np ? p : 0];
                     const int ja = tv & 0xff, jb = tv >> 8;      // jb <= ja < depth
@@ -1013,9 +1030,9 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
                     yv[u] = Lk[jb];
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) av[u] = *tg[u];
+                for (int u = 0; u < kElimU; ++u) av[u] = *tg[u];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < kElimU; ++u)
                     if (p0 + g.N * u < np) *tg[u] = df_fms(av[u], xv[u], yv[u]);
             }
             const df yk = Y[k];
