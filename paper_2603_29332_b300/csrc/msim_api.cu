@@ -752,15 +752,15 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
             StepArgs a;
             std::memset(&a, 0, sizeof(a));
             a.img = h->d_img[i];
-            a.stage = 0;
-            a.staged_bytes = staged_bytes(M.hdr, 0);
+            a.stage = 2;   // the smallest staged prefix: the reference lengths of any model that fits
+            a.staged_bytes = staged_bytes(M.hdr, 2);
             a.env_begin = 0; a.env_end = 1;
             a.q = zq; a.qd = zq + h->pitch_n; a.act = zm; a.exc = zm + h->pitch_m;
             a.pitch_n = h->pitch_n; a.pitch_m = h->pitch_m;
             a.env_status = h->env_status; a.gflags = h->gflags;
             a.n_sub = 1; a.dt = h->dt; a.envs_per_block = 1; a.wpe = 1;
             a.ev.L = Lbuf;
-            const size_t smem = step_smem_bytes(M.hdr, 1, false, 1);
+            const size_t smem = step_smem_bytes(M.hdr, 1, 2, 1);
             if (smem > h->smem_optin) {
                 g_create_error = "model " + std::to_string(i) + " does not fit in shared memory";
                 cudaFree(zq); cudaFree(zm); free_all(h); delete h;
