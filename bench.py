@@ -277,6 +277,12 @@ def run_gpu(args, rank, world, local_rank):
         roof["frac_of_fma_microbenchmark"] = achieved / pk_meas
     except Exception:
         pass
+    # algorithmic HBM bytes per launch: read exc, act, q, qd; write act, force, v_m, q, qd, q_dd
+    alg = 4 * E * (5 * model.n_muscles + 5 * model.n_dofs)
+    pk_hbm = _peaks().get("hbm_gbs", 6400.0)
+    roof["hbm_algorithmic"] = {"bytes_per_launch": alg, "achieved_gbs": alg / (launch_ms * 1e-3) / 1e9,
+                               "peak_gbs": pk_hbm, "frac": alg / (launch_ms * 1e-3) / 1e9 / pk_hbm,
+                               "peak_note": "hbm_gbs of measured"}
     tr = measured_traffic(E)
     if tr:
         roof["hbm"] = {"achieved_gbs": tr / (launch_ms * 1e-3) / 1e9, "peak_gbs": _peaks().get("hbm_gbs", 6400.0),
