@@ -110,16 +110,18 @@ struct alignas(16) ImgHeader {
 //   fi[nb][20]                        spatial inertia about the world origin (m, h, Ibar) as 10
 //                                     float-float pairs, summed over subtrees in place
 //   S[n][6]                           joint motion axis [s; o x s]
-//   A[max(n_packed, 9 nb)][2]         packed M + dt D as float-float (hi, lo) pairs, factorised in
+//   A[max(n_packed, 12 nb)][2]        packed M + dt D as float-float (hi, lo) pairs, factorised in
 //                                     place.  Before that it holds, during the kinematics pass and
-//                                     the subtree sums, the bias accelerations a[nb][6], the
-//                                     spatial velocities v[nb][6] = [w; v_O] (w_v) and the body
-//                                     forces f[nb][6] = [n; f] (w_f, summed over subtrees), FP32;
+//                                     the subtree sums, the bias accelerations a[nb][6] and the
+//                                     spatial velocities v[nb][6] = [w; v_O] (w_v), FP32, and the
+//                                     body forces f[nb][6] = [n; f] (w_f, float-float, summed over
+//                                     subtrees);
 //                                     then the damping sums dt D as fixed-point int32 pairs (see
 //                                     fx_red) until the mass matrix is added
-//   rhs[n]                            tau_l - C (FP32)
-//   racc[n][2]                        R^T F + tau_c as fixed-point int32 pairs; the float-float
-//                                     solution y of the triangular solves replaces it (w_y)
+//   rhs[n]                            tau_l (FP32)
+//   racc[n][2]                        -C + R^T F + tau_c as fixed-point int32 pairs; the
+//                                     float-float solution y of the triangular solves replaces it
+//                                     (w_y)
 //   rk[max(max_nx 32 wpe, 2 n, 12 ns)] per-lane moment arms of the muscle being processed (last);
 //                                     sin, cos of the joint angles during the kinematics pass;
 //                                     per-sphere contact point, force, damping, flags during the

@@ -389,8 +389,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.w_frame = slot(12 * nb);
     h.w_fi = slot(kFiStride * nb);
     h.w_S = slot(6 * n);
-    h.w_A = slot(2 * std::max(nM, 9 * nb));
-    h.w_v = h.w_A + 6 * nb;    // inside A: velocities and body forces until the mass matrix
+    h.w_A = slot(2 * std::max(nM, 12 * nb));
+    h.w_v = h.w_A + 6 * nb;    // inside A: velocities and float-float body forces until the mass matrix
     h.w_f = h.w_A + 12 * nb;
     h.w_rhs = slot(n);
     h.w_racc = slot(2 * n);

@@ -192,6 +192,13 @@ __device__ __forceinline__ void fx_red(int32_t* acc2, float v) {
     red_add_i32(acc2, hi);
     red_add_i32(acc2 + 1, lo);
 }
+// the fixed-point pair of a float-float value (plain store: the accumulator's first term)
+__device__ __forceinline__ void fx_store(int32_t* acc2, df v) {
+    const int32_t hi = __float2int_rn(v.hi * kFxCoarse);
+    const float rem = fmaf(-static_cast<float>(hi), kFxInvCoarse, v.hi) + v.lo;
+    acc2[0] = hi;
+    acc2[1] = __float2int_rn(rem * kFxFine);
+}
 __device__ __forceinline__ df df_from_i32(int32_t x) {
     const float f = __int2float_rn(x);
     const long long r = static_cast<long long>(x) - __float2ll_rn(f);
@@ -262,7 +269,7 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
     float* frame = ws + H.w_frame;
     float* V = ws + H.w_v;     // in the A region during this pass (with Acc and FB)
     float* FI = ws + H.w_fi;
-    float* FB = ws + H.w_f;
+    df* FB = reinterpret_cast<df*>(ws + H.w_f);
     float* S = ws + H.w_S;
     float* Acc = ws + H.w_A;   // bias accelerations live in the A region during this pass
     float* SC = ws + H.w_rk;   // sin, cos of every joint angle (the moment-arm scratch is free here)
@@ -423,32 +430,41 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
             Ibd[5] = df_add_f(df_neg(df_mul_f(two_prod(c[1], c[2]), m)), ryz);
         }
         const df hd[3] = {two_prod(m, c[0]), two_prod(m, c[1]), two_prod(m, c[2])};
-        // FP32 body force from the rounded inertia: f = I a + v x* (I v)
-        const float h[3] = {hd[0].hi, hd[1].hi, hd[2].hi};
-        const float Ib[6] = {Ibd[0].hi, Ibd[1].hi, Ibd[2].hi, Ibd[3].hi, Ibd[4].hi, Ibd[5].hi};
-        auto imul = [&](const float xw[3], const float xl[3], float ow[3], float ol[3]) {
-            float t1[3], t2[3];
-            cross3(h, xl, t1);
-            cross3(h, xw, t2);
-            ow[0] = Ib[0] * xw[0] + Ib[3] * xw[1] + Ib[4] * xw[2] + t1[0];
-            ow[1] = Ib[3] * xw[0] + Ib[1] * xw[1] + Ib[5] * xw[2] + t1[1];
-            ow[2] = Ib[4] * xw[0] + Ib[5] * xw[1] + Ib[2] * xw[2] + t1[2];
-            ol[0] = m * xl[0] - t2[0];
-            ol[1] = m * xl[1] - t2[1];
-            ol[2] = m * xl[2] - t2[2];
+        // float-float body force f = I a + v x* (I v) from the float-float inertia (the bias
+        // enters the right-hand side exactly, so that the conditioning of M does not amplify
+        // FP32 rounding of the force sums)
+        auto imul = [&](const float xw[3], const float xl[3], df ow[3], df ol[3]) {
+            // ow = Ibar xw + h x xl, ol = m xl - h x xw
+            const df hxl[3] = {df_add(df_mul_f(hd[1], xl[2]), df_neg(df_mul_f(hd[2], xl[1]))),
+                               df_add(df_mul_f(hd[2], xl[0]), df_neg(df_mul_f(hd[0], xl[2]))),
+                               df_add(df_mul_f(hd[0], xl[1]), df_neg(df_mul_f(hd[1], xl[0])))};
+            const df hxw[3] = {df_add(df_mul_f(hd[1], xw[2]), df_neg(df_mul_f(hd[2], xw[1]))),
+                               df_add(df_mul_f(hd[2], xw[0]), df_neg(df_mul_f(hd[0], xw[2]))),
+                               df_add(df_mul_f(hd[0], xw[1]), df_neg(df_mul_f(hd[1], xw[0])))};
+            ow[0] = df_add(df_add(df_add(df_mul_f(Ibd[0], xw[0]), df_mul_f(Ibd[3], xw[1])), df_mul_f(Ibd[4], xw[2])), hxl[0]);
+            ow[1] = df_add(df_add(df_add(df_mul_f(Ibd[3], xw[0]), df_mul_f(Ibd[1], xw[1])), df_mul_f(Ibd[5], xw[2])), hxl[1]);
+            ow[2] = df_add(df_add(df_add(df_mul_f(Ibd[4], xw[0]), df_mul_f(Ibd[5], xw[1])), df_mul_f(Ibd[2], xw[2])), hxl[2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ol[k] = df_add(two_prod(m, xl[k]), df_neg(hxw[k]));
         };
-        float Ivw[3], Ivl[3], Iaw[3], Ial[3];
+        // a x b, a FP32, b float-float
+        auto xfd = [](const float a[3], const df bb[3], df o[3]) {
+            o[0] = df_add(df_mul_f(bb[2], a[1]), df_neg(df_mul_f(bb[1], a[2])));
+            o[1] = df_add(df_mul_f(bb[0], a[2]), df_neg(df_mul_f(bb[2], a[0])));
+            o[2] = df_add(df_mul_f(bb[1], a[0]), df_neg(df_mul_f(bb[0], a[1])));
+        };
+        df Ivw[3], Ivl[3], Iaw[3], Ial[3];
         imul(w, vl, Ivw, Ivl);
         imul(aw, al, Iaw, Ial);
-        float t1[3], t2[3], t3[3];
-        cross3(w, Ivw, t1);
-        cross3(vl, Ivl, t2);
-        cross3(w, Ivl, t3);
-        float* fb = FB + 6 * b;
+        df t1[3], t2[3], t3[3];
+        xfd(w, Ivw, t1);
+        xfd(vl, Ivl, t2);
+        xfd(w, Ivl, t3);
+        df* fb = FB + 6 * b;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            fb[k] = Iaw[k] + t1[k] + t2[k];
-            fb[3 + k] = Ial[k] + t3[k];
+            fb[k] = df_add(df_add(Iaw[k], t1[k]), t2[k]);
+            fb[3 + k] = df_add(Ial[k], t3[k]);
         }
         df* Id = reinterpret_cast<df*>(FI + kFiStride * b);   // m, h[3], Ibar[6]
         Id[0] = df_make(m);
@@ -464,9 +480,10 @@ template <int WPE>
 __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
     float* FI = ws + H.w_fi;
-    float* FB = ws + H.w_f;
+    df* FB = reinterpret_cast<df*>(ws + H.w_f);
     const float* S = ws + H.w_S;
     float* rhs = ws + H.w_rhs;
+    int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
     // subtree sums leaves first; every body's 16 components (force 6, float-float inertia 10) go
     // to their own lanes, so a level costs one chain of child additions per component
     for (int l = H.n_blevels - 1; l >= 0; --l) {
@@ -475,8 +492,8 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
             const int b = T.border[i0 + t / 16], comp = t % 16;
             const BodyRec& B = T.body[b];
             if (comp < 6) {
-                float f = FB[6 * b + comp];
-                for (int c = 0; c < B.nchild; ++c) f += FB[6 * T.child[B.child0 + c] + comp];
+                df f = FB[6 * b + comp];
+                for (int c = 0; c < B.nchild; ++c) f = df_add(f, FB[6 * T.child[B.child0 + c] + comp]);
                 FB[6 * b + comp] = f;
             } else {
                 df* Io = reinterpret_cast<df*>(FI + kFiStride * b) + (comp - 6);
@@ -488,11 +505,17 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
         }
         g.sync();
     }
-    // bias of every DoF from its body's subtree force, all DoFs in parallel: rhs = -S^T f
+    // bias of every DoF from its body's subtree force, all DoFs in parallel, in float-float:
+    // -S^T f starts the exact fixed-point accumulator of the right-hand side (the muscle and
+    // contact terms follow); rhs keeps the FP32 terms (limits, damping)
     for (int d = g.lane; d < H.n; d += g.N) {
         const float* Sd = S + 6 * d;
-        const float* f = FB + 6 * T.dof[d].body;
-        rhs[d] = -(Sd[0] * f[0] + Sd[1] * f[1] + Sd[2] * f[2] + Sd[3] * f[3] + Sd[4] * f[4] + Sd[5] * f[5]);
+        const df* f = FB + 6 * T.dof[d].body;
+        df c = df_mul_f(f[0], Sd[0]);
+#pragma unroll
+        for (int k = 1; k < 6; ++k) c = df_fma_f(c, f[k], Sd[k]);
+        fx_store(&racc[2 * d], df_neg(c));
+        rhs[d] = 0.f;
     }
     g.sync();
 }
@@ -1135,16 +1158,18 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     PHASE_MARK(0);
     phase_subtree(T, ws, g);
     PHASE_MARK(1);
-    {   // fixed-point accumulators: damping sums in the A storage (the bias accelerations it held
-        // are no longer needed), rhs sums beside it
+    {   // fixed-point accumulator of the damping sums in the A storage (the velocities, bias
+        // accelerations and body forces it held are no longer needed); the right-hand side's
+        // accumulator already holds -C
         int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);
         for (int t = g.lane; t < 2 * H.n_packed; t += g.N) Ai[t] = 0;
-        int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
-        for (int t = g.lane; t < 2 * H.n; t += g.N) racc[t] = 0;
     }
     if ((MODE == kModeEval)) {
-        for (int d = g.lane; d < H.n; d += g.N)
-            if (ev->bias) ev->bias[d] = -ws[H.w_rhs + d];
+        const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
+        for (int d = g.lane; d < H.n; d += g.N) {
+            const df c = fx_decode(racc[2 * d], racc[2 * d + 1]);
+            if (ev->bias) ev->bias[d] = -(c.hi + c.lo);
+        }
     }
     g.sync();
     const uint32_t mflags = phase_muscles<MODE>(T, ws, g, dt, exc, act, force_out, vm_out, ev, sc);

@@ -104,8 +104,8 @@ def test_model_at_every_limit_matches_the_oracle():
     print("\nlimits model: %d packed entries, %d envs/block, worst qdd rel err %.2e, err / cond(A) %.1e"
           % (d.n_packed[0], d.envs_per_block[0], worst, ratio))
     # the whole body's target holds although this model's chains of 62 light links make
-    # cond(M + dt D) ~3e7 (the whole body's is ~1e5); the FP32 kinematics and bias keep the
-    # error near cond x 1e-11 as long as no contact force is extreme
+    # cond(M + dt D) ~3e7 (the whole body's is ~1e5): the FP32 kinematics perturb the mechanism
+    # consistently and the bias is float-float, unless penalty forces are extreme
     assert worst <= 1e-4
     assert ratio <= 2e-10
 

@@ -5,8 +5,7 @@ Sixteen seeded draws of the synthetic generator over its whole parameter space (
 on or off, cylinders and spheres, fixed or free root) each run one substep stage by stage and
 30 substeps against the oracle.  The fixed configurations of the other tests are single points
 of this space; here tree shapes, depths, muscle lengths and feature combinations vary.  A free
-root starts within 2 cm of its model pose.  q_dd is held to max(1e-4, 2e-9 cond(M + dt D)), and to
-1e-3 in states whose feet carry more than 2 kN of penalty force (comment in the test).
+root starts within 2 cm of its model pose; q_dd within 1e-4, q within 1e-3 after 30 substeps.
 """
 import numpy as np
 import pytest
@@ -44,34 +43,18 @@ def test_random_model_matches_the_oracle(i):
     lay = sim.layout(0)
     q, qd, act, exc = random_states(model, E, seed=i, q_scale=0.4)
     if model.free_root:
-        # keep the root within 2 cm of its model pose: pushed tens of cm into the ground, the
-        # feet's penalty forces (tens of kN) amplify FP32 rounding past the 1e-4 target
-        q[:, :3] *= 0.05
+        q[:, :3] *= 0.05   # the root within 2 cm of its model pose, not tens of cm into the ground
     res = sim.eval(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act), sim.pad_m(exc))
     g = {k: v.double().cpu().numpy() for k, v in res.items()}
-    worst, worst_deep, excess = 0.0, 0.0, 0.0
+    worst = 0.0
     for e in sample_envs(E, 6, seed=i):
         r = oracle_eval(om, DT, q[e], qd[e], act[e], exc[e])
-        ev_ = np.linalg.eigvalsh(r["A"])
-        kappa = ev_.max() / ev_.min()
         assert r["status"] == 0
         np.testing.assert_allclose(g["L"][e, :m], r["L"], rtol=0, atol=2e-6)
         np.testing.assert_allclose(msim.unpack_R(g["R"][e], lay, n), r["R"], rtol=0, atol=2e-6)
         np.testing.assert_allclose(msim.unpack_packed(g["M"][e], lay), r["M"], rtol=0, atol=2e-6 * np.abs(r["M"]).max())
-        err = qdd_rel_err(g["qdd"][e, :n], r["qdd"])
-        # The FP32 kinematics and bias C (relative error ~1e-6) bound q_dd at about cond(A) x 1e-9
-        # in unfavourable states (q_dd small next to the bias); the whole-body workloads (cond ~1e5)
-        # sit far below 1e-4, long chains of light links (cond ~5e5) can reach it.  A foot pushed
-        # centimetres into the ground carries kN of penalty force (k = 1e5 N/m), which turns the
-        # kinematics' rounding (~1e-7 m) into force errors of ~1e-2 N: those states get 1e-3.
-        bound = max(1e-4, 2e-9 * kappa)
-        if model.n_spheres and np.abs(r["sphere_force"]).max() > 2000.0:
-            worst_deep = max(worst_deep, err)
-            bound = max(bound, 1e-3)
-        else:
-            worst = max(worst, err)
-        excess = max(excess, err / bound)
-    assert excess <= 1.0, (worst, worst_deep)
+        worst = max(worst, qdd_rel_err(g["qdd"][e, :n], r["qdd"]))
+    assert worst <= 1e-4, worst
     # 30 substeps from the generator's initial state under uniform excitations
     q0, qd0, a0 = mg.initial_state(model, E, seed=i)
     u = mg.uniform_excitations(model, E, 1, seed=i)[0]
@@ -82,8 +65,7 @@ def test_random_model_matches_the_oracle(i):
     qo, *_ = ora.step(om, DT, q0[idx].astype(np.float64), qd0[idx].astype(np.float64), a0[idx].astype(np.float64),
                       u[idx].astype(np.float64), 30)
     err = np.abs(qg[idx] - qo).max()
-    print("\nrandom model %d: n %d, bodies %d, muscles %d, wraps %d, free root %d, spheres %d: qdd %.1e "
-          "(deep contact %.1e), q %.1e" % (i, n, model.n_bodies, m, len(model.wrap_muscle), model.free_root,
-                                          model.n_spheres, worst, worst_deep, err))
+    print("\nrandom model %d: n %d, bodies %d, muscles %d, wraps %d, free root %d, spheres %d: qdd %.1e, q %.1e"
+          % (i, n, model.n_bodies, m, len(model.wrap_muscle), model.free_root, model.n_spheres, worst, err))
     assert err <= 1e-3
     assert sim.status() == (0, 0)
