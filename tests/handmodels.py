@@ -45,3 +45,14 @@ def chain(n_links=3, seed=0, gravity=True, root_axis=(0, 1, 0)):
     inert = [[0.02, 0.03, 0.025, 0.001, -0.002, 0.0015]] * n_links
     return make_model("chain", list(range(-1, n_links - 1)), [1] * n_links, offs, masses, coms, inert, axes,
                       gravity=[0, 0, -G] if gravity else [0, 0, 0])
+
+
+def free_ball(mass=2.0, radius=0.05, inertia=0.002, height=None, **scalars):
+    """A free-floating ball: body 0 on a free root, COM at its origin, one contact sphere of the
+    ball's radius centred there.  With q = 0 its origin is at ``height`` (default: resting on
+    z = 0, sphere touching the ground)."""
+    from paper_2603_29332_b300.modelgen import with_free_root
+    h = radius if height is None else height
+    base = make_model("ball", [-1], [1], [[0, 0, h]], [mass], [[0, 0, 0]], [[inertia, inertia, inertia, 0, 0, 0]],
+                      [[0, 0, 1]], spheres=[(0, (0.0, 0.0, 0.0), radius)], **scalars)
+    return with_free_root(base)

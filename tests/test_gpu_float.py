@@ -132,3 +132,42 @@ def test_free_root_checks():
     bad.free_root = False
     with pytest.raises(msim.MsimError, match="body_ndof"):
         msim.Sim(bad, 4, dt=DT)
+
+
+def test_ball_on_the_ground_contact_closed_forms():
+    """A free ball at its static penetration sliding at v (device vs oracle, both with the
+    friction and contact damping taken implicitly), and a ball dropped onto the ground against
+    the overdamped oscillator m z'' = k (r - z) - c z' - m g."""
+    import math
+    from tests import handmodels as hm
+    model = hm.free_ball()
+    om = ora.OracleModel(model)
+    m, r, g = model.body_mass[0], model.sphere_radius[0], -model.gravity[2]
+    k, c = model.contact_k, model.contact_c
+    E = 3
+    sim = msim.Sim(model, E, dt=DT)
+    q = np.zeros((E, 6), np.float32)
+    q[:, 2] = -m * g / k
+    qd = np.zeros((E, 6), np.float32)
+    qd[:, 0] = [0.05, 0.5, 3.0]
+    z = np.zeros((E, 1), np.float32)
+    res = sim.eval(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(z), sim.pad_m(z))
+    qdd = res["qdd"][:, :6].double().cpu().numpy()
+    for e in range(E):
+        ref = ora.evaluate(om, DT, q[e].astype(np.float64), qd[e].astype(np.float64), np.zeros(1), np.zeros(1))["qdd"]
+        np.testing.assert_allclose(qdd[e], ref, rtol=0, atol=1e-4 * np.abs(ref).max())
+        assert qdd[e, 0] < 0 and qdd[e, 4] > 0
+    # drop: 1000 substeps of 10 us in one call
+    dt, n, v0 = 1e-5, 1000, -0.2
+    sim2 = msim.Sim(model, 1, dt=dt)
+    qd0 = np.zeros((1, 6), np.float32)
+    qd0[0, 2] = v0
+    sim2.reset(sim2.pad_n(np.zeros((1, 6), np.float32)), sim2.pad_n(qd0), sim2.pad_m(np.zeros((1, 1), np.float32)))
+    sim2.step(sim2.pad_m(np.zeros((1, 1), np.float32)), n)
+    zg = r + float(sim2.state()["q"][0, 2])
+    s1, s2 = (float(np.real(x)) for x in np.roots([m, c, k]))
+    x0 = m * g / k
+    B = (v0 - s1 * x0) / (s2 - s1)
+    zT = (r - m * g / k) + (x0 - B) * math.exp(s1 * n * dt) + B * math.exp(s2 * n * dt)
+    print("\nball drop: z after 10 ms %.7f m, closed form %.7f m" % (zg, zT))
+    assert abs(zg - zT) < 5e-6

@@ -463,3 +463,55 @@ def test_step_matches_eval_solution():
     assert r["status"] == 0
     np.testing.assert_allclose(r["qdd"], np.linalg.solve(r["A"], r["rhs"]), rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(r["rhs"], r["tau_m"] + r["tau_c"] + r["tau_l"] - r["bias"], rtol=1e-14, atol=1e-10)
+
+
+def test_sliding_ball_decelerates_with_smoothed_coulomb_friction():
+    """A ball resting on the ground at its static penetration m g / k and sliding at v: the
+    friction force is mu f_n v / sqrt(v^2 + eps^2) with f_n = m g, so (explicit damping) the
+    horizontal acceleration is -mu g v / sqrt(v^2 + eps^2), about -mu g for v >> eps; the
+    vertical one vanishes; the torque r x F about the centre spins the ball up."""
+    mdl = hm.free_ball()
+    m, r, g = mdl.body_mass[0], mdl.sphere_radius[0], -mdl.gravity[2]
+    k, mu, eps = mdl.contact_k, mdl.contact_mu, mdl.contact_eps
+    om = ora.OracleModel(mdl, implicit_damping=False)
+    I = mdl.body_inertia[0][0]
+    for v in (0.05, 0.5, 3.0):
+        q = np.zeros(6)
+        q[2] = -m * g / k                        # static penetration
+        qd = np.zeros(6)
+        qd[0] = v
+        qdd = ora.evaluate(om, 1e-3, q, qd, np.zeros(0), np.zeros(0))["qdd"]
+        ax = -mu * g * v / math.sqrt(v * v + eps * eps)
+        assert qdd[0] == pytest.approx(ax, rel=1e-9)
+        assert abs(qdd[2]) < 1e-9 * g and abs(qdd[1]) < 1e-12
+        # friction -x applied at the sphere's lowest point, r below the centre: +y spin
+        assert qdd[4] == pytest.approx(-r * m * ax / I, rel=1e-9)
+    assert abs(ax + mu * g) < 2e-3 * mu * g       # v = 3 m/s >> eps: about mu g
+
+
+def test_dropped_ball_follows_the_damped_oscillator_in_contact():
+    """A ball touching the ground with downward speed v0: in contact m z'' = k (r - z) - c z' - m g,
+    a linear oscillator about the equilibrium z_eq = r - m g / k, here overdamped (zeta ~1.1),
+    z - z_eq = A e^{s1 t} + B e^{s2 t}.  The oracle's semi-implicit Euler with the damping taken
+    implicitly converges to it at first order in dt."""
+    mdl = hm.free_ball()
+    m, r, g = mdl.body_mass[0], mdl.sphere_radius[0], -mdl.gravity[2]
+    k, c = mdl.contact_k, mdl.contact_c
+    om = ora.OracleModel(mdl)
+    v0, T = -0.2, 0.01
+    s1, s2 = np.roots([m, c, k])
+    assert np.all(np.isreal([s1, s2])) and s1.real < 0 and s2.real < 0
+    s1, s2 = float(np.real(s1)), float(np.real(s2))
+    x0 = m * g / k                               # z(0) - z_eq with z(0) = r (origin at height r)
+    B = (v0 - s1 * x0) / (s2 - s1)
+    A = x0 - B
+    zT = (r - m * g / k) + A * math.exp(s1 * T) + B * math.exp(s2 * T)
+    errs = []
+    for dt in (1e-5, 5e-6):
+        q, qd = np.zeros((1, 6)), np.zeros((1, 6))
+        qd[0, 2] = v0
+        n = int(round(T / dt))
+        q, qd, *_ = ora.step(om, dt, q, qd, np.zeros((1, 0)), np.zeros((1, 0)), n)
+        errs.append(abs((r + q[0, 2]) - zT))
+        assert abs(q[0, 0]) < 1e-15 and abs(qd[0, 4]) < 1e-12   # no friction, no spin
+    assert errs[0] < 2e-6 and errs[0] / errs[1] == pytest.approx(2.0, rel=0.15)
