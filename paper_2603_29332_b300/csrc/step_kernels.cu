@@ -520,6 +520,34 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     g.sync();
 }
 
+// Arithmetic of the system matrix A = M + dt D, its factorisation and the solves: float-float
+// pairs by default; FP64 with MSIM_FP64_FACTOR (same 8 bytes per entry).
+#ifdef MSIM_FP64_FACTOR
+using fac = double;
+__device__ __forceinline__ fac fac_of(df x) { return static_cast<double>(x.hi) + static_cast<double>(x.lo); }
+__device__ __forceinline__ fac fac_add_f(fac a, float b) { return a + static_cast<double>(b); }
+__device__ __forceinline__ fac fac_mul(fac a, fac b) { return a * b; }
+__device__ __forceinline__ fac fac_fms(fac acc, fac x, fac y) { return fma(-x, y, acc); }
+__device__ __forceinline__ fac fac_rsqrt(fac x) { return rsqrt(x); }
+__device__ __forceinline__ float fac_f(fac x) { return static_cast<float>(x); }
+__device__ __forceinline__ bool fac_pos(fac x) { return x > 0.0; }
+__device__ __forceinline__ fac fac_one() { return 1.0; }
+__device__ __forceinline__ fac fac_decode(int32_t hi, int32_t lo) {
+    return static_cast<double>(hi) * (1.0 / 256.0) + static_cast<double>(lo) * (1.0 / 268435456.0);
+}
+#else
+using fac = df;
+__device__ __forceinline__ fac fac_of(df x) { return x; }
+__device__ __forceinline__ fac fac_add_f(fac a, float b) { return df_add_f(a, b); }
+__device__ __forceinline__ fac fac_mul(fac a, fac b) { return df_mul(a, b); }
+__device__ __forceinline__ fac fac_fms(fac acc, fac x, fac y) { return df_fms(acc, x, y); }
+__device__ __forceinline__ fac fac_rsqrt(fac x) { return df_rsqrt(x); }
+__device__ __forceinline__ float fac_f(fac x) { return x.hi + x.lo; }
+__device__ __forceinline__ bool fac_pos(fac x) { return x.hi > 0.f; }
+__device__ __forceinline__ fac fac_one() { return df_make(1.f); }
+__device__ __forceinline__ fac fac_decode(int32_t hi, int32_t lo) { return fx_decode(hi, lo); }
+#endif
+
 // ------------------------------------------------------------------ phase 3: CRBA (float-float)
 // Adds M to the damping sums already accumulated (fixed point) in the same storage.  DoFs are
 // taken in the image's balanced order (similar entry counts per lane).
@@ -528,7 +556,7 @@ __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float*
     const ImgHeader& H = *T.H;
     const float* FI = ws + H.w_fi;
     const float* S = ws + H.w_S;
-    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    fac* A = reinterpret_cast<fac*>(ws + H.w_A);
     const int32_t* Ai = reinterpret_cast<const int32_t*>(ws + H.w_A);
     for (int t = g.lane; t < H.n; t += g.N) {
         const int d = T.crba_order[t];
@@ -560,8 +588,11 @@ __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float*
             acc = df_fma_f(acc, Fl[1], Sa[4]);
             acc = df_fma_f(acc, Fl[2], Sa[5]);
             if (evM) evM[row + k] = acc.hi + acc.lo;
-            const df dsum = fx_decode(Ai[2 * (row + k)], Ai[2 * (row + k) + 1]);
-            A[row + k] = df_add(acc, dsum);
+#ifdef MSIM_FP64_FACTOR
+            A[row + k] = fac_of(acc) + fac_decode(Ai[2 * (row + k)], Ai[2 * (row + k) + 1]);
+#else
+            A[row + k] = df_add(acc, fx_decode(Ai[2 * (row + k)], Ai[2 * (row + k) + 1]));
+#endif
         }
     }
     g.sync();
@@ -956,7 +987,7 @@ __device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, floa
     const ImgHeader& H = *T.H;
     const float* q = ws + H.w_q;
     const float* qd = ws + H.w_qd;
-    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    fac* A = reinterpret_cast<fac*>(ws + H.w_A);
     float* rhs = ws + H.w_rhs;
     for (int d = g.lane; d < H.n; d += g.N) {
         const DofRec& D = T.dof[d];
@@ -970,7 +1001,7 @@ __device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, floa
             else if (qv < D.lo) { t += H.limit_k * (D.lo - qv) - kd * qdv; dd += kd; }
         }
         rhs[d] += t;
-        A[D.row + D.depth] = df_add_f(A[D.row + D.depth], dt * dd);
+        A[D.row + D.depth] = fac_add_f(A[D.row + D.depth], dt * dd);
         if ((MODE == kModeEval) && ev->tau_l) ev->tau_l[d] = t;
     }
     g.sync();
@@ -990,22 +1021,22 @@ constexpr int kElimU = MSIM_ELIM_UNROLL;
 template <int WPE>
 __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
-    df* A = reinterpret_cast<df*>(ws + H.w_A);
+    fac* A = reinterpret_cast<fac*>(ws + H.w_A);
     const float* rhs = ws + H.w_rhs;
-    df* Y = reinterpret_cast<df*>(ws + H.w_y);
+    fac* Y = reinterpret_cast<fac*>(ws + H.w_y);
     const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
     bool ok = true;
     SUB_T0();
-    for (int d = g.lane; d < H.n; d += g.N) Y[d] = df_add_f(fx_decode(racc[2 * d], racc[2 * d + 1]), rhs[d]);
+    for (int d = g.lane; d < H.n; d += g.N) Y[d] = fac_add_f(fac_decode(racc[2 * d], racc[2 * d + 1]), rhs[d]);
     g.sync();
     for (int l = H.n_dlevels - 1; l >= 0; --l) {
         const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
         // pivots of this level (1 / L_kk into the diagonal slots)
         for (int i = i0 + g.lane; i < i1; i += g.N) {
             const DofRec& D = T.dof[T.dorder[i]];
-            df akk = A[D.row + D.depth];
-            if (!(akk.hi > 0.f)) { ok = false; akk = df_make(1.f); }
-            A[D.row + D.depth] = df_rsqrt(akk);
+            fac akk = A[D.row + D.depth];
+            if (!fac_pos(akk)) { ok = false; akk = fac_one(); }
+            A[D.row + D.depth] = fac_rsqrt(akk);
         }
         g.sync();
         SUB_MARK(11);
@@ -1013,8 +1044,8 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
         // nodes at a time, every load before the first store (entry j of each node per lane)
         for (int c0 = i0; c0 < i1; c0 += 4) {
             for (int j = g.lane; j <= kMaxDepth; j += g.N) {
-                df* ptr[4];
-                df val[4], inv[4];
+                fac* ptr[4];
+                fac val[4], inv[4];
                 bool on[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -1028,7 +1059,7 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (on[u]) *ptr[u] = df_mul(val[u], inv[u]);
+                    if (on[u]) *ptr[u] = fac_mul(val[u], inv[u]);
             }
         }
         g.sync();
@@ -1039,10 +1070,10 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
             const int k = T.dorder[i];
             const DofRec& D = T.dof[k];
             const int np = D.depth * (D.depth + 1) / 2;
-            const df* Lk = A + D.row;
+            const fac* Lk = A + D.row;
             for (int p0 = g.lane; p0 < np; p0 += kElimU * g.N) {
-                df* tg[kElimU];
-                df av[kElimU], xv[kElimU], yv[kElimU];
+                fac* tg[kElimU];
+                fac av[kElimU], xv[kElimU], yv[kElimU];
 #pragma unroll
                 for (int u = 0; u < kElimU; ++u) {
                     const int p = p0 + g.N * u;
@@ -1056,12 +1087,12 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
                 for (int u = 0; u < kElimU; ++u) av[u] = *tg[u];
 #pragma unroll
                 for (int u = 0; u < kElimU; ++u)
-                    if (p0 + g.N * u < np) *tg[u] = df_fms(av[u], xv[u], yv[u]);
+                    if (p0 + g.N * u < np) *tg[u] = fac_fms(av[u], xv[u], yv[u]);
             }
-            const df yk = Y[k];
+            const fac yk = Y[k];
             for (int j = g.lane; j < D.depth; j += g.N) {
-                df* t = &Y[T.anc[D.row + j]];
-                *t = df_fms(*t, Lk[j], yk);
+                fac* t = &Y[T.anc[D.row + j]];
+                *t = fac_fms(*t, Lk[j], yk);
             }
             g.sync();
         }
@@ -1074,7 +1105,7 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
     const int n_all = T.dlevel[H.n_dlevels];
     for (int i = g.lane; i < T.dlevel[1]; i += g.N) {   // roots
         const DofRec& D = T.dof[T.dorder[i]];
-        Y[T.dorder[i]] = df_mul(Y[T.dorder[i]], A[D.row + D.depth]);
+        Y[T.dorder[i]] = fac_mul(Y[T.dorder[i]], A[D.row + D.depth]);
     }
     g.sync();
     for (int l = 0; l + 1 < H.n_dlevels; ++l) {
@@ -1082,8 +1113,8 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
         for (int i = T.dlevel[l + 1] + g.lane; i < n_all; i += g.N) {
             const int k = T.dorder[i];
             const DofRec& D = T.dof[k];
-            df y = df_fms(Y[k], A[D.row + l], Y[T.anc[D.row + l]]);
-            if (i < next_end) y = df_mul(y, A[D.row + D.depth]);   // depth l + 1: complete
+            fac y = fac_fms(Y[k], A[D.row + l], Y[T.anc[D.row + l]]);
+            if (i < next_end) y = fac_mul(y, A[D.row + D.depth]);   // depth l + 1: complete
             Y[k] = y;
         }
         g.sync();
@@ -1181,10 +1212,10 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     PHASE_MARK(2);
     phase_limits<MODE>(T, ws, g, dt, ev);
     PHASE_MARK(5);
-    const df* A = reinterpret_cast<const df*>(ws + H.w_A);
+    const fac* A = reinterpret_cast<const fac*>(ws + H.w_A);
     if ((MODE == kModeEval)) {
         for (int t = g.lane; t < H.n_packed; t += g.N)
-            if (ev->A) ev->A[t] = A[t].hi + A[t].lo;
+            if (ev->A) ev->A[t] = fac_f(A[t]);
         const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
         for (int d = g.lane; d < H.n; d += g.N) {
             const df r = df_add_f(fx_decode(racc[2 * d], racc[2 * d + 1]), ws[H.w_rhs + d]);
@@ -1195,12 +1226,12 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     const bool ok = phase_factor_solve(T, ws, g);
     PHASE_MARK(6);
     uint32_t st = (ok ? 0u : kEnvNotSpd) | (bad ? kEnvNonFinite : 0u) | ((mflags & 2u) ? 0x100u : 0u);
-    const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
+    const fac* Y = reinterpret_cast<const fac*>(ws + H.w_y);
     if (!(MODE == kModeEval)) {
         float* q = ws + H.w_q;
         float* qd = ws + H.w_qd;
         for (int d = g.lane; d < H.n; d += g.N) {
-            const float v = qd[d] + dt * (Y[d].hi + Y[d].lo);
+            const float v = qd[d] + dt * fac_f(Y[d]);
             qd[d] = v;
             if (!(H.free_root && d >= 3 && d < 6)) q[d] += dt * v;
         }
@@ -1210,7 +1241,7 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
             g.sync();
         }
     } else if (ev->qdd) {
-        for (int d = g.lane; d < H.n; d += g.N) ev->qdd[d] = Y[d].hi + Y[d].lo;
+        for (int d = g.lane; d < H.n; d += g.N) ev->qdd[d] = fac_f(Y[d]);
     }
     return st;
 }
@@ -1298,13 +1329,13 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             }
         }
         bool bad = false;
-        const df* Y = reinterpret_cast<const df*>(ws + H.w_y);
+        const fac* Y = reinterpret_cast<const fac*>(ws + H.w_y);
         for (int d = g.lane; d < H.n; d += g.N) {
             const float v0 = ws[H.w_q + d], v1 = ws[H.w_qd + d];
             bad |= !(isfinite(v0) && isfinite(v1));
             a.q[rn + d] = v0;
             a.qd[rn + d] = v1;
-            if (a.qdd_out) a.qdd_out[rn + d] = Y[d].hi + Y[d].lo;
+            if (a.qdd_out) a.qdd_out[rn + d] = fac_f(Y[d]);
         }
         for (int k = g.lane; k < H.m; k += g.N) bad |= !isfinite(a.act[rm + k]);
         if (g.any(bad)) st |= kEnvNonFinite;
