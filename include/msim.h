@@ -79,8 +79,10 @@ typedef struct {
 
 /* msim_create -- build a simulator for one or more models (<= 8) on one device.
  *   Copies every model description (host memory, caller keeps ownership; nothing is retained),
- *   validates it (MSIM_ERR_MODEL: parent order, DoF counts 1..3, unit axes, muscle paths that
- *   do not follow one ancestor chain, sizes above the limits in msim_model.h), builds the
+ *   validates it (MSIM_ERR_MODEL: parent order, DoF counts 1..3 (6 for a free root, without
+ *   limits), unit axes, muscle paths that do not follow one ancestor chain, wrapping surfaces
+ *   off the wrapped segment's chain or of an unknown kind, sizes above the limits in
+ *   msim_model.h), builds the
  *   device model images, computes each muscle's reference length L0 = L(q = 0) on the device
  *   and allocates the state (q, q_d, act all zero).  Synchronises the device before returning.
  *   *out receives the handle, owned by the library until msim_destroy. */
