@@ -273,6 +273,7 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
     float* S = ws + H.w_S;
     float* Acc = ws + H.w_A;   // bias accelerations live in the A region during this pass
     float* SC = ws + H.w_rk;   // sin, cos of every joint angle (the moment-arm scratch is free here)
+    SUB_T0();
     // 1. joint-angle sines and cosines, all DoFs in parallel (off the level-by-level chain)
     for (int d = g.lane; d < H.n; d += g.N) sincosf(q[d], &SC[2 * d], &SC[2 * d + 1]);
     g.sync();
@@ -385,6 +386,7 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
         }
         g.sync();
     }
+    SUB_MARK(15);   // profiling builds: sines, cosines and the recursion
     // 3. spatial inertia and body force of every body, all bodies in parallel
     for (int b = g.lane; b < H.nb; b += g.N) {
         const BodyRec& B = T.body[b];
@@ -537,7 +539,6 @@ __device__ __forceinline__ fac fac_decode(int32_t hi, int32_t lo) {
 }
 #else
 using fac = df;
-__device__ __forceinline__ fac fac_of(df x) { return x; }
 __device__ __forceinline__ fac fac_add_f(fac a, float b) { return df_add_f(a, b); }
 __device__ __forceinline__ fac fac_mul(fac a, fac b) { return df_mul(a, b); }
 __device__ __forceinline__ fac fac_fms(fac acc, fac x, fac y) { return df_fms(acc, x, y); }
