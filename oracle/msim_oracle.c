@@ -21,6 +21,9 @@
  *      joint-limit penalty are taken linearly implicit: (M + dt D) q_dd = rhs
  *   9. semi-implicit Euler: qd += dt q_dd, q += dt qd, act = clamp(act + dt act_dot, 0, 1)
  *
+ * Compliant tendon (optional, per muscle; the paper's model keeps the tendon rigid): the fibre
+ * and an elastic tendon in series, the tendon strain a state (ora_tendon below).
+ *
  * Free root (optional, the paper's skeleton has a floating pelvis): body 0 joined to the world
  * by six DoFs.  DoFs 0-2 translate its origin along world x, y, z (q = position, qd = velocity);
  * DoFs 3-5 turn it about world x, y, z through its origin (qd = world angular velocity, q = the
@@ -59,9 +62,11 @@ typedef struct {
     const double *wrap_center, *wrap_axis, *wrap_radius;
     int free_root;   /* 1: body 0 has the six free DoFs 0-5 described above */
     const int* wrap_kind;   /* per wrap: 0 cylinder, 1 sphere (wrap_axis unused); NULL: cylinders */
+    /* per muscle: tendon strain at F_max (> 0: compliant tendon, below; 0: rigid); NULL: all rigid */
+    const double* tendon_strain;
 } ora_model;
 
-int ora_abi_version(void) { return 6; }
+int ora_abi_version(void) { return 7; }
 
 /* DoF kinds: a translation of the free root (its point Jacobian is the axis itself), else a
  * rotation about the axis s_d through o_d (point Jacobian s_d x (x - o_d)). */
@@ -352,6 +357,76 @@ double ora_dfv(double v) {
     return 0.4 * 0.08 / ((v + 0.08) * (v + 0.08));
 }
 
+double ora_dfl(double l) { return -2.0 * (l - 1.0) / 0.45 * ora_fl(l); }
+double ora_dfp(double l) {
+    const double kpe = 4.0, e0 = 0.6;
+    if (l <= 1.0) return 0.0;
+    if (l <= 1.0 + e0) return (kpe / e0) * exp(kpe * (l - 1.0) / e0) / (exp(kpe) - 1.0);
+    return (kpe / e0) * exp(kpe) / (exp(kpe) - 1.0);
+}
+
+/* ---------------------------------------------------------------- compliant tendon
+ * Reading (not in the paper, whose tendon is rigid): the Hill model's series elastic tendon in
+ * the damped-equilibrium form of Millard 2013.
+ *   slack length   l_s = L0 - l_opt, so that l_m = 1 at q = 0 with the tendon unstretched and
+ *                  the rigid tendon is the stiff limit;
+ *   state          the tendon strain eps (0 after a reset: tendon at its slack length);
+ *   fibre length   l_m = (L - l_s (1 + eps)) / l_opt;
+ *   tendon force   F_max f_t(eps / eps0), eps0 the strain at F_max: f_t(x) = (e^{3x} - 1)/(e^3 - 1)
+ *                  on [0, 1] (toe region), linear with the same slope beyond, 0 when slack;
+ *   fibre          carries the tendon's force with a parallel damper beta = 0.1:
+ *                  act f_l(l_m) f_v(v_m) + f_p(l_m) + beta v_m = f_t, which fixes v_m (the left side
+ *                  increases strictly with v_m);
+ *   strain rate    d eps/dt = (dL/dt - v_max v_m) / l_s, taken linearly implicit in eps (with the
+ *                  non-negative part of d v_m / d eps): eps_next = eps + dt rate / (1 + dt v_max J / l_s);
+ *   skeleton       receives F = F_max f_t(eps_next / eps0); dF/d(dL/dt) joins the implicit damping. */
+#define ORA_TENDON_BETA 0.1
+double ora_ft(double x) {
+    if (x <= 0.0) return 0.0;
+    if (x <= 1.0) return (exp(3.0 * x) - 1.0) / (exp(3.0) - 1.0);
+    return 1.0 + 3.0 * exp(3.0) / (exp(3.0) - 1.0) * (x - 1.0);
+}
+double ora_dft(double x) {
+    if (x <= 0.0) return 0.0;
+    if (x <= 1.0) return 3.0 * exp(3.0 * x) / (exp(3.0) - 1.0);
+    return 3.0 * exp(3.0) / (exp(3.0) - 1.0);
+}
+
+/* root of A f_v(v) + beta v + c0 = 0 (A >= 0, beta > 0) by bisection: the left side is below zero
+ * at v = (-c0 - 1.4 A)/beta - 1 and above it at v = -c0/beta + 1 (0 <= f_v <= 1.4) */
+double ora_fibre_velocity(double A, double c0, double beta) {
+    double lo = (-c0 - 1.4 * A) / beta - 1.0, hi = -c0 / beta + 1.0;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (A * ora_fv(mid) + beta * mid + c0 < 0.0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+/* One substep of a compliant muscle at length L, dL/dt = Ldot, activation act and strain eps.
+ * out[0] l_m, [1] v_m, [2] eps_next, [3] F / F_max, [4] d(F / F_max)/d(dL/dt), [5] J. */
+void ora_tendon(double eps0, double lopt, double ls, double vmax, double act, double L, double Ldot, double eps,
+                double dt, double* out) {
+    const double beta = ORA_TENDON_BETA;
+    double lm = (L - ls * (1.0 + eps)) / lopt;
+    double ft = ora_ft(eps / eps0);
+    double A = act * ora_fl(lm);
+    double vm = ora_fibre_velocity(A, ora_fp(lm) - ft, beta);
+    /* d v_m / d eps from the fibre equation: d l_m / d eps = -l_s / l_opt */
+    double num = ora_dft(eps / eps0) / eps0 + (act * ora_dfl(lm) * ora_fv(vm) + ora_dfp(lm)) * ls / lopt;
+    double J = num / (A * ora_dfv(vm) + beta);
+    if (J < 0.0) J = 0.0;
+    double g = 1.0 + dt * vmax * J / ls;
+    double en = eps + dt * (Ldot - vmax * vm) / ls / g;
+    out[0] = lm;
+    out[1] = vm;
+    out[2] = en;
+    out[3] = ora_ft(en / eps0);
+    out[4] = ora_dft(en / eps0) / eps0 * dt / (ls * g);
+    out[5] = J;
+}
+
 /* ---------------------------------------------------------------- Newton-Euler (world frame)
  * tau = M(q) qdd + C(q, qd) [+ gravity term if grav]. */
 void ora_rnea(const ora_model* M, const double* q, const double* qd, const double* qdd, int grav,
@@ -601,11 +676,12 @@ void ora_rest_lengths(const ora_model* M, double* L0) {
  * Any output pointer may be NULL.  Returns 0, or 1 if the system matrix was not SPD. */
 typedef struct {
     double *qdd, *force, *L, *R, *lm, *vm, *dFdv, *tau_m, *tau_c, *tau_l, *bias, *M, *A, *rhs, *act_next,
-        *sphere_force;
+        *sphere_force, *eps_next;
 } ora_eval_out;
 
+/* eps: tendon strains [m] (NULL: zero); only compliant muscles read theirs */
 int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, const double* qd,
-             const double* act, const double* exc, const ora_eval_out* out) {
+             const double* act, const double* exc, const double* eps, const ora_eval_out* out) {
     int nb = M->nb, n = M->n, m = M->m;
     double* Rb = malloc(sizeof(double) * 9 * nb);
     double* pb = malloc(sizeof(double) * 3 * nb);
@@ -617,6 +693,7 @@ int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, c
     double* dF = malloc(sizeof(double) * m);
     double* lm = malloc(sizeof(double) * m);
     double* vm = malloc(sizeof(double) * m);
+    double* en = malloc(sizeof(double) * m);
     double* tau_m = calloc(n, sizeof(double));
     double* tau_c = calloc(n, sizeof(double));
     double* tau_l = calloc(n, sizeof(double));
@@ -637,11 +714,22 @@ int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, c
         double ldot = 0.0;
         for (int d = 0; d < n; ++d) ldot -= row[d] * qd[d];       /* dL/dt = (dL/dq) qd = -R qd */
         double vmax = M->vmax_per_lopt * M->lopt[k];
-        lm[k] = 1.0 + (L[k] - L0[k]) / M->lopt[k];
-        vm[k] = ldot / vmax;
         double a = act[k];
-        F[k] = M->fmax[k] * (a * ora_fl(lm[k]) * ora_fv(vm[k]) + ora_fp(lm[k]));
-        dF[k] = M->fmax[k] * a * ora_fl(lm[k]) * ora_dfv(vm[k]) / vmax;
+        en[k] = eps ? eps[k] : 0.0;
+        if (M->tendon_strain && M->tendon_strain[k] > 0.0) {
+            double t[6];
+            ora_tendon(M->tendon_strain[k], M->lopt[k], L0[k] - M->lopt[k], vmax, a, L[k], ldot, en[k], dt, t);
+            lm[k] = t[0];
+            vm[k] = t[1];
+            en[k] = t[2];
+            F[k] = M->fmax[k] * t[3];
+            dF[k] = M->fmax[k] * t[4];
+        } else {
+            lm[k] = 1.0 + (L[k] - L0[k]) / M->lopt[k];
+            vm[k] = ldot / vmax;
+            F[k] = M->fmax[k] * (a * ora_fl(lm[k]) * ora_fv(vm[k]) + ora_fp(lm[k]));
+            dF[k] = M->fmax[k] * a * ora_fl(lm[k]) * ora_dfv(vm[k]) / vmax;
+        }
         for (int d = 0; d < n; ++d) tau_m[d] += row[d] * F[k];
         if (M->implicit_damping) {
             /* d tau_m / d qd = -R^T diag(dF/dLdot) R; only the non-zeros of the row matter */
@@ -673,6 +761,7 @@ int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, c
         if (out->R) memcpy(out->R, R, sizeof(double) * (size_t)m * n);
         if (out->lm) memcpy(out->lm, lm, sizeof(double) * m);
         if (out->vm) memcpy(out->vm, vm, sizeof(double) * m);
+        if (out->eps_next) memcpy(out->eps_next, en, sizeof(double) * m);
         if (out->dFdv) memcpy(out->dFdv, dF, sizeof(double) * m);
         if (out->tau_m) memcpy(out->tau_m, tau_m, sizeof(double) * n);
         if (out->tau_c) memcpy(out->tau_c, tau_c, sizeof(double) * n);
@@ -688,7 +777,7 @@ int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, c
                 out->act_next[k] = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
             }
     }
-    free(Rb); free(pb); free(s); free(o); free(L); free(R); free(F); free(dF); free(lm); free(vm);
+    free(Rb); free(pb); free(s); free(o); free(L); free(R); free(F); free(dF); free(lm); free(vm); free(en);
     free(tau_m); free(tau_c); free(tau_l); free(Dj); free(C); free(Mm); free(A); free(D); free(rhs);
     free(qdd); free(zero); free(nz);
     return bad;
@@ -721,11 +810,14 @@ void ora_integrate_q(const ora_model* M, double dt, double* q, const double* qd)
 }
 
 /* n_sub substeps for each of n_envs environments, states updated in place (rows [E][n], [E][m]);
- * exc [E][m] is held over the substeps.  qdd_out / force_out (optional) receive the last substep's
- * accelerations and muscle forces.  status (optional, [E]) gets 1 where a solve failed.
- * Environments run in parallel on n_threads host threads (<= 0: the OpenMP default). */
+ * exc [E][m] is held over the substeps.  eps (optional, [E][m]): tendon strains, updated in place
+ * (NULL: zero at every substep, for models without compliant tendons).  qdd_out / force_out
+ * (optional) receive the last substep's accelerations and muscle forces.  status (optional, [E])
+ * gets 1 where a solve failed.  Environments run in parallel on n_threads host threads (<= 0:
+ * the OpenMP default). */
 void ora_step(const ora_model* M, const double* L0, double dt, int n_envs, int n_sub, double* q, double* qd,
-              double* act, const double* exc, double* qdd_out, double* force_out, int* status, int n_threads) {
+              double* act, const double* exc, double* eps, double* qdd_out, double* force_out, int* status,
+              int n_threads) {
     int n = M->n, m = M->m;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -739,16 +831,20 @@ void ora_step(const ora_model* M, const double* L0, double dt, int n_envs, int n
         double* qdd = malloc(sizeof(double) * n);
         double* F = malloc(sizeof(double) * m);
         double* anext = malloc(sizeof(double) * m);
+        double* ee = eps ? eps + (size_t)e * m : NULL;
+        double* enext = malloc(sizeof(double) * (m > 0 ? m : 1));
         int bad = 0;
         for (int t = 0; t < n_sub; ++t) {
             ora_eval_out out;
             memset(&out, 0, sizeof(out));
-            out.qdd = qdd; out.force = F; out.act_next = anext;
-            bad |= ora_eval(M, L0, dt, qe, qde, ae, ue, &out);
+            out.qdd = qdd; out.force = F; out.act_next = anext; out.eps_next = enext;
+            bad |= ora_eval(M, L0, dt, qe, qde, ae, ue, ee, &out);
             for (int d = 0; d < n; ++d) qde[d] += dt * qdd[d];
             ora_integrate_q(M, dt, qe, qde);
             memcpy(ae, anext, sizeof(double) * m);
+            if (ee) memcpy(ee, enext, sizeof(double) * m);
         }
+        free(enext);
         if (qdd_out) memcpy(qdd_out + (size_t)e * n, qdd, sizeof(double) * n);
         if (force_out) memcpy(force_out + (size_t)e * m, F, sizeof(double) * m);
         if (status) status[e] = bad;

@@ -41,12 +41,12 @@ class _OraModel(C.Structure):
                 ("implicit_damping", C.c_int),
                 ("nw", C.c_int), ("wrap_muscle", _ip), ("wrap_segment", _ip), ("wrap_body", _ip),
                 ("wrap_center", _dp), ("wrap_axis", _dp), ("wrap_radius", _dp),
-                ("free_root", C.c_int), ("wrap_kind", _ip)]
+                ("free_root", C.c_int), ("wrap_kind", _ip), ("tendon_strain", _dp)]
 
 
 class _EvalOut(C.Structure):
     _fields_ = [(k, _dp) for k in ("qdd", "force", "L", "R", "lm", "vm", "dFdv", "tau_m", "tau_c", "tau_l",
-                                   "bias", "M", "A", "rhs", "act_next", "sphere_force")]
+                                   "bias", "M", "A", "rhs", "act_next", "sphere_force", "eps_next")]
 
 
 def build(force=False):
@@ -64,9 +64,9 @@ def lib():
         build()
         _lib = C.CDLL(_LIB)
         _lib.ora_abi_version.restype = C.c_int
-        if _lib.ora_abi_version() != 6:
+        if _lib.ora_abi_version() != 7:
             raise RuntimeError("stale oracle library: rebuild with oracle.build(force=True)")
-        for name in ("ora_fl", "ora_fp", "ora_fv", "ora_dfv"):
+        for name in ("ora_fl", "ora_fp", "ora_fv", "ora_dfv", "ora_dfl", "ora_dfp", "ora_ft", "ora_dft"):
             getattr(_lib, name).restype = C.c_double
             getattr(_lib, name).argtypes = [C.c_double]
         _lib.ora_act_rate.restype = C.c_double
@@ -76,7 +76,19 @@ def lib():
         _lib.ora_max_threads.restype = C.c_int
         _lib.ora_wrap_cylinder.restype = C.c_double
         _lib.ora_wrap_sphere.restype = C.c_double
+        _lib.ora_fibre_velocity.restype = C.c_double
+        _lib.ora_fibre_velocity.argtypes = [C.c_double] * 3
+        _lib.ora_tendon.argtypes = [C.c_double] * 9 + [_dp]
     return _lib
+
+
+def tendon_strains(model):
+    """Per-muscle tendon strain at F_max (0: rigid tendon); None when every tendon is rigid."""
+    t = getattr(model, "muscle_tendon_strain", None)
+    if t is None:
+        return None
+    t = np.asarray(t, dtype=np.float64).reshape(-1)
+    return t if t.shape[0] == model.n_muscles and np.any(t > 0) else None
 
 
 def _wrap_kinds(model, nw):
@@ -125,6 +137,11 @@ class OracleModel:
         s.implicit_damping = 1 if implicit_damping else 0
         s.nw = nw
         s.free_root = 1 if getattr(model, "free_root", False) else 0
+        ts = tendon_strains(model)
+        if ts is not None:
+            self._keep["tendon_strain"] = np.ascontiguousarray(ts)
+            s.tendon_strain = _ptr(self._keep["tendon_strain"])
+        self.compliant = ts is not None
         self.s = s
         self.n, self.m, self.nb = model.n_dofs, model.n_muscles, model.n_bodies
         self.L0 = np.zeros(self.m)
@@ -154,6 +171,39 @@ def fv(v):
 
 def dfv(v):
     return lib().ora_dfv(float(v))
+
+
+def dfl(l):
+    return lib().ora_dfl(float(l))
+
+
+def dfp(l):
+    return lib().ora_dfp(float(l))
+
+
+def ft(x):
+    """Normalised tendon force at x = strain / strain at F_max."""
+    return lib().ora_ft(float(x))
+
+
+def dft(x):
+    return lib().ora_dft(float(x))
+
+
+TENDON_BETA = 0.1
+
+
+def fibre_velocity(A, c0, beta=TENDON_BETA):
+    """Root v of A f_v(v) + beta v + c0 = 0 (bisection)."""
+    return lib().ora_fibre_velocity(float(A), float(c0), float(beta))
+
+
+def tendon(eps0, lopt, ls, vmax, act, L, Ldot, eps, dt):
+    """One substep of a compliant muscle: dict l_m, v_m, eps_next, F (normalised by F_max),
+    dF (its derivative by dL/dt), J (the implicit part of d v_m / d eps)."""
+    out = np.zeros(6)
+    lib().ora_tendon(*(float(x) for x in (eps0, lopt, ls, vmax, act, L, Ldot, eps, dt)), _ptr(out))
+    return dict(zip(("lm", "vm", "eps_next", "F", "dF", "J"), out))
 
 
 def act_rate(u, a, tau_act=0.010, tau_deact=0.040):
@@ -249,36 +299,42 @@ def cholesky_solve(A, b):
 
 
 _EVAL_KEYS = ("qdd", "force", "L", "R", "lm", "vm", "dFdv", "tau_m", "tau_c", "tau_l", "bias", "M", "A", "rhs",
-              "act_next", "sphere_force")
+              "act_next", "sphere_force", "eps_next")
 
 
-def evaluate(model, dt, q, qd, act, exc):
-    """All intermediates of one substep at one state (dict of float64 arrays, plus 'status')."""
+def evaluate(model, dt, q, qd, act, exc, eps=None):
+    """All intermediates of one substep at one state (dict of float64 arrays, plus 'status').
+    eps: tendon strains [m] (None: zero)."""
     om = _as(model)
     n, m, S = om.n, om.m, om.model.n_spheres
     shapes = dict(qdd=(n,), force=(m,), L=(m,), R=(m, n), lm=(m,), vm=(m,), dFdv=(m,), tau_m=(n,), tau_c=(n,),
-                  tau_l=(n,), bias=(n,), M=(n, n), A=(n, n), rhs=(n,), act_next=(m,), sphere_force=(max(S, 1), 3))
+                  tau_l=(n,), bias=(n,), M=(n, n), A=(n, n), rhs=(n,), act_next=(m,), sphere_force=(max(S, 1), 3),
+                  eps_next=(max(m, 1),))
     res = {k: np.zeros(shapes[k]) for k in _EVAL_KEYS}
     out = _EvalOut(**{k: _ptr(v) for k, v in res.items()})
     a = [np.ascontiguousarray(x, dtype=np.float64) for x in (q, qd, act, exc)]
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
     st = lib().ora_eval(om.ref, _ptr(om.L0), C.c_double(dt), _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]),
-                        C.byref(out))
+                        _ptr(e) if e is not None else None, C.byref(out))
+    res["eps_next"] = res["eps_next"][:m]
     res["sphere_force"] = res["sphere_force"][:S]
     res["status"] = st
     return res
 
 
-def step(model, dt, q, qd, act, exc, n_sub=1, n_threads=0):
-    """Advance E environments by n_sub substeps (exc [E, m] held).  Returns new (q, qd, act, qdd, force,
-    status); inputs are not modified."""
+def step(model, dt, q, qd, act, exc, n_sub=1, n_threads=0, eps=None):
+    """Advance E environments by n_sub substeps (exc [E, m] held).  eps [E, m]: tendon strains
+    (None: zero, the state after a reset).  Returns new (q, qd, act, qdd, force, status, eps);
+    inputs are not modified."""
     om = _as(model)
     q = np.array(q, dtype=np.float64, order="C"); qd = np.array(qd, dtype=np.float64, order="C")
     act = np.array(act, dtype=np.float64, order="C"); exc = np.ascontiguousarray(exc, dtype=np.float64)
     E = q.shape[0]
+    eps = np.zeros((E, om.m)) if eps is None else np.array(eps, dtype=np.float64, order="C").reshape(E, om.m)
     qdd = np.zeros((E, om.n)); F = np.zeros((E, om.m)); status = np.zeros(E, dtype=np.int32)
     lib().ora_step(om.ref, _ptr(om.L0), C.c_double(dt), C.c_int(E), C.c_int(n_sub), _ptr(q), _ptr(qd), _ptr(act),
-                   _ptr(exc), _ptr(qdd), _ptr(F), _ptr(status, _ip), C.c_int(n_threads))
-    return q, qd, act, qdd, F, status
+                   _ptr(exc), _ptr(eps), _ptr(qdd), _ptr(F), _ptr(status, _ip), C.c_int(n_threads))
+    return q, qd, act, qdd, F, status, eps
 
 
 def max_threads():

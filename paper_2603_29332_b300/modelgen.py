@@ -90,6 +90,9 @@ class Model:
     wrap_axis: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))     # unit, body frame
     wrap_radius: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float32))
     wrap_kind: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))   # 0 cylinder, 1 sphere
+    # per muscle: tendon strain at F_max; > 0 makes the tendon compliant (its slack length is the
+    # muscle's length at q = 0 less l_opt), 0 keeps it rigid.  Empty: every tendon rigid.
+    muscle_tendon_strain: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float32))
 
     def __post_init__(self):
         # scalar parameters are FP32 values too, like every array
@@ -104,6 +107,8 @@ class Model:
         self.wrap_center = _f32(np.asarray(self.wrap_center, dtype=np.float64).reshape(-1, 3))
         self.wrap_axis = _f32(np.asarray(self.wrap_axis, dtype=np.float64).reshape(-1, 3))
         self.wrap_radius = _f32(np.asarray(self.wrap_radius, dtype=np.float64).reshape(-1))
+        ts = np.asarray(self.muscle_tendon_strain, dtype=np.float64).reshape(-1)
+        self.muscle_tendon_strain = _f32(ts if ts.shape[0] else np.zeros(self.muscle_fmax.shape[0]))
 
     @property
     def n_bodies(self):
@@ -283,6 +288,21 @@ def with_free_root(model, name=None):
     kw = {f: getattr(model, f) for f in model.__dataclass_fields__}
     kw.update(name=name or model.name + "_float", body_ndof=ndof.astype(np.int32), body_dof_start=starts.astype(np.int32),
               dof_axis=_f32(axis), dof_limit=_f32(lim), dof_damping=_f32(damp), free_root=True)
+    return Model(**kw).validate()
+
+
+def with_tendons(model, rest_lengths, frac=1.0, strain=(0.033, 0.06), min_ratio=0.6, seed=0, name=None):
+    """The same model with compliant tendons: each muscle whose slack length (its length at q = 0,
+    ``rest_lengths``, less l_opt) is at least ``min_ratio`` l_opt gets, with probability ``frac``, a
+    tendon strain at F_max drawn from U(strain).  The rest lengths are the caller's (the path
+    geometry is not this module's)."""
+    L0 = np.asarray(rest_lengths, dtype=np.float64).reshape(model.n_muscles)
+    ratio = (L0 - model.muscle_lopt) / model.muscle_lopt
+    rng = np.random.default_rng(seed + 7000)
+    pick = (ratio >= min_ratio) & (rng.uniform(size=model.n_muscles) < frac)
+    eps0 = np.where(pick, rng.uniform(strain[0], strain[1], size=model.n_muscles), 0.0)
+    kw = {f: getattr(model, f) for f in model.__dataclass_fields__}
+    kw.update(name=name or model.name + "_tendon", muscle_tendon_strain=_f32(eps0))
     return Model(**kw).validate()
 
 
