@@ -372,8 +372,11 @@ double ora_dfp(double l) {
  *                  the rigid tendon is the stiff limit;
  *   state          the tendon strain eps (0 after a reset: tendon at its slack length);
  *   fibre length   l_m = (L - l_s (1 + eps)) / l_opt;
- *   tendon force   F_max f_t(eps / eps0), eps0 the strain at F_max: f_t(x) = (e^{3x} - 1)/(e^3 - 1)
- *                  on [0, 1] (toe region), linear with the same slope beyond, 0 when slack;
+ *   tendon force   F_max f_t(eps / eps0), eps0 the strain at F_max: f_t(x) = (e^{3x} - 1 - 3x)/(e^3 - 4)
+ *                  on [0, 1] (toe region, starting with zero slope at slack), linear with the same
+ *                  slope beyond, 0 when slack: C1 everywhere, so the linearly implicit update below
+ *                  is continuous in the strain (an inactive muscle with an unstretched fibre rests
+ *                  at eps = 0);
  *   fibre          carries the tendon's force with a parallel damper beta = 0.1:
  *                  act f_l(l_m) f_v(v_m) + f_p(l_m) + beta v_m = f_t, which fixes v_m (the left side
  *                  increases strictly with v_m);
@@ -383,13 +386,13 @@ double ora_dfp(double l) {
 #define ORA_TENDON_BETA 0.1
 double ora_ft(double x) {
     if (x <= 0.0) return 0.0;
-    if (x <= 1.0) return (exp(3.0 * x) - 1.0) / (exp(3.0) - 1.0);
-    return 1.0 + 3.0 * exp(3.0) / (exp(3.0) - 1.0) * (x - 1.0);
+    if (x <= 1.0) return (expm1(3.0 * x) - 3.0 * x) / (exp(3.0) - 4.0);
+    return 1.0 + 3.0 * (exp(3.0) - 1.0) / (exp(3.0) - 4.0) * (x - 1.0);
 }
 double ora_dft(double x) {
     if (x <= 0.0) return 0.0;
-    if (x <= 1.0) return 3.0 * exp(3.0 * x) / (exp(3.0) - 1.0);
-    return 3.0 * exp(3.0) / (exp(3.0) - 1.0);
+    if (x <= 1.0) return 3.0 * expm1(3.0 * x) / (exp(3.0) - 4.0);
+    return 3.0 * (exp(3.0) - 1.0) / (exp(3.0) - 4.0);
 }
 
 /* root of A f_v(v) + beta v + c0 = 0 (A >= 0, beta > 0) by bisection: the left side is below zero

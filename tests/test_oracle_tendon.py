@@ -1,7 +1,7 @@
 """Pins of the oracle's compliant tendon (a reading: the paper's tendon is rigid; the series
 elastic tendon follows the damped-equilibrium Hill model of Millard 2013).
 
-What fixes it independently of its own code: the tendon curve's end values and C1 join; the
+What fixes it independently of its own code: the tendon curve's end values and C1 joins; the
 fibre velocity of the damped equilibrium against the roots of the quadratics that the two Hill
 branches reduce to (the oracle bisects instead); the fixed point of the strain update against
 the steady-state equation solved by a library root finder; the stiff-tendon limit, which must
@@ -22,15 +22,16 @@ def _fd(f, x, h=1e-6):
     return (f(x + h) - f(x - h)) / (2 * h)
 
 
-def test_tendon_curve_end_values_and_c1_join():
+def test_tendon_curve_end_values_and_c1_joins():
     assert ora.ft(0.0) == 0.0 and ora.ft(-0.3) == 0.0
     assert ora.ft(1.0) == pytest.approx(1.0, abs=1e-15)
     h = 1e-7
     left = (ora.ft(1.0) - ora.ft(1.0 - h)) / h
     right = (ora.ft(1.0 + h) - ora.ft(1.0)) / h
     assert left == pytest.approx(right, rel=1e-5)
-    # slack to taut: value continuous at 0, slope 3 / (e^3 - 1) from the right
-    assert ora.ft(1e-9) == pytest.approx(3e-9 / (np.e ** 3 - 1), rel=1e-6)
+    # slack to taut: zero slope on both sides, the toe rising as (9/2) x^2 / (e^3 - 4)
+    assert ora.dft(0.0) == 0.0 and ora.dft(1e-9) == pytest.approx(0.0, abs=1e-7)
+    assert ora.ft(1e-3) == pytest.approx(4.5e-6 / (np.e ** 3 - 4), rel=2e-3)
     for x in (0.1, 0.5, 0.9, 1.5, 3.0):
         assert ora.dft(x) == pytest.approx(_fd(ora.ft, x), rel=1e-7)
     for l in (0.4, 0.8, 1.2, 1.5, 1.9):
