@@ -166,11 +166,31 @@ def cpu_baseline(model, envs=512, substeps=20):
     return out
 
 
+def bench_model(name, rest_lengths=None):
+    """The workload's model.  c1_tendon: the whole body with compliant tendons on every muscle
+    whose slack length (its length at q = 0 less l_opt) is at least 0.6 l_opt; the rest lengths
+    come from the caller (the library's device geometry on the GPU arm, the oracle on the CPU
+    arm)."""
+    if name != "c1_tendon":
+        return mg.config_model(name)
+    return mg.with_tendons(mg.config_model(MODEL), rest_lengths, seed=1)
+
+
+def _device_rest_lengths(device):
+    import torch
+    from paper_2603_29332_b300 import msim
+    base = mg.config_model(MODEL)
+    sim = msim.Sim([base], [1], dt=DT, device=device)
+    L0 = sim.geometry(torch.zeros((1, sim.pitch_n), device=sim.device))[0, :base.n_muscles].double().cpu().numpy()
+    sim.close()
+    return L0
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
-    model = mg.config_model(args.model)
     from oracle import oracle as ora
+    model = bench_model(args.model, ora.OracleModel(mg.config_model(MODEL)).L0 if args.model == "c1_tendon" else None)
     om = ora.OracleModel(model)
     envs, sub = args.ref_envs, args.substeps
     q0, qd0, a0 = mg.initial_state(model, envs, seed=1)
@@ -187,16 +207,18 @@ def run_reference(args, rank):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": _config(args),
+            "config": _config(args, model),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d envs x %d substeps per step (bounded sample of %d envs)" %
                                        (envs, sub, args.envs)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def _config(args):
+def _config(args, model):
     wrap = {"c1_wrap": ", 188 of them wrapping a cylinder",
-            "c1_wrap_mix": ", 188 of them wrapping a cylinder (92) or a sphere (96)"}.get(args.model, "")
+            "c1_wrap_mix": ", 188 of them wrapping a cylinder (92) or a sphere (96)",
+            "c1_tendon": ", %d of them with compliant tendons" % int((model.muscle_tendon_strain > 0).sum())
+            }.get(args.model, "")
     dofs = "a free root (6 DoF) and 89 hinge DoF" if args.model == "c1_float" else "90 hinge DoF"
     return {"workload": "whole-body synthetic model (60 bodies, %s, 700 Hill muscles%s, 8 contact "
                         "spheres), %d envs, %d substeps x dt %.0e s per step, smooth excitations, exact geometry"
@@ -209,7 +231,7 @@ def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2603_29332_b300 import msim
     torch.cuda.set_device(local_rank)
-    model = mg.config_model(args.model)
+    model = bench_model(args.model, _device_rest_lengths(local_rank) if args.model == "c1_tendon" else None)
     E, sub = args.envs, args.substeps
     sim = msim.Sim([model], [E], dt=DT, device=local_rank)
     q0, qd0, a0 = mg.initial_state(model, E, seed=1 + rank)
@@ -290,7 +312,7 @@ def run_gpu(args, rank, world, local_rank):
                        "peak_note": "hbm_gbs of measured"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": launch_ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(args),
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(args, model),
            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
            "launch_shape": {"warps_per_env": sim.dims.warps_per_env[0], "envs_per_block": sim.dims.envs_per_block[0],
                             "points_in_smem": sim.dims.points_in_smem[0],
@@ -603,8 +625,9 @@ def main():
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
     ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
-    ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_wrap_mix", "c1_float"],
-                    help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; c1_float: a free root)")
+    ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_wrap_mix", "c1_float", "c1_tendon"],
+                    help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; "
+                         "c1_float: a free root; c1_tendon: compliant tendons)")
     ap.add_argument("--policy-envs", type=int, default=16384)
     ap.add_argument("--policy-steps", type=int, default=2000)
     args = ap.parse_args()

@@ -97,7 +97,8 @@ MSIM_API msim_status msim_get_dims(msim_handle h, msim_dims* out);
 /* msim_reset -- set the state of environments (Eq. 2's act and the generalised coordinates).
  *   q0, qd0: [rows][pitch_n]; act0: [rows][pitch_m] (device).  rows = n_ids if env_ids is
  *   non-NULL (device int32 [n_ids], each in [0, n_envs)), else n_envs.  Any of q0, qd0, act0
- *   may be NULL: that part is set to zero.  Clears the status bits of those environments. */
+ *   may be NULL: that part is set to zero.  Clears the status bits of those environments and
+ *   sets their tendon strains to zero (compliant tendons at slack length). */
 MSIM_API msim_status msim_reset(msim_handle h, const float* q0, const float* qd0, const float* act0,
                        const int32_t* env_ids, int32_t n_ids, msim_stream_t stream);
 
@@ -109,7 +110,8 @@ MSIM_API msim_status msim_reset(msim_handle h, const float* q0, const float* qd0
  *     (M + dt D) q_dd = R^T F + tau_contact + tau_limits - C;
  *     q_d += dt q_dd;  q += dt q_d;  act = clamp(act + dt act_dot, 0, 1)
  *   where D collects the velocity derivatives of the muscle, contact and joint damping forces
- *   (linearly implicit damping).  1 <= n_substeps <= 100000.  Asynchronous. */
+ *   (linearly implicit damping).  A compliant tendon (msim_model.h) replaces F by its tendon
+ *   force and advances its strain.  1 <= n_substeps <= 100000.  Asynchronous. */
 MSIM_API msim_status msim_step(msim_handle h, const float* excitations, int32_t n_substeps, msim_stream_t stream);
 
 /* msim_step_host -- msim_step from HOST excitations with the resulting q and q_d copied back
@@ -125,6 +127,11 @@ MSIM_API msim_status msim_step_host(msim_handle h, const float* excitations_host
  *   env_status: uint32 [n_envs] (MSIM_ENV_* bits). */
 MSIM_API msim_status msim_get_state(msim_handle h, float* q, float* qd, float* act, float* qdd, float* muscle_force,
                            uint32_t* env_status, msim_stream_t stream);
+
+/* msim_tendon_strain -- the tendon strain state of compliant tendons (msim_model.h),
+ *   [n_envs][pitch_m] rows (device): `set` (if non-NULL) replaces it, then `get` (if non-NULL)
+ *   receives it.  Rigid muscles carry zeros.  Asynchronous. */
+MSIM_API msim_status msim_tendon_strain(msim_handle h, const float* set, float* get, msim_stream_t stream);
 
 /* msim_get_status -- synchronise the handle's device work and return the global flag word
  *   (OR of all MSIM_ENV_* bits and MSIM_FLAG_*).  Returns MSIM_ERR_STATE if any
@@ -148,6 +155,11 @@ MSIM_API msim_status msim_clear_status(msim_handle h, msim_stream_t stream);
 typedef struct {
     float *L, *lm, *vm, *force, *act_next, *R, *tau_m, *tau_c, *tau_l, *bias, *rhs, *qdd, *M, *A;
     int32_t nnz_pitch, packed_pitch;
+    /* compliant tendons: tendon_strain, an INPUT [n_envs][pitch_m] (NULL: zero strain), and
+     * tendon_strain_next [n_envs][pitch_m], the strain after the substep (rigid muscles: the
+     * input copied through) */
+    const float* tendon_strain;
+    float* tendon_strain_next;
 } msim_eval_out;
 MSIM_API msim_status msim_eval(msim_handle h, const float* q, const float* qd, const float* act, const float* exc,
                       const msim_eval_out* out, msim_stream_t stream);

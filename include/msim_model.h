@@ -47,7 +47,8 @@ typedef struct {
     const int32_t* muscle_point_start; /* [n_muscles + 1] */
     const float* muscle_fmax;          /* [n_muscles] maximum isometric force F_max (Eq. 1) */
     const float* muscle_lopt;          /* [n_muscles] optimal fibre length */
-    const float* muscle_lslack;        /* [n_muscles] tendon slack length (recorded; rigid tendon) */
+    const float* muscle_lslack;        /* [n_muscles] tendon slack length (recorded, unused: a
+                                        * compliant tendon's slack length follows from L0 below) */
     const int32_t* point_body;         /* [n_points] */
     const float* point_pos;            /* [n_points][3] */
     const int32_t* sphere_body;        /* [n_spheres] */
@@ -82,6 +83,17 @@ typedef struct {
      * wrap_radius; wrap_axis unused): the wrapped segment follows the great circle in the plane
      * through its two points and the centre.  NULL = all cylinders. */
     const int32_t* wrap_kind;          /* [n_wraps] or NULL */
+    /* compliant tendons (NULL = every tendon rigid, the paper's model): per muscle, the tendon
+     * strain at F_max, eps0 in (0, 0.5] for a compliant tendon, 0 for a rigid one.  A compliant
+     * tendon's slack length is l_s = L0 - l_opt (L0 the length at q = 0), which must be at least
+     * 0.5 l_opt (checked at create); its strain eps is a state (msim_tendon_strain, zero after a
+     * reset).  Per substep: fibre length l_m = (L - l_s (1 + eps)) / l_opt; tendon force
+     * F_max f_t(eps / eps0) with f_t(x) = (e^{3x} - 1 - 3x)/(e^3 - 4) on [0, 1], linear (C1)
+     * beyond, 0 when slack (C1 at slack too); the fibre velocity v_m solves act f_l f_v(v_m) + f_p + 0.1 v_m = f_t (a
+     * damped fibre, Millard 2013); eps advances linearly implicitly by
+     * d eps/dt = (dL/dt - v_max v_m) / l_s, and the skeleton receives the tendon force at the
+     * new strain, its dL/dt derivative taken into the implicit damping. */
+    const float* muscle_tendon_strain; /* [n_muscles] or NULL */
 } msim_model_desc;
 
 #ifdef __cplusplus

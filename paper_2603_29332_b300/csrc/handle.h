@@ -74,6 +74,7 @@ struct msim_handle_ {
     int flow_steps = 20;
     float flow_dt = 0.05f, flow_sigma = 0.f;
     float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *exc_stage = nullptr;
+    float* eps = nullptr;                    // [n_envs][pitch_m] tendon strains (compliant tendons)
     uint32_t* env_status = nullptr;
     uint32_t* gflags = nullptr;
     unsigned long long* timers = nullptr;   // profiling builds (MSIM_PHASE_TIMERS) only

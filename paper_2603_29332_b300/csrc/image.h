@@ -72,6 +72,14 @@ struct alignas(16) WrapRec {    // 32 B, a muscle's wrapping surface (MuscleRec:
                                 // | kind << 24 (0 cylinder, 1 sphere)
 };
 
+struct alignas(16) TendonRec {  // 16 B, per muscle record (same order) when the model has
+                                // compliant tendons
+    float inv_eps0;             // 1 / tendon strain at F_max; 0: rigid tendon
+    float lopt;                 // optimal fibre length
+    float vmax;                 // maximum fibre velocity (vmax_per_lopt l_opt)
+    float pad;
+};
+
 struct alignas(16) SphereRec {  // 32 B
     float pos[3];
     float radius;
@@ -92,7 +100,8 @@ struct alignas(16) ImgHeader {
     int32_t w_q, w_qd, w_frame, w_v, w_fi, w_S, w_A, w_rhs, w_racc, w_y, w_sph, w_rk,
         max_nx,                 // most DoFs one muscle crosses (rows of the moment-arm region)
         w_f,                    // body forces (inside the A region, kinematics to subtree sums)
-        w_pad2, w_pad3;
+        n_tendons,              // compliant tendons (0: none, and no tendon table)
+        o_tendon;               // byte offset of the tendon table (after the wrapping surfaces)
     float gravity[3];
     float contact_k, contact_c, contact_mu, contact_eps2;
     float limit_k, limit_c, tau_act, tau_deact;
@@ -100,8 +109,14 @@ struct alignas(16) ImgHeader {
     float fp_slope;             // slope of the passive curve's linear extension
     int32_t free_root;          // 1: body 0 has the six free DoFs 0-5 (msim_model.h)
     int32_t n_wraps;            // wrapping cylinders (their records follow the via points)
-    float pad[1];
+    float ft_den;               // e^3 - 4 of the tendon curve's toe
+    float ft_slope;             // slope of the tendon curve's linear part (per unit eps / eps0)
+    float pad[3];
 };
+
+// Models with wrapping surfaces or compliant tendons take the step variants that compile those
+// branches in.
+__host__ __device__ inline bool uses_ext(const ImgHeader& h) { return h.n_wraps > 0 || h.n_tendons > 0; }
 
 // Per environment workspace (floats), laid out by the host (msim_api.cu).  Regions whose
 // lifetimes do not overlap share storage, so that more environments fit a block:
@@ -128,9 +143,9 @@ struct alignas(16) ImgHeader {
 //                                     contact pass (w_sph)
 
 // Bytes of the image a block copies to shared memory at staging level `stage`: 1 = all of it;
-// 0 = all but the via points and wrapping cylinders (read through the cache); 2 = also without
-// the muscle records and the crossed-DoF table (the image places these four sections last, in
-// this order: muscles, crossed DoFs, via points, cylinders).
+// 0 = all but the via points, wrapping surfaces and tendon table (read through the cache); 2 =
+// also without the muscle records and the crossed-DoF table (the image places these five
+// sections last, in this order: muscles, crossed DoFs, via points, wrapping surfaces, tendons).
 __host__ __device__ inline int staged_bytes(const ImgHeader& h, int stage) {
     return stage == 1 ? h.total_bytes : (stage == 2 ? h.o_muscle : h.o_point);
 }

@@ -13,6 +13,7 @@ struct EvalPtrs {                 // per-stage outputs of one substep (msim_eval
     int nnz_pitch, packed_pitch;
     float* xpos;                  // body-position mode: rows [env][xpos_pitch], body origins x, y, z
     int xpos_pitch;
+    float* eps_next;              // eval: tendon strains after the substep (pitch_m)
 };
 
 struct StepArgs {
@@ -24,6 +25,8 @@ struct StepArgs {
     float* q;                     // state rows (pitch_n / pitch_m)
     float* qd;
     float* act;
+    float* eps;                   // tendon strains (pitch_m; the eval input rows in eval mode, may
+                                  // be null there: zero strain)
     const float* exc;
     int pitch_n, pitch_m;
     float* qdd_out;               // optional: last substep's accelerations
@@ -35,8 +38,8 @@ struct StepArgs {
     float dt;
     int envs_per_block;
     int wpe;                      // warps per environment: 1, 2 or 4
-    int wrap;                     // 1: the model has wrapping cylinders (step launches take the
-                                  // variant with the wrapping branch)
+    int wrap;                     // 1: the model has wrapping surfaces or compliant tendons (step
+                                  // launches take the variant with those branches, uses_ext)
     EvalPtrs ev;                  // eval: per-stage outputs; geometry mode: ev.L = label rows
                                   // [env][ev.nnz_pitch] (L then R), rows from env_begin
     // surrogate step (one substep per launch)
@@ -79,7 +82,7 @@ struct MixedArgs {
     int slots;                    // environment slots per block (threads = 32 wpe slots)
     int img_region;               // shared bytes reserved for the image (max over models, 128-aligned)
     uint32_t* queue;              // work counter (zeroed by launch_mixed before the kernel)
-    int wrap;                     // 1: some model has wrapping cylinders
+    int wrap;                     // 1: some model has wrapping surfaces or compliant tendons
 };
 cudaError_t launch_mixed(const MixedArgs& m, int grid, size_t smem, cudaStream_t s);
 int mixed_blocks_per_sm(int threads, size_t smem, int wpe, bool wrap);
@@ -95,8 +98,9 @@ cudaError_t launch_set_l0(uint8_t* img, const float* L, int m, cudaStream_t s);
 // policy observation rows [q | qd | act | force * inv_fmax | 0], BF16, pitch ldx (policy.cu)
 cudaError_t launch_obs(const float* q, const float* qd, const float* act, const float* force, const float* inv_fmax,
                        int pitch_n, int pitch_m, int n, int m, int n_envs, __nv_bfloat16* X, int ldx, cudaStream_t s);
-// fallback (optional): per-environment surrogate fallback flags, cleared with the state
-cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
+// fallback (optional): per-environment surrogate fallback flags, cleared with the state; eps
+// (optional): tendon strains, zeroed
+cudaError_t launch_reset(float* q, float* qd, float* act, float* eps, uint32_t* status, uint8_t* fallback, const float* q0,
                          const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,
                          int n_envs, cudaStream_t s);
 // flow refinement of the policy's action (policy.cu): a = mu + sigma N(0, 1) (advances *act_ctr),

@@ -199,6 +199,15 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         }
     }
     std::vector<WrapRec> wraps(nw);
+    // compliant tendons
+    int n_ten = 0;
+    if (d.muscle_tendon_strain)
+        for (int k = 0; k < m; ++k) {
+            const float t = d.muscle_tendon_strain[k];
+            if (!(t >= 0.f && t <= 0.5f)) FAIL("muscle %d: tendon strain at F_max must be 0 (rigid) or in (0, 0.5]", k);
+            n_ten += t > 0.f;
+        }
+    auto compliant = [&](int k) { return d.muscle_tendon_strain && d.muscle_tendon_strain[k] > 0.f; };
     std::vector<uint32_t> cross;
     std::vector<int32_t> mus_ptr(m + 1, 0), mus_dof;
     if (m > 0) {
@@ -280,8 +289,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             }
         mus_ptr[k + 1] = (int32_t)cross.size();
     }
-    // records sorted by (wrapped segment, points, crossed DoFs): a warp's 32 lanes then share
-    // loop trip counts and take the wrapping branch together
+    // records sorted by (compliant tendon, wrapped segment, points, crossed DoFs): a warp's 32
+    // lanes then share loop trip counts and take the tendon and wrapping branches together
     std::vector<int> wseg(m, 0);
     for (int k = 0; k < m; ++k)
         if (mus[k].wrap) wseg[k] = d.wrap_segment[mus[k].wrap - 1];
@@ -290,12 +299,21 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         for (int k = 0; k < m; ++k) order[k] = k;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             const MuscleRec &A = mus[a], &B = mus[b];
+            if (compliant(A.orig) != compliant(B.orig)) return compliant(B.orig);
             if (wseg[a] != wseg[b]) return wseg[a] < wseg[b];
             return A.np != B.np ? A.np < B.np : A.nx < B.nx;
         });
         std::vector<MuscleRec> sorted(m);
         for (int k = 0; k < m; ++k) sorted[k] = mus[order[k]];
         mus.swap(sorted);
+    }
+    std::vector<TendonRec> tens(n_ten ? m : 0);
+    for (int r = 0; r < (int)tens.size(); ++r) {
+        const int k = mus[r].orig;
+        tens[r].inv_eps0 = compliant(k) ? 1.f / d.muscle_tendon_strain[k] : 0.f;
+        tens[r].lopt = d.muscle_lopt[k];
+        tens[r].vmax = d.vmax_per_lopt * d.muscle_lopt[k];
+        tens[r].pad = 0.f;
     }
     if (!(d.vmax_per_lopt > 0.f) || !(d.tau_act > 0.f) || !(d.tau_deact > 0.f)) FAIL("time constants must be > 0");
 
@@ -376,6 +394,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.o_cross = place(sizeof(uint32_t) * cross.size());
     h.o_point = place(sizeof(PointRec) * np);
     h.o_wrap = place(sizeof(WrapRec) * std::max(nw, 1));
+    h.n_tendons = n_ten;
+    h.o_tendon = n_ten ? place(sizeof(TendonRec) * m) : 0;
     h.total_bytes = (int32_t)off;
     // per-environment workspace
     int w = 0;
@@ -413,6 +433,9 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.fp_slope = (float)((4.0 / 0.6) * e4 / (e4 - 1.0));
     h.free_root = d.free_root;
     h.n_wraps = nw;
+    const double e3 = std::exp(3.0);
+    h.ft_den = (float)(e3 - 4.0);
+    h.ft_slope = (float)(3.0 * (e3 - 1.0) / (e3 - 4.0));
 
     out.blob.assign(h.total_bytes, 0);
     auto put = [&](int32_t o, const void* src, size_t bytes) {
@@ -424,6 +447,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     put(h.o_muscle, mus.data(), sizeof(MuscleRec) * m);
     put(h.o_point, pts.data(), sizeof(PointRec) * np);
     if (nw > 0) put(h.o_wrap, wraps.data(), sizeof(WrapRec) * nw);
+    if (n_ten) put(h.o_tendon, tens.data(), sizeof(TendonRec) * m);
     put(h.o_sphere, sph.data(), sizeof(SphereRec) * ns);
     put(h.o_cross, cross.data(), sizeof(uint32_t) * cross.size());
     put(h.o_border, border.data(), border.size());
@@ -473,7 +497,7 @@ int model_grid(msim_handle h, int i) {
     const int groups = (ne + h->epb[i] - 1) / h->epb[i];
     const size_t smem = step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i], h->wpe[i]);
     const int per_sm =
-        std::max(1, step_blocks_per_sm(32 * h->wpe[i] * h->epb[i], smem, h->wpe[i], h->models[i].hdr.n_wraps > 0));
+        std::max(1, step_blocks_per_sm(32 * h->wpe[i] * h->epb[i], smem, h->wpe[i], uses_ext(h->models[i].hdr)));
     return std::max(1, std::min(groups, h->num_sms * per_sm));
 }
 
@@ -481,12 +505,12 @@ StepArgs base_args(msim_handle h, int i) {
     StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.img = h->d_img[i];
-    a.wrap = h->models[i].hdr.n_wraps > 0 ? 1 : 0;
+    a.wrap = uses_ext(h->models[i].hdr) ? 1 : 0;
     a.stage = h->pts_smem[i];
     a.staged_bytes = staged_bytes(h->models[i].hdr, h->pts_smem[i]);
     a.env_begin = h->env_begin[i];
     a.env_end = h->env_begin[i + 1];
-    a.q = h->q; a.qd = h->qd; a.act = h->act;
+    a.q = h->q; a.qd = h->qd; a.act = h->act; a.eps = h->eps;
     a.pitch_n = h->pitch_n; a.pitch_m = h->pitch_m;
     a.qdd_out = h->qdd; a.force_out = h->force; a.vm_out = h->vm;
     a.env_status = h->env_status; a.gflags = h->gflags;
@@ -524,7 +548,7 @@ void auto_launch(msim_handle h, int i) {
             if (stage_of[e] < 0 && max_epb(h, i, st, w) >= e) stage_of[e] = st;
         if (stage_of[e] < 0) continue;
         const size_t smem = step_smem_bytes(h->models[i].hdr, e, stage_of[e], w);
-        per_sm_of[e] = std::max(1, step_blocks_per_sm(32 * w * e, smem, w, h->models[i].hdr.n_wraps > 0));
+        per_sm_of[e] = std::max(1, step_blocks_per_sm(32 * w * e, smem, w, uses_ext(h->models[i].hdr)));
         cmax = std::max(cmax, e * per_sm_of[e]);
     }
     int best_e = 1;
@@ -568,7 +592,7 @@ void free_all(msim_handle h) {
     h->sur = nullptr;
     for (int i = 0; i < kMaxModels; ++i)
         if (h->d_img[i]) cudaFree(h->d_img[i]);
-    cudaFree(h->q); cudaFree(h->qd); cudaFree(h->act); cudaFree(h->qdd); cudaFree(h->force);
+    cudaFree(h->q); cudaFree(h->qd); cudaFree(h->act); cudaFree(h->qdd); cudaFree(h->force); cudaFree(h->eps);
     cudaFree(h->exc_stage); cudaFree(h->env_status); cudaFree(h->gflags); cudaFree(h->queue);
     cudaFree(h->obs); cudaFree(h->exc_policy); cudaFree(h->inv_fmax);
     if (h->timers) cudaFree(h->timers);
@@ -589,12 +613,12 @@ cudaError_t geometry_launch(msim_handle h, int i, const float* q, int ldq, int n
     a.q = const_cast<float*>(q);
     a.qd = const_cast<float*>(q);
     a.pitch_n = ldq;
-    a.act = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr; a.vm_out = nullptr;
+    a.act = nullptr; a.eps = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr; a.vm_out = nullptr;
     a.ev.L = out;
     a.ev.nnz_pitch = ldo;
     const size_t smem = step_smem_bytes(h->models[i].hdr, epb, h->pts_smem[i], wpe);
     const int groups = (n_rows + epb - 1) / epb;
-    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe, h->models[i].hdr.n_wraps > 0));
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe, uses_ext(h->models[i].hdr)));
     return launch_geom(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
 }
 
@@ -612,12 +636,12 @@ cudaError_t fk_launch(msim_handle h, int i, const float* q, int ldq, int n_rows,
     a.q = const_cast<float*>(q);
     a.qd = const_cast<float*>(q);
     a.pitch_n = ldq;
-    a.act = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr; a.vm_out = nullptr;
+    a.act = nullptr; a.eps = nullptr; a.exc = nullptr; a.qdd_out = nullptr; a.force_out = nullptr; a.vm_out = nullptr;
     a.ev.xpos = xpos;
     a.ev.xpos_pitch = 3 * h->models[i].hdr.nb;
     const size_t smem = step_smem_bytes(h->models[i].hdr, epb, h->pts_smem[i], wpe);
     const int groups = (n_rows + epb - 1) / epb;
-    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe, h->models[i].hdr.n_wraps > 0));
+    const int per_sm = std::max(1, step_blocks_per_sm(32 * wpe * epb, smem, wpe, uses_ext(h->models[i].hdr)));
     return launch_fk(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
 }
 
@@ -724,7 +748,7 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
         }                                                                        \
     } while (0)
     ALLOC(h->q, rn); ALLOC(h->qd, rn); ALLOC(h->qdd, rn);
-    ALLOC(h->act, rm); ALLOC(h->force, rm); ALLOC(h->exc_stage, rm);
+    ALLOC(h->act, rm); ALLOC(h->force, rm); ALLOC(h->exc_stage, rm); ALLOC(h->eps, rm);
     ALLOC(h->env_status, sizeof(uint32_t) * total);
     ALLOC(h->gflags, sizeof(uint32_t));
     ALLOC(h->queue, sizeof(uint32_t));
@@ -733,7 +757,7 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
     cudaMemset(h->timers, 0, sizeof(unsigned long long) * 16);
 #endif
     cudaMemset(h->q, 0, rn); cudaMemset(h->qd, 0, rn); cudaMemset(h->qdd, 0, rn);
-    cudaMemset(h->act, 0, rm); cudaMemset(h->force, 0, rm); cudaMemset(h->exc_stage, 0, rm);
+    cudaMemset(h->act, 0, rm); cudaMemset(h->force, 0, rm); cudaMemset(h->exc_stage, 0, rm); cudaMemset(h->eps, 0, rm);
     cudaMemset(h->env_status, 0, sizeof(uint32_t) * total);
     cudaMemset(h->gflags, 0, sizeof(uint32_t));
 
@@ -769,6 +793,20 @@ msim_status msim_create(const msim_create_args* args, msim_handle* out) {
             e = launch_eval(a, 1, smem, 0);
             if (e == cudaSuccess) e = launch_set_l0(h->d_img[i], Lbuf, M.hdr.m, 0);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e == cudaSuccess && M.hdr.n_tendons) {
+                // a compliant tendon needs a slack length L0 - l_opt of at least 0.5 l_opt
+                const msim_model_desc& dm = args->models[i];
+                std::vector<float> L0(M.hdr.m);
+                e = cudaMemcpy(L0.data(), Lbuf, sizeof(float) * M.hdr.m, cudaMemcpyDeviceToHost);
+                for (int k = 0; e == cudaSuccess && k < M.hdr.m; ++k)
+                    if (dm.muscle_tendon_strain[k] > 0.f && !(L0[k] - dm.muscle_lopt[k] >= 0.5f * dm.muscle_lopt[k])) {
+                        g_create_error = "model " + std::to_string(i) + ": muscle " + std::to_string(k) +
+                                         ": a compliant tendon needs a slack length L0 - l_opt >= 0.5 l_opt (L0 = " +
+                                         std::to_string(L0[k]) + ")";
+                        cudaFree(zq); cudaFree(zm); free_all(h); delete h;
+                        return MSIM_ERR_MODEL;
+                    }
+            }
         }
         if (e != cudaSuccess) {
             msim_status s = cuda_fail(nullptr, e, "model image upload / L0");
@@ -856,7 +894,7 @@ msim_status msim_reset(msim_handle h, const float* q0, const float* qd0, const f
     if (!aligned16(q0) || !aligned16(qd0) || !aligned16(act0)) return arg_fail(h, "msim_reset: unaligned pointer");
     const int rows = env_ids ? n_ids : h->n_envs;
     cudaSetDevice(h->device);
-    cudaError_t e = launch_reset(h->q, h->qd, h->act, h->env_status, h->sur ? h->sur->fallback : nullptr, q0, qd0,
+    cudaError_t e = launch_reset(h->q, h->qd, h->act, h->eps, h->env_status, h->sur ? h->sur->fallback : nullptr, q0, qd0,
                                  act0, env_ids, rows, h->pitch_n, h->pitch_m, h->n_envs, (cudaStream_t)stream);
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_reset");
 }
@@ -906,6 +944,17 @@ msim_status msim_get_state(msim_handle h, float* q, float* qd, float* act, float
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_get_state");
 }
 
+msim_status msim_tendon_strain(msim_handle h, const float* set, float* get, msim_stream_t stream) {
+    if (!h) return arg_fail(h, "msim_tendon_strain: NULL handle");
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rm = (size_t)h->n_envs * h->pitch_m * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (set) e = cudaMemcpyAsync(h->eps, set, rm, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && get) e = cudaMemcpyAsync(get, h->eps, rm, cudaMemcpyDeviceToDevice, s);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_tendon_strain");
+}
+
 msim_status msim_get_status(msim_handle h, uint32_t* global_flags) {
     if (!h || !global_flags) return arg_fail(h, "msim_get_status: NULL argument");
     cudaSetDevice(h->device);
@@ -950,6 +999,8 @@ msim_status msim_eval(msim_handle h, const float* q, const float* qd, const floa
         a.ev.R = out->R; a.ev.tau_m = out->tau_m; a.ev.tau_c = out->tau_c; a.ev.tau_l = out->tau_l;
         a.ev.bias = out->bias; a.ev.rhs = out->rhs; a.ev.qdd = out->qdd; a.ev.M = out->M; a.ev.A = out->A;
         a.ev.nnz_pitch = out->nnz_pitch; a.ev.packed_pitch = out->packed_pitch;
+        a.eps = const_cast<float*>(out->tendon_strain);
+        a.ev.eps_next = out->tendon_strain_next;
         const cudaError_t e = launch_eval(a, model_grid(h, i),
                                           step_smem_bytes(h->models[i].hdr, h->epb[i], h->pts_smem[i], h->wpe[i]),
                                           (cudaStream_t)stream);

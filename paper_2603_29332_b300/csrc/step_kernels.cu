@@ -39,14 +39,14 @@ namespace {
 
 // kernel modes: one substep loop, one-substep evaluation with every intermediate, muscle
 // geometry only (surrogate training labels), surrogate step (geometry from the learned model)
-// kModeStepW / kModeSurrW: the step and the learned-geometry substep with the wrapping-cylinder
-// branch compiled in (models that have cylinders); kModeStep and kModeSurr leave it out (so that
-// the two stay alike instruction for instruction, their exact geometry agrees bit for bit); the
-// other modes always keep it.
+// kModeStepW / kModeSurrW: the step and the learned-geometry substep with the wrapping-surface
+// and compliant-tendon branches compiled in (models that have either); kModeStep and kModeSurr
+// leave them out (so that the two stay alike instruction for instruction, their exact geometry
+// agrees bit for bit); the other modes always keep them.
 constexpr int kModeStep = 0, kModeEval = 1, kModeGeom = 2, kModeSurr = 3, kModeFk = 4, kModeStepW = 5,
               kModeSurrW = 6;
 __host__ __device__ constexpr bool is_surr(int mode) { return mode == kModeSurr || mode == kModeSurrW; }
-__host__ __device__ constexpr bool has_wrap(int mode) { return mode != kModeStep && mode != kModeSurr; }
+__host__ __device__ constexpr bool has_ext(int mode) { return mode != kModeStep && mode != kModeSurr; }
 
 constexpr uint32_t kEnvNonFinite = 0x1u;
 constexpr uint32_t kEnvNotSpd = 0x2u;
@@ -71,6 +71,7 @@ struct Tables {
     const uint16_t* tri;
     const uint16_t* rowanc;
     const uint8_t* crba_order;
+    const TendonRec* ten;       // null: every tendon rigid
 };
 
 __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
@@ -93,6 +94,7 @@ __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     t.tri = reinterpret_cast<const uint16_t*>(img + h.o_tri);
     t.rowanc = reinterpret_cast<const uint16_t*>(img + h.o_rowanc);
     t.crba_order = img + h.o_crba;
+    t.ten = h.n_tendons ? reinterpret_cast<const TendonRec*>(img + h.o_tendon) : nullptr;
     return t;
 }
 
@@ -101,6 +103,7 @@ __device__ __forceinline__ void unstaged_tables(Tables& T, const uint8_t* gimg, 
     if (stage == 1) return;
     T.pt = reinterpret_cast<const PointRec*>(gimg + T.H->o_point);
     T.wrap = reinterpret_cast<const WrapRec*>(gimg + T.H->o_wrap);
+    if (T.H->n_tendons) T.ten = reinterpret_cast<const TendonRec*>(gimg + T.H->o_tendon);
     if (stage == 2) {
         T.mus = reinterpret_cast<const MuscleRec*>(gimg + T.H->o_muscle);
         T.cross = reinterpret_cast<const uint32_t*>(gimg + T.H->o_cross);
@@ -627,6 +630,48 @@ __device__ __forceinline__ float hill_dfv(float v) {
     const float den = v + 0.08f;
     return 0.032f / (den * den);
 }
+__device__ __forceinline__ float hill_dfl(float l) { return (l - 1.f) * (-2.f / 0.45f) * hill_fl(l); }
+__device__ __forceinline__ float hill_dfp(float l, float den, float slope) {
+    if (l <= 1.f) return 0.f;
+    if (l <= 1.6f) return (4.f / 0.6f) * expf((l - 1.f) * (4.f / 0.6f)) / den;
+    return slope;
+}
+
+// ------------------------------------------------------------------ compliant tendon
+// Reading of the Hill model's series elastic tendon (the paper's is rigid), damped-equilibrium
+// form (Millard 2013): the tendon strain eps is a state; tendon curve f_t(x), x = eps / eps0,
+// (e^{3x} - 1 - 3x)/(e^3 - 4) on [0, 1] (zero slope at slack, 1 at x = 1), linear beyond with
+// the same slope, 0 when slack; the fibre, with a parallel damper beta, carries the tendon's
+// force.
+constexpr float kTendonBeta = 0.1f;
+__device__ __forceinline__ float tendon_f(float x, float den, float slope) {
+    if (x <= 0.f) return 0.f;
+    if (x <= 1.f) return (expm1f(3.f * x) - 3.f * x) / den;
+    return 1.f + slope * (x - 1.f);
+}
+__device__ __forceinline__ float tendon_df(float x, float den, float slope) {
+    if (x <= 0.f) return 0.f;
+    if (x <= 1.f) return 3.f * expm1f(3.f * x) / den;
+    return slope;
+}
+// Root v of A f_v(v) + beta v + c0 = 0 (A >= 0).  The left side increases strictly with v, so
+// its signs at the joins of f_v's branches (v = -1: c0 - beta; v = 0: A + c0) select the branch,
+// where the equation is linear (v < -1, f_v = 0) or, cleared of f_v's denominator, a quadratic
+// with one root in the branch, taken in the form without cancellation.
+__device__ __forceinline__ float fibre_velocity(float A, float c0) {
+    constexpr float b = kTendonBeta;
+    if (c0 - b >= 0.f) return -c0 * (1.f / b);
+    if (A + c0 >= 0.f) {
+        // (1 - 4v) g = 0:  4b v^2 - B v - C = 0, B = A + b - 4 c0, C = A + c0 >= 0; the root <= 0
+        const float B = A + b - 4.f * c0, C = A + c0;
+        const float sq = sqrtf(fmaf(B, B, 16.f * b * C));
+        return B >= 0.f ? -2.f * C / (B + sq) : (B - sq) * (1.f / (8.f * b));
+    }
+    // (v + 0.08) g = 0:  b v^2 + B v + C = 0, B = 1.4 A + 0.08 b + c0, C = 0.08 (A + c0) < 0; the root > 0
+    const float B = fmaf(1.4f, A, 0.08f * b + c0), C = 0.08f * (A + c0);
+    const float sq = sqrtf(fmaf(B, B, -4.f * b * C));
+    return B <= 0.f ? (sq - B) * (1.f / (2.f * b)) : -2.f * C / (B + sq);
+}
 
 // Per-environment context of a surrogate step: the network's normalised output row and its
 // de-normalisation, whether this environment must use the exact geometry (outside the training
@@ -702,7 +747,8 @@ __device__ bool wrap_path(const float x0[3], const float x1[3], const float c[3]
 // (The statements after its `continue` are unreachable in that mode only: warning 128 is off.)
 template <int MODE, int WPE>
 __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc,
-                                  float* act, float* force_out, float* vm_out, const EvalPtrs* ev, const SurrCtx* sc) {
+                                  float* act, float* eps, float* force_out, float* vm_out, const EvalPtrs* ev,
+                                  const SurrCtx* sc) {
     const ImgHeader& H = *T.H;
     const float* qd = ws + H.w_qd;
     const float* frame = ws + H.w_frame;
@@ -745,7 +791,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                     ldot -= Rv * qd[d];
                 }
             };
-            const int wseg = (has_wrap(MODE) && M.wrap) ? ((T.wrap[M.wrap - 1].body_cross >> 16) & 0xff) : 0;
+            const int wseg = (has_ext(MODE) && M.wrap) ? ((T.wrap[M.wrap - 1].body_cross >> 16) & 0xff) : 0;
             for (int j = 1; j < M.np; ++j) {
                 P = T.pt[M.p0 + j];
                 b = P.body_cross & 0xff;
@@ -755,7 +801,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                 rot3(fb, P.pos, x1);
                 x1[0] += fb[9]; x1[1] += fb[10]; x1[2] += fb[11];
                 bool wrapped = false;
-                if (has_wrap(MODE) && j == wseg) {
+                if (has_ext(MODE) && j == wseg) {
                     // the wrapped segment: tangent points held on the cylinder's body for the arms
                     const WrapRec W = T.wrap[M.wrap - 1];
                     const float* fw = frame + 12 * (W.body_cross & 0xff);
@@ -830,11 +876,36 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             continue;
         }
         SUB_MARK(8);
-        const float lm = 1.f + (L - M.L0) * M.inv_lopt;
-        const float vm = ldot * M.inv_vmax;
-        const float fl = hill_fl(lm);
-        const float F = M.fmax * (a * fl * hill_fv(vm) + hill_fp(lm, H.fp_den, H.fp_slope));
-        const float dFdl = M.fmax * a * fl * hill_dfv(vm) * M.inv_vmax;
+        float lm, vm, F, dFdl, en = 0.f;
+        const TendonRec Tn = (has_ext(MODE) && T.ten) ? T.ten[r] : TendonRec{0.f, 0.f, 0.f, 0.f};
+        if (has_ext(MODE) && Tn.inv_eps0 > 0.f) {
+            // compliant tendon: fibre velocity from the damped equilibrium at the current strain,
+            // strain advanced linearly implicitly, the tendon force at the new strain
+            const float ls = M.L0 - Tn.lopt;
+            const float inv_ls = 1.f / ls;
+            const float e0 = eps ? eps[k] : 0.f;
+            const float x = e0 * Tn.inv_eps0;
+            lm = (L - ls * (1.f + e0)) * M.inv_lopt;
+            const float fl = hill_fl(lm);
+            const float A = a * fl;
+            vm = fibre_velocity(A, hill_fp(lm, H.fp_den, H.fp_slope) - tendon_f(x, H.ft_den, H.ft_slope));
+            const float num = tendon_df(x, H.ft_den, H.ft_slope) * Tn.inv_eps0 +
+                              (a * hill_dfl(lm) * hill_fv(vm) + hill_dfp(lm, H.fp_den, H.fp_slope)) * ls * M.inv_lopt;
+            const float J = fmaxf(num / fmaf(A, hill_dfv(vm), kTendonBeta), 0.f);
+            const float gi = 1.f / fmaf(dt * Tn.vmax * J, inv_ls, 1.f);
+            en = e0 + dt * (ldot - Tn.vmax * vm) * inv_ls * gi;
+            const float xn = en * Tn.inv_eps0;
+            F = M.fmax * tendon_f(xn, H.ft_den, H.ft_slope);
+            dFdl = M.fmax * tendon_df(xn, H.ft_den, H.ft_slope) * Tn.inv_eps0 * dt * inv_ls * gi;
+            if (MODE != kModeEval && eps) eps[k] = en;
+        } else {
+            lm = 1.f + (L - M.L0) * M.inv_lopt;
+            vm = ldot * M.inv_vmax;
+            const float fl = hill_fl(lm);
+            F = M.fmax * (a * fl * hill_fv(vm) + hill_fp(lm, H.fp_den, H.fp_slope));
+            dFdl = M.fmax * a * fl * hill_dfv(vm) * M.inv_vmax;
+            if (has_ext(MODE)) en = eps ? eps[k] : 0.f;
+        }
         const float tau = (u > a) ? H.tau_act * (0.5f + 1.5f * a) : H.tau_deact / (0.5f + 1.5f * a);
         const float an = fminf(fmaxf(a + dt * (u - a) / tau, 0.f), 1.f);
         if (MODE != kModeEval) act[k] = an;
@@ -871,6 +942,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             if (ev->vm) ev->vm[k] = vm;
             if (ev->force) ev->force[k] = F;
             if (ev->act_next) ev->act_next[k] = an;
+            if (ev->eps_next) ev->eps_next[k] = en;
             if (ev->R)
                 for (int i = 0; i < M.nx; ++i) ev->R[M.x0 + i] = Rr[i];
         }
@@ -1167,12 +1239,12 @@ __device__ void free_root_turn(float* r, const float* w, float dt) {
 // Returns the environment status bits; in a surrogate step bit 8 reports a failed cross-check.
 template <int MODE, int WPE>
 __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const float* exc, float* act,
-                            float* force_out, float* vm_out, const EvalPtrs* ev, const SurrCtx* sc,
+                            float* eps, float* force_out, float* vm_out, const EvalPtrs* ev, const SurrCtx* sc,
                             unsigned long long* timers) {
     const ImgHeader& H = *T.H;
     if (MODE == kModeGeom) {
         phase_kinematics(T, ws, g);
-        phase_muscles<kModeGeom>(T, ws, g, dt, exc, act, nullptr, nullptr, ev, nullptr);
+        phase_muscles<kModeGeom>(T, ws, g, dt, exc, act, nullptr, nullptr, nullptr, ev, nullptr);
         return 0u;
     }
     if (MODE == kModeFk) {   // body origins only
@@ -1204,7 +1276,7 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
         }
     }
     g.sync();
-    const uint32_t mflags = phase_muscles<MODE>(T, ws, g, dt, exc, act, force_out, vm_out, ev, sc);
+    const uint32_t mflags = phase_muscles<MODE>(T, ws, g, dt, exc, act, eps, force_out, vm_out, ev, sc);
     const bool bad = (mflags & 1u) != 0;
     PHASE_MARK(3);
     phase_contact<MODE>(T, ws, g, dt, ev);
@@ -1270,22 +1342,24 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
         ev.tau_l = off(ev.tau_l, a.pitch_n); ev.bias = off(ev.bias, a.pitch_n); ev.rhs = off(ev.rhs, a.pitch_n);
         ev.qdd = off(ev.qdd, a.pitch_n);
         ev.M = off(ev.M, ev.packed_pitch); ev.A = off(ev.A, ev.packed_pitch);
+        ev.eps_next = off(ev.eps_next, a.pitch_m);
         for (int d = g.lane; d < H.n; d += g.N) {
             if (ev.tau_m) ev.tau_m[d] = 0.f;
             if (ev.tau_c) ev.tau_c[d] = 0.f;
             if (ev.tau_l) ev.tau_l[d] = 0.f;
         }
         g.sync();
-        st |= substep<kModeEval>(T, ws, g, a.dt, a.exc + rm, a.act + rm, nullptr, nullptr, &ev, nullptr, a.timers);
+        st |= substep<kModeEval>(T, ws, g, a.dt, a.exc + rm, a.act + rm, a.eps ? a.eps + rm : nullptr, nullptr,
+                                 nullptr, &ev, nullptr, a.timers);
     } else if (MODE == kModeGeom) {
         EvalPtrs ev = a.ev;
         ev.L = a.ev.L + (size_t)(e - a.env_begin) * ev.nnz_pitch;   // label row: L then R
         ev.R = ev.L + H.m;
-        substep<kModeGeom>(T, ws, g, a.dt, nullptr, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
+        substep<kModeGeom>(T, ws, g, a.dt, nullptr, nullptr, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
     } else if (MODE == kModeFk) {
         EvalPtrs ev = a.ev;
         ev.xpos = a.ev.xpos + (size_t)(e - a.env_begin) * ev.xpos_pitch;
-        substep<kModeFk>(T, ws, g, a.dt, nullptr, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
+        substep<kModeFk>(T, ws, g, a.dt, nullptr, nullptr, nullptr, nullptr, nullptr, &ev, nullptr, a.timers);
     } else {
         if (is_surr(MODE)) {
             // one substep with the learned geometry (the host loops over substeps)
@@ -1304,7 +1378,7 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             sc.check = !sc.use_exact && u01_from_bits(c[0]) < a.check_frac;
             sc.tol = a.tol;
             sc.max_err_bits = reinterpret_cast<unsigned int*>(a.surr_stats + 6);
-            const uint32_t s1 = substep<MODE>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+            const uint32_t s1 = substep<MODE>(T, ws, g, a.dt, a.exc + rm, a.act + rm, a.eps ? a.eps + rm : nullptr,
                                                    a.force_out ? a.force_out + rm : nullptr,
                                                    a.vm_out ? a.vm_out + rm : nullptr, nullptr, &sc, a.timers);
             st |= s1 & 0xffu;
@@ -1324,6 +1398,7 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             for (int s = 0; s < a.n_sub; ++s) {
                 const bool last = (s == a.n_sub - 1);
                 st |= substep<MODE == kModeStepW ? kModeStepW : kModeStep>(T, ws, g, a.dt, a.exc + rm, a.act + rm,
+                                         a.eps ? a.eps + rm : nullptr,
                                          (last && a.force_out) ? a.force_out + rm : nullptr,
                                          (last && a.vm_out) ? a.vm_out + rm : nullptr, nullptr, nullptr,
                                          a.timers);
@@ -1448,10 +1523,11 @@ __global__ void __launch_bounds__(512, 1) k_step_mixed(MixedArgs ma) {
         float* ws = ws_all + (size_t)slot * ws_floats(*T.H, WPE);
         if (slot < M.epb) {
             const int e = M.env_begin + (item - M.item_begin) * M.epb + slot;
-            // a model without cylinders takes the variant without them, as in its own launch
+            // a model without wrapping surfaces or compliant tendons takes the variant without
+            // those branches, as in its own launch
             if (e < M.env_end) {
                 if constexpr (MODE == kModeStepW) {
-                    if (T.H->n_wraps == 0) run_env<kModeStep, WPE>(ma.a, T, ws, g, e);
+                    if (!uses_ext(*T.H)) run_env<kModeStep, WPE>(ma.a, T, ws, g, e);
                     else run_env<kModeStepW, WPE>(ma.a, T, ws, g, e);
                 } else {
                     run_env<MODE, WPE>(ma.a, T, ws, g, e);
@@ -1467,7 +1543,7 @@ __global__ void k_set_l0(uint8_t* img, const float* L, int m) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) mus[r].L0 = L[mus[r].orig];
 }
 
-__global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
+__global__ void k_reset(float* q, float* qd, float* act, float* eps, uint32_t* status, uint8_t* fallback, const float* q0,
                         const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,
                         int n_envs) {
     const int r = blockIdx.x;
@@ -1480,6 +1556,8 @@ __global__ void k_reset(float* q, float* qd, float* act, uint32_t* status, uint8
     }
     for (int i = threadIdx.x; i < pitch_m; i += blockDim.x)
         act[(size_t)e * pitch_m + i] = act0 ? act0[(size_t)r * pitch_m + i] : 0.f;
+    if (eps)
+        for (int i = threadIdx.x; i < pitch_m; i += blockDim.x) eps[(size_t)e * pitch_m + i] = 0.f;
     if (threadIdx.x == 0) {
         status[e] = 0u;
         if (fallback) fallback[e] = 0;
@@ -1633,11 +1711,12 @@ cudaError_t launch_set_l0(uint8_t* img, const float* L, int m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset(float* q, float* qd, float* act, uint32_t* status, uint8_t* fallback, const float* q0,
+cudaError_t launch_reset(float* q, float* qd, float* act, float* eps, uint32_t* status, uint8_t* fallback, const float* q0,
                          const float* qd0, const float* act0, const int32_t* ids, int n_rows, int pitch_n, int pitch_m,
                          int n_envs, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
-    k_reset<<<n_rows, 128, 0, s>>>(q, qd, act, status, fallback, q0, qd0, act0, ids, n_rows, pitch_n, pitch_m, n_envs);
+    k_reset<<<n_rows, 128, 0, s>>>(q, qd, act, eps, status, fallback, q0, qd0, act0, ids, n_rows, pitch_n, pitch_m,
+                                   n_envs);
     return cudaGetLastError();
 }
 

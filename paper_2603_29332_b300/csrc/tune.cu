@@ -119,7 +119,7 @@ bool mixed_args(msim_handle h, int wpe, int slots, const int* pts, MixedArgs* ou
     m.queue = h->queue;
     const size_t sm = 16 + region + ws_max;
     if (sm > h->smem_optin) return false;
-    for (int k = 0; k < no; ++k) m.wrap |= h->models[order[k]].hdr.n_wraps > 0 ? 1 : 0;
+    for (int k = 0; k < no; ++k) m.wrap |= uses_ext(h->models[order[k]].hdr) ? 1 : 0;
     const int per_sm = mixed_blocks_per_sm(32 * wpe * slots, sm, wpe, m.wrap != 0);
     if (per_sm < 1) return false;
     *out = m;

@@ -39,7 +39,7 @@ class ModelDesc(C.Structure):
                 ("vmax_per_lopt", C.c_float),
                 ("n_wraps", C.c_int32), ("wrap_muscle", _i32p), ("wrap_segment", _i32p), ("wrap_body", _i32p),
                 ("wrap_center", _f32p), ("wrap_axis", _f32p), ("wrap_radius", _f32p), ("free_root", C.c_int32),
-                ("wrap_kind", _i32p)]
+                ("wrap_kind", _i32p), ("muscle_tendon_strain", _f32p)]
 
 
 class CreateArgs(C.Structure):
@@ -84,7 +84,9 @@ class TuneResult(C.Structure):
 
 
 class EvalOut(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in _EVAL_FIELDS] + [("nnz_pitch", C.c_int32), ("packed_pitch", C.c_int32)]
+    _fields_ = [(k, C.c_void_p) for k in _EVAL_FIELDS] + [("nnz_pitch", C.c_int32), ("packed_pitch", C.c_int32),
+                                                           ("tendon_strain", C.c_void_p),
+                                                           ("tendon_strain_next", C.c_void_p)]
 
 
 EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_step", "msim_step_host",
@@ -95,7 +97,7 @@ EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_s
            "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
            "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_surrogate_set_width", "msim_policy_attach",
            "msim_policy_step", "msim_policy_excitations", "msim_measure_fp32_peak", "msim_flow_attach",
-           "msim_flow_actions", "msim_reward_attach", "msim_reward", "msim_body_positions",
+           "msim_flow_actions", "msim_reward_attach", "msim_reward", "msim_body_positions", "msim_tendon_strain",
            "msim_last_error", "msim_version")
 
 _lib = None
@@ -120,6 +122,7 @@ def load_library(path=LIB_PATH):
     lib.msim_get_status.argtypes = [vp, C.POINTER(C.c_uint32)]
     lib.msim_clear_status.argtypes = [vp, vp]
     lib.msim_eval.argtypes = [vp, vp, vp, vp, vp, C.POINTER(EvalOut), vp]
+    lib.msim_tendon_strain.argtypes = [vp, vp, vp, vp]
     lib.msim_get_layout.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp]
     lib.msim_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     lib.msim_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -201,6 +204,9 @@ def model_desc(model):
                 wrap_muscle=i(model.wrap_muscle), wrap_segment=i(model.wrap_segment), wrap_body=i(model.wrap_body),
                 wrap_center=f(model.wrap_center), wrap_axis=f(model.wrap_axis), wrap_radius=f(model.wrap_radius),
                 wrap_kind=i(getattr(model, "wrap_kind", np.zeros(0))))
+    ts = np.asarray(getattr(model, "muscle_tendon_strain", np.zeros(0)), dtype=np.float32).reshape(-1)
+    if ts.shape[0] == model.n_muscles and np.any(ts > 0):
+        keep["muscle_tendon_strain"] = f(ts)
     d = ModelDesc()
     d.n_bodies, d.n_dofs, d.n_muscles = model.n_bodies, model.n_dofs, model.n_muscles
     d.n_points, d.n_spheres = model.n_points, model.n_spheres
@@ -319,15 +325,24 @@ class Sim:
                                              int(warps_per_env)))
         self._check(self.lib.msim_get_dims(self.h, C.byref(self.dims)))
 
-    def eval(self, q, qd, act, exc, stream=None):
-        """All intermediates of one substep (dict of device tensors, padded rows)."""
+    def tendon_strain(self, set=None, stream=None):
+        """The tendon strains of compliant tendons ([n_envs, pitch_m] device tensor); ``set``
+        (same shape) replaces them first."""
+        out = self.zeros(self.pitch_m)
+        self._check(self.lib.msim_tendon_strain(self.h, _ptr(set), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def eval(self, q, qd, act, exc, stream=None, eps=None):
+        """All intermediates of one substep (dict of device tensors, padded rows); ``eps``: the
+        tendon strains of the evaluated states (None: zero), their update in 'eps_next'."""
         nnz_p = max(4, (max(self.dims.nnz[: len(self.models)]) + 3) // 4 * 4)
         pk_p = max(4, (max(self.dims.n_packed[: len(self.models)]) + 3) // 4 * 4)
         cols = dict(L=self.pitch_m, lm=self.pitch_m, vm=self.pitch_m, force=self.pitch_m, act_next=self.pitch_m,
                     R=nnz_p, tau_m=self.pitch_n, tau_c=self.pitch_n, tau_l=self.pitch_n, bias=self.pitch_n,
                     rhs=self.pitch_n, qdd=self.pitch_n, M=pk_p, A=pk_p)
         res = {k: self.zeros(c) for k, c in cols.items()}
-        out = EvalOut(*[_ptr(res[k]) for k in _EVAL_FIELDS], nnz_p, pk_p)
+        res["eps_next"] = self.zeros(self.pitch_m)
+        out = EvalOut(*[_ptr(res[k]) for k in _EVAL_FIELDS], nnz_p, pk_p, _ptr(eps), _ptr(res["eps_next"]))
         self._check(self.lib.msim_eval(self.h, _ptr(q), _ptr(qd), _ptr(act), _ptr(exc), C.byref(out),
                                        _stream_ptr(stream)))
         return res

@@ -24,9 +24,9 @@ def sample_envs(E, k, seed=0):
     return np.sort(np.concatenate([[0, E - 1], mid]))
 
 
-def oracle_eval(om, dt, q, qd, act, exc):
+def oracle_eval(om, dt, q, qd, act, exc, eps=None):
     return ora.evaluate(om, dt, q.astype(np.float64), qd.astype(np.float64), act.astype(np.float64),
-                        exc.astype(np.float64))
+                        exc.astype(np.float64), None if eps is None else eps.astype(np.float64))
 
 
 def qdd_rel_err(qdd_gpu, qdd_ref):

@@ -2,7 +2,8 @@
 
 Sixteen seeded draws of the synthetic generator over its whole parameter space (2-30 bodies,
 1-3 DoFs per body, 1-200 muscles of 2-8 path points spanning 1-3 joints, limits and foot contact
-on or off, cylinders and spheres, fixed or free root) each run one substep stage by stage and
+on or off, cylinders and spheres, fixed or free root, compliant tendons on about 40 % of the
+draws) each run one substep stage by stage and
 30 substeps against the oracle.  The fixed configurations of the other tests are single points
 of this space; here tree shapes, depths, muscle lengths and feature combinations vary.  A free
 root starts within 2 cm of its model pose; q_dd within 1e-4, q within 1e-3 after 30 substeps.
@@ -36,6 +37,8 @@ def draw(i):
 @pytest.mark.parametrize("i", range(16))
 def test_random_model_matches_the_oracle(i):
     model = mg.generate("random%d" % i, **draw(i))
+    if np.random.default_rng(5000 + i).uniform() < 0.4:   # compliant tendons on half the eligible muscles
+        model = mg.with_tendons(model, ora.OracleModel(model).L0, frac=0.5, seed=i)
     om = ora.OracleModel(model)
     n, m = model.n_dofs, model.n_muscles
     E = 48
@@ -44,11 +47,12 @@ def test_random_model_matches_the_oracle(i):
     q, qd, act, exc = random_states(model, E, seed=i, q_scale=0.4)
     if model.free_root:
         q[:, :3] *= 0.05   # the root within 2 cm of its model pose, not tens of cm into the ground
-    res = sim.eval(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act), sim.pad_m(exc))
+    eps = (np.random.default_rng(i).uniform(-0.3, 1.6, (E, m)) * model.muscle_tendon_strain).astype(np.float32)
+    res = sim.eval(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act), sim.pad_m(exc), eps=sim.pad_m(eps))
     g = {k: v.double().cpu().numpy() for k, v in res.items()}
     worst = 0.0
     for e in sample_envs(E, 6, seed=i):
-        r = oracle_eval(om, DT, q[e], qd[e], act[e], exc[e])
+        r = oracle_eval(om, DT, q[e], qd[e], act[e], exc[e], eps[e])
         assert r["status"] == 0
         np.testing.assert_allclose(g["L"][e, :m], r["L"], rtol=0, atol=2e-6)
         np.testing.assert_allclose(msim.unpack_R(g["R"][e], lay, n), r["R"], rtol=0, atol=2e-6)
@@ -65,7 +69,8 @@ def test_random_model_matches_the_oracle(i):
     qo, *_ = ora.step(om, DT, q0[idx].astype(np.float64), qd0[idx].astype(np.float64), a0[idx].astype(np.float64),
                       u[idx].astype(np.float64), 30)
     err = np.abs(qg[idx] - qo).max()
-    print("\nrandom model %d: n %d, bodies %d, muscles %d, wraps %d, free root %d, spheres %d: qdd %.1e, q %.1e"
-          % (i, n, model.n_bodies, m, len(model.wrap_muscle), model.free_root, model.n_spheres, worst, err))
+    print("\nrandom model %d: n %d, bodies %d, muscles %d, wraps %d, free root %d, spheres %d, tendons %d: "
+          "qdd %.1e, q %.1e" % (i, n, model.n_bodies, m, len(model.wrap_muscle), model.free_root, model.n_spheres,
+                                int((model.muscle_tendon_strain > 0).sum()), worst, err))
     assert err <= 1e-3
     assert sim.status() == (0, 0)
