@@ -273,7 +273,7 @@ MSIM_API msim_status msim_mlp_adam(msim_mlp m, float lr, float beta1, float beta
  * The equation of motion (Methods, "Musculoskeletal dynamics") needs the muscle lengths (for l_m,
  * v_m of Eq. 1) and the moment-arm matrix J_m(q) of the muscle paths.  The paper computes them
  * from the paths; a learned map q -> (lengths, moment arms) is this library's option, with no
- * counterpart in the paper, judged against the exact path it replaces.  Single-model handles
+ * counterpart in the paper, checked against the exact path it replaces.  Single-model handles
  * only (MSIM_ERR_UNSUPPORTED otherwise).  Outputs of
  * msim_geometry / msim_surrogate_predict are rows [L (m, caller's muscle order) | R (nnz, the
  * sparse order of msim_get_layout's muscle_dof)], FP32, pitch ld_out >= m + nnz.
