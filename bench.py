@@ -122,17 +122,20 @@ def job_rate(envs_per_rank, substeps, steps, world, seconds):
     return world * envs_per_rank * substeps * steps / seconds
 
 
-def measured_traffic(envs):
-    """DRAM bytes per step launch from the committed ncu summary, or None if the kernel sources
-    changed since those counters were taken."""
+def measured_traffic(envs, workload):
+    """(DRAM bytes per step launch, kernel) of a workload from the committed ncu summaries, or
+    (None, None) if it has none or the kernel sources changed since those counters were taken.
+    The capture ran 2 substeps; the figure is scaled by environments only (a workload whose
+    state is read and written every substep, the tendon strains, moves a little more at 10)."""
     try:
         from paper_2603_29332_b300 import build
         d = json.load(open(os.path.join(ROOT, "profiles", "k_step_traffic.json")))
-        if d.get("source_digest") != build.step_digest():
-            return None
-        return d["dram_bytes_per_env_per_launch"] * envs
+        w = d["workloads"].get(workload)
+        if w is None or d.get("source_digest") != build.step_digest():
+            return None, None
+        return w["dram_bytes_per_env_per_launch"] * envs, w["kernel"]
     except Exception:
-        return None
+        return None, None
 
 
 def cpu_baseline(model, envs=512, substeps=20):
@@ -286,9 +289,10 @@ def run_gpu(args, rank, world, local_rank):
     achieved = fl * E * sub / (launch_ms * 1e-3) / 1e12
     clocks = clk.summary()
     peak_max = fp32_peak_tflops(2032.0)
+    tr, tr_kernel = measured_traffic(E, args.model)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
-            "traffic": measured_traffic(E), "traffic_unit": "bytes per launch (ncu dram read + write)",
-            "kernel": "k_step (one launch per bench step)",
+            "traffic": tr, "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "kernel": (tr_kernel or "k_step") + " (one launch per bench step)",
             "flops_per_env_substep": fl,
             "peak_note": "FP32 FMA peak 148 SMs x 128 lanes x 2 x 2032 MHz (no FP32 figure in MEASURED_PEAKS.json)"}
     if clocks:
@@ -299,13 +303,13 @@ def run_gpu(args, rank, world, local_rank):
         roof["frac_of_fma_microbenchmark"] = achieved / pk_meas
     except Exception:
         pass
-    # algorithmic HBM bytes per launch: read exc, act, q, qd; write act, force, v_m, q, qd, q_dd
-    alg = 4 * E * (5 * model.n_muscles + 5 * model.n_dofs)
+    # algorithmic HBM bytes per launch: read exc, act, q, qd; write act, force, v_m, q, qd, q_dd;
+    # compliant tendons: read and write their strains
+    alg = 4 * E * (5 * model.n_muscles + 5 * model.n_dofs) + 8 * E * int((model.muscle_tendon_strain > 0).sum())
     pk_hbm = _peaks().get("hbm_gbs", 6400.0)
     roof["hbm_algorithmic"] = {"bytes_per_launch": alg, "achieved_gbs": alg / (launch_ms * 1e-3) / 1e9,
                                "peak_gbs": pk_hbm, "frac": alg / (launch_ms * 1e-3) / 1e9 / pk_hbm,
                                "peak_note": "hbm_gbs of measured"}
-    tr = measured_traffic(E)
     if tr:
         roof["hbm"] = {"achieved_gbs": tr / (launch_ms * 1e-3) / 1e9, "peak_gbs": _peaks().get("hbm_gbs", 6400.0),
                        "frac": tr / (launch_ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6400.0),

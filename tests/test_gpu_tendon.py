@@ -171,3 +171,38 @@ def test_short_tendon_is_rejected():
     model.muscle_tendon_strain[short] = 0.04
     with pytest.raises(msim.MsimError, match="slack length"):
         msim.Sim(model, 4, dt=DT)
+
+
+def test_learned_geometry_steps_with_tendons_follow_the_exact_path_when_checked():
+    """The learned-geometry step of a model with compliant tendons: with every environment
+    checked, each substep uses the exact geometry, so positions, strains and forces equal an
+    exact-geometry twin bit for bit; unchecked learned steps advance the strains too."""
+    model = _tendon_model()
+    E, m = 256, model.n_muscles
+    sim = msim.Sim(model, E, dt=DT, seed=5)
+    sim.train_surrogate(65536, 2, batch=4096, lr=1e-3)
+    ex = msim.Sim(model, E, dt=DT, seed=5)
+    q0, qd0, a0 = mg.initial_state(model, E, seed=21)
+    for s in (sim, ex):
+        s.reset(s.pad_n(q0), s.pad_n(qd0), s.pad_m(a0))
+    exc = sim.pad_m(mg.smooth_excitations(model, E, 1, seed=21)[0])
+    sim.set_geometry_mode(1)
+    sim.surrogate_set_check(1.0, 1e-3)
+    for _ in range(4):
+        sim.step(exc, 3)
+        ex.step(exc, 3)
+    sa, sb = sim.state(), ex.state()
+    for k in ("q", "qd", "act", "qdd", "force"):
+        assert torch.equal(sa[k], sb[k]), k
+    assert torch.equal(sim.tendon_strain(), ex.tendon_strain())
+    assert float(sim.tendon_strain()[:, :m].abs().max()) > 0
+    # learned geometry without checks (a reset clears the flags the checks set): the strains of
+    # the environments inside the training box advance from the network's lengths
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    sim.surrogate_set_check(0.0, 1e-3)
+    sim.surrogate_stats(reset=True)
+    sim.step(exc, 3)
+    e1 = sim.tendon_strain()[:, :m]
+    assert sim.surrogate_stats()["learned"] > 0
+    assert bool(torch.isfinite(e1).all()) and float(e1.abs().max()) > 0
+    assert sim.status() == (0, 0)
