@@ -278,9 +278,24 @@ def run_gpu(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for t in range(k_e2e):
         sim.step_host(pinned[t % len(pinned)], sub, q_out, qd_out)
+    sync_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    # pipelined: every step still uploads its excitations and downloads q and qd, on the handle's
+    # copy streams, overlapping the neighbouring steps
+    sim.step_host_async(pinned[0], sub, q_out, qd_out)
+    sim.host_wait()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for t in range(k_e2e):
+        sim.step_host_async(pinned[t % len(pinned)], sub, q_out, qd_out)
+    sim.host_wait()
+    torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
     e2e = {"value": job_rate(E, sub, k_e2e, world, e2e_s), "unit": UNIT,
-           "h2d_bytes_per_step": E * sim.pitch_m * 4, "d2h_bytes_per_step": 2 * E * sim.pitch_n * 4}
+           "h2d_bytes_per_step": E * sim.pitch_m * 4, "d2h_bytes_per_step": 2 * E * sim.pitch_n * 4,
+           "api": "msim_step_host_async x %d, then msim_host_wait (pinned host buffers)" % k_e2e,
+           "synchronous": {"value": job_rate(E, sub, k_e2e, world, sync_s), "api": "msim_step_host"}}
     if rank != 0:
         return None
     value = job_rate(E, sub, args.steps, world, total_ms * 1e-3)

@@ -121,6 +121,20 @@ MSIM_API msim_status msim_step(msim_handle h, const float* excitations, int32_t 
 MSIM_API msim_status msim_step_host(msim_handle h, const float* excitations_host, int32_t n_substeps, float* q_host,
                            float* qd_host, msim_stream_t stream);
 
+/* msim_step_host_async -- msim_step_host, pipelined: the call returns once its work is queued.
+ *   The excitations go up on the handle's upload stream into one of two device staging buffers,
+ *   the step runs on `stream` once they have landed, q and q_d are then copied (device to
+ *   device) into one of two output staging buffers and go down on the handle's download stream.
+ *   So the copies of one call overlap the steps of its neighbours.  Call t + 2 reuses call t's
+ *   staging buffers and waits for call t's copies.  The host buffers must be pinned and left
+ *   untouched until msim_host_wait returns; q_host / qd_host (either may be NULL) receive the
+ *   state after this call's step, the calls' copies landing in call order. */
+MSIM_API msim_status msim_step_host_async(msim_handle h, const float* excitations_host, int32_t n_substeps,
+                                          float* q_host, float* qd_host, msim_stream_t stream);
+/* msim_host_wait -- block until every copy of the earlier msim_step_host_async calls (up and
+ *   down) has landed. */
+MSIM_API msim_status msim_host_wait(msim_handle h);
+
 /* msim_get_state -- copy state out (device pointers, any may be NULL):
  *   q, qd, qdd: [n_envs][pitch_n] (qdd: the accelerations of the last substep);
  *   act, muscle_force: [n_envs][pitch_m] (force: F of the last substep, Eq. 1);

@@ -75,6 +75,13 @@ struct msim_handle_ {
     float flow_dt = 0.05f, flow_sigma = 0.f;
     float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *exc_stage = nullptr;
     float* eps = nullptr;                    // [n_envs][pitch_m] tendon strains (compliant tendons)
+    // pipelined host stepping (msim_step_host_async): upload / download streams, two staging
+    // slots of excitations and of q | qd, and the events that order them
+    cudaStream_t pipe_up = nullptr, pipe_down = nullptr;
+    float* pipe_exc[2] = {};
+    float* pipe_out[2] = {};
+    cudaEvent_t pipe_in[2] = {}, pipe_used[2] = {}, pipe_snap[2] = {}, pipe_done[2] = {};
+    int pipe_slot = 0;
     uint32_t* env_status = nullptr;
     uint32_t* gflags = nullptr;
     unsigned long long* timers = nullptr;   // profiling builds (MSIM_PHASE_TIMERS) only

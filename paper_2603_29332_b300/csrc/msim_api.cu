@@ -594,6 +594,14 @@ void free_all(msim_handle h) {
         if (h->d_img[i]) cudaFree(h->d_img[i]);
     cudaFree(h->q); cudaFree(h->qd); cudaFree(h->act); cudaFree(h->qdd); cudaFree(h->force); cudaFree(h->eps);
     cudaFree(h->exc_stage); cudaFree(h->env_status); cudaFree(h->gflags); cudaFree(h->queue);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->pipe_exc[b]); cudaFree(h->pipe_out[b]);
+        h->pipe_exc[b] = h->pipe_out[b] = nullptr;
+        for (cudaEvent_t* ev : {&h->pipe_in[b], &h->pipe_used[b], &h->pipe_snap[b], &h->pipe_done[b]})
+            if (*ev) { cudaEventDestroy(*ev); *ev = nullptr; }
+    }
+    if (h->pipe_up) { cudaStreamDestroy(h->pipe_up); h->pipe_up = nullptr; }
+    if (h->pipe_down) { cudaStreamDestroy(h->pipe_down); h->pipe_down = nullptr; }
     cudaFree(h->obs); cudaFree(h->exc_policy); cudaFree(h->inv_fmax);
     if (h->timers) cudaFree(h->timers);
 }
@@ -924,6 +932,63 @@ msim_status msim_step_host(msim_handle h, const float* excitations_host, int32_t
     if (e == cudaSuccess && qd_host) e = cudaMemcpyAsync(qd_host, h->qd, rn, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_step_host D2H");
+}
+
+msim_status msim_step_host_async(msim_handle h, const float* excitations_host, int32_t n_substeps, float* q_host,
+                                 float* qd_host, msim_stream_t stream) {
+    if (!h || !excitations_host) return arg_fail(h, "msim_step_host_async: NULL argument");
+    if (n_substeps < 1 || n_substeps > 100000) return arg_fail(h, "msim_step_host_async: n_substeps must be 1..100000");
+    cudaSetDevice(h->device);
+    const size_t rm = (size_t)h->n_envs * h->pitch_m * sizeof(float);
+    const size_t rn = (size_t)h->n_envs * h->pitch_n * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (!h->pipe_up) {   // first call: streams, staging slots, events
+        e = cudaStreamCreateWithFlags(&h->pipe_up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->pipe_down, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaMalloc(&h->pipe_exc[b], rm);
+            if (e == cudaSuccess) e = cudaMalloc(&h->pipe_out[b], 2 * rn);
+            for (cudaEvent_t* ev : {&h->pipe_in[b], &h->pipe_used[b], &h->pipe_snap[b], &h->pipe_done[b]})
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "msim_step_host_async set-up");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int b = h->pipe_slot;
+    h->pipe_slot ^= 1;
+    // up: once the step two calls back has read this slot
+    e = cudaStreamWaitEvent(h->pipe_up, h->pipe_used[b], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->pipe_exc[b], excitations_host, rm, cudaMemcpyHostToDevice, h->pipe_up);
+    if (e == cudaSuccess) e = cudaEventRecord(h->pipe_in[b], h->pipe_up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->pipe_in[b], 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "msim_step_host_async upload");
+    const msim_status st = msim_step(h, h->pipe_exc[b], n_substeps, stream);
+    if (st != MSIM_OK) return st;
+    e = cudaEventRecord(h->pipe_used[b], s);
+    // snapshot of the new state into the output slot (once its previous download is done), down
+    float* oq = h->pipe_out[b];
+    float* oqd = oq + (size_t)h->n_envs * h->pitch_n;
+    if (e == cudaSuccess && (q_host || qd_host)) {
+        e = cudaStreamWaitEvent(s, h->pipe_done[b], 0);
+        if (e == cudaSuccess && q_host) e = cudaMemcpyAsync(oq, h->q, rn, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && qd_host) e = cudaMemcpyAsync(oqd, h->qd, rn, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(h->pipe_snap[b], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->pipe_down, h->pipe_snap[b], 0);
+        if (e == cudaSuccess && q_host) e = cudaMemcpyAsync(q_host, oq, rn, cudaMemcpyDeviceToHost, h->pipe_down);
+        if (e == cudaSuccess && qd_host) e = cudaMemcpyAsync(qd_host, oqd, rn, cudaMemcpyDeviceToHost, h->pipe_down);
+        if (e == cudaSuccess) e = cudaEventRecord(h->pipe_done[b], h->pipe_down);
+    }
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_step_host_async download");
+}
+
+msim_status msim_host_wait(msim_handle h) {
+    if (!h) return arg_fail(h, "msim_host_wait: NULL handle");
+    if (!h->pipe_up) return MSIM_OK;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize(h->pipe_up);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->pipe_down);
+    return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_host_wait");
 }
 
 msim_status msim_get_state(msim_handle h, float* q, float* qd, float* act, float* qdd, float* muscle_force,

@@ -90,6 +90,7 @@ class EvalOut(C.Structure):
 
 
 EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_step", "msim_step_host",
+           "msim_step_host_async", "msim_host_wait",
            "msim_get_state", "msim_get_status", "msim_clear_status", "msim_eval", "msim_get_layout",
            "msim_set_launch", "msim_gemm_bf16", "msim_mlp_create", "msim_mlp_destroy", "msim_mlp_layout",
            "msim_mlp_get", "msim_mlp_set", "msim_mlp_forward", "msim_mlp_backward", "msim_mlp_adam",
@@ -118,6 +119,8 @@ def load_library(path=LIB_PATH):
     lib.msim_reset.argtypes = [vp, vp, vp, vp, vp, C.c_int32, vp]
     lib.msim_step.argtypes = [vp, vp, C.c_int32, vp]
     lib.msim_step_host.argtypes = [vp, vp, C.c_int32, vp, vp, vp]
+    lib.msim_step_host_async.argtypes = [vp, vp, C.c_int32, vp, vp, vp]
+    lib.msim_host_wait.argtypes = [vp]
     lib.msim_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.msim_get_status.argtypes = [vp, C.POINTER(C.c_uint32)]
     lib.msim_clear_status.argtypes = [vp, vp]
@@ -301,6 +304,15 @@ class Sim:
     def step_host(self, exc_host, n_sub=1, q_host=None, qd_host=None, stream=None):
         self._check(self.lib.msim_step_host(self.h, _ptr(exc_host), int(n_sub), _ptr(q_host), _ptr(qd_host),
                                             _stream_ptr(stream)))
+
+    def step_host_async(self, exc_host, n_sub=1, q_host=None, qd_host=None, stream=None):
+        """Pipelined host stepping: queue the upload, the step and the download and return; the
+        pinned host buffers must stay untouched until :meth:`host_wait`."""
+        self._check(self.lib.msim_step_host_async(self.h, _ptr(exc_host), int(n_sub), _ptr(q_host), _ptr(qd_host),
+                                                  _stream_ptr(stream)))
+
+    def host_wait(self):
+        self._check(self.lib.msim_host_wait(self.h))
 
     def state(self, stream=None):
         import torch
