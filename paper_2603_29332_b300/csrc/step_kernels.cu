@@ -280,50 +280,41 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
     // 1. joint-angle sines and cosines, all DoFs in parallel (off the level-by-level chain)
     for (int d = g.lane; d < H.n; d += g.N) sincosf(q[d], &SC[2 * d], &SC[2 * d + 1]);
     g.sync();
-    // 2. frames, velocities and bias accelerations, root first, the bodies of a level in parallel
-    for (int l = 0; l < H.n_blevels; ++l) {
-        const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
-        for (int i = i0 + g.lane; i < i1; i += g.N) {
-            const int b = T.border[i];
-            const BodyRec& B = T.body[b];
-            float R[9], p[3], w[3], vl[3], aw[3], al[3];
-            if (B.parent < 0) {
+    // 2. frames, velocities and bias accelerations: one lane per body walks the DoF chain from
+    // the root to the body's last DoF (the ancestor table of that DoF's packed row) in
+    // registers, entering each body on the way at its joint origin.  A lane repeats its
+    // ancestors' steps in the same order as their own lanes, so every body gets the values of a
+    // root-first recursion, bit for bit, without a barrier per tree level.
+    for (int b = g.lane; b < H.nb; b += g.N) {
+        const BodyRec& Bb = T.body[b];
+        const DofRec& Dl = T.dof[Bb.dof0 + Bb.ndof - 1];
+        float R[9], p[3], w[3], vl[3], aw[3], al[3];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.f : 0.f;
-                p[0] = B.off[0]; p[1] = B.off[1]; p[2] = B.off[2];
+        for (int k = 0; k < 9; ++k) R[k] = (k % 4 == 0) ? 1.f : 0.f;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) { w[k] = 0.f; vl[k] = 0.f; aw[k] = 0.f; al[k] = -H.gravity[k]; }
-            } else {
-                const float* Fp = frame + 12 * B.parent;
+        for (int k = 0; k < 3; ++k) { p[k] = 0.f; w[k] = 0.f; vl[k] = 0.f; aw[k] = 0.f; al[k] = -H.gravity[k]; }
+        int j0 = 0, cur = -1;
+        if (H.free_root && T.anc[Dl.row] == 0) {   // the chain starts at the free root (body 0)
+            // free root (body 0, DoFs 0-5): origin at offset + q[0..2], orientation exp(q[3..5])
+            // (Rodrigues: R = I + (sin t / t) K + ((1 - cos t) / t^2) K^2, K = [r]x, with
+            // 1 - cos t = 2 sin^2(t / 2)); axes world x, y, z: slides S = [0; e], turns
+            // S = [e; p x e]
+            const BodyRec& B0 = T.body[0];
+            const float r0 = q[3], r1 = q[4], r2 = q[5];
+            const float t2 = r0 * r0 + r1 * r1 + r2 * r2, t = sqrtf(t2);
+            float sh, ch;
+            sincosf(0.5f * t, &sh, &ch);
+            const float ka = t > 1e-20f ? 2.f * sh * ch / t : 1.f;
+            const float kb = t > 1e-20f ? 2.f * sh * sh / t2 : 0.5f;
+            const float rr[3] = {r0, r1, r2};
 #pragma unroll
-                for (int k = 0; k < 9; ++k) R[k] = Fp[k];
-                rot3(R, B.off, p);
-                p[0] += Fp[9]; p[1] += Fp[10]; p[2] += Fp[11];
-                const float* Vp = V + 6 * B.parent;
-                const float* Ap = Acc + 6 * B.parent;
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    w[k] = Vp[k]; vl[k] = Vp[3 + k]; aw[k] = Ap[k]; al[k] = Ap[3 + k];
-                }
-            }
-            if (b == 0 && H.free_root) {
-                // free root: origin at offset + q[0..2], orientation exp(q[3..5]) (Rodrigues:
-                // R = I + (sin t / t) K + ((1 - cos t) / t^2) K^2, K = [r]x, with 1 - cos t =
-                // 2 sin^2(t / 2)); axes world x, y, z: slides S = [0; e], turns S = [e; p x e]
-                const float r0 = q[3], r1 = q[4], r2 = q[5];
-                const float t2 = r0 * r0 + r1 * r1 + r2 * r2, t = sqrtf(t2);
-                float sh, ch;
-                sincosf(0.5f * t, &sh, &ch);
-                const float ka = t > 1e-20f ? 2.f * sh * ch / t : 1.f;
-                const float kb = t > 1e-20f ? 2.f * sh * sh / t2 : 0.5f;
-                const float rr[3] = {r0, r1, r2};
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) R[3 * i + k] = kb * rr[i] * rr[k] + (i == k ? 1.f - kb * t2 : 0.f);
-                R[1] -= ka * r2; R[2] += ka * r1; R[3] += ka * r2; R[5] -= ka * r0; R[6] -= ka * r1; R[7] += ka * r0;
-                p[0] += q[0]; p[1] += q[1]; p[2] += q[2];
-                const float om[3] = {qd[3], qd[4], qd[5]}, vp[3] = {qd[0], qd[1], qd[2]};
+                for (int k = 0; k < 3; ++k) R[3 * i + k] = kb * rr[i] * rr[k] + (i == k ? 1.f - kb * t2 : 0.f);
+            R[1] -= ka * r2; R[2] += ka * r1; R[3] += ka * r2; R[5] -= ka * r0; R[6] -= ka * r1; R[7] += ka * r0;
+            p[0] = B0.off[0] + q[0]; p[1] = B0.off[1] + q[1]; p[2] = B0.off[2] + q[2];
+            const float om[3] = {qd[3], qd[4], qd[5]}, vp[3] = {qd[0], qd[1], qd[2]};
+            if (b == 0) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     float* St = S + 6 * i;
@@ -334,61 +325,72 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
                     St[0] = St[1] = St[2] = 0.f; St[3] = e[0]; St[4] = e[1]; St[5] = e[2];
                     Sr[0] = e[0]; Sr[1] = e[1]; Sr[2] = e[2]; Sr[3] = pe[0]; Sr[4] = pe[1]; Sr[5] = pe[2];
                 }
-                // velocity [w; v_p + p x w]; bias [0; v_p x w] (the turn axes move with the origin)
-                float pw[3], vw[3];
-                cross3(p, om, pw);
-                cross3(vp, om, vw);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { w[k] = om[k]; vl[k] = vp[k] + pw[k]; al[k] += vw[k]; }
             }
-            for (int j = 0; j < B.ndof && !(b == 0 && H.free_root); ++j) {
-                const int d = B.dof0 + j;
-                const DofRec& D = T.dof[d];
-                float s[3], ps[3];
-                rot3(R, D.axis, s);
-                cross3(p, s, ps);
-                float* Sd = S + 6 * d;
-                Sd[0] = s[0]; Sd[1] = s[1]; Sd[2] = s[2]; Sd[3] = ps[0]; Sd[4] = ps[1]; Sd[5] = ps[2];
-                const float qdj = qd[d];
-                const float sw[3] = {s[0] * qdj, s[1] * qdj, s[2] * qdj};
-                const float sl[3] = {ps[0] * qdj, ps[1] * qdj, ps[2] * qdj};
-                float c1[3], c2[3], c3[3];
-                cross3(w, sw, c1);      // a += v x (S qd)
-                cross3(w, sl, c2);
-                cross3(vl, sw, c3);
+            // velocity [w; v_p + p x w]; bias [0; v_p x w] (the turn axes move with the origin)
+            float pw[3], vw[3];
+            cross3(p, om, pw);
+            cross3(vp, om, vw);
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    aw[k] += c1[k];
-                    al[k] += c2[k] + c3[k];
-                    w[k] += sw[k];
-                    vl[k] += sl[k];
-                }
-                // R <- R Rot(axis, q) = c R + s (rows x axis) + (1 - c) (R axis) axis^T
-                const float sn = SC[2 * d], cs = SC[2 * d + 1];
-                const float* ax = D.axis;
-                const float omc = 1.f - cs;
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    const float r0 = R[3 * r], r1 = R[3 * r + 1], r2 = R[3 * r + 2];
-                    const float x0 = r1 * ax[2] - r2 * ax[1];
-                    const float x1 = r2 * ax[0] - r0 * ax[2];
-                    const float x2 = r0 * ax[1] - r1 * ax[0];
-                    R[3 * r] = cs * r0 + sn * x0 + omc * s[r] * ax[0];
-                    R[3 * r + 1] = cs * r1 + sn * x1 + omc * s[r] * ax[1];
-                    R[3 * r + 2] = cs * r2 + sn * x2 + omc * s[r] * ax[2];
-                }
-            }
-            float* Fb = frame + 12 * b;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) Fb[k] = R[k];
-            Fb[9] = p[0]; Fb[10] = p[1]; Fb[11] = p[2];
-            float* Vb = V + 6 * b;
-            float* Ab = Acc + 6 * b;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) { Vb[k] = w[k]; Vb[3 + k] = vl[k]; Ab[k] = aw[k]; Ab[3 + k] = al[k]; }
+            for (int k = 0; k < 3; ++k) { w[k] = om[k]; vl[k] = vp[k] + pw[k]; al[k] += vw[k]; }
+            j0 = 6;
+            cur = 0;
         }
-        g.sync();
+        const int own0 = Dl.depth + 1 - Bb.ndof;   // chain position of the body's first DoF
+        for (int j = j0; j <= Dl.depth; ++j) {
+            const int d = T.anc[Dl.row + j];
+            const DofRec& D = T.dof[d];
+            if (D.body != cur) {   // entering the next body: its joint origin in the parent frame
+                cur = D.body;
+                float o[3];
+                rot3(R, T.body[cur].off, o);
+                p[0] += o[0]; p[1] += o[1]; p[2] += o[2];
+            }
+            float sv[3], ps[3];
+            rot3(R, D.axis, sv);
+            cross3(p, sv, ps);
+            if (j >= own0) {
+                float* Sd = S + 6 * d;
+                Sd[0] = sv[0]; Sd[1] = sv[1]; Sd[2] = sv[2]; Sd[3] = ps[0]; Sd[4] = ps[1]; Sd[5] = ps[2];
+            }
+            const float qdj = qd[d];
+            const float sw[3] = {sv[0] * qdj, sv[1] * qdj, sv[2] * qdj};
+            const float sl[3] = {ps[0] * qdj, ps[1] * qdj, ps[2] * qdj};
+            float c1[3], c2[3], c3[3];
+            cross3(w, sw, c1);      // a += v x (S qd)
+            cross3(w, sl, c2);
+            cross3(vl, sw, c3);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                aw[k] += c1[k];
+                al[k] += c2[k] + c3[k];
+                w[k] += sw[k];
+                vl[k] += sl[k];
+            }
+            // R <- R Rot(axis, q) = c R + s (rows x axis) + (1 - c) (R axis) axis^T
+            const float sn = SC[2 * d], cs = SC[2 * d + 1];
+            const float* ax = D.axis;
+            const float omc = 1.f - cs;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float r0 = R[3 * r], r1 = R[3 * r + 1], r2 = R[3 * r + 2];
+                const float x0 = r1 * ax[2] - r2 * ax[1];
+                const float x1 = r2 * ax[0] - r0 * ax[2];
+                const float x2 = r0 * ax[1] - r1 * ax[0];
+                R[3 * r] = cs * r0 + sn * x0 + omc * sv[r] * ax[0];
+                R[3 * r + 1] = cs * r1 + sn * x1 + omc * sv[r] * ax[1];
+                R[3 * r + 2] = cs * r2 + sn * x2 + omc * sv[r] * ax[2];
+            }
+        }
+        float* Fb = frame + 12 * b;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Fb[k] = R[k];
+        Fb[9] = p[0]; Fb[10] = p[1]; Fb[11] = p[2];
+        float* Vb = V + 6 * b;
+        float* Ab = Acc + 6 * b;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { Vb[k] = w[k]; Vb[3 + k] = vl[k]; Ab[k] = aw[k]; Ab[3 + k] = al[k]; }
     }
+    g.sync();
     SUB_MARK(15);   // profiling builds: sines, cosines and the recursion
     // 3. spatial inertia and body force of every body, all bodies in parallel
     for (int b = g.lane; b < H.nb; b += g.N) {
