@@ -111,7 +111,11 @@ struct alignas(16) ImgHeader {
     int32_t n_wraps;            // wrapping cylinders (their records follow the via points)
     float ft_den;               // e^3 - 4 of the tendon curve's toe
     float ft_slope;             // slope of the tendon curve's linear part (per unit eps / eps0)
-    float pad[3];
+    // body chains (maximal runs of single-child bodies) for the subtree sums: at o_chain,
+    // int16 round starts [n_crounds + 1] (indices into the chains, a round's chains hang only
+    // below chains of earlier rounds), int16 chain starts [n_chains + 1] (indices into the body
+    // list), uint8 bodies [nb] (each chain bottom to top)
+    int32_t o_chain, n_crounds, n_chains;
 };
 
 // Models with wrapping surfaces or compliant tendons take the step variants that compile those

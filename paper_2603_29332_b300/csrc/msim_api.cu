@@ -126,6 +126,46 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             if (d.body_parent[c] == b) child.push_back((uint8_t)c);
         nchild[b] = (int)child.size() - child0[b];
     }
+    // body chains for the subtree sums: maximal runs of single-child bodies, bottom to top, in
+    // rounds (a chain whose bottom has children comes after the chains hanging below it)
+    std::vector<int16_t> cround, cstart;
+    std::vector<uint8_t> cbody;
+    {
+        std::vector<std::vector<int>> chains;
+        std::vector<int> top_of(nb, -1);
+        for (int t = 0; t < nb; ++t) {
+            const int pb = d.body_parent[t];
+            if (pb >= 0 && nchild[pb] == 1) continue;   // not a chain top
+            std::vector<int> path{t};
+            while (nchild[path.back()] == 1) path.push_back(child[child0[path.back()]]);
+            std::reverse(path.begin(), path.end());
+            top_of[t] = (int)chains.size();
+            chains.push_back(path);
+        }
+        std::vector<int> rnd(chains.size(), -1);
+        // bodies are numbered parents first, so chains whose top has the larger index are deeper:
+        // resolve rounds from the last chain top backwards
+        std::vector<int> order(chains.size());
+        for (size_t c = 0; c < chains.size(); ++c) order[c] = (int)c;
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return chains[a].back() > chains[b].back(); });
+        for (int c : order) {
+            const int bot = chains[c][0];
+            int r = 0;
+            for (int k = 0; k < nchild[bot]; ++k) r = std::max(r, 1 + rnd[top_of[child[child0[bot] + k]]]);
+            rnd[c] = r;
+        }
+        const int nr = chains.empty() ? 0 : *std::max_element(rnd.begin(), rnd.end()) + 1;
+        for (int r = 0; r < nr; ++r) {
+            cround.push_back((int16_t)(cstart.size()));
+            for (size_t c = 0; c < chains.size(); ++c)
+                if (rnd[c] == r) {
+                    cstart.push_back((int16_t)cbody.size());
+                    for (int b : chains[c]) cbody.push_back((uint8_t)b);
+                }
+        }
+        cround.push_back((int16_t)cstart.size());
+        cstart.push_back((int16_t)cbody.size());
+    }
     // DoF levels
     const int n_dl = max_depth + 1;
     std::vector<uint8_t> dorder;
@@ -386,6 +426,9 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.o_anc = place(anc.size());
     h.o_dorder = place(dorder.size());
     h.o_dlevel = place(sizeof(int16_t) * dlevel.size());
+    h.n_crounds = (int32_t)cround.size() - 1;
+    h.n_chains = (int32_t)cstart.size() - 1;
+    h.o_chain = place(sizeof(int16_t) * (cround.size() + cstart.size()) + cbody.size());
     h.o_tri = place(sizeof(uint16_t) * tri.size());
     h.o_rowanc = place(sizeof(uint16_t) * rowanc.size());
     h.o_crba = place(crba_order.size());
@@ -456,6 +499,9 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     put(h.o_anc, anc.data(), anc.size());
     put(h.o_dorder, dorder.data(), dorder.size());
     put(h.o_dlevel, dlevel.data(), sizeof(int16_t) * dlevel.size());
+    put(h.o_chain, cround.data(), sizeof(int16_t) * cround.size());
+    put(h.o_chain + (int32_t)(sizeof(int16_t) * cround.size()), cstart.data(), sizeof(int16_t) * cstart.size());
+    put(h.o_chain + (int32_t)(sizeof(int16_t) * (cround.size() + cstart.size())), cbody.data(), cbody.size());
     put(h.o_tri, tri.data(), sizeof(uint16_t) * tri.size());
     put(h.o_rowanc, rowanc.data(), sizeof(uint16_t) * rowanc.size());
     put(h.o_crba, crba_order.data(), crba_order.size());

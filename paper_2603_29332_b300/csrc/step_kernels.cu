@@ -72,6 +72,9 @@ struct Tables {
     const uint16_t* rowanc;
     const uint8_t* crba_order;
     const TendonRec* ten;       // null: every tendon rigid
+    const int16_t* cround;      // body chains of the subtree sums (ImgHeader::o_chain)
+    const int16_t* cstart;
+    const uint8_t* cbody;
 };
 
 __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
@@ -95,6 +98,9 @@ __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     t.rowanc = reinterpret_cast<const uint16_t*>(img + h.o_rowanc);
     t.crba_order = img + h.o_crba;
     t.ten = h.n_tendons ? reinterpret_cast<const TendonRec*>(img + h.o_tendon) : nullptr;
+    t.cround = reinterpret_cast<const int16_t*>(img + h.o_chain);
+    t.cstart = t.cround + h.n_crounds + 1;
+    t.cbody = reinterpret_cast<const uint8_t*>(t.cstart + h.n_chains + 1);
     return t;
 }
 
@@ -491,23 +497,26 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     const float* S = ws + H.w_S;
     float* rhs = ws + H.w_rhs;
     int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
-    // subtree sums leaves first; every body's 16 components (force 6, float-float inertia 10) go
-    // to their own lanes, so a level costs one chain of child additions per component
-    for (int l = H.n_blevels - 1; l >= 0; --l) {
-        const int i0 = T.blevel[l], i1 = T.blevel[l + 1];
-        for (int t = g.lane; t < 16 * (i1 - i0); t += g.N) {
-            const int b = T.border[i0 + t / 16], comp = t % 16;
-            const BodyRec& B = T.body[b];
-            if (comp < 6) {
-                df f = FB[6 * b + comp];
-                for (int c = 0; c < B.nchild; ++c) f = df_add(f, FB[6 * T.child[B.child0 + c] + comp]);
-                FB[6 * b + comp] = f;
-            } else {
-                df* Io = reinterpret_cast<df*>(FI + kFiStride * b) + (comp - 6);
-                df I = *Io;
-                for (int c = 0; c < B.nchild; ++c)
-                    I = df_add(I, reinterpret_cast<const df*>(FI + kFiStride * T.child[B.child0 + c])[comp - 6]);
-                *Io = I;
+    // subtree sums, leaves first, along the body chains (maximal runs of single-child bodies):
+    // every chain's 16 components (force 6, float-float inertia 10) go to their own lanes, which
+    // walk the chain bottom to top carrying the running sum; the bottom body adds its children
+    // (tops of chains of earlier rounds), so a round costs one barrier.  Each body's sum is its
+    // own term plus its children's sums in child order, as a leaves-first level pass would add.
+    for (int r = 0; r < H.n_crounds; ++r) {
+        const int c0 = T.cround[r], c1 = T.cround[r + 1];
+        for (int t = g.lane; t < 16 * (c1 - c0); t += g.N) {
+            const int c = c0 + t / 16, comp = t % 16;
+            const int j0 = T.cstart[c], j1 = T.cstart[c + 1];
+            df* base = comp < 6 ? FB + comp : reinterpret_cast<df*>(FI) + (comp - 6);
+            const int stride = comp < 6 ? 6 : kFiStride / 2;   // df entries per body
+            const BodyRec& Bb = T.body[T.cbody[j0]];
+            df f = base[stride * T.cbody[j0]];
+            for (int k = 0; k < Bb.nchild; ++k) f = df_add(f, base[stride * T.child[Bb.child0 + k]]);
+            base[stride * T.cbody[j0]] = f;
+            for (int j = j0 + 1; j < j1; ++j) {
+                const int b = T.cbody[j];
+                f = df_add(base[stride * b], f);
+                base[stride * b] = f;
             }
         }
         g.sync();
