@@ -43,7 +43,8 @@ struct alignas(16) MuscleRec {  // 32 B
     float inv_lopt;             // 1 / l_opt
     float L0;                   // reference length L(q = 0), filled on the device at create
     float inv_vmax;             // 1 / (vmax_per_lopt * l_opt)
-    int32_t p0;                 // first path point
+    int32_t p0;                 // first path point; point j at p0 + 32 j (the point table holds
+                                // the points of each group of 32 records interleaved)
     int32_t x0;                 // first entry in the crossed-DoF table (== offset in sparse R)
     uint8_t np, nx;             // number of points, number of crossed DoFs
     uint8_t dep0;               // depth of the first crossed DoF (the others follow it, +1 each)

@@ -347,6 +347,26 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         for (int k = 0; k < m; ++k) sorted[k] = mus[order[k]];
         mus.swap(sorted);
     }
+    // via points interleaved by groups of 32 muscle records (the muscles one warp handles in one
+    // pass): point j of record r at group base + 32 j + r % 32, so that a warp's loads of point j
+    // are one contiguous run
+    int np_lay = 0;
+    {
+        std::vector<PointRec> lay;
+        for (int g0 = 0; g0 < m; g0 += 32) {
+            int npg = 0;
+            for (int r = g0; r < std::min(m, g0 + 32); ++r) npg = std::max(npg, (int)mus[r].np);
+            const int base = (int)lay.size();
+            lay.resize(base + 32 * npg);
+            for (int r = g0; r < std::min(m, g0 + 32); ++r) {
+                const int src = mus[r].p0;
+                for (int j = 0; j < mus[r].np; ++j) lay[base + 32 * j + (r - g0)] = pts[src + j];
+                mus[r].p0 = base + (r - g0);
+            }
+        }
+        pts.swap(lay);
+        np_lay = (int)pts.size();
+    }
     std::vector<TendonRec> tens(n_ten ? m : 0);
     for (int r = 0; r < (int)tens.size(); ++r) {
         const int k = mus[r].orig;
@@ -435,7 +455,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     // last: the sections that may stay in global memory (staged_bytes in image.h)
     h.o_muscle = place(sizeof(MuscleRec) * m);
     h.o_cross = place(sizeof(uint32_t) * cross.size());
-    h.o_point = place(sizeof(PointRec) * np);
+    h.o_point = place(sizeof(PointRec) * np_lay);
     h.o_wrap = place(sizeof(WrapRec) * std::max(nw, 1));
     h.n_tendons = n_ten;
     h.o_tendon = n_ten ? place(sizeof(TendonRec) * m) : 0;
@@ -488,7 +508,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     put(h.o_body, bodies.data(), sizeof(BodyRec) * nb);
     put(h.o_dof, dofs.data(), sizeof(DofRec) * n);
     put(h.o_muscle, mus.data(), sizeof(MuscleRec) * m);
-    put(h.o_point, pts.data(), sizeof(PointRec) * np);
+    put(h.o_point, pts.data(), sizeof(PointRec) * np_lay);
     if (nw > 0) put(h.o_wrap, wraps.data(), sizeof(WrapRec) * nw);
     if (n_ten) put(h.o_tendon, tens.data(), sizeof(TendonRec) * m);
     put(h.o_sphere, sph.data(), sizeof(SphereRec) * ns);

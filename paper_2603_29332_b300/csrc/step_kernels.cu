@@ -804,7 +804,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             };
             const int wseg = (has_ext(MODE) && M.wrap) ? ((T.wrap[M.wrap - 1].body_cross >> 16) & 0xff) : 0;
             for (int j = 1; j < M.np; ++j) {
-                P = T.pt[M.p0 + j];
+                P = T.pt[M.p0 + 32 * j];   // points interleaved by groups of 32 records
                 b = P.body_cross & 0xff;
                 const int c = P.body_cross >> 8;
                 fb = frame + 12 * b;
