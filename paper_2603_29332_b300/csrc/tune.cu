@@ -157,7 +157,8 @@ namespace {
 
 // Saves the handle's state buffers so that timed launches leave no trace.
 struct Snapshot {
-    float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr;
+    float *q = nullptr, *qd = nullptr, *act = nullptr, *qdd = nullptr, *force = nullptr, *eps = nullptr,
+          *vm = nullptr;
     uint32_t *st = nullptr, *gf = nullptr;
     size_t rn = 0, rm = 0, ne = 0;
     cudaError_t take(msim_handle h, cudaStream_t s) {
@@ -169,6 +170,8 @@ struct Snapshot {
         if (e == cudaSuccess) e = cudaMalloc(&qdd, rn);
         if (e == cudaSuccess) e = cudaMalloc(&act, rm);
         if (e == cudaSuccess) e = cudaMalloc(&force, rm);
+        if (e == cudaSuccess) e = cudaMalloc(&eps, rm);
+        if (e == cudaSuccess && h->vm) e = cudaMalloc(&vm, rm);
         if (e == cudaSuccess) e = cudaMalloc(&st, ne);
         if (e == cudaSuccess) e = cudaMalloc(&gf, 4);
         if (e == cudaSuccess) e = copy(h, true, s);
@@ -183,12 +186,15 @@ struct Snapshot {
         if (e == cudaSuccess) e = cp(qdd, h->qdd, rn);
         if (e == cudaSuccess) e = cp(act, h->act, rm);
         if (e == cudaSuccess) e = cp(force, h->force, rm);
+        if (e == cudaSuccess) e = cp(eps, h->eps, rm);   // tendon strains: state like q and act
+        if (e == cudaSuccess && vm) e = cp(vm, h->vm, rm);
         if (e == cudaSuccess) e = cp(st, h->env_status, ne);
         if (e == cudaSuccess) e = cp(gf, h->gflags, 4);
         return e;
     }
     ~Snapshot() {
-        cudaFree(q); cudaFree(qd); cudaFree(qdd); cudaFree(act); cudaFree(force); cudaFree(st); cudaFree(gf);
+        cudaFree(q); cudaFree(qd); cudaFree(qdd); cudaFree(act); cudaFree(force); cudaFree(eps); cudaFree(vm);
+        cudaFree(st); cudaFree(gf);
     }
 };
 

@@ -206,3 +206,22 @@ def test_learned_geometry_steps_with_tendons_follow_the_exact_path_when_checked(
     assert sim.surrogate_stats()["learned"] > 0
     assert bool(torch.isfinite(e1).all()) and float(e1.abs().max()) > 0
     assert sim.status() == (0, 0)
+
+
+def test_autotune_keeps_the_strain_state():
+    """The autotuner times real steps on the handle's environments and restores their state,
+    tendon strains included (a tuner that left its strains behind under the restored positions
+    sent later rollouts elsewhere)."""
+    model = _tendon_model()
+    E = 256
+    sim = msim.Sim(model, E, dt=DT)
+    q0, qd0, a0 = mg.initial_state(model, E, seed=8)
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    sim.step(sim.pad_m(mg.smooth_excitations(model, E, 1, seed=8)[0]), 5)
+    before, eb = sim.state(), sim.tendon_strain()
+    assert float(eb.abs().max()) > 0
+    sim.autotune(None, n_sub=3)
+    after, ea = sim.state(), sim.tendon_strain()
+    for k in ("q", "qd", "act", "qdd", "force", "status"):
+        assert torch.equal(before[k], after[k]), k
+    assert torch.equal(eb, ea)
