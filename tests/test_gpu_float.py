@@ -171,3 +171,45 @@ def test_ball_on_the_ground_contact_closed_forms():
     zT = (r - m * g / k) + (x0 - B) * math.exp(s1 * n * dt) + B * math.exp(s2 * n * dt)
     print("\nball drop: z after 10 ms %.7f m, closed form %.7f m" % (zg, zT))
     assert abs(zg - zT) < 5e-6
+
+
+def _two_roots():
+    """Body 0 on a free root with a child; body 1 a second root on a hinge, with a child."""
+    base = mg.make_model("tworoots", [-1, -1, 1, 0], [1, 1, 1, 1],
+                         [[0, 0, 1.0], [1.0, 0, 1.0], [0, 0, -0.4], [0.1, 0, -0.2]],
+                         [2.0, 1.5, 1.0, 0.8],
+                         [[0, 0, 0], [0, 0, -0.2], [0, 0, -0.2], [0, 0, -0.1]],
+                         [[0.02, 0.02, 0.02, 0, 0, 0], [0.03, 0.03, 0.01, 0, 0, 0], [0.02, 0.02, 0.01, 0, 0, 0],
+                          [0.01, 0.01, 0.005, 0, 0, 0]],
+                         [[0, 0, 1], [0, 0, 1], [0, 1, 0], [1, 0, 0]],
+                         muscle_points=[[(1, (0.05, 0, -0.1)), (2, (0.05, 0, -0.2))],
+                                        [(0, (0.0, 0.08, 0.0)), (3, (0.0, 0.05, -0.05))]],
+                         muscle_fmax=[200.0, 100.0], muscle_lopt=[0.1, 0.08])
+    return mg.with_free_root(base)
+
+
+def test_a_fixed_second_root_beside_the_free_root():
+    """Only the chains that start at the free root take its transform: the second root's
+    bodies stay on their fixed hinge (one substep at random states and 50 substeps)."""
+    model = _two_roots()
+    om = ora.OracleModel(model)
+    E, n, m = 64, model.n_dofs, model.n_muscles
+    sim = msim.Sim(model, E, dt=DT)
+    lay = sim.layout(0)
+    q, qd, act, exc = random_states(model, E, seed=12, q_scale=0.6)
+    res = sim.eval(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act), sim.pad_m(exc))
+    g = {k: v.double().cpu().numpy() for k, v in res.items()}
+    for e in sample_envs(E, 12, seed=3):
+        r = oracle_eval(om, DT, q[e], qd[e], act[e], exc[e])
+        np.testing.assert_allclose(g["L"][e, :m], r["L"], rtol=0, atol=2e-6)
+        np.testing.assert_allclose(msim.unpack_R(g["R"][e], lay, n), r["R"], rtol=0, atol=2e-6)
+        np.testing.assert_allclose(msim.unpack_packed(g["M"][e], lay), r["M"], rtol=0, atol=2e-6 * np.abs(r["M"]).max())
+        assert qdd_rel_err(g["qdd"][e, :n], r["qdd"]) <= 1e-4
+    sim.reset(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act))
+    sim.step(sim.pad_m(exc), 50)
+    qg = sim.state()["q"][:, :n].double().cpu().numpy()
+    idx = sample_envs(E, 6, seed=4)
+    qo, *_ = ora.step(om, DT, q[idx].astype(np.float64), qd[idx].astype(np.float64), act[idx].astype(np.float64),
+                      exc[idx].astype(np.float64), 50)
+    assert np.abs(qg[idx] - qo).max() <= 1e-3
+    assert sim.status() == (0, 0)
