@@ -28,6 +28,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "image.h"
 #include "kernels.h"
@@ -1155,24 +1157,33 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
             const DofRec& D = T.dof[k];
             const int np = D.depth * (D.depth + 1) / 2;
             const fac* Lk = A + D.row;
-            for (int p0 = g.lane; p0 < np; p0 += kElimU * g.N) {
-                fac* tg[kElimU];
-                fac av[kElimU], xv[kElimU], yv[kElimU];
+            // U targets per lane per iteration, U as small as the node's triangle allows (the
+            // group's lanes share the node, so the choice is uniform): a shallow node does not
+            // issue updates for lanes that have none
+            auto eliminate = [&](auto u_count) {
+                constexpr int U = decltype(u_count)::value;
+                for (int p0 = g.lane; p0 < np; p0 += U * g.N) {
+                    fac* tg[U];
+                    fac av[U], xv[U], yv[U];
 #pragma unroll
-                for (int u = 0; u < kElimU; ++u) {
-                    const int p = p0 + g.N * u;
-                    const int tv = T.tri[p < np ? p : 0];
-                    const int ja = tv & 0xff, jb = tv >> 8;      // jb <= ja < depth
-                    tg[u] = &A[T.rowanc[D.row + ja] + jb];
-                    xv[u] = Lk[ja];
-                    yv[u] = Lk[jb];
+                    for (int u = 0; u < U; ++u) {
+                        const int p = p0 + g.N * u;
+                        const int tv = T.tri[p < np ? p : 0];
+                        const int ja = tv & 0xff, jb = tv >> 8;      // jb <= ja < depth
+                        tg[u] = &A[T.rowanc[D.row + ja] + jb];
+                        xv[u] = Lk[ja];
+                        yv[u] = Lk[jb];
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) av[u] = *tg[u];
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (p0 + g.N * u < np) *tg[u] = fac_fms(av[u], xv[u], yv[u]);
                 }
-#pragma unroll
-                for (int u = 0; u < kElimU; ++u) av[u] = *tg[u];
-#pragma unroll
-                for (int u = 0; u < kElimU; ++u)
-                    if (p0 + g.N * u < np) *tg[u] = fac_fms(av[u], xv[u], yv[u]);
-            }
+            };
+            if (np <= g.N) eliminate(std::integral_constant<int, 1>{});
+            else if (np <= 2 * g.N) eliminate(std::integral_constant<int, 2>{});
+            else eliminate(std::integral_constant<int, kElimU>{});
             const fac yk = Y[k];
             for (int j = g.lane; j < D.depth; j += g.N) {
                 fac* t = &Y[T.anc[D.row + j]];
