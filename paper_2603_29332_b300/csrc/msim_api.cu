@@ -604,9 +604,12 @@ int max_epb(msim_handle h, int i, int stage, int wpe) {
 // staging levels 0 and 2) only when that is needed for the chosen count.
 void auto_launch(msim_handle h, int i) {
     const int ne = std::max(1, h->env_begin[i + 1] - h->env_begin[i]);
-    const int w = 2;
-    int stage_of[9], per_sm_of[9], cmax = 0;
-    for (int e = 1; e <= 8; ++e) {
+    // one warp per environment for small skeletons (what the autotuner picks for the 30- and
+    // 40-DoF bodies), two for larger ones
+    const int w = h->models[i].hdr.n <= 48 ? 1 : 2;
+    const int emax = w == 1 ? 16 : 8;
+    int stage_of[17], per_sm_of[17], cmax = 0;
+    for (int e = 1; e <= emax; ++e) {
         stage_of[e] = -1;
         per_sm_of[e] = 0;
         if (e > ne) continue;
@@ -619,7 +622,7 @@ void auto_launch(msim_handle h, int i) {
     }
     int best_e = 1;
     long best_load = -1, best_c = 0;
-    for (int e = 1; e <= 8; ++e) {
+    for (int e = 1; e <= emax; ++e) {
         if (stage_of[e] < 0) continue;
         const long c = (long)e * per_sm_of[e];
         if (100 * c < 85L * cmax) continue;
