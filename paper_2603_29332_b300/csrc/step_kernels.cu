@@ -782,6 +782,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
         if (!learned || sc->check) {
             // exact via-point geometry: L = sum |x_{j+1} - x_j|, R = -dL/dq of the crossed DoFs
             PointRec P = T.pt[M.p0];
+            PointRec Pn = T.pt[M.p0 + 32];   // the next point is loaded one segment ahead
             int b = P.body_cross & 0xff;
             int cprev = P.body_cross >> 8;
             const float* fb = frame + 12 * b;
@@ -806,7 +807,8 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             };
             const int wseg = (has_ext(MODE) && M.wrap) ? ((T.wrap[M.wrap - 1].body_cross >> 16) & 0xff) : 0;
             for (int j = 1; j < M.np; ++j) {
-                P = T.pt[M.p0 + 32 * j];   // points interleaved by groups of 32 records
+                P = Pn;   // points interleaved by groups of 32 records: point j at p0 + 32 j
+                if (j + 1 < M.np) Pn = T.pt[M.p0 + 32 * (j + 1)];
                 b = P.body_cross & 0xff;
                 const int c = P.body_cross >> 8;
                 fb = frame + 12 * b;
