@@ -94,6 +94,12 @@ typedef struct {
      * d eps/dt = (dL/dt - v_max v_m) / l_s, and the skeleton receives the tendon force at the
      * new strain, its dL/dt derivative taken into the implicit damping. */
     const float* muscle_tendon_strain; /* [n_muscles] or NULL */
+    /* onset width of the joint-limit penalty, rad (>= 0): over the first limit_delta of the
+     * excess x past a limit the spring torque grows as limit_k x^2 / (2 limit_delta) and the
+     * damper as limit_c x / limit_delta; beyond, limit_k (x - limit_delta / 2) and limit_c.  The
+     * torque and its derivatives in q and qd are then continuous at the limit, so the linearly
+     * implicit step has no jump there.  0 = the plain penalty limit_k x, limit_c. */
+    float limit_delta;
 } msim_model_desc;
 
 #ifdef __cplusplus

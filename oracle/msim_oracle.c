@@ -64,9 +64,10 @@ typedef struct {
     const int* wrap_kind;   /* per wrap: 0 cylinder, 1 sphere (wrap_axis unused); NULL: cylinders */
     /* per muscle: tendon strain at F_max (> 0: compliant tendon, below; 0: rigid); NULL: all rigid */
     const double* tendon_strain;
+    double limit_delta;   /* onset width of the joint-limit penalty (ora_joint_limits) */
 } ora_model;
 
-int ora_abi_version(void) { return 7; }
+int ora_abi_version(void) { return 9; }
 
 /* DoF kinds: a translation of the free root (its point Jacobian is the axis itself), else a
  * rotation about the axis s_d through o_d (point Jacobian s_d x (x - o_d)). */
@@ -609,19 +610,30 @@ void ora_contact(const ora_model* M, const double* Rb, const double* pb, const d
 }
 
 /* ---------------------------------------------------------------- joint limits and damping
- * Outside [lo, hi] (enabled when lo < hi) a penalty spring-damper acts, taken linearly implicit in
- * position and velocity: its torque is evaluated at the end-of-step state predicted by
- * qd' = qd + dt qdd, q' = q + dt qd', i.e. tau = -k_l (q - hi + dt qd') - c_l qd' above hi (and
- * symmetrically below lo).  The explicit part goes to tau_l, the part proportional to qdd to Dj
- * (the system matrix receives dt * Dj = dt c_l + dt^2 k_l).  Joint damping: tau -= b qd, Dj += b. */
+ * Outside [lo, hi] (enabled when lo < hi) a penalty spring-damper acts on the excess x past the
+ * limit.  Spring torque k_l phi(x), damper c_l psi(x) qd, with a smooth onset of width delta:
+ *   phi(x) = x^2 / (2 delta), psi(x) = x / delta     for 0 < x < delta,
+ *   phi(x) = x - delta / 2,   psi(x) = 1             for x >= delta,
+ * so phi' = psi, and torque, phi' and psi are continuous in x (delta = 0: the plain penalty k_l x,
+ * c_l).  Linearly implicit in position and velocity: the spring is taken at the end-of-step excess
+ * x' = x + dt qd' (above hi; x - dt qd' below lo) to first order, phi(x') = phi(x) + psi(x) dt qd',
+ * and the damper at the new velocity qd' = qd + dt qdd, so above hi
+ *   tau = -k_l phi(x) - (k_l dt + c_l) psi(x) qd'
+ * (below lo the spring term changes sign).  The explicit part goes to tau_l, the coefficient of
+ * qd' to Dj (the system matrix receives dt * Dj).  Joint damping: tau -= b qd, Dj += b. */
 void ora_joint_limits(const ora_model* M, double dt, const double* q, const double* qd, double* tau_l, double* Dj) {
     for (int d = 0; d < M->n; ++d) {
         double lo = M->dof_limit[2 * d], hi = M->dof_limit[2 * d + 1];
         double t = -M->dof_damping[d] * qd[d], dd = M->dof_damping[d];
-        double kk = M->limit_k, cc = M->limit_c;
-        if (lo < hi) {
-            if (q[d] > hi) { t += -kk * (q[d] - hi) - (kk * dt + cc) * qd[d]; dd += cc + kk * dt; }
-            else if (q[d] < lo) { t += kk * (lo - q[d]) - (kk * dt + cc) * qd[d]; dd += cc + kk * dt; }
+        double kk = M->limit_k, cc = M->limit_c, del = M->limit_delta;
+        if (lo < hi && (q[d] > hi || q[d] < lo)) {
+            double x = q[d] > hi ? q[d] - hi : lo - q[d];
+            double phi, psi;
+            if (del > 0.0 && x < del) { phi = 0.5 * x * x / del; psi = x / del; }
+            else { phi = x - 0.5 * del; psi = 1.0; }
+            double spring = kk * phi, kd = (kk * dt + cc) * psi;
+            t += (q[d] > hi ? -spring : spring) - kd * qd[d];
+            dd += kd;
         }
         tau_l[d] = t;
         if (Dj) Dj[d] = dd;
@@ -682,9 +694,24 @@ typedef struct {
         *sphere_force, *eps_next;
 } ora_eval_out;
 
-/* eps: tendon strains [m] (NULL: zero); only compliant muscles read theirs */
+/* eps: tendon strains [m] (NULL: zero); only compliant muscles read theirs.
+ * L_in [m], R_in [m][n] (either may be NULL): muscle-tendon lengths and moment arms to use in
+ * place of the via-point geometry at q, for a substep driven by an approximation of J_m(q) (a
+ * learned geometry); everything downstream of the geometry (fibre state, Eq. 1, R^T F, the
+ * implicit damping R^T diag(dF/dLdot) R over the non-zero entries of each row, contact, limits,
+ * Newton-Euler, Cholesky) is the same as for the exact geometry. */
+int ora_eval_geom(const ora_model* M, const double* L0, double dt, const double* q, const double* qd,
+                  const double* act, const double* exc, const double* eps, const double* L_in,
+                  const double* R_in, const ora_eval_out* out);
+
 int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, const double* qd,
              const double* act, const double* exc, const double* eps, const ora_eval_out* out) {
+    return ora_eval_geom(M, L0, dt, q, qd, act, exc, eps, NULL, NULL, out);
+}
+
+int ora_eval_geom(const ora_model* M, const double* L0, double dt, const double* q, const double* qd,
+                  const double* act, const double* exc, const double* eps, const double* L_in,
+                  const double* R_in, const ora_eval_out* out) {
     int nb = M->nb, n = M->n, m = M->m;
     double* Rb = malloc(sizeof(double) * 9 * nb);
     double* pb = malloc(sizeof(double) * 3 * nb);
@@ -712,6 +739,8 @@ int ora_eval(const ora_model* M, const double* L0, double dt, const double* q, c
 
     ora_fk(M, q, Rb, pb, s, o);
     ora_muscle_geometry(M, Rb, pb, s, o, L, R);
+    if (L_in) memcpy(L, L_in, sizeof(double) * m);
+    if (R_in) memcpy(R, R_in, sizeof(double) * (size_t)m * n);
     for (int k = 0; k < m; ++k) {
         const double* row = R + (size_t)k * n;
         double ldot = 0.0;

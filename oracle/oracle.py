@@ -41,7 +41,7 @@ class _OraModel(C.Structure):
                 ("implicit_damping", C.c_int),
                 ("nw", C.c_int), ("wrap_muscle", _ip), ("wrap_segment", _ip), ("wrap_body", _ip),
                 ("wrap_center", _dp), ("wrap_axis", _dp), ("wrap_radius", _dp),
-                ("free_root", C.c_int), ("wrap_kind", _ip), ("tendon_strain", _dp)]
+                ("free_root", C.c_int), ("wrap_kind", _ip), ("tendon_strain", _dp), ("limit_delta", C.c_double)]
 
 
 class _EvalOut(C.Structure):
@@ -64,7 +64,7 @@ def lib():
         build()
         _lib = C.CDLL(_LIB)
         _lib.ora_abi_version.restype = C.c_int
-        if _lib.ora_abi_version() != 7:
+        if _lib.ora_abi_version() != 9:
             raise RuntimeError("stale oracle library: rebuild with oracle.build(force=True)")
         for name in ("ora_fl", "ora_fp", "ora_fv", "ora_dfv", "ora_dfl", "ora_dfp", "ora_ft", "ora_dft"):
             getattr(_lib, name).restype = C.c_double
@@ -72,6 +72,7 @@ def lib():
         _lib.ora_act_rate.restype = C.c_double
         _lib.ora_act_rate.argtypes = [C.c_double] * 4
         _lib.ora_eval.restype = C.c_int
+        _lib.ora_eval_geom.restype = C.c_int
         _lib.ora_cholesky_solve.restype = C.c_int
         _lib.ora_max_threads.restype = C.c_int
         _lib.ora_wrap_cylinder.restype = C.c_double
@@ -302,9 +303,11 @@ _EVAL_KEYS = ("qdd", "force", "L", "R", "lm", "vm", "dFdv", "tau_m", "tau_c", "t
               "act_next", "sphere_force", "eps_next")
 
 
-def evaluate(model, dt, q, qd, act, exc, eps=None):
+def evaluate(model, dt, q, qd, act, exc, eps=None, L=None, R=None):
     """All intermediates of one substep at one state (dict of float64 arrays, plus 'status').
-    eps: tendon strains [m] (None: zero)."""
+    eps: tendon strains [m] (None: zero).  L [m] and R [m, n] (optional): muscle-tendon lengths
+    and moment arms used in place of the via-point geometry at q (a substep driven by a learned
+    geometry); the output's L and R are then these."""
     om = _as(model)
     n, m, S = om.n, om.m, om.model.n_spheres
     shapes = dict(qdd=(n,), force=(m,), L=(m,), R=(m, n), lm=(m,), vm=(m,), dFdv=(m,), tau_m=(n,), tau_c=(n,),
@@ -314,8 +317,11 @@ def evaluate(model, dt, q, qd, act, exc, eps=None):
     out = _EvalOut(**{k: _ptr(v) for k, v in res.items()})
     a = [np.ascontiguousarray(x, dtype=np.float64) for x in (q, qd, act, exc)]
     e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
-    st = lib().ora_eval(om.ref, _ptr(om.L0), C.c_double(dt), _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]),
-                        _ptr(e) if e is not None else None, C.byref(out))
+    Lg = None if L is None else np.ascontiguousarray(L, dtype=np.float64).reshape(m)
+    Rg = None if R is None else np.ascontiguousarray(R, dtype=np.float64).reshape(m, n)
+    st = lib().ora_eval_geom(om.ref, _ptr(om.L0), C.c_double(dt), _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]),
+                             _ptr(e) if e is not None else None, _ptr(Lg) if Lg is not None else None,
+                             _ptr(Rg) if Rg is not None else None, C.byref(out))
     res["eps_next"] = res["eps_next"][:m]
     res["sphere_force"] = res["sphere_force"][:S]
     res["status"] = st

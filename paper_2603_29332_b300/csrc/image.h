@@ -117,6 +117,7 @@ struct alignas(16) ImgHeader {
     // below chains of earlier rounds), int16 chain starts [n_chains + 1] (indices into the body
     // list), uint8 bodies [nb] (each chain bottom to top)
     int32_t o_chain, n_crounds, n_chains;
+    float limit_delta;          // onset width of the joint-limit penalty (msim_model.h)
 };
 
 // Models with wrapping surfaces or compliant tendons take the step variants that compile those

@@ -61,6 +61,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     if (!finite_all(d.body_offset, 3 * nb) || !finite_all(d.body_mass, nb) || !finite_all(d.body_com, 3 * nb) ||
         !finite_all(d.body_inertia, 6 * nb) || !finite_all(d.dof_axis, 3 * n))
         FAIL("non-finite body or DoF parameter");
+    if (!(d.limit_delta >= 0.f) || !std::isfinite(d.limit_delta)) FAIL("limit_delta must be finite and >= 0");
 
     // ---- DoF tree
     std::vector<int> dof0(nb), dof_body(n), dpar(n), depth(n), bdepth(nb);
@@ -489,6 +490,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.contact_eps2 = d.contact_eps * d.contact_eps;
     h.limit_k = d.limit_k;
     h.limit_c = d.limit_c;
+    h.limit_delta = d.limit_delta;
     h.tau_act = d.tau_act;
     h.tau_deact = d.tau_deact;
     const double e4 = std::exp(4.0);

@@ -1080,13 +1080,20 @@ __device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, floa
     for (int d = g.lane; d < H.n; d += g.N) {
         const DofRec& D = T.dof[d];
         const float qv = q[d], qdv = qd[d];
-        // limit spring-damper evaluated at the predicted end-of-step state (linearly implicit
-        // in position and velocity): explicit part to rhs, dt c_l + dt^2 k_l to the diagonal
+        // limit spring-damper on the excess x past the limit, evaluated at the predicted
+        // end-of-step state (linearly implicit in position and velocity): spring k_l phi(x),
+        // damper c_l psi(x) with a smooth onset over limit_delta (phi = x^2 / (2 delta),
+        // psi = x / delta below it; x - delta / 2 and 1 beyond), explicit part to rhs,
+        // dt (dt k_l + c_l) psi to the diagonal
         float t = -D.damp * qdv, dd = D.damp;
-        if (D.lo < D.hi) {
-            const float kd = H.limit_k * dt + H.limit_c;
-            if (qv > D.hi) { t += -H.limit_k * (qv - D.hi) - kd * qdv; dd += kd; }
-            else if (qv < D.lo) { t += H.limit_k * (D.lo - qv) - kd * qdv; dd += kd; }
+        if (D.lo < D.hi && (qv > D.hi || qv < D.lo)) {
+            const float x = qv > D.hi ? qv - D.hi : D.lo - qv;
+            float phi, psi;
+            if (x < H.limit_delta) { psi = x / H.limit_delta; phi = 0.5f * x * psi; }
+            else { psi = 1.f; phi = x - 0.5f * H.limit_delta; }
+            const float spring = H.limit_k * phi, kd = (H.limit_k * dt + H.limit_c) * psi;
+            t += (qv > D.hi ? -spring : spring) - kd * qdv;
+            dd += kd;
         }
         rhs[d] += t;
         A[D.row + D.depth] = fac_add_f(A[D.row + D.depth], dt * dd);

@@ -74,6 +74,7 @@ class Model:
     contact_eps: float = 0.1
     limit_k: float = 1000.0
     limit_c: float = 10.0
+    limit_delta: float = 0.0
     tau_act: float = TAU_ACT
     tau_deact: float = TAU_DEACT
     vmax_per_lopt: float = 10.0
@@ -96,8 +97,8 @@ class Model:
 
     def __post_init__(self):
         # scalar parameters are FP32 values too, like every array
-        for k in ("contact_k", "contact_c", "contact_mu", "contact_eps", "limit_k", "limit_c", "tau_act",
-                  "tau_deact", "vmax_per_lopt"):
+        for k in ("contact_k", "contact_c", "contact_mu", "contact_eps", "limit_k", "limit_c", "limit_delta",
+                  "tau_act", "tau_deact", "vmax_per_lopt"):
             setattr(self, k, float(np.float32(getattr(self, k))))
         self.gravity = _f32(self.gravity)
         for k in ("wrap_muscle", "wrap_segment", "wrap_body", "wrap_kind"):
@@ -133,6 +134,7 @@ class Model:
     def scalars(self):
         return dict(contact_k=self.contact_k, contact_c=self.contact_c, contact_mu=self.contact_mu,
                     contact_eps=self.contact_eps, limit_k=self.limit_k, limit_c=self.limit_c,
+                    limit_delta=self.limit_delta,
                     tau_act=self.tau_act, tau_deact=self.tau_deact, vmax_per_lopt=self.vmax_per_lopt)
 
     def validate(self):

@@ -39,7 +39,7 @@ class ModelDesc(C.Structure):
                 ("vmax_per_lopt", C.c_float),
                 ("n_wraps", C.c_int32), ("wrap_muscle", _i32p), ("wrap_segment", _i32p), ("wrap_body", _i32p),
                 ("wrap_center", _f32p), ("wrap_axis", _f32p), ("wrap_radius", _f32p), ("free_root", C.c_int32),
-                ("wrap_kind", _i32p), ("muscle_tendon_strain", _f32p)]
+                ("wrap_kind", _i32p), ("muscle_tendon_strain", _f32p), ("limit_delta", C.c_float)]
 
 
 class CreateArgs(C.Structure):

@@ -390,45 +390,101 @@ def test_contact_static_penetration():
     assert abs(qd[0, 0]) < 1e-9
 
 
-def test_joint_limit_static_deflection():
-    """A horizontal pendulum held by its upper limit at 0 rests at q = m g lc cos q / k_l (the
-    implicit treatment of the penalty changes the transient, not the equilibrium)."""
+def _limit_phi(x, delta):
+    """Spring shape of the limit penalty: x^2 / (2 delta) up to delta, then x - delta / 2."""
+    return 0.5 * x * x / delta if (delta > 0 and x < delta) else x - 0.5 * delta
+
+
+def _limit_pendulum(name, k, c, delta):
     base = hm.pendulum(mass=1.0, lc=0.1)
+    return base, mg.make_model(name, base.body_parent, base.body_ndof, base.body_offset, base.body_mass,
+                               base.body_com, base.body_inertia, base.dof_axis, dof_limit=[[-1.0, 0.0]],
+                               limit_k=k, limit_c=c, limit_delta=delta)
+
+
+@pytest.mark.parametrize("k, delta", [(100.0, 0.0), (100.0, 0.004), (100.0, 0.05), (4000.0, 0.01)])
+def test_joint_limit_static_deflection(k, delta):
+    """A horizontal pendulum held by its upper limit at 0 rests where the limit spring balances
+    gravity, k_l phi(q) = m g lc cos q, phi the spring shape (linear past the onset width delta,
+    quadratic inside it); the implicit treatment changes the transient, not the equilibrium.
+    The cases put the rest point past the onset (delta = 0.004), inside it (0.05) and at a
+    stiffness where it sits in the quadratic part (k = 4000)."""
+    base, mdl = _limit_pendulum("lim", k, 1.0, delta)
     mass, lc, g = base.body_mass[0], base.body_com[0][0], -base.gravity[2]
-    mdl = mg.make_model("lim", base.body_parent, base.body_ndof, base.body_offset, base.body_mass, base.body_com,
-                        base.body_inertia, base.dof_axis, dof_limit=[[-1.0, 0.0]], limit_k=100.0, limit_c=1.0)
-    assert mdl.limit_k == 100.0
+    assert mdl.limit_k == k
     om = ora.OracleModel(mdl)
     q, qd, act = np.zeros((1, 1)), np.zeros((1, 1)), np.zeros((1, 0))
-    for _ in range(50):
+    for _ in range(60):
         q, qd, act, *_ = ora.step(om, 1e-3, q, qd, act, np.zeros((1, 0)), 100)
     qs = q[0, 0]
     assert qs > 0
-    # equilibrium: m g lc cos q = k_l q  (fixed point solved by iteration)
+    delta = mdl.limit_delta   # the model's FP32 value
+    # closed-form inverse of the spring shape, iterated on the gravity torque's cos q
     x = 0.0
-    for _ in range(100):
-        x = mass * g * lc * math.cos(x) / mdl.limit_k
+    for _ in range(200):
+        tq = mass * g * lc * math.cos(x) / mdl.limit_k
+        x = (tq + 0.5 * delta) if (delta == 0 or tq >= 0.5 * delta) else math.sqrt(2.0 * delta * tq)
     assert qs == pytest.approx(x, rel=1e-6)
+    inside = delta > 0 and x < delta
+    assert inside == (mdl.limit_delta > 0.04 or k == 4000.0)
 
 
-def test_implicit_limit_penalty_is_backward_euler_of_the_spring_damper():
-    """Outside a limit the penalty is evaluated at the predicted end-of-step state: the solved
-    q_dd satisfies M q_dd = -C - k_l (q - hi + dt qd') - c_l qd' with qd' = qd + dt q_dd."""
-    base = hm.pendulum(mass=1.0, lc=0.1)
-    mdl = mg.make_model("lim2", base.body_parent, base.body_ndof, base.body_offset, base.body_mass, base.body_com,
-                        base.body_inertia, base.dof_axis, dof_limit=[[-1.0, 0.0]], limit_k=5000.0, limit_c=20.0)
+@pytest.mark.parametrize("q, delta", [(0.3, 0.0), (0.3, 0.01), (0.004, 0.01), (-1.006, 0.01)])
+def test_implicit_limit_penalty_is_backward_euler_of_the_spring_damper(q, delta):
+    """Outside a limit the penalty is the first-order prediction at the end of the step: the
+    solved q_dd satisfies M q_dd + C = +-k_l [phi(x) + psi(x) dt qd'] - c_l psi(x) qd', with
+    qd' = qd + dt q_dd, x the excess past the limit, psi = phi' (1 past the onset width).  The
+    cases: past the onset (plain penalty and smooth onset), inside the onset and below the
+    lower limit."""
+    base, mdl = _limit_pendulum("lim2", 5000.0, 20.0, delta)
     om = ora.OracleModel(mdl)
-    dt, q, qd = 1e-3, 0.3, 2.0
+    dt, qd = 1e-3, 2.0
     r = ora.evaluate(om, dt, [q], [qd], np.zeros(0), np.zeros(0))
-    x = r["qdd"][0]
-    qd1 = qd + dt * x
-    lhs = r["M"][0, 0] * x + r["bias"][0]
-    assert lhs == pytest.approx(-mdl.limit_k * (q - 0.0 + dt * qd1) - mdl.limit_c * qd1, rel=1e-12)
+    xdd = r["qdd"][0]
+    qd1 = qd + dt * xdd
+    lhs = r["M"][0, 0] * xdd + r["bias"][0]
+    upper = q > 0.0
+    x = q - 0.0 if upper else -1.0 - q
+    delta = mdl.limit_delta   # the model's FP32 value
+    psi = min(x / delta, 1.0) if delta > 0 else 1.0
+    # the spring's first-order Taylor expansion in the excess at the end of the step
+    x1 = x + (dt * qd1 if upper else -dt * qd1)
+    spring = mdl.limit_k * (_limit_phi(x, delta) + psi * (x1 - x))
+    want = (-spring if upper else spring) - mdl.limit_c * psi * qd1
+    assert lhs == pytest.approx(want, rel=1e-12)
     # unconditionally stable: a very stiff limit on a light pendulum does not blow up
     q_, qd_, act = np.array([[0.5]]), np.zeros((1, 1)), np.zeros((1, 0))
     for _ in range(20):
         q_, qd_, act, *_ = ora.step(om, 1e-2, q_, qd_, act, np.zeros((1, 0)), 10)
     assert abs(q_[0, 0]) < 0.05 and np.isfinite(qd_[0, 0])
+
+
+def test_limit_penalty_is_continuous_at_the_limit_and_at_the_onset_width():
+    """With a smooth onset the limit torque at fixed velocity and its implicit coefficient (the
+    diagonal added to M) are continuous in q at the limit and at the end of the onset, and their
+    slope in q at the onset's end matches from both sides (C1 spring); the plain penalty
+    (delta = 0) jumps in the implicit coefficient at the limit by dt (dt k_l + c_l)."""
+    dt, qd, k, c, delta = 1e-3, 0.7, 1e5, 300.0, 0.01
+
+    def parts(mdl, q):
+        r = ora.evaluate(ora.OracleModel(mdl), dt, [q], [qd], np.zeros(0), np.zeros(0))
+        return r["tau_l"][0], r["A"][0, 0] - r["M"][0, 0]
+
+    _, smooth = _limit_pendulum("lim3", k, c, delta)
+    _, plain = _limit_pendulum("lim4", k, c, 0.0)
+    h = 1e-9
+    for edge in (0.0, delta):
+        (t0, a0), (t1, a1) = parts(smooth, edge - h), parts(smooth, edge + h)
+        assert abs(t1 - t0) < 1e-3 and abs(a1 - a0) < 1e-6
+    # the spring's slope at the end of the onset: k_l from both sides (torque at qd = 0)
+    _, still = _limit_pendulum("lim5", k, c, delta)
+    r = lambda q: ora.evaluate(ora.OracleModel(still), dt, [q], [0.0], np.zeros(0), np.zeros(0))["tau_l"][0]
+    e = 1e-6
+    left = (r(delta) - r(delta - e)) / e
+    right = (r(delta + e) - r(delta)) / e
+    assert left == pytest.approx(-k, rel=1e-3) and right == pytest.approx(-k, rel=1e-6)
+    (_, a0), (_, a1) = parts(plain, -h), parts(plain, h)
+    assert a1 - a0 == pytest.approx(dt * (dt * k + c), rel=1e-9)
 
 
 def test_implicit_muscle_damping_is_the_force_velocity_jacobian():
