@@ -309,8 +309,11 @@ MSIM_API msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int3
  * environments whose q is outside the training box, or that a failed check has flagged (these
  * use the exact geometry).  Each substep, a Philox-4x32-10 draw keyed by the create seed selects a
  * fraction check_frac (default 0.01) of the other environments for a check: they compute both and
- * use the exact one; an error above tol (default 1e-3, i.e. 1 mm for lengths and moment arms)
- * flags the environment until its msim_reset.  Mode 1 before msim_surrogate_train: MSIM_ERR_STATE. */
+ * use the exact one.  The check error of an environment is the larger of the root-mean-square
+ * errors of its moment arms (over its nnz entries) and of its muscle-tendon lengths (over its m
+ * muscles) against the exact geometry; an error above tol (default 1e-3, i.e. 1 mm), or a
+ * non-finite one, flags the environment until its msim_reset.  Mode 1 before
+ * msim_surrogate_train: MSIM_ERR_STATE. */
 MSIM_API msim_status msim_set_geometry_mode(msim_handle h, int32_t mode);
 /* msim_surrogate_set_box -- training-box margin in half-ranges, 0 <= margin <= 10, for the next
  * msim_surrogate_train (the penalty joint limits let states pass the limits, so a box wider than
@@ -319,6 +322,17 @@ MSIM_API msim_status msim_surrogate_set_box(msim_handle h, float margin);
 /* msim_surrogate_set_width -- hidden width of the next msim_surrogate_train's network (default
  * 512; a multiple of 64 in [64, 4096]): accuracy against cost. */
 MSIM_API msim_status msim_surrogate_set_width(msim_handle h, int32_t hidden);
+/* msim_surrogate_set_structure -- connectivity of the next msim_surrogate_train's network.  1
+ * (default): joint blocks.  When every muscle path segment joins points on the same or on
+ * adjacent bodies, each length is a sum of one-joint terms and each moment arm R_kd depends on
+ * the DoFs of d's joint alone (the structure of J_m(q) in the equation of motion, Methods,
+ * "Musculoskeletal dynamics"); the hidden units are then split into one block per joint, in
+ * proportion to sqrt(outputs depending on the joint) x (its DoFs)^2 with at least 2 units each, a
+ * block reading only its joint's DoFs, the second layer block diagonal, and each output reading
+ * the blocks its value depends on.  The network keeps its dense shape and dense GEMMs (masked
+ * weights are zeros held by the training); models with a segment spanning several joints, or
+ * widths below 2 units per joint, get the dense network.  0: dense network. */
+MSIM_API msim_status msim_surrogate_set_structure(msim_handle h, int32_t structured);
 /* msim_surrogate_set_check -- check fraction in [0, 1] and tolerance > 0 (metres). */
 MSIM_API msim_status msim_surrogate_set_check(msim_handle h, float check_frac, float tol);
 
@@ -329,7 +343,7 @@ typedef struct {
     uint64_t flagged;           /* ... of which were flagged by an earlier failed check */
     uint64_t checked;           /* ... of which were checked against the exact geometry */
     uint64_t check_failed;      /* ... of which exceeded the tolerance */
-    float max_check_error;      /* largest |network - exact| seen by a check (metres) */
+    float max_check_error;      /* largest check error seen (metres; msim_set_geometry_mode) */
     float train_loss;           /* mean squared normalised error, last training epoch */
     int32_t flagged_envs;       /* environments flagged now */
     int32_t trained;
@@ -356,8 +370,11 @@ MSIM_API msim_status msim_surrogate_predict(msim_handle h, const float* q, int32
  * MSIM_NOALLOC_MAX_ACT_ELEMS x 2 BF16 values (32 MiB) plus a 256-byte header, so B * hidden must
  * not exceed MSIM_NOALLOC_MAX_ACT_ELEMS (MSIM_ERR_ARG with a message in msim_last_error(NULL)
  * otherwise; split larger batches).  The first call on a device, made with that device current,
- * looks up the array's device address (cudaGetSymbolAddress) once; make that first call before
- * any stream capture.  Every call on a device shares the array, which keeps the last call's
+ * looks up the array's device address (cudaGetSymbolAddress) once.  With lazy module loading (the
+ * CUDA default) that first call may also load this library's device code on that device, and the
+ * driver then commits the array's memory: make the first call at start-up, while memory is still
+ * available, and before any stream capture; later calls allocate nothing.  Every call on a device
+ * shares the array, which keeps the last call's
  * contents; the GEMMs' wait-expiry word in it is cleared by each call.  Calls whose GPU work
  * overlaps (streams not ordered with each other) race on the array.
  *   W1 [hidden][ldw1] BF16 (ldw1 >= in, multiple of 8), b1 [hidden] FP32, W2 [hidden][hidden] BF16,

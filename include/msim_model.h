@@ -98,7 +98,11 @@ typedef struct {
      * excess x past a limit the spring torque grows as limit_k x^2 / (2 limit_delta) and the
      * damper as limit_c x / limit_delta; beyond, limit_k (x - limit_delta / 2) and limit_c.  The
      * torque and its derivatives in q and qd are then continuous at the limit, so the linearly
-     * implicit step has no jump there.  0 = the plain penalty limit_k x, limit_c. */
+     * implicit step has no jump there.  0 = the plain penalty limit_k x, limit_c.  Stability: the
+     * implicit coefficient (limit_k dt + limit_c) x / limit_delta then depends on the excess, and a
+     * joint entering the onset at speed qd meets an explicit stiffness
+     * (limit_k dt + limit_c) |qd| / limit_delta, which must stay well below I / dt^2 (I the joint's
+     * effective inertia); the plain penalty has no such term. */
     float limit_delta;
 } msim_model_desc;
 

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <mutex>
 
 #include "gemm_tc.h"
 
@@ -277,16 +278,19 @@ __global__ void __launch_bounds__(192, 2)
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
 
+// the driver's tensor-map encoder, looked up once per process (thread-safe)
 bool get_encode() {
-    if (g_encode) return true;
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-        return false;
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    return true;
+    std::call_once(g_encode_once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && fn)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode != nullptr;
 }
 
 // 2-D tensor map over a row-major [rows][ld] BF16 matrix with `cols` valid columns; box of
@@ -308,17 +312,47 @@ constexpr size_t gemm_smem() {
 // the epilogue staging (4 warps x 32 rows x kStage floats) reuses the operand ring
 static_assert(4 * 32 * kStage * 4 <= 2 * (kBM * kBK * 2 + 128 * kBK * 2), "staging must fit in the ring");
 
+// Per-device launch state: the dynamic shared-memory attribute of each kernel instance is a
+// property of the device it was set on, and the tile choice depends on the device's SM count.
+// Both are set once per device under a lock (host threads may launch concurrently).
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mu;
+
+int current_device() {
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess ? dev : -1;
+}
+
 template <int BN, int kStages>
-cudaError_t launch_bn(const GemmArgs& a, const void* A, int lda, const void* B, int ldb, cudaStream_t s) {
+cudaError_t ensure_smem_attr(int dev) {
+    static bool done[kMaxDevices] = {};
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (!done[dev]) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)gemm_smem<BN, kStages>());
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+int block_slots(int dev) {
+    static int slots[kMaxDevices] = {};
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (!slots[dev]) {
+        int sms = 148;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 148;
+        slots[dev] = 2 * sms;
+    }
+    return slots[dev];
+}
+
+template <int BN, int kStages>
+cudaError_t launch_bn(const GemmArgs& a, const void* A, int lda, const void* B, int ldb, int dev, cudaStream_t s) {
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, a.M, a.K, lda, kBM) || !make_map(&mb, B, a.N, a.K, ldb, BN)) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm<BN, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gemm_smem<BN, kStages>());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    const cudaError_t e = ensure_smem_attr<BN, kStages>(dev);
+    if (e != cudaSuccess) return e;
     dim3 grid((a.N + BN - 1) / BN, (a.M + kBM - 1) / kBM);
     k_gemm<BN, kStages><<<grid, 192, gemm_smem<BN, kStages>(), s>>>(ma, mb, a);
     return cudaGetLastError();
@@ -337,18 +371,14 @@ cudaError_t gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, GemmArg
     // two blocks per SM (<= 113 KB of shared memory and <= 256 TMEM columns each).  Tile width:
     // fewest waves of tiles over the 2 x SMs block slots, a 128-wide tile costing half a 256-wide
     // one; ties go to 256 (more reuse of each A tile)
-    static int slots = 0;
-    if (!slots) {
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        slots = 2 * sms;
-    }
+    const int dev = current_device();
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const int slots = block_slots(dev);
     const long long mt = (args.M + kBM - 1) / kBM;
     const long long w256 = (mt * ((args.N + 255) / 256) + slots - 1) / slots;
     const long long w128 = (mt * ((args.N + 127) / 128) + slots - 1) / slots;
-    if (args.N > 128 && 2 * w256 <= w128) return launch_bn<256, MSIM_GEMM_STAGES_256>(args, A, lda, B, ldb, s);
-    return launch_bn<128, MSIM_GEMM_STAGES_128>(args, A, lda, B, ldb, s);
+    if (args.N > 128 && 2 * w256 <= w128) return launch_bn<256, MSIM_GEMM_STAGES_256>(args, A, lda, B, ldb, dev, s);
+    return launch_bn<128, MSIM_GEMM_STAGES_128>(args, A, lda, B, ldb, dev, s);
 }
 
 }  // namespace msim

@@ -18,6 +18,11 @@ struct ModelHost {
     ImgHeader hdr;
     std::vector<uint8_t> blob;
     std::vector<int32_t> dof_parent, dof_depth, packed_row, mus_ptr, mus_dof;
+    // joint structure of the muscle geometry (the learned geometry's connectivity): the body
+    // owning each crossed DoF (parallel to mus_dof), and per muscle whether every path segment
+    // crosses at most one joint (its length then depends on that joint's DoFs alone)
+    std::vector<int32_t> mus_body;
+    std::vector<uint8_t> mus_one_joint_segments;
 };
 
 }  // namespace msim
@@ -34,6 +39,7 @@ struct msim_handle_ {
     msim::Surrogate* sur = nullptr;
     float box_margin = 0.05f;   // training box of the next msim_surrogate_train
     int surr_hidden = msim::kSurrHidden;   // hidden width of the next msim_surrogate_train
+    int surr_structured = 1;               // joint-block connectivity for the next training
     msim_mlp_ sur_view;
     int n_models = 0, n_envs = 0, pitch_n = 0, pitch_m = 0;
     float dt = 0.f;

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "gemm_tc.h"
 #include "mlp.h"
@@ -107,8 +108,9 @@ __global__ void k_colsum(const __nv_bfloat16* src, int B, int N, int ld, float* 
 }
 
 __global__ void k_adam(float* P, const float* G, float* Am, float* Av, size_t n, float lr, float b1, float b2,
-                       float eps, float bc1, float bc2, __nv_bfloat16* Ph) {
+                       float eps, float bc1, float bc2, __nv_bfloat16* Ph, const uint8_t* mask) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;   // held at zero
         const float g = G[i];
         const float m = b1 * Am[i] + (1.f - b1) * g;
         const float v = b2 * Av[i] + (1.f - b2) * g * g;
@@ -117,6 +119,19 @@ __global__ void k_adam(float* P, const float* G, float* Am, float* Av, size_t n,
         const float p = P[i] - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
         P[i] = p;
         Ph[i] = __float2bfloat16_rn(p);
+    }
+}
+
+// P[i] *= scale[row of i] for weights inside the mask, 0 outside it (biases untouched)
+__global__ void k_mask_params(float* P, const uint8_t* mask, const float* row_scale, size_t n, size_t oW1, int inp,
+                              int hid, size_t oW2, size_t oW3, int outp) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        int row = -1;
+        if (i >= oW1 && i < oW1 + (size_t)hid * inp) row = (int)((i - oW1) / inp);
+        else if (i >= oW2 && i < oW2 + (size_t)hid * hid) row = hid + (int)((i - oW2) / hid);
+        else if (i >= oW3 && i < oW3 + (size_t)outp * hid) row = 2 * hid + (int)((i - oW3) / hid);
+        if (row < 0) continue;
+        P[i] = mask[i] ? P[i] * row_scale[row] : 0.f;
     }
 }
 
@@ -189,7 +204,8 @@ cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp
 void mlp_destroy(Mlp* m) {
     if (!m) return;
     void* ptrs[] = {m->P, m->G, m->Am, m->Av, m->Ph, m->W2t, m->W3t, m->H1, m->Z1, m->H2, m->Z2, m->dY, m->dZ1,
-                    m->dZ2, m->Xt, m->H1t, m->H2t, m->dYt, m->dZ1t, m->dZ2t, m->Y, m->dH, m->loss_acc, m->err};
+                    m->dZ2, m->Xt, m->H1t, m->H2t, m->dYt, m->dZ1t, m->dZ2t, m->Y, m->dH, m->loss_acc, m->err,
+                    m->mask};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -216,6 +232,35 @@ cudaError_t mlp_init(Mlp* m, uint64_t seed, float out_scale, cudaStream_t s) {
     CK(cudaMemsetAsync(m->Av, 0, m->n_params * 4, s));
     m->adam_t = 0;
     return mlp_sync_bf16(m, s);
+}
+
+cudaError_t mlp_set_mask(Mlp* m, const uint8_t* host_mask, cudaStream_t s) {
+    // per weight row: the mlp_init bound sqrt(6 / fan_in) becomes sqrt(3 / fan) over the row's
+    // unmasked entries
+    const int rows = 2 * m->hid + m->outp;
+    std::vector<float> scale(rows, 1.f);
+    auto row_scale = [&](size_t off, int r, int width, int fan_in) {
+        int fan = 0;
+        for (int c = 0; c < width; ++c) fan += host_mask[off + (size_t)r * width + c] != 0;
+        return fan > 0 ? std::sqrt((3.f / fan) / (6.f / fan_in)) : 0.f;
+    };
+    for (int r = 0; r < m->hid; ++r) scale[r] = row_scale(m->oW1, r, m->inp, m->in);
+    for (int r = 0; r < m->hid; ++r) scale[m->hid + r] = row_scale(m->oW2, r, m->hid, m->hid);
+    for (int r = 0; r < m->outp; ++r) scale[2 * m->hid + r] = row_scale(m->oW3, r, m->hid, m->hid);
+    float* d_scale = nullptr;
+    if (!m->mask) CK(cudaMalloc(&m->mask, m->n_params));
+    CK(cudaMalloc(&d_scale, rows * sizeof(float)));
+    cudaError_t e = cudaMemcpyAsync(m->mask, host_mask, m->n_params, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_scale, scale.data(), rows * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_mask_params<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->mask, d_scale, m->n_params, m->oW1, m->inp, m->hid,
+                                                             m->oW2, m->oW3, m->outp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = mlp_sync_bf16(m, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host arrays go out of scope
+    cudaFree(d_scale);
+    return e;
 }
 
 cudaError_t mlp_forward(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s) {
@@ -273,7 +318,7 @@ cudaError_t mlp_adam(Mlp* m, float lr, float beta1, float beta2, float eps, cuda
     m->adam_t += 1;
     const float bc1 = 1.f - powf(beta1, (float)m->adam_t), bc2 = 1.f - powf(beta2, (float)m->adam_t);
     k_adam<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->G, m->Am, m->Av, m->n_params, lr, beta1, beta2, eps, bc1,
-                                                  bc2, m->Ph);
+                                                  bc2, m->Ph, m->mask);
     CK(cudaGetLastError());
     dim3 block(32, 8);
     k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->hid + 31) / 32), block, 0, s>>>(

@@ -33,6 +33,7 @@ struct Mlp {
     float *Y, *dH;
     float* loss_acc;       // device scalar: sum of squared errors of the last backward
     uint32_t* err;         // device word: GEMM bounded-wait failures
+    uint8_t* mask;         // [n_params] 1 = trainable, 0 = held at zero (nullptr: every parameter)
 };
 
 cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp** out_mlp);
@@ -48,8 +49,14 @@ cudaError_t mlp_forward(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y
 cudaError_t mlp_infer(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s);
 // gradients of mean((y - t)^2) into G (forward included); T [B][ldt] FP32
 cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T, int ldt, int B, cudaStream_t s);
-// one Adam step (Kingma & Ba 2015) on G, refreshes the BF16 copies
+// one Adam step (Kingma & Ba 2015) on G, refreshes the BF16 copies; parameters outside the mask
+// stay zero
 cudaError_t mlp_adam(Mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t s);
+// Connectivity mask (host array [n_params] in the flat layout, 1 = trainable): masked weights are
+// set to zero and stay there; each weight row is re-drawn to the uniform bound sqrt(3 / fan),
+// fan = its unmasked entries (variance 1 / fan), from the values mlp_init drew.  Call after
+// mlp_init.  Synchronous (the host array may be freed on return).
+cudaError_t mlp_set_mask(Mlp* m, const uint8_t* host_mask, cudaStream_t s);
 
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): 4 x 32 random bits for a 128-bit counter
 // and a 64-bit key.  Shared by the surrogate's sampler and the policy's exploration.

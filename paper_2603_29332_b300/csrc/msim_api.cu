@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -250,7 +251,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         }
     auto compliant = [&](int k) { return d.muscle_tendon_strain && d.muscle_tendon_strain[k] > 0.f; };
     std::vector<uint32_t> cross;
-    std::vector<int32_t> mus_ptr(m + 1, 0), mus_dof;
+    std::vector<int32_t> mus_ptr(m + 1, 0), mus_dof, mus_body;
+    std::vector<uint8_t> one_joint(m, 1);
     if (m > 0) {
         if (d.muscle_point_start[0] != 0 || d.muscle_point_start[m] != np)
             FAIL("muscle_point_start must start at 0 and end at n_points");
@@ -287,6 +289,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         for (int j = j0; j < j1; ++j) {
             const int t = pos_of(d.point_body[j]);
             if (t < 0 || t < prev) FAIL("muscle %d: path points must follow the origin-to-insertion chain", k);
+            if (j > j0 && t - prev > 1) one_joint[k] = 0;   // this segment spans several joints
             prev = t;
             PointRec& P = pts[j];
             P.pos[0] = d.point_pos[3 * j]; P.pos[1] = d.point_pos[3 * j + 1]; P.pos[2] = d.point_pos[3 * j + 2];
@@ -327,6 +330,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
                 const int dd = dof0[chain[t]] + j;
                 cross.push_back((uint32_t)dd | ((uint32_t)chain[t] << 8) | ((uint32_t)row[dd] << 16));
                 mus_dof.push_back(dd);
+                mus_body.push_back(chain[t]);
             }
         mus_ptr[k + 1] = (int32_t)cross.size();
     }
@@ -533,6 +537,8 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     out.packed_row.assign(row.begin(), row.end());
     out.mus_ptr = mus_ptr;
     out.mus_dof = mus_dof;
+    out.mus_body = mus_body;
+    out.mus_one_joint_segments = one_joint;
     return true;
 }
 #undef FAIL
@@ -648,6 +654,91 @@ void auto_launch(msim_handle h, int i) {
 using namespace msim::host;
 
 namespace {
+
+// Connectivity of the learned geometry.  Every path segment of the generated models joins points
+// on the same or on adjacent bodies, so a segment's length depends on the DoFs of one joint only:
+// each muscle length is a sum of one-joint terms, and the moment arm R_kd = -dL_k/dq_d depends on
+// the DoFs of d's joint alone.  The network is given that structure: its hidden units are split
+// into one block per joint (a body whose DoFs some muscle crosses), a block's first-layer units
+// read only that joint's DoFs, the second layer is block diagonal, the length of muscle k reads
+// the blocks of the joints k crosses and R_kd the block of d's joint.  The GEMMs stay dense (the
+// masked weights are zeros); only training honours the mask.  Block sizes: the hidden width split
+// in proportion to sqrt(outputs depending on the joint) x (its DoFs)^2, at least 2 units each: a
+// joint's functions have as many arguments as it has DoFs, and a three-angle function takes many
+// more units than a one-angle function to the same accuracy (the weights were chosen by the
+// moment-arm error of networks trained with several of them).  Returns false (dense network) when
+// some segment spans several joints or the width cannot give every joint its 2 units.
+bool surrogate_mask(const ModelHost& M, const Mlp* net, int m, std::vector<uint8_t>& mask) {
+    for (uint8_t v : M.mus_one_joint_segments)
+        if (!v) return false;
+    const int nnz = (int)M.mus_dof.size();
+    std::map<int, int> block_of;          // joint body -> block index
+    std::vector<int> dof_body(net->in, -1);
+    for (int t = 0; t < nnz; ++t) {
+        block_of.emplace(M.mus_body[t], 0);
+        dof_body[M.mus_dof[t]] = M.mus_body[t];
+    }
+    const int nj = (int)block_of.size(), H = net->hid;
+    constexpr int kFloor = 2;
+    if (nj == 0 || nj * kFloor > H) return false;
+    std::vector<int> joints;
+    for (auto& kv : block_of) {
+        kv.second = (int)joints.size();
+        joints.push_back(kv.first);
+    }
+    std::vector<double> outs(nj, 0.0), ndof(nj, 0.0);
+    for (int d = 0; d < net->in; ++d)
+        if (dof_body[d] >= 0) ndof[block_of[dof_body[d]]] += 1.0;
+    for (int k = 0; k < m; ++k) {
+        std::vector<int> seen;
+        for (int t = M.mus_ptr[k]; t < M.mus_ptr[k + 1]; ++t) {
+            const int j = block_of[M.mus_body[t]];
+            outs[j] += 1.0;   // the moment arm
+            if (std::find(seen.begin(), seen.end(), j) == seen.end()) {
+                seen.push_back(j);
+                outs[j] += 1.0;   // the length's term of this joint
+            }
+        }
+    }
+    std::vector<double> w(nj);
+    double wsum = 0.0;
+    for (int j = 0; j < nj; ++j) wsum += (w[j] = std::sqrt(outs[j]) * ndof[j] * ndof[j]);
+    std::vector<int> units(nj);
+    int total = 0;
+    for (int j = 0; j < nj; ++j) total += (units[j] = std::max(kFloor, (int)std::floor(w[j] / wsum * H)));
+    while (total > H) {   // take from the largest block
+        const int j = (int)(std::max_element(units.begin(), units.end()) - units.begin());
+        --units[j];
+        --total;
+    }
+    while (total < H) {   // give to the block with the most weight per unit
+        int jb = 0;
+        for (int j = 1; j < nj; ++j)
+            if (w[j] / units[j] > w[jb] / units[jb]) jb = j;
+        ++units[jb];
+        ++total;
+    }
+    std::vector<int> b0(nj + 1, 0);
+    for (int j = 0; j < nj; ++j) b0[j + 1] = b0[j] + units[j];
+    mask.assign(net->n_params, 0);
+    for (int j = 0; j < nj; ++j)
+        for (int u = b0[j]; u < b0[j + 1]; ++u) {
+            for (int d = 0; d < net->in; ++d)
+                if (dof_body[d] == joints[j]) mask[net->oW1 + (size_t)u * net->inp + d] = 1;
+            for (int v = b0[j]; v < b0[j + 1]; ++v) mask[net->oW2 + (size_t)u * H + v] = 1;
+        }
+    for (int u = 0; u < H; ++u) mask[net->ob1 + u] = mask[net->ob2 + u] = 1;
+    auto read_block = [&](int row, int j) {
+        for (int u = b0[j]; u < b0[j + 1]; ++u) mask[net->oW3 + (size_t)row * H + u] = 1;
+    };
+    for (int k = 0; k < m; ++k)
+        for (int t = M.mus_ptr[k]; t < M.mus_ptr[k + 1]; ++t) {
+            read_block(k, block_of[M.mus_body[t]]);        // the length
+            read_block(m + t, block_of[M.mus_body[t]]);    // the moment arm R_kd
+        }
+    for (int r = 0; r < net->out; ++r) mask[net->ob3 + r] = 1;
+    return true;
+}
 
 void surr_free(Surrogate* s) {
     if (!s) return;
@@ -1324,6 +1415,13 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
     S->tol = tol;
     cudaError_t e = mlp_create(n, h->surr_hidden, out, 0, std::max(batch, h->n_envs), &S->net);
     if (e == cudaSuccess) e = mlp_init(S->net, (uint64_t)h->seed * 2654435761ull + 17u, 1.f, s);
+    if (e == cudaSuccess && h->surr_structured) {
+        std::vector<uint8_t> mask;
+        if (surrogate_mask(h->models[0], S->net, m, mask)) {
+            e = mlp_set_mask(S->net, mask.data(), s);
+            S->structured = 1;
+        }
+    }
     auto A = [&](void** p, size_t b) {
         if (e == cudaSuccess) e = cudaMalloc(p, b);
     };
@@ -1438,6 +1536,13 @@ msim_status msim_surrogate_set_width(msim_handle h, int32_t hidden) {
     if (!h || hidden < 64 || hidden > 4096 || hidden % 64)
         return arg_fail(h, "msim_surrogate_set_width: hidden must be a multiple of 64 in [64, 4096]");
     h->surr_hidden = hidden;   // takes effect at the next msim_surrogate_train
+    return MSIM_OK;
+}
+
+msim_status msim_surrogate_set_structure(msim_handle h, int32_t structured) {
+    if (!h || (structured != 0 && structured != 1))
+        return arg_fail(h, "msim_surrogate_set_structure: structured must be 0 or 1");
+    h->surr_structured = structured;   // takes effect at the next msim_surrogate_train
     return MSIM_OK;
 }
 

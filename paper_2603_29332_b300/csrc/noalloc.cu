@@ -2,7 +2,9 @@
 //
 // The two hidden activation matrices live in one file-scope device array of fixed size; its
 // device address is looked up once per device (cudaGetSymbolAddress, with that device current) on
-// the first call made while that device is current.  Every call on a device shares the array:
+// the first call made while that device is current.  Under lazy module loading that first lookup
+// may load the library's device code and make the driver commit the array, so callers make the
+// first call at start-up; later calls allocate nothing.  Every call on a device shares the array:
 // the array keeps the last call's contents, and calls whose GPU work overlaps (different streams
 // without ordering between them) race on it.  The GEMMs are the same tcgen05 kernels as
 // msim_mlp_forward's, launched on the caller's stream.

@@ -770,7 +770,7 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
     int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
     float* rk = ws + H.w_rk;                                  // [max_nx][N]
     bool bad = false;
-    uint32_t flags = 0;
+    float se_len = 0.f, se_arm = 0.f;   // check: squared errors of the learned lengths and arms
     SUB_T0();
     for (int r = g.lane; r < H.m; r += g.N) {
         const MuscleRec M = T.mus[r];
@@ -868,13 +868,14 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             const int mm = H.m;
             const float Ls = sc->Y[k] * sc->sd[k] + sc->mu[k];
             if (sc->check) {
-                float e = fabsf(Ls - L);
+                // squared errors against the exact geometry, summed over the environment below
+                const float dl = Ls - L;
+                se_len += dl * dl;
                 for (int i = 0; i < M.nx; ++i) {
                     const int o = mm + M.x0 + i;
-                    e = fmaxf(e, fabsf(sc->Y[o] * sc->sd[o] + sc->mu[o] - rk[i * g.N + g.lane]));
+                    const float dr = sc->Y[o] * sc->sd[o] + sc->mu[o] - rk[i * g.N + g.lane];
+                    se_arm += dr * dr;
                 }
-                if (!(e <= sc->tol)) flags |= 2u;   // a non-finite state or output fails too
-                if (e > 0.f) atomicMax(sc->max_err_bits, __float_as_uint(e));
             } else {
                 L = Ls;
                 for (int i = 0; i < M.nx; ++i) {
@@ -963,8 +964,36 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
         }
         SUB_MARK(10);
     }
-    // also orders the reductions before the next phase
-    const bool fail = g.any((flags & 2u) != 0);
+    bool fail = false;
+    if (is_surr(MODE) && sc->check) {
+        // the environment's check error: the larger of the root-mean-square errors of its moment
+        // arms (over the nnz entries) and of its lengths (over the m muscles); a non-finite state
+        // or output fails.  Warp sums, then the warps' sums in a fixed order through the
+        // moment-arm region, which every lane has finished with after the first barrier.
+        float v0 = se_arm, v1 = se_len;
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+            v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        }
+        if (WPE > 1) {
+            g.sync();
+            if (g.wl == 0) {
+                rk[2 * g.wi] = v0;
+                rk[2 * g.wi + 1] = v1;
+            }
+            g.sync();
+            v0 = v1 = 0.f;
+            for (int w = 0; w < WPE; ++w) {
+                v0 += rk[2 * w];
+                v1 += rk[2 * w + 1];
+            }
+        }
+        const float e = fmaxf(sqrtf(v0 / (float)max(H.nnz, 1)), sqrtf(v1 / (float)max(H.m, 1)));
+        fail = !(e <= sc->tol);
+        if (g.lane == 0) atomicMax(sc->max_err_bits, __float_as_uint(fail && !(e > 0.f) ? INFINITY : e));
+    }
+    // also orders the reductions (and the check's reads of the moment-arm region) before the
+    // next phase
     return (g.any(bad) ? 1u : 0u) | (fail ? 2u : 0u);
 }
 

@@ -34,6 +34,7 @@ struct Surrogate {
     float check_frac = 0.01f, tol = 1e-3f;
     float box_margin = 0.05f;             // box half-width = (1 + margin) x half the limit range
     int trained = 0;
+    int structured = 0;                   // 1: joint-block connectivity (msim_surrogate_set_structure)
     float loss = 0.f;                     // mean squared normalised error of the last epoch
 };
 

@@ -72,8 +72,9 @@ class Model:
     contact_c: float = 1.0e3
     contact_mu: float = 0.9
     contact_eps: float = 0.1
-    limit_k: float = 1000.0
-    limit_c: float = 10.0
+    # joint-limit penalty: stiffness k_l, damping c_l, onset width (see the limit reading)
+    limit_k: float = 1.0e5
+    limit_c: float = 1.0e3
     limit_delta: float = 0.0
     tau_act: float = TAU_ACT
     tau_deact: float = TAU_DEACT

@@ -96,7 +96,8 @@ EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_s
            "msim_mlp_get", "msim_mlp_set", "msim_mlp_forward", "msim_mlp_backward", "msim_mlp_adam",
            "msim_surrogate_train", "msim_set_geometry_mode", "msim_surrogate_set_check", "msim_surrogate_stats",
            "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
-           "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_surrogate_set_width", "msim_policy_attach",
+           "msim_set_mixed_launch", "msim_autotune", "msim_surrogate_set_box", "msim_surrogate_set_width",
+           "msim_surrogate_set_structure", "msim_policy_attach",
            "msim_policy_step", "msim_policy_excitations", "msim_measure_fp32_peak", "msim_flow_attach",
            "msim_flow_actions", "msim_reward_attach", "msim_reward", "msim_body_positions", "msim_tendon_strain",
            "msim_last_error", "msim_version")
@@ -145,6 +146,7 @@ def load_library(path=LIB_PATH):
     lib.msim_surrogate_set_check.argtypes = [vp, C.c_float, C.c_float]
     lib.msim_surrogate_set_box.argtypes = [vp, C.c_float]
     lib.msim_surrogate_set_width.argtypes = [vp, C.c_int32]
+    lib.msim_surrogate_set_structure.argtypes = [vp, C.c_int32]
     lib.msim_surrogate_stats.argtypes = [vp, C.POINTER(SurrogateInfo), C.c_int32]
     lib.msim_surrogate_network.argtypes = [vp, C.POINTER(vp)]
     lib.msim_geometry.argtypes = [vp, C.c_int32, vp, C.c_int32, C.c_int32, vp, C.c_int32, vp]
@@ -455,6 +457,9 @@ class Sim:
     def surrogate_set_width(self, hidden):
         self._check(self.lib.msim_surrogate_set_width(self.h, int(hidden)))
 
+    def surrogate_set_structure(self, structured):
+        self._check(self.lib.msim_surrogate_set_structure(self.h, 1 if structured else 0))
+
     def set_geometry_mode(self, mode):
         self._check(self.lib.msim_set_geometry_mode(self.h, int(mode)))
 
@@ -633,12 +638,27 @@ def mlp_forward_noalloc(W1, b1, W2, b2, W3, b3, X, d_in, out_sigmoid=False, Y=No
     import torch
     lib = load_library()
     hidden, out, B = W2.shape[0], W3.shape[0], X.shape[0]
+    dev = X.device
+    if dev.type != "cuda":
+        raise ValueError("mlp_forward_noalloc: X must be a CUDA tensor")
     if Y is None:
-        Y = torch.empty((B, out), dtype=torch.float32, device=X.device)
-    st = lib.msim_mlp_forward_noalloc(d_in, hidden, out, 2 if out_sigmoid else 0, W1.data_ptr(), W1.stride(0),
-                                      b1.data_ptr(), W2.data_ptr(), b2.data_ptr(), W3.data_ptr(), b3.data_ptr(),
-                                      X.data_ptr(), X.stride(0), B, Y.data_ptr(), Y.stride(0),
-                                      status.data_ptr() if status is not None else None, _stream_ptr(stream))
+        Y = torch.empty((B, out), dtype=torch.float32, device=dev)
+    want = dict(W1=(W1, torch.bfloat16), W2=(W2, torch.bfloat16), W3=(W3, torch.bfloat16), X=(X, torch.bfloat16),
+                b1=(b1, torch.float32), b2=(b2, torch.float32), b3=(b3, torch.float32), Y=(Y, torch.float32))
+    if status is not None:
+        want["status"] = (status, status.dtype if status.dtype in (torch.int32, torch.uint32) else torch.int32)
+    for name, (t, dt) in want.items():
+        # the scratch array and the stream are those of the current device: every operand must
+        # live there (a peer device's memory is not reachable by the GEMMs' tensor maps)
+        if t.device != dev or t.dtype != dt or (t.dim() > 0 and t.stride(-1) != 1):
+            raise ValueError("mlp_forward_noalloc: %s must be %s on %s with unit inner stride" % (name, dt, dev))
+    if W2.stride(0) != hidden or W3.stride(0) != hidden or W1.stride(0) < d_in or X.stride(0) < d_in:
+        raise ValueError("mlp_forward_noalloc: W2 and W3 rows must be contiguous, W1 and X pitches >= d_in")
+    with torch.cuda.device(dev):
+        st = lib.msim_mlp_forward_noalloc(d_in, hidden, out, 2 if out_sigmoid else 0, W1.data_ptr(), W1.stride(0),
+                                          b1.data_ptr(), W2.data_ptr(), b2.data_ptr(), W3.data_ptr(), b3.data_ptr(),
+                                          X.data_ptr(), X.stride(0), B, Y.data_ptr(), Y.stride(0),
+                                          status.data_ptr() if status is not None else None, _stream_ptr(stream))
     if st != MSIM_OK:
         raise MsimError(st, lib.msim_last_error(None).decode())
     return Y

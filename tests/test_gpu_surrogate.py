@@ -3,10 +3,11 @@
 The surrogate is judged against the exact path it replaces (its labels come from the exact
 geometry kernel, itself checked here against the FP64 oracle).  Deterministic properties are
 checked exactly: an environment that uses the exact geometry inside a learned-geometry step
-(checked, outside the box, or flagged) follows the exact path bit for bit.  Accuracy is reported
-and compared with the untrained network (what training gains), not with a hard 1 mm bound, which
-the configured network does not reach everywhere; the per-environment check and fallback are
-what keep the dynamics within it.
+(checked, outside the box, or flagged) follows the exact path bit for bit.  The substep that
+consumes the network's geometry is pinned to the oracle fed the same geometry (q_dd within
+1e-4).  Accuracy at this file's small training budget is compared with the best constant
+predictor and with the dense network (what training and the joint structure gain); a rollout
+compares the learned path with the exact one in throughput and in q after 100 substeps.
 """
 import numpy as np
 import pytest
@@ -41,7 +42,7 @@ def _q_in_box(model, rows, seed, margin=0.05, frac=0.98):
 def trained():
     model = mg.config_model("c1_whole")
     sim = msim.Sim(model, E, dt=DT, seed=3)
-    sim.train_surrogate(524288, 8, batch=4096, lr=1e-3)
+    sim.train_surrogate(1048576, 8, batch=4096, lr=1e-3)
     return model, sim
 
 
@@ -70,28 +71,35 @@ def test_geometry_kernel_matches_oracle(name):
         np.testing.assert_allclose(msim.unpack_R(out[r, m:], lay, model.n_dofs), R, rtol=0, atol=5e-6)
 
 
-def test_training_gains_over_the_untrained_network(trained):
-    model, sim = trained
-    q = torch.from_numpy(_q_in_box(model, 2048, seed=77)).cuda()
+def _fresh_errors(model, sim, rows=2048, seed=77):
+    q = torch.from_numpy(_q_in_box(model, rows, seed=seed)).cuda()
     qp = torch.zeros((q.shape[0], sim.pitch_n), device="cuda")
     qp[:, : model.n_dofs] = q
     exact = sim.geometry(qp)
-    pred = sim.surrogate_predict(qp)
-    net = sim.surrogate_network()
-    trained_params = net.get(0)
-    fresh = msim.MLP(model.n_dofs, 512, net.d_out, max_batch=16, seed=3 * 2654435761 + 17 & (2**64 - 1))
-    net.set(fresh.get(0))   # the same initialisation the training started from
-    fresh.close()
-    pred0 = sim.surrogate_predict(qp)
-    net.set(trained_params)
+    return sim.surrogate_predict(qp) - exact, exact
+
+
+def test_training_gains_over_the_best_constant_and_the_dense_network(trained):
+    """At this file's small budget (1M samples, 8 epochs) the trained network's error is a
+    fraction of the best constant predictor's (each output's mean), and the joint-structured
+    network beats the dense one trained on the same samples."""
+    model, sim = trained
     m = model.n_muscles
-    e1, e0 = (pred - exact).abs(), (pred0 - exact).abs()
-    rms1, rms0 = float(e1.pow(2).mean().sqrt()), float(e0.pow(2).mean().sqrt())
-    print("\nsurrogate |error| m: trained median L %.2e R %.2e, rms %.2e; untrained rms %.2e; "
-          "envs with max <= 1 mm: %.3f" % (float(e1[:, :m].median()), float(e1[:, m:].median()), rms1, rms0,
-                                          float((e1.max(1).values <= 1e-3).float().mean())))
-    assert rms1 < 0.35 * rms0
-    assert float(e1[:, m:].median()) < 5e-3
+    err, exact = _fresh_errors(model, sim)
+    rms1 = float(err.pow(2).mean().sqrt())
+    rms0 = float((exact - exact.mean(0)).pow(2).mean().sqrt())
+    dense = msim.Sim(model, E, dt=DT, seed=3)
+    dense.surrogate_set_structure(False)
+    dense.train_surrogate(1048576, 8, batch=4096, lr=1e-3)
+    errd, _ = _fresh_errors(model, dense)
+    rmsd = float(errd.pow(2).mean().sqrt())
+    env_rms = err[:, m:].pow(2).mean(1).sqrt()
+    print("\nsurrogate error (m): structured rms %.2e (median R %.2e, p99 R %.2e, envs with moment-arm rms "
+          "<= 1 mm %.3f); dense rms %.2e; best constant rms %.2e"
+          % (rms1, float(err[:, m:].abs().median()), float(err[:, m:].abs().flatten()[::7].quantile(0.99)),
+             float((env_rms <= 1e-3).float().mean()), rmsd, rms0))
+    assert rms1 < 0.2 * rms0
+    assert rms1 < 0.8 * rmsd
 
 
 def test_checked_environments_follow_the_exact_path_bitwise(trained):
@@ -150,7 +158,7 @@ def test_injected_network_error_is_caught_and_falls_back_until_reset(trained):
     good = net.get(0)
     bad = good.copy()
     b3 = net.offsets[5]
-    bad[b3] += 50.0   # muscle 0's length off by 50 standard deviations
+    bad[b3:b3 + 100] += 50.0   # 100 muscle lengths off by 50 standard deviations each
     q0, qd0, a0 = mg.initial_state(model, E, seed=10)
     sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
     exc = sim.pad_m(mg.smooth_excitations(model, E, 1, seed=10)[0])
@@ -175,24 +183,80 @@ def test_injected_network_error_is_caught_and_falls_back_until_reset(trained):
         sim.surrogate_set_check(0.01, 1e-3)
 
 
-def test_learned_step_accelerations_against_the_oracle(trained):
+def test_learned_substep_matches_the_oracle_fed_the_network_geometry(trained):
+    """The learned-geometry substep on 512 environments against the FP64 oracle's substep given
+    the network's own lengths and moment arms at the same FP32 state (msim_surrogate_predict):
+    muscle forces and q_dd agree at the exact path's tolerances, so everything downstream of the
+    geometry consumes the network's output as the method says.  The oracle with the exact
+    geometry is reported beside it (the network's own error)."""
     model, sim = trained
+    n, m = model.n_dofs, model.n_muscles
     q, qd, act, exc = random_states(model, E, seed=12, q_scale=0.3)
     sim.reset(sim.pad_n(q), sim.pad_n(qd), sim.pad_m(act))
     sim.set_geometry_mode(1)
     sim.surrogate_set_check(0.0, 1e-3)
     try:
         sim.step(sim.pad_m(exc), 1)
-        qdd = sim.state()["qdd"][:, : model.n_dofs].double().cpu().numpy()
+        st = sim.state()
+        qdd = st["qdd"][:, :n].double().cpu().numpy()
+        force = st["force"][:, :m].double().cpu().numpy()
+        assert sim.surrogate_stats()["out_of_box"] == 0
     finally:
         sim.set_geometry_mode(0)
         sim.surrogate_set_check(0.01, 1e-3)
+    geo = sim.surrogate_predict(sim.pad_n(q)).double().cpu().numpy()
+    lay = sim.layout(0)
     om = ora.OracleModel(model)
-    errs = [qdd_rel_err(qdd[e], oracle_eval(om, DT, q[e], qd[e], act[e], exc[e])["qdd"])
-            for e in sample_envs(E, 16, seed=4)]
-    print("\nlearned-geometry qdd rel. error vs FP64 oracle (exact geometry): median %.2e max %.2e"
-          % (np.median(errs), np.max(errs)))
-    assert np.isfinite(errs).all()
+    errs, errs_exact = [], []
+    for e in sample_envs(E, 16, seed=4):
+        Lg, Rg = geo[e, :m], msim.unpack_R(geo[e, m:], lay, n)
+        r = ora.evaluate(om, DT, q[e].astype(np.float64), qd[e].astype(np.float64), act[e].astype(np.float64),
+                         exc[e].astype(np.float64), L=Lg, R=Rg)
+        assert r["status"] == 0
+        np.testing.assert_allclose(force[e], r["force"], rtol=0, atol=2e-3 * model.muscle_fmax.max())
+        errs.append(qdd_rel_err(qdd[e], r["qdd"]))
+        errs_exact.append(qdd_rel_err(qdd[e], oracle_eval(om, DT, q[e], qd[e], act[e], exc[e])["qdd"]))
+    print("\nlearned substep q_dd vs oracle fed the network geometry: max %.2e; vs oracle with the exact "
+          "geometry: median %.2e max %.2e" % (np.max(errs), np.median(errs_exact), np.max(errs_exact)))
+    assert np.max(errs) <= 1e-4
+
+
+def test_learned_rollout_against_the_exact_rollout(trained):
+    """100 substeps of 512 environments from the same state and excitations, learned geometry (1 %
+    checks, fallback) against exact geometry: both timed with CUDA events, the learned path used
+    on most environment-substeps, and q after 100 substeps reported against the exact rollout."""
+    model, sim = trained
+    q0, qd0, a0 = mg.initial_state(model, E, seed=14)
+    excs = [sim.pad_m(x) for x in mg.smooth_excitations(model, E, 100, seed=14)]
+    ex = _exact_twin(model, q0, qd0, a0)
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    sim.set_geometry_mode(1)
+    sim.surrogate_stats(reset=True)
+    times = {}
+    try:
+        for name, s_ in (("exact", ex), ("learned", sim)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for t in range(100):
+                s_.step(excs[t], 1)
+            e1.record()
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1)
+        st = sim.surrogate_stats()
+        qa = sim.state()["q"][:, : model.n_dofs]
+        qb = ex.state()["q"][:, : model.n_dofs]
+    finally:
+        sim.set_geometry_mode(0)
+    dq = (qa - qb).abs().max(1).values
+    frac = st["learned"] / max(st["env_substeps"], 1)
+    print("\nrollout 512 envs x 100 substeps: exact %.2f ms, learned %.2f ms; learned on %.3f of env-substeps "
+          "(%d checked, %d failed, %d out of box); |q_learned - q_exact| after 100 substeps: median %.2e max %.2e"
+          % (times["exact"], times["learned"], frac, st["checked"], st["check_failed"], st["out_of_box"],
+             float(dq.median()), float(dq.max())))
+    assert torch.isfinite(qa).all()
+    assert frac >= 0.5
+    assert float(dq.median()) < 0.05
 
 
 def test_surrogate_argument_and_state_errors():
