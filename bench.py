@@ -350,20 +350,23 @@ def _mlp_flops(sizes):
     return sum(2 * a * b for a, b in zip(sizes[:-1], sizes[1:]))
 
 
-def run_surrogate(args, sim, model, excs, flush, exact_value):
-    """Same rollout with the learned geometry: train, then time K steps (1 % checks, fallback).
+def run_surrogate(args, sim, model, excs, flush, exact_value, hidden=512):
+    """Same rollout with the learned geometry: train, then time K steps twice, as configured (1 %
+    checks, fallback per environment) and with the checks off (every environment inside the box
+    on the network: the learned path's own throughput).
 
     Reports the network's accuracy on fresh configurations of the training box (per entry and
     per environment, the check's measure), the fractions of environment-substeps that used the
-    network / fell outside the box / were flagged / were checked, the q drift of the learned
+    network / fell outside the box / were flagged / were checked, the q drift of each learned
     rollout from the exact rollout of the same initial state and excitations, and the network's
     forward pass alone against the tensor-core peak."""
     import torch
     E, sub = args.envs, args.substeps
     n_buf = len(excs)
+    sim.surrogate_set_width(hidden)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=1e-3)
+    sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=3e-3)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # accuracy on fresh configurations in the training box
@@ -380,9 +383,11 @@ def run_surrogate(args, sim, model, excs, flush, exact_value):
     env_err = torch.maximum(err[:, m:].pow(2).mean(1).sqrt(), err[:, :m].pow(2).mean(1).sqrt())
     q0, qd0, a0 = mg.initial_state(model, E, seed=1)
 
-    def rollout(mode, timed):
+    def rollout(mode, check_frac):
         sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
         sim.set_geometry_mode(mode)
+        if mode == 1:
+            sim.surrogate_set_check(check_frac, 1e-3)
         for t in range(args.warmup):
             sim.step(excs[t % n_buf], sub)
         torch.cuda.synchronize()
@@ -391,20 +396,35 @@ def run_surrogate(args, sim, model, excs, flush, exact_value):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         for t in range(args.steps):
-            if timed:
-                flush.fill_(float(t))
+            flush.fill_(float(t))
             starts[t].record(stream)
             sim.step(excs[(args.warmup + t) % n_buf], sub)
             ends[t].record(stream)
         torch.cuda.synchronize()
-        return float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))), sim.state()["q"][:, : model.n_dofs]
+        ms = float(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)))
+        st = sim.surrogate_stats()
+        _, flags = sim.status()
+        state = sim.state()
+        sim.surrogate_set_check(0.01, 1e-3)
+        return ms, st, flags, state["q"][:, : model.n_dofs].clone(), int((state["status"] & 1).count_nonzero())
 
-    total_ms, q_learned = rollout(1, True)
-    st = sim.surrogate_stats()
-    status, flags = sim.status()
-    nonfinite = int((sim.state()["status"] & 1).count_nonzero())
-    _, q_exact = rollout(0, False)
-    dq = (q_learned - q_exact).abs().max(1).values
+    _, _, _, q_exact, _ = rollout(0, 0.0)
+    runs = {}
+    for name, frac in (("checked", 0.01), ("unchecked", 0.0)):
+        ms, st, flags, q_l, nonfinite = rollout(1, frac)
+        n = max(st["env_substeps"], 1)
+        value = E * sub * args.steps / (ms * 1e-3)
+        dq = (q_l - q_exact).abs().max(1).values
+        runs[name] = {"value": value, "ms_per_step": ms / args.steps, "vs_exact": value / exact_value,
+                      "check_fraction": frac, "fraction_learned": st["learned"] / n,
+                      "fraction_out_of_box": st["out_of_box"] / n, "fraction_flagged": st["flagged"] / n,
+                      "fraction_checked": st["checked"] / n, "checks": st["checked"],
+                      "checks_failed": st["check_failed"],
+                      "checks_failed_fraction": st["check_failed"] / max(st["checked"], 1),
+                      "max_check_error_m": st["max_check_error"], "flagged_envs_at_end": st["flagged_envs"],
+                      "q_vs_exact_rollout_rad": {"median": float(dq.median()), "max": float(dq.max()),
+                                                 "after_substeps": (args.warmup + args.steps) * sub},
+                      "envs_non_finite": nonfinite, "status_flags": flags}
     sim.set_geometry_mode(0)
     # the network alone at this batch, for its tensor-pipe fraction (timed alone: burst peak)
     net = sim.surrogate_network()
@@ -422,37 +442,28 @@ def run_surrogate(args, sim, model, excs, flush, exact_value):
     torch.cuda.synchronize()
     mlp_ms = e0.elapsed_time(e1) / 20
     mlp_tf = _mlp_flops([model.n_dofs, net.hidden, net.hidden, net.d_out]) * E / (mlp_ms * 1e-3) / 1e12
-    peaks = _peaks()
-    pk = peaks.get("bf16_tflops") or 1800.0
-    n = max(st["env_substeps"], 1)
-    value = E * sub * args.steps / (total_ms * 1e-3)
-    frac_learned = st["learned"] / n
+    pk = _peaks().get("bf16_tflops") or 1800.0
     q = lambda x, p: float(x.quantile(p))
-    return {"value": value, "unit": UNIT, "ms_per_step": total_ms / args.steps, "vs_exact": value / exact_value,
-            "label": ("learned geometry" if frac_learned >= 0.5 else
-                      "exact geometry plus a mostly unused network (fraction_learned below 0.5)"),
-            "train_s": train_s, "train_samples": args.surr_samples, "train_epochs": args.surr_epochs,
-            "train_loss_normalised_mse": st["train_loss"],
-            "fraction_learned": frac_learned, "fraction_out_of_box": st["out_of_box"] / n,
-            "fraction_flagged": st["flagged"] / n, "fraction_checked": st["checked"] / n,
-            "checks": st["checked"], "checks_failed": st["check_failed"],
-            "checks_failed_fraction": st["check_failed"] / max(st["checked"], 1),
-            "max_check_error_m": st["max_check_error"], "flagged_envs_at_end": st["flagged_envs"],
-            "moment_arm_abs_err_m": {"median": q(eR, 0.5), "p99": q(eR, 0.99), "p999": q(eR, 0.999),
-                                     "max": float(err[:, m:].max())},
-            "length_abs_err_m": {"median": q(eL[::3], 0.5), "p99": q(eL[::3], 0.99), "max": float(err[:, :m].max())},
-            "env_check_error_m": {"median": q(env_err, 0.5), "p99": q(env_err, 0.99),
-                                  "fraction_within_tol": float((env_err <= 1e-3).float().mean()),
-                                  "definition": "max(rms of the env's moment-arm errors, rms of its length errors)"},
-            "q_vs_exact_rollout_rad": {"median": float(dq.median()), "max": float(dq.max()),
-                                       "after_substeps": (args.warmup + args.steps) * sub},
-            "mlp_forward": {"ms": mlp_ms, "tflops": mlp_tf, "peak_tflops": pk, "frac": mlp_tf / pk,
-                            "peak_note": "bf16_tflops (burst) of measured: the forward is timed alone"},
-            "envs_non_finite": nonfinite, "status_flags": flags,
-            "network": "90 -> %d -> %d -> %d, SiLU, BF16, joint-block connectivity" % (net.hidden, net.hidden,
-                                                                                     net.d_out),
-            "box": "joint limits widened by 5 % of each range",
-            "check": "1 % of envs per substep; fallback when the env's check error exceeds 1 mm"}
+    ck = runs["checked"]
+    out = {"value": ck["value"], "unit": UNIT, "ms_per_step": ck["ms_per_step"], "vs_exact": ck["vs_exact"],
+           "label": ("learned geometry" if ck["fraction_learned"] >= 0.5 else
+                     "mostly exact geometry (fallback) plus the network (fraction_learned below 0.5)"),
+           "hidden": hidden, "train_s": train_s, "train_samples": args.surr_samples,
+           "train_epochs": args.surr_epochs, "train_loss_normalised_mse": sim.surrogate_stats()["train_loss"],
+           "moment_arm_abs_err_m": {"median": q(eR, 0.5), "p99": q(eR, 0.99), "p999": q(eR, 0.999),
+                                    "max": float(err[:, m:].max())},
+           "length_abs_err_m": {"median": q(eL[::3], 0.5), "p99": q(eL[::3], 0.99), "max": float(err[:, :m].max())},
+           "env_check_error_m": {"median": q(env_err, 0.5), "p99": q(env_err, 0.99),
+                                 "fraction_within_tol": float((env_err <= 1e-3).float().mean()),
+                                 "definition": "max(rms of the env's moment-arm errors, rms of its length errors)"},
+           "rollouts": runs,
+           "mlp_forward": {"ms": mlp_ms, "tflops": mlp_tf, "peak_tflops": pk, "frac": mlp_tf / pk,
+                           "peak_note": "bf16_tflops (burst) of measured: the forward is timed alone"},
+           "network": "90 -> %d -> %d -> %d, SiLU, BF16, joint-block connectivity" % (net.hidden, net.hidden,
+                                                                                    net.d_out),
+           "box": "joint limits widened by 5 % of each range",
+           "check": "1 % of envs per substep; fallback when the env's check error exceeds 1 mm"}
+    return out
 
 
 def run_mlp(args):
@@ -488,54 +499,36 @@ def run_mlp(args):
 
 
 def run_width(args):
-    """Learned geometry: accuracy and network cost against the hidden width (2M samples, 50
-    epochs each, training box = limits + 5 %), on fresh configurations of the box."""
+    """Learned geometry against the hidden width (2M samples, 50 epochs each, training box =
+    limits + 5 %, joint-block connectivity): accuracy on fresh configurations of the box, network
+    cost, and the whole-body rollout with the learned geometry (checked as configured, and with
+    the checks off) beside the exact rollout."""
     import torch
     from paper_2603_29332_b300 import msim
     model = mg.config_model(MODEL)
-    E = args.envs
+    E, sub = args.envs, args.substeps
     sim = msim.Sim(model, E, dt=DT, seed=3)
-    m = model.n_muscles
-    lo, hi = model.dof_limit[:, 0].astype(np.float64), model.dof_limit[:, 1].astype(np.float64)
-    c, hw = 0.5 * (lo + hi), 0.5 * (hi - lo) * 1.05
-    qs = (c + hw * np.random.default_rng(99).uniform(-1, 1, (8192, model.n_dofs))).astype(np.float32)
-    qg = torch.zeros((8192, sim.pitch_n), device="cuda")
-    qg[:, : model.n_dofs] = torch.from_numpy(qs).cuda()
-    exact = sim.geometry(qg)
-    rows = []
-    for hidden in (512, 1024, 2048):
-        sim.surrogate_set_width(hidden)
-        t0 = time.perf_counter()
-        sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=1e-3)
-        torch.cuda.synchronize()
-        train_s = time.perf_counter() - t0
-        err = (sim.surrogate_predict(qg) - exact).abs()
-        eR = err[:, m:]
-        net = sim.surrogate_network()
-        X = torch.zeros((E, net.in_pitch), dtype=torch.bfloat16, device="cuda")
-        Y = torch.empty((E, net.out_pitch), device="cuda")
-        for _ in range(3):
-            net.forward(X, Y)
-        cur = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(cur)
-        for _ in range(20):
-            net.forward(X, Y)
-        e1.record(cur)
-        torch.cuda.synchronize()
-        rows.append({"hidden": hidden, "train_s": train_s,
-                     "moment_arm_abs_err_m": {"median": float(eR.median()),
-                                              "p99": float(eR.flatten()[::3].quantile(0.99)),
-                                              "max": float(eR.max())},
-                     "length_abs_err_m_median": float(err[:, :m].median()),
-                     "env_rms_err_m_median": float(err.pow(2).mean(1).sqrt().median()),
-                     "envs_with_max_err_within_1mm": float((err.max(1).values <= 1e-3).float().mean()),
-                     "forward_us_at_batch": e0.elapsed_time(e1) / 20 * 1e3})
-    return {"metric": "learned geometry accuracy vs hidden width (whole body, %d samples x %d epochs)"
-                      % (args.surr_samples, args.surr_epochs),
-            "value": rows[0]["moment_arm_abs_err_m"]["median"], "unit": "m (median moment-arm error, width 512)",
-            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "batch": E, "widths": rows}
+    n_buf = 32
+    excs = [sim.pad_m(x) for x in mg.smooth_excitations(model, E, n_buf, seed=1, dt=DT * sub)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    q0, qd0, a0 = mg.initial_state(model, E, seed=1)
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    for t in range(args.warmup):
+        sim.step(excs[t % n_buf], sub)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(args.steps):
+        sim.step(excs[(args.warmup + t) % n_buf], sub)
+    e1.record()
+    torch.cuda.synchronize()
+    exact_value = E * sub * args.steps / (e0.elapsed_time(e1) * 1e-3)
+    rows = [run_surrogate(args, sim, model, excs, flush, exact_value, hidden) for hidden in args.widths]
+    return {"metric": "learned geometry vs hidden width (whole body, %d samples x %d epochs, %d envs)"
+                      % (args.surr_samples, args.surr_epochs, E),
+            "value": rows[0]["moment_arm_abs_err_m"]["p99"], "unit": "m (p99 moment-arm error, first width)",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "exact_value": exact_value,
+            "widths": rows}
 
 
 def run_mixed(args):
@@ -623,7 +616,7 @@ def run_policy(args):
             sim.flow_attach(flow, n_steps=20, dt=0.05, sigma=0.05)
         if mode == "learned":
             sim.flow_attach(None)
-            sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=1e-3)
+            sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=3e-3)
             sim.set_geometry_mode(1)
         sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
         torch.cuda.synchronize()
@@ -676,6 +669,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
+    ap.add_argument("--widths", type=int, nargs="+", default=[512, 1024, 2048])
     ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
     ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_wrap_mix", "c1_float", "c1_tendon"],
                     help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; "

@@ -135,6 +135,18 @@ __global__ void k_mask_params(float* P, const uint8_t* mask, const float* row_sc
     }
 }
 
+// first-layer biases drawn U(-r, r), r = sum |W1 row| (the unit's largest pre-activation over
+// inputs in [-1, 1]), so that the units' SiLU bends spread over the input range
+__global__ void k_spread_b1(float* P, size_t oW1, size_t ob1, int inp, int hid, uint32_t k0, uint32_t k1) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= hid) return;
+    float r = 0.f;
+    for (int c = 0; c < inp; ++c) r += fabsf(P[oW1 + (size_t)u * inp + c]);
+    uint32_t ctr[4] = {(uint32_t)u, 0xb1a5u, 0u, 0u};
+    philox4x32_10(ctr, k0, k1);
+    P[ob1 + u] = r * (2.f * u01_from_bits(ctr[0]) - 1.f);
+}
+
 int nblocks(size_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
 
 cudaError_t transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds, __nv_bfloat16* dst, int ldd,
@@ -234,7 +246,7 @@ cudaError_t mlp_init(Mlp* m, uint64_t seed, float out_scale, cudaStream_t s) {
     return mlp_sync_bf16(m, s);
 }
 
-cudaError_t mlp_set_mask(Mlp* m, const uint8_t* host_mask, cudaStream_t s) {
+cudaError_t mlp_set_mask(Mlp* m, const uint8_t* host_mask, uint64_t spread_seed, cudaStream_t s) {
     // per weight row: the mlp_init bound sqrt(6 / fan_in) becomes sqrt(3 / fan) over the row's
     // unmasked entries
     const int rows = 2 * m->hid + m->outp;
@@ -255,6 +267,11 @@ cudaError_t mlp_set_mask(Mlp* m, const uint8_t* host_mask, cudaStream_t s) {
     if (e == cudaSuccess) {
         k_mask_params<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->mask, d_scale, m->n_params, m->oW1, m->inp, m->hid,
                                                              m->oW2, m->oW3, m->outp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && spread_seed) {
+        k_spread_b1<<<(m->hid + 127) / 128, 128, 0, s>>>(m->P, m->oW1, m->ob1, m->inp, m->hid, (uint32_t)spread_seed,
+                                                        (uint32_t)(spread_seed >> 32));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = mlp_sync_bf16(m, s);

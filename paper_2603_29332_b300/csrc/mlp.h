@@ -54,9 +54,11 @@ cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T
 cudaError_t mlp_adam(Mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t s);
 // Connectivity mask (host array [n_params] in the flat layout, 1 = trainable): masked weights are
 // set to zero and stay there; each weight row is re-drawn to the uniform bound sqrt(3 / fan),
-// fan = its unmasked entries (variance 1 / fan), from the values mlp_init drew.  Call after
-// mlp_init.  Synchronous (the host array may be freed on return).
-cudaError_t mlp_set_mask(Mlp* m, const uint8_t* host_mask, cudaStream_t s);
+// fan = its unmasked entries (variance 1 / fan), from the values mlp_init drew; with a non-zero
+// spread_seed the first-layer biases are drawn U(-r, r), r the sum of the row's |weights|, so the
+// units' bends spread over inputs in [-1, 1].  Call after mlp_init.  Synchronous (the host array
+// may be freed on return).
+cudaError_t mlp_set_mask(Mlp* m, const uint8_t* host_mask, uint64_t spread_seed, cudaStream_t s);
 
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): 4 x 32 random bits for a 128-bit counter
 // and a 64-bit key.  Shared by the surrogate's sampler and the policy's exploration.

@@ -1418,7 +1418,8 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
     if (e == cudaSuccess && h->surr_structured) {
         std::vector<uint8_t> mask;
         if (surrogate_mask(h->models[0], S->net, m, mask)) {
-            e = mlp_set_mask(S->net, mask.data(), s);
+            e = mlp_set_mask(S->net, mask.data(), kSurrSpreadBias ? (uint64_t)h->seed * 0x9e3779b97f4a7c15ull + 5u : 0u,
+                             s);
             S->structured = 1;
         }
     }

@@ -1356,7 +1356,22 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
         }
         g.sync();
     }
+#ifdef MSIM_FACTOR_ONE_WARP
+    // the factorisation and solves on the group's first warp alone (warp-synchronous), the other
+    // warps wait at the group barrier below
+    bool ok = true;
+    if (WPE == 1 || g.wi == 0) {
+        Grp<1> g1;
+        g1.wl = g.wl;
+        g1.wi = 0;
+        g1.lane = g.wl;
+        g1.bar = g.bar;
+        ok = phase_factor_solve(T, ws, g1);
+    }
+    ok = g.all(ok);
+#else
     const bool ok = phase_factor_solve(T, ws, g);
+#endif
     PHASE_MARK(6);
     uint32_t st = (ok ? 0u : kEnvNotSpd) | (bad ? kEnvNonFinite : 0u) | ((mflags & 2u) ? 0x100u : 0u);
     const fac* Y = reinterpret_cast<const fac*>(ws + H.w_y);

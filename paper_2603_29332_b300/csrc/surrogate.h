@@ -16,6 +16,8 @@
 namespace msim {
 
 constexpr int kSurrHidden = 512;
+// joint-structured network: first-layer biases spread over each unit's input range at init
+constexpr bool kSurrSpreadBias = false;
 
 struct Surrogate {
     int n = 0, m = 0, nnz = 0, out = 0;   // DoFs, muscles, moment-arm entries, outputs m + nnz
