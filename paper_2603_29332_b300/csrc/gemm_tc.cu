@@ -161,6 +161,8 @@ __global__ void __launch_bounds__(192, 2)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     int* failed = reinterpret_cast<int*>(tmem_slot + 1);
     float* sbias = reinterpret_cast<float*>(tmem_slot + 4);   // BN floats
+    float* sscale = sbias + BN;                                  // BN floats (with p.scale)
+    float* sshift = sscale + BN;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
@@ -231,7 +233,13 @@ __global__ void __launch_bounds__(192, 2)
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. output rows of that quarter;
         // once `done` fired every MMA has completed, so the operand ring is free for staging.
         // The tile's bias goes to shared memory while the main loop runs.
-        for (int j = threadIdx.x - 64; j < BN; j += 128) sbias[j] = (p.bias && n0 + j < p.N) ? p.bias[n0 + j] : 0.f;
+        for (int j = threadIdx.x - 64; j < BN; j += 128) {
+            sbias[j] = (p.bias && n0 + j < p.N) ? p.bias[n0 + j] : 0.f;
+            if (p.scale) {
+                sscale[j] = n0 + j < p.N ? p.scale[n0 + j] : 0.f;
+                sshift[j] = n0 + j < p.N ? p.shift[n0 + j] : 0.f;
+            }
+        }
         asm volatile("bar.sync 1, 128;" ::: "memory");
         const bool ok = mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -263,6 +271,10 @@ __global__ void __launch_bounds__(192, 2)
             for (int j = 0; j < 32; ++j) {
                 z[j] = __uint_as_float(r[j]) + sbias[c + j];
                 v[j] = act_fn(z[j], p.act);
+            }
+            if (p.scale) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = fmaf(v[j], sscale[c + j], sshift[c + j]);
             }
             store_block(stg, v, lane, p.C, p.ldc, p.c_bf16 != 0, row0, cn, p.M, p.N, p.vec_ok != 0);
             if (p.Z) store_block(stg, z, lane, p.Z, p.ldz, true, row0, cn, p.M, p.N, p.z_vec_ok != 0);
@@ -307,7 +319,7 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int 
 
 template <int BN, int kStages>
 constexpr size_t gemm_smem() {
-    return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16 + BN * 4;
+    return 1024 + (size_t)kStages * (kBM * kBK * 2 + BN * kBK * 2) + (2 * kStages + 1) * 8 + 16 + 3 * BN * 4;
 }
 // the epilogue staging (4 warps x 32 rows x kStage floats) reuses the operand ring
 static_assert(4 * 32 * kStage * 4 <= 2 * (kBM * kBK * 2 + 128 * kBK * 2), "staging must fit in the ring");

@@ -45,8 +45,7 @@ struct StepArgs {
     // surrogate step (one substep per launch)
     const float* surr_Y;          // network output rows, row (e - env_begin), pitch surr_ld
     int surr_ld;
-    const float* surr_mu;         // output de-normalisation
-    const float* surr_sd;
+    const int* surr_colbase;      // head layout: first column of each group of 32 muscle records
     const float* box_c;           // training box: |q - box_c| <= box_s per DoF
     const float* box_s;
     uint8_t* fallback;            // per environment: 1 = exact geometry until reset

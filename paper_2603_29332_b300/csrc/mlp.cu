@@ -157,11 +157,12 @@ cudaError_t transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds, __nv
 }
 
 cudaError_t gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, void* C, int ldc, int c_bf16,
-                 const float* bias, int act, void* Z, int ldz, uint32_t* err, cudaStream_t s) {
+                 const float* bias, int act, void* Z, int ldz, uint32_t* err, cudaStream_t s,
+                 const float* scale = nullptr, const float* shift = nullptr) {
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));
     g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc; g.c_bf16 = c_bf16; g.bias = bias; g.act = act;
-    g.Z = Z; g.ldz = ldz; g.err = err;
+    g.Z = Z; g.ldz = ldz; g.err = err; g.scale = scale; g.shift = shift;
     return gemm_bf16_tc(A, lda, B, ldb, g, s);
 }
 
@@ -224,6 +225,7 @@ void mlp_destroy(Mlp* m) {
 }
 
 cudaError_t mlp_sync_bf16(Mlp* m, cudaStream_t s) {
+    ++m->version;
     k_to_bf16<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->Ph, m->n_params);
     CK(cudaGetLastError());
     dim3 block(32, 8);
@@ -296,6 +298,15 @@ cudaError_t mlp_infer(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, 
     return gemm(m->H2, h, m->Ph + m->oW3, h, B, m->out, h, Y, ldy, 0, m->P + m->ob3, m->out_act, nullptr, 0, m->err, s);
 }
 
+cudaError_t mlp_infer_head(Mlp* m, const __nv_bfloat16* X, int ldx, int B, const __nv_bfloat16* W3, const float* b3,
+                           int N, const float* scale, const float* shift, float* Y, int ldy, cudaStream_t s) {
+    if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;
+    const int h = m->hid;
+    CK(gemm(X, ldx, m->Ph + m->oW1, m->inp, B, h, m->in, m->H1, h, 1, m->P + m->ob1, 1, nullptr, 0, m->err, s));
+    CK(gemm(m->H1, h, m->Ph + m->oW2, h, B, h, h, m->H2, h, 1, m->P + m->ob2, 1, nullptr, 0, m->err, s));
+    return gemm(m->H2, h, W3, h, B, N, h, Y, ldy, 0, b3, 0, nullptr, 0, m->err, s, scale, shift);
+}
+
 cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T, int ldt, int B, cudaStream_t s) {
     if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;
     const int h = m->hid, bp = pad8(B);
@@ -333,6 +344,7 @@ cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T
 
 cudaError_t mlp_adam(Mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t s) {
     m->adam_t += 1;
+    ++m->version;
     const float bc1 = 1.f - powf(beta1, (float)m->adam_t), bc2 = 1.f - powf(beta2, (float)m->adam_t);
     k_adam<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->G, m->Am, m->Av, m->n_params, lr, beta1, beta2, eps, bc1,
                                                   bc2, m->Ph, m->mask);

@@ -34,6 +34,7 @@ struct Mlp {
     float* loss_acc;       // device scalar: sum of squared errors of the last backward
     uint32_t* err;         // device word: GEMM bounded-wait failures
     uint8_t* mask;         // [n_params] 1 = trainable, 0 = held at zero (nullptr: every parameter)
+    uint64_t version;      // counts changes of the parameters (set, init, Adam steps)
 };
 
 cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp** out_mlp);
@@ -47,6 +48,10 @@ cudaError_t mlp_sync_bf16(Mlp* m, cudaStream_t s);
 cudaError_t mlp_forward(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s);
 // the same without the pre-activation copies a later backward needs (inference)
 cudaError_t mlp_infer(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s);
+// inference with another output layer: layers 1-2 of m, then Y = (H2 W3^T + b3) * scale + shift
+// (W3 [N][hid] BF16, b3, scale, shift [N]; identity output activation)
+cudaError_t mlp_infer_head(Mlp* m, const __nv_bfloat16* X, int ldx, int B, const __nv_bfloat16* W3, const float* b3,
+                           int N, const float* scale, const float* shift, float* Y, int ldy, cudaStream_t s);
 // gradients of mean((y - t)^2) into G (forward included); T [B][ldt] FP32
 cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T, int ldt, int B, cudaStream_t s);
 // one Adam step (Kingma & Ba 2015) on G, refreshes the BF16 copies; parameters outside the mask

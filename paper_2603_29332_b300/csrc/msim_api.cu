@@ -746,6 +746,8 @@ void surr_free(Surrogate* s) {
     cudaFree(s->mu); cudaFree(s->sd); cudaFree(s->box_c); cudaFree(s->box_s);
     cudaFree(s->X); cudaFree(s->Y); cudaFree(s->fallback); cudaFree(s->stats); cudaFree(s->step_ctr);
     cudaFree(s->out_tmp);
+    cudaFree(s->colbase); cudaFree(s->head_src); cudaFree(s->W3h); cudaFree(s->b3h); cudaFree(s->scale_h);
+    cudaFree(s->shift_h);
     delete s;
 }
 
@@ -815,6 +817,35 @@ cudaError_t fk_launch(msim_handle h, int i, const float* q, int ldq, int n_rows,
     return launch_fk(a, std::max(1, std::min(groups, h->num_sms * per_sm)), smem, s);
 }
 
+// Column layout of the inference head (see Surrogate): muscle records in the model image's order,
+// by groups of 32 (the records one warp takes in one pass); group g's C_g = 32 (1 + its largest
+// crossed-DoF count) columns hold entry s of record 32 g + l at colbase[g] + 32 s + l.
+void head_layout(const ModelHost& M, int m, std::vector<int>& colbase, std::vector<int>& src) {
+    const MuscleRec* mus = reinterpret_cast<const MuscleRec*>(M.blob.data() + M.hdr.o_muscle);
+    colbase.clear();
+    src.clear();
+    for (int g0 = 0; g0 < m; g0 += 32) {
+        int J = 1;
+        for (int r = g0; r < std::min(m, g0 + 32); ++r) J = std::max(J, 1 + (int)mus[r].nx);
+        colbase.push_back((int)src.size());
+        const size_t base = src.size();
+        src.resize(base + 32 * (size_t)J, -1);
+        for (int r = g0; r < std::min(m, g0 + 32); ++r)
+            for (int e = 0; e <= mus[r].nx; ++e)
+                src[base + 32 * e + (r - g0)] = e == 0 ? mus[r].orig : m + mus[r].x0 + e - 1;
+    }
+}
+
+// the inference head gathered again if the network changed since (training, msim_mlp_set)
+cudaError_t surr_head(Surrogate* S, cudaStream_t s) {
+    const Mlp* net = S->net;
+    if (S->head_version == net->version) return cudaSuccess;
+    const cudaError_t e = surr_gather_head(net->Ph + net->oW3, net->P + net->ob3, S->mu, S->sd, net->hid, S->head_src,
+                                           S->cols, S->W3h, S->b3h, S->scale_h, S->shift_h, s);
+    if (e == cudaSuccess) S->head_version = net->version;
+    return e;
+}
+
 msim_status surrogate_step(msim_handle h, const float* exc, int n_sub, cudaStream_t s) {
     Surrogate* S = h->sur;
     if (!S || !S->trained) {
@@ -825,13 +856,16 @@ msim_status surrogate_step(msim_handle h, const float* exc, int n_sub, cudaStrea
     for (int k = 0; k < n_sub; ++k) {
         cudaError_t e = launch_surr_input(h->q, h->pitch_n, 0, h->n_envs, S->box_c, S->box_s, S->n, S->X, net->inp,
                                           S->step_ctr, s);
-        if (e == cudaSuccess) e = mlp_infer(S->net, S->X, net->inp, h->n_envs, S->Y, net->outp, s);
+        if (e == cudaSuccess) e = surr_head(S, s);
+        if (e == cudaSuccess)
+            e = mlp_infer_head(S->net, S->X, net->inp, h->n_envs, S->W3h, S->b3h, S->cols, S->scale_h, S->shift_h,
+                               S->Y, S->cols, s);
         if (e == cudaSuccess) {
             StepArgs a = base_args(h, 0);
             a.exc = exc;
             a.n_sub = 1;
-            a.surr_Y = S->Y; a.surr_ld = net->outp;
-            a.surr_mu = S->mu; a.surr_sd = S->sd;
+            a.surr_Y = S->Y; a.surr_ld = S->cols;
+            a.surr_colbase = S->colbase;
             a.box_c = S->box_c; a.box_s = S->box_s;
             a.fallback = S->fallback; a.surr_stats = S->stats;
             a.check_frac = S->check_frac; a.tol = S->tol;
@@ -1428,8 +1462,16 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
     };
     A((void**)&S->mu, outp * 4); A((void**)&S->sd, outp * 4);
     A((void**)&S->box_c, h->pitch_n * 4); A((void**)&S->box_s, h->pitch_n * 4);
-    A((void**)&S->X, (size_t)h->n_envs * inp * 2); A((void**)&S->Y, (size_t)h->n_envs * outp * 4);
-    A((void**)&S->out_tmp, (size_t)h->n_envs * outp * 4);
+    std::vector<int> colbase, head_src;
+    head_layout(h->models[0], m, colbase, head_src);
+    S->cols = (int)head_src.size();
+    A((void**)&S->X, (size_t)h->n_envs * inp * 2); A((void**)&S->Y, (size_t)h->n_envs * S->cols * 4);
+    A((void**)&S->out_tmp, (size_t)h->n_envs * S->cols * 4);
+    A((void**)&S->colbase, colbase.size() * 4); A((void**)&S->head_src, head_src.size() * 4);
+    A((void**)&S->W3h, (size_t)S->cols * h->surr_hidden * 2); A((void**)&S->b3h, S->cols * 4);
+    A((void**)&S->scale_h, S->cols * 4); A((void**)&S->shift_h, S->cols * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(S->colbase, colbase.data(), colbase.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(S->head_src, head_src.data(), head_src.size() * 4, cudaMemcpyHostToDevice);
     A((void**)&S->fallback, h->n_envs); A((void**)&S->stats, 8 * 8); A((void**)&S->step_ctr, 4);
     __nv_bfloat16* Xall = nullptr;
     float *T = nullptr, *qc = nullptr;
@@ -1609,9 +1651,12 @@ msim_status msim_surrogate_predict(msim_handle h, const float* q, int32_t ldq, i
     for (int r0 = 0; r0 < n_rows && e == cudaSuccess; r0 += h->n_envs) {
         const int rows = std::min(h->n_envs, n_rows - r0);
         e = launch_surr_input(q, ldq, r0, rows, S->box_c, S->box_s, S->n, S->X, S->net->inp, nullptr, s);
-        if (e == cudaSuccess) e = mlp_infer(S->net, S->X, S->net->inp, rows, S->out_tmp, S->net->outp, s);
+        if (e == cudaSuccess) e = surr_head(S, s);
         if (e == cudaSuccess)
-            e = surr_denorm(S->out_tmp, S->net->outp, rows, S->out, S->mu, S->sd, out + (size_t)r0 * ld_out, ld_out, s);
+            e = mlp_infer_head(S->net, S->X, S->net->inp, rows, S->W3h, S->b3h, S->cols, S->scale_h, S->shift_h,
+                               S->out_tmp, S->cols, s);
+        if (e == cudaSuccess)
+            e = surr_unpermute(S->out_tmp, S->cols, rows, S->head_src, S->cols, out + (size_t)r0 * ld_out, ld_out, s);
     }
     return e == cudaSuccess ? MSIM_OK : cuda_fail(h, e, "msim_surrogate_predict");
 }

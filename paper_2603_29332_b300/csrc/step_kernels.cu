@@ -690,9 +690,8 @@ __device__ __forceinline__ float fibre_velocity(float A, float c0) {
 // de-normalisation, whether this environment must use the exact geometry (outside the training
 // box, or flagged), whether this substep cross-checks the two, and the check's tolerance.
 struct SurrCtx {
-    const float* Y;
-    const float* mu;
-    const float* sd;
+    const float* Y;               // the environment's row of the inference head (physical units)
+    const int* colbase;           // first column of each group of 32 muscle records
     bool use_exact;
     bool check;
     float tol;
@@ -864,23 +863,22 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             }
         }
         if (is_surr(MODE) && learned) {
-            // learned geometry: de-normalised network outputs (L first, then R in sparse order)
-            const int mm = H.m;
-            const float Ls = sc->Y[k] * sc->sd[k] + sc->mu[k];
+            // learned geometry: the record's length and moment arms from the inference head, entry
+            // e at column colbase[r / 32] + 32 e + r % 32 (a warp reads each entry as one run)
+            const float* Yr = sc->Y + sc->colbase[r >> 5] + (r & 31);
+            const float Ls = Yr[0];
             if (sc->check) {
                 // squared errors against the exact geometry, summed over the environment below
                 const float dl = Ls - L;
                 se_len += dl * dl;
                 for (int i = 0; i < M.nx; ++i) {
-                    const int o = mm + M.x0 + i;
-                    const float dr = sc->Y[o] * sc->sd[o] + sc->mu[o] - rk[i * g.N + g.lane];
+                    const float dr = Yr[32 * (i + 1)] - rk[i * g.N + g.lane];
                     se_arm += dr * dr;
                 }
             } else {
                 L = Ls;
                 for (int i = 0; i < M.nx; ++i) {
-                    const int o = mm + M.x0 + i;
-                    const float Rv = sc->Y[o] * sc->sd[o] + sc->mu[o];
+                    const float Rv = Yr[32 * (i + 1)];
                     rk[i * g.N + g.lane] = Rv;
                     ldot -= Rv * qd[cross_dof(T.cross[M.x0 + i])];
                 }
@@ -1356,22 +1354,7 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
         }
         g.sync();
     }
-#ifdef MSIM_FACTOR_ONE_WARP
-    // the factorisation and solves on the group's first warp alone (warp-synchronous), the other
-    // warps wait at the group barrier below
-    bool ok = true;
-    if (WPE == 1 || g.wi == 0) {
-        Grp<1> g1;
-        g1.wl = g.wl;
-        g1.wi = 0;
-        g1.lane = g.wl;
-        g1.bar = g.bar;
-        ok = phase_factor_solve(T, ws, g1);
-    }
-    ok = g.all(ok);
-#else
     const bool ok = phase_factor_solve(T, ws, g);
-#endif
     PHASE_MARK(6);
     uint32_t st = (ok ? 0u : kEnvNotSpd) | (bad ? kEnvNonFinite : 0u) | ((mflags & 2u) ? 0x100u : 0u);
     const fac* Y = reinterpret_cast<const fac*>(ws + H.w_y);
@@ -1447,8 +1430,7 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             philox4x32_10(c, a.surr_seed, 0x9e3779b9u);
             SurrCtx sc;
             sc.Y = a.surr_Y + (size_t)(e - a.env_begin) * a.surr_ld;
-            sc.mu = a.surr_mu;
-            sc.sd = a.surr_sd;
+            sc.colbase = a.surr_colbase;
             sc.use_exact = oob || flagged;
             sc.check = !sc.use_exact && u01_from_bits(c[0]) < a.check_frac;
             sc.tol = a.tol;

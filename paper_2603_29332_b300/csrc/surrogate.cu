@@ -78,12 +78,28 @@ __global__ void k_normalize(float* T, int ldt, int64_t n_rows, int cols, const f
     }
 }
 
-__global__ void k_denorm(const float* Y, int ldy, int n_rows, int cols, const float* mu, const float* sd, float* out,
-                         int ldo) {
+__global__ void k_gather_head(const __nv_bfloat16* W3, const float* b3, const float* mu, const float* sd, int hid,
+                              const int* head_src, int cols, __nv_bfloat16* W3h, float* b3h, float* scale_h,
+                              float* shift_h) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)cols * hid;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / hid), j = (int)(i % hid);
+        const int src = head_src[c];
+        W3h[i] = src >= 0 ? W3[(size_t)src * hid + j] : __float2bfloat16_rn(0.f);
+        if (j == 0) {
+            b3h[c] = src >= 0 ? b3[src] : 0.f;
+            scale_h[c] = src >= 0 ? sd[src] : 0.f;
+            shift_h[c] = src >= 0 ? mu[src] : 0.f;
+        }
+    }
+}
+
+__global__ void k_unpermute(const float* Yh, int ldh, int n_rows, const int* head_src, int cols, float* out, int ldo) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_rows * cols;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / cols), j = (int)(i % cols);
-        out[(size_t)r * ldo + j] = Y[(size_t)r * ldy + j] * sd[j] + mu[j];
+        const int r = (int)(i / cols), c = (int)(i % cols);
+        const int src = head_src[c];
+        if (src >= 0) out[(size_t)r * ldo + src] = Yh[(size_t)r * ldh + c];
     }
 }
 
@@ -115,10 +131,18 @@ cudaError_t surr_finalize(const double* acc, int cols, int colp, double N, float
     return cudaGetLastError();
 }
 
-cudaError_t surr_denorm(const float* Y, int ldy, int n_rows, int cols, const float* mu, const float* sd, float* out,
-                        int ldo, cudaStream_t st) {
+cudaError_t surr_gather_head(const __nv_bfloat16* W3, const float* b3, const float* mu, const float* sd, int hid,
+                             const int* head_src, int cols, __nv_bfloat16* W3h, float* b3h, float* scale_h,
+                             float* shift_h, cudaStream_t st) {
+    k_gather_head<<<blocks_for((size_t)cols * hid, 256), 256, 0, st>>>(W3, b3, mu, sd, hid, head_src, cols, W3h, b3h,
+                                                                        scale_h, shift_h);
+    return cudaGetLastError();
+}
+
+cudaError_t surr_unpermute(const float* Yh, int ldh, int n_rows, const int* head_src, int cols, float* out, int ldo,
+                           cudaStream_t st) {
     if (n_rows <= 0) return cudaSuccess;
-    k_denorm<<<blocks_for((size_t)n_rows * cols, 256), 256, 0, st>>>(Y, ldy, n_rows, cols, mu, sd, out, ldo);
+    k_unpermute<<<blocks_for((size_t)n_rows * cols, 256), 256, 0, st>>>(Yh, ldh, n_rows, head_src, cols, out, ldo);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,19 @@ struct Surrogate {
     uint32_t seed = 0;
     float check_frac = 0.01f, tol = 1e-3f;
     float box_margin = 0.05f;             // box half-width = (1 + margin) x half the limit range
+    // inference head in the step kernel's order: output column c = colbase[g] + 32 s + l holds
+    // entry s (0 the length, 1.. the moment arms) of muscle record 32 g + l, so that a warp's 32
+    // lanes read one contiguous run; head_src[c] = the network output it comes from (-1: padding).
+    // Its rows are those of the network's output layer, gathered, with the de-normalisation as the
+    // GEMM epilogue's scale (sd) and shift (mu): the values are the network's, in physical units.
+    int cols = 0;                         // C, a multiple of 32
+    int* colbase = nullptr;               // [record groups]
+    int* head_src = nullptr;              // [C]
+    __nv_bfloat16* W3h = nullptr;         // [C][hid]
+    float* b3h = nullptr;                 // [C]
+    float* scale_h = nullptr;             // [C] sd of the source output (0 for padding)
+    float* shift_h = nullptr;             // [C] mu of the source output
+    uint64_t head_version = ~0ull;        // network version the head was gathered from
     int trained = 0;
     int structured = 0;                   // 1: joint-block connectivity (msim_surrogate_set_structure)
     float loss = 0.f;                     // mean squared normalised error of the last epoch
@@ -49,9 +62,14 @@ cudaError_t surr_col_stats(const float* T, int ldt, int n_rows, int cols, double
 // mu = mean, sd = max(std, sd_floor) from acc over N rows; columns [cols, colp) get mu 0, sd 1
 cudaError_t surr_finalize(const double* acc, int cols, int colp, double N, float sd_floor, float* mu, float* sd,
                           cudaStream_t st);
-// out[r][j] = Y[r][j] * sd[j] + mu[j] for j < cols
-cudaError_t surr_denorm(const float* Y, int ldy, int n_rows, int cols, const float* mu, const float* sd, float* out,
-                        int ldo, cudaStream_t st);
+// the inference head from the network's output layer (rows of W3 [outp][hid] BF16 and b3), mu
+// and sd, per head_src (see Surrogate)
+cudaError_t surr_gather_head(const __nv_bfloat16* W3, const float* b3, const float* mu, const float* sd, int hid,
+                             const int* head_src, int cols, __nv_bfloat16* W3h, float* b3h, float* scale_h,
+                             float* shift_h, cudaStream_t st);
+// out[r][head_src[c]] = Yh[r][c] for the head's non-padding columns (back to the network's order)
+cudaError_t surr_unpermute(const float* Yh, int ldh, int n_rows, const int* head_src, int cols, float* out, int ldo,
+                           cudaStream_t st);
 // T = (T - mu) / sd over the first `cols` columns; the pad columns become 0
 cudaError_t surr_normalize(float* T, int ldt, int64_t n_rows, int cols, const float* mu, const float* sd,
                            cudaStream_t st);
