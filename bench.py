@@ -366,7 +366,7 @@ def run_surrogate(args, sim, model, excs, flush, exact_value, hidden=512):
     sim.surrogate_set_width(hidden)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=3e-3)
+    sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=args.surr_lr)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # accuracy on fresh configurations in the training box
@@ -616,7 +616,7 @@ def run_policy(args):
             sim.flow_attach(flow, n_steps=20, dt=0.05, sigma=0.05)
         if mode == "learned":
             sim.flow_attach(None)
-            sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=3e-3)
+            sim.train_surrogate(args.surr_samples, args.surr_epochs, batch=4096, lr=args.surr_lr)
             sim.set_geometry_mode(1)
         sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
         torch.cuda.synchronize()
@@ -670,6 +670,7 @@ def main():
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
     ap.add_argument("--widths", type=int, nargs="+", default=[512, 1024, 2048])
+    ap.add_argument("--surr-lr", type=float, default=3e-3)
     ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
     ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_wrap_mix", "c1_float", "c1_tendon"],
                     help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; "
