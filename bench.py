@@ -340,7 +340,10 @@ def run_gpu(args, rank, world, local_rank):
            "precision_note": "FP32 throughout except the mass-matrix entries and their L^T L factorisation, "
                              "which use float-float pairs on the FP32 pipes"}
     if args.surrogate and world == 1:
-        out["surrogate"] = run_surrogate(args, sim, model, excs, flush, value)
+        # the network that meets the stated error (1 mm), then the configured 512-wide one
+        out["surrogate"] = run_surrogate(args, sim, model, excs, flush, value, args.surr_hidden)
+        if args.surr_hidden != 512:
+            out["surrogate_configured_width"] = run_surrogate(args, sim, model, excs, flush, value, 512)
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model)
     return out
@@ -670,7 +673,8 @@ def main():
     ap.add_argument("--surr-samples", type=int, default=2097152)
     ap.add_argument("--surr-epochs", type=int, default=50)
     ap.add_argument("--widths", type=int, nargs="+", default=[512, 1024, 2048])
-    ap.add_argument("--surr-lr", type=float, default=3e-3)
+    ap.add_argument("--surr-lr", type=float, default=6e-3)
+    ap.add_argument("--surr-hidden", type=int, default=2048)
     ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
     ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_wrap_mix", "c1_float", "c1_tendon"],
                     help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; "
