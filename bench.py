@@ -469,6 +469,39 @@ def run_surrogate(args, sim, model, excs, flush, exact_value, hidden=512):
     return out
 
 
+def run_substep(args):
+    """The learned-geometry substep against the exact one, per substep (for launch lists): the
+    whole body, a briefly trained network (8192 configurations, 1 epoch: its accuracy is not the
+    point), the exact step of 2 substeps, then K learned substeps with the checks off."""
+    import torch
+    from paper_2603_29332_b300 import msim
+    model = mg.config_model(MODEL)
+    E = args.envs
+    sim = msim.Sim(model, E, dt=DT, seed=3)
+    sim.surrogate_set_width(args.surr_hidden)
+    sim.train_surrogate(8192, 1, batch=4096, lr=args.surr_lr)
+    q0, qd0, a0 = mg.initial_state(model, E, seed=1)
+    exc = sim.pad_m(mg.smooth_excitations(model, E, 1, seed=1, dt=DT * 10)[0])
+    sim.reset(sim.pad_n(q0), sim.pad_n(qd0), sim.pad_m(a0))
+    cur = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(cur)
+    sim.step(exc, 2)
+    e1.record(cur)
+    sim.set_geometry_mode(1)
+    sim.surrogate_set_check(0.0, 1e-3)
+    for _ in range(args.steps):
+        sim.step(exc, 1)
+    e2.record(cur)
+    torch.cuda.synchronize()
+    sim.set_geometry_mode(0)
+    exact_us, learned_us = e0.elapsed_time(e1) * 1e3 / 2, e1.elapsed_time(e2) * 1e3 / args.steps
+    return {"metric": "us per substep, learned geometry (width %d, checks off) vs exact, whole body x %d envs"
+                      % (args.surr_hidden, E), "value": learned_us, "unit": "us per substep",
+            "exact_us_per_substep": exact_us, "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+            "data": "synthetic"}
+
+
 def run_mlp(args):
     """The surrogate network's forward pass alone (90 -> 512 -> 512 -> m + nnz, random init) at
     the whole-body batch: the tensor-core kernels of the learned geometry, for profiling."""
@@ -675,7 +708,7 @@ def main():
     ap.add_argument("--widths", type=int, nargs="+", default=[512, 1024, 2048])
     ap.add_argument("--surr-lr", type=float, default=6e-3)
     ap.add_argument("--surr-hidden", type=int, default=2048)
-    ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width"])
+    ap.add_argument("--workload", default="c1_exact", choices=["c1_exact", "c2_mixed", "c4_policy", "c3_mlp", "c3_width", "c3_substep"])
     ap.add_argument("--model", default=MODEL, choices=[MODEL, "c1_wrap", "c1_wrap_mix", "c1_float", "c1_tendon"],
                     help="model of the c1_exact workload (c1_wrap: a quarter of the muscles wrap a cylinder; "
                          "c1_float: a free root; c1_tendon: compliant tendons)")
@@ -695,6 +728,8 @@ def main():
         out = run_policy(args)
     elif args.workload == "c3_mlp":
         out = run_mlp(args)
+    elif args.workload == "c3_substep":
+        out = run_substep(args)
     elif args.workload == "c3_width":
         out = run_width(args)
     else:
