@@ -12,6 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmsim.so")
+# the same library with every index through the step kernel's views checked (MSIM_BOUNDS_CHECK):
+# test infrastructure, the stand-in for a memory checker
+CHECK_LIB = os.path.join(HERE, "libmsim_check.so")
 SOURCES = ["msim_api.cu", "step_kernels.cu", "gemm_tc.cu", "mlp.cu", "surrogate.cu", "noalloc.cu", "tune.cu", "policy.cu", "peak.cu"]
 HEADERS = ["image.h", "kernels.h", "dfloat.cuh", "gemm_tc.h", "mlp.h", "surrogate.h", "handle.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -41,21 +44,27 @@ def step_digest():
     return _digest(STEP_FILES)
 
 
-def build(force=False, verbose=False):
-    stamp = LIB + ".sha256"
-    dig = _digest()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read().strip() == dig:
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["nvcc"] + ARCH + FLAGS + ["-I", os.path.join(ROOT, "include"), "-o", tmp] + \
+def build(force=False, verbose=False, lib=LIB, defines=()):
+    stamp = lib + ".sha256"
+    dig = _digest() + " ".join(defines)
+    if not force and os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read().strip() == dig:
+        return lib
+    tmp = lib + ".tmp%d" % os.getpid()
+    cmd = ["nvcc"] + ARCH + FLAGS + list(defines) + ["-I", os.path.join(ROOT, "include"), "-o", tmp] + \
           [os.path.join(CSRC, s) for s in SOURCES] + ["-lcudart"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(dig + "\n")
-    return LIB
+    return lib
+
+
+def build_check(force=False, verbose=False):
+    """The bounds-checking library (``libmsim_check.so``): every index through the step kernel's
+    views of its workspace and model tables is checked; see ``msim_debug_bounds``."""
+    return build(force, verbose, CHECK_LIB, ("-DMSIM_BOUNDS_CHECK",))
 
 
 if __name__ == "__main__":

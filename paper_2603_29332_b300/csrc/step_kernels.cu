@@ -55,66 +55,178 @@ constexpr uint32_t kEnvNotSpd = 0x2u;
 constexpr uint32_t kFlagTimeout = 0x100u;
 constexpr long long kWaitLimit = 1LL << 22;   // bounded mbarrier wait (iterations of try_wait)
 
+// Views of the workspace regions, the image tables and the environment's global rows.  In the
+// normal build a view is the raw pointer.  Built with -DMSIM_BOUNDS_CHECK (the stand-in for a
+// memory checker: compute-sanitizer is not used), every index through a view is checked against
+// the extent of its region, table or row; an index outside it is recorded (count, and site =
+// source line, index and extent of the first one) and replaced by 0, so the access itself stays
+// in bounds and the run goes on.  The host reads the record with msim_debug_bounds.
+#ifdef MSIM_BOUNDS_CHECK
+__device__ unsigned int g_bounds_rec[4];   // hits, first site, first index, first extent
+
+__device__ __noinline__ void bounds_hit(int site, long long i, int n) {
+    if (atomicAdd(&g_bounds_rec[0], 1u) == 0u) {
+        g_bounds_rec[1] = (unsigned)site;
+        g_bounds_rec[2] = (unsigned)i;
+        g_bounds_rec[3] = (unsigned)n;
+    }
+}
+
+template <class T>
+struct View {
+    T* p;
+    int n;      // elements in range
+    int site;   // source line that made the view
+    template <class I>
+    __device__ __forceinline__ T& operator[](I i) const {
+        long long k = (long long)i;
+        if (k < 0 || k >= n) {
+            bounds_hit(site, k, n);
+            k = 0;
+        }
+        return p[k];
+    }
+    template <class I>
+    __device__ __forceinline__ View operator+(I i) const {
+        long long k = (long long)i;
+        if (k < 0 || k > n) {
+            bounds_hit(site, k, n);
+            k = 0;
+        }
+        return View{p + k, n - (int)k, site};
+    }
+    __device__ __forceinline__ operator T*() const { return p; }
+};
+#define VIEW_T(T) View<T>
+template <class T>
+__device__ __forceinline__ View<T> mkview(T* p, int n, int site) {
+    return View<T>{p, n, site};
+}
+#else
+#define VIEW_T(T) T*
+template <class T>
+__device__ __forceinline__ T* mkview(T* p, int, int) {
+    return p;
+}
+#endif
+
+// the raw pointer of a view (or of a pointer)
+template <class T>
+__device__ __forceinline__ T* raw(T* p) { return p; }
+#ifdef MSIM_BOUNDS_CHECK
+template <class T>
+__device__ __forceinline__ T* raw(const View<T>& v) { return v.p; }
+#endif
+
+#ifdef MSIM_BOUNDS_CHECK
+// end (float offset) of the workspace region holding float offset `off`: the regions are laid
+// out q, qd, frame, fi, S, A, rhs, racc, rk (msim_api.cu), the last sized by the warps per env
+__device__ __forceinline__ int ws_region_end(const ImgHeader& H, int off, int wpe) {
+    const int ends[8] = {H.w_qd, H.w_frame, H.w_fi, H.w_S, H.w_A, H.w_rhs, H.w_racc, H.w_rk};
+    for (int i = 0; i < 8; ++i)
+        if (off < ends[i]) return ends[i];
+    return ws_floats(H, wpe);
+}
+#endif
+
+// view of the workspace from float offset `off` to the end of its region, as elements of T
+#ifdef MSIM_BOUNDS_CHECK
+#define WS(T, off) mkview(reinterpret_cast<T*>(ws + (off)), \
+                          (int)((ws_region_end(H, (off), WPE) - (off)) * sizeof(float) / sizeof(T)), __LINE__)
+#else
+#define WS(T, off) reinterpret_cast<T*>(ws + (off))
+#endif
+
 struct Tables {
     const ImgHeader* H;
-    const BodyRec* body;
-    const DofRec* dof;
-    const MuscleRec* mus;
-    const PointRec* pt;
-    const WrapRec* wrap;
-    const SphereRec* sph;
-    const uint32_t* cross;
-    const uint8_t* border;
-    const int16_t* blevel;
-    const uint8_t* child;
-    const uint8_t* anc;
-    const uint8_t* dorder;
-    const int16_t* dlevel;
-    const uint16_t* tri;
-    const uint16_t* rowanc;
-    const uint8_t* crba_order;
-    const TendonRec* ten;       // null: every tendon rigid
-    const int16_t* cround;      // body chains of the subtree sums (ImgHeader::o_chain)
-    const int16_t* cstart;
-    const uint8_t* cbody;
+    VIEW_T(const BodyRec) body;
+    VIEW_T(const DofRec) dof;
+    VIEW_T(const MuscleRec) mus;
+    VIEW_T(const PointRec) pt;
+    VIEW_T(const WrapRec) wrap;
+    VIEW_T(const SphereRec) sph;
+    VIEW_T(const uint32_t) cross;
+    VIEW_T(const uint8_t) border;
+    VIEW_T(const int16_t) blevel;
+    VIEW_T(const uint8_t) child;
+    VIEW_T(const uint8_t) anc;
+    VIEW_T(const uint8_t) dorder;
+    VIEW_T(const int16_t) dlevel;
+    VIEW_T(const uint16_t) tri;
+    VIEW_T(const uint16_t) rowanc;
+    VIEW_T(const uint8_t) crba_order;
+    VIEW_T(const TendonRec) ten;       // null: every tendon rigid
+    VIEW_T(const int16_t) cround;      // body chains of the subtree sums (ImgHeader::o_chain)
+    VIEW_T(const int16_t) cstart;
+    VIEW_T(const uint8_t) cbody;
 };
+
+#ifdef MSIM_BOUNDS_CHECK
+// byte extent of the image section starting at byte offset `o`: up to the next section's start
+// (the sections are placed in the order of msim_api.cu's image builder) or the image's end
+__device__ __forceinline__ int img_section_end(const ImgHeader& h, int o) {
+    const int starts[18] = {h.o_body, h.o_dof, h.o_sphere, h.o_border, h.o_blevel, h.o_child, h.o_anc,
+                            h.o_dorder, h.o_dlevel, h.o_chain, h.o_tri, h.o_rowanc, h.o_crba, h.o_muscle,
+                            h.o_cross, h.o_point, h.o_wrap, h.n_tendons ? h.o_tendon : h.total_bytes};
+    int e = h.total_bytes;
+    for (int i = 0; i < 18; ++i)
+        if (starts[i] > o && starts[i] < e) e = starts[i];
+    return e;
+}
+#endif
+
+// view of the table of type T at byte offset o of an image (staged in shared memory or global)
+#ifdef MSIM_BOUNDS_CHECK
+#define TAB(T, base, o) mkview(reinterpret_cast<T*>((base) + (o)), \
+                               (int)((img_section_end(h, (o)) - (o)) / (int)sizeof(T)), __LINE__)
+#else
+#define TAB(T, base, o) reinterpret_cast<T*>((base) + (o))
+#endif
 
 __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     Tables t;
     t.H = reinterpret_cast<const ImgHeader*>(img);
     const ImgHeader& h = *t.H;
-    t.body = reinterpret_cast<const BodyRec*>(img + h.o_body);
-    t.dof = reinterpret_cast<const DofRec*>(img + h.o_dof);
-    t.mus = reinterpret_cast<const MuscleRec*>(img + h.o_muscle);
-    t.pt = reinterpret_cast<const PointRec*>(img + h.o_point);
-    t.wrap = reinterpret_cast<const WrapRec*>(img + h.o_wrap);
-    t.sph = reinterpret_cast<const SphereRec*>(img + h.o_sphere);
-    t.cross = reinterpret_cast<const uint32_t*>(img + h.o_cross);
-    t.border = img + h.o_border;
-    t.blevel = reinterpret_cast<const int16_t*>(img + h.o_blevel);
-    t.child = img + h.o_child;
-    t.anc = img + h.o_anc;
-    t.dorder = img + h.o_dorder;
-    t.dlevel = reinterpret_cast<const int16_t*>(img + h.o_dlevel);
-    t.tri = reinterpret_cast<const uint16_t*>(img + h.o_tri);
-    t.rowanc = reinterpret_cast<const uint16_t*>(img + h.o_rowanc);
-    t.crba_order = img + h.o_crba;
+    t.body = TAB(const BodyRec, img, h.o_body);
+    t.dof = TAB(const DofRec, img, h.o_dof);
+    t.mus = TAB(const MuscleRec, img, h.o_muscle);
+    t.pt = TAB(const PointRec, img, h.o_point);
+    t.wrap = TAB(const WrapRec, img, h.o_wrap);
+    t.sph = TAB(const SphereRec, img, h.o_sphere);
+    t.cross = TAB(const uint32_t, img, h.o_cross);
+    t.border = TAB(const uint8_t, img, h.o_border);
+    t.blevel = TAB(const int16_t, img, h.o_blevel);
+    t.child = TAB(const uint8_t, img, h.o_child);
+    t.anc = TAB(const uint8_t, img, h.o_anc);
+    t.dorder = TAB(const uint8_t, img, h.o_dorder);
+    t.dlevel = TAB(const int16_t, img, h.o_dlevel);
+    t.tri = TAB(const uint16_t, img, h.o_tri);
+    t.rowanc = TAB(const uint16_t, img, h.o_rowanc);
+    t.crba_order = TAB(const uint8_t, img, h.o_crba);
+#ifdef MSIM_BOUNDS_CHECK
+    t.ten = h.n_tendons ? TAB(const TendonRec, img, h.o_tendon) : mkview<const TendonRec>(nullptr, 0, __LINE__);
+#else
     t.ten = h.n_tendons ? reinterpret_cast<const TendonRec*>(img + h.o_tendon) : nullptr;
-    t.cround = reinterpret_cast<const int16_t*>(img + h.o_chain);
-    t.cstart = t.cround + h.n_crounds + 1;
-    t.cbody = reinterpret_cast<const uint8_t*>(t.cstart + h.n_chains + 1);
+#endif
+    // the chain section holds three arrays: round starts, chain starts, bodies
+    const int16_t* cr = reinterpret_cast<const int16_t*>(img + h.o_chain);
+    const int16_t* cs = cr + h.n_crounds + 1;
+    t.cround = mkview(cr, h.n_crounds + 1, __LINE__);
+    t.cstart = mkview(cs, h.n_chains + 1, __LINE__);
+    t.cbody = mkview(reinterpret_cast<const uint8_t*>(cs + h.n_chains + 1), h.nb, __LINE__);
     return t;
 }
 
 // Sections left out of the staged prefix are read from the image in global memory.
 __device__ __forceinline__ void unstaged_tables(Tables& T, const uint8_t* gimg, int stage) {
     if (stage == 1) return;
-    T.pt = reinterpret_cast<const PointRec*>(gimg + T.H->o_point);
-    T.wrap = reinterpret_cast<const WrapRec*>(gimg + T.H->o_wrap);
-    if (T.H->n_tendons) T.ten = reinterpret_cast<const TendonRec*>(gimg + T.H->o_tendon);
+    const ImgHeader& h = *T.H;
+    T.pt = TAB(const PointRec, gimg, h.o_point);
+    T.wrap = TAB(const WrapRec, gimg, h.o_wrap);
+    if (h.n_tendons) T.ten = TAB(const TendonRec, gimg, h.o_tendon);
     if (stage == 2) {
-        T.mus = reinterpret_cast<const MuscleRec*>(gimg + T.H->o_muscle);
-        T.cross = reinterpret_cast<const uint32_t*>(gimg + T.H->o_cross);
+        T.mus = TAB(const MuscleRec, gimg, h.o_muscle);
+        T.cross = TAB(const uint32_t, gimg, h.o_cross);
     }
 }
 
@@ -275,15 +387,15 @@ __device__ bool stage_image(uint8_t* dst, const uint8_t* src, int bytes, uint64_
 template <int WPE>
 __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
-    const float* q = ws + H.w_q;
-    const float* qd = ws + H.w_qd;
-    float* frame = ws + H.w_frame;
-    float* V = ws + H.w_v;     // in the A region during this pass (with Acc and FB)
-    float* FI = ws + H.w_fi;
-    df* FB = reinterpret_cast<df*>(ws + H.w_f);
-    float* S = ws + H.w_S;
-    float* Acc = ws + H.w_A;   // bias accelerations live in the A region during this pass
-    float* SC = ws + H.w_rk;   // sin, cos of every joint angle (the moment-arm scratch is free here)
+    auto q = WS(const float, H.w_q);
+    auto qd = WS(const float, H.w_qd);
+    auto frame = WS(float, H.w_frame);
+    auto V = WS(float, H.w_v);     // in the A region during this pass (with Acc and FB)
+    auto FI = WS(float, H.w_fi);
+    auto FB = WS(df, H.w_f);
+    auto S = WS(float, H.w_S);
+    auto Acc = WS(float, H.w_A);   // bias accelerations live in the A region during this pass
+    auto SC = WS(float, H.w_rk);   // sin, cos of every joint angle (the moment-arm scratch is free here)
     SUB_T0();
     // 1. joint-angle sines and cosines, all DoFs in parallel (off the level-by-level chain)
     for (int d = g.lane; d < H.n; d += g.N) sincosf(q[d], &SC[2 * d], &SC[2 * d + 1]);
@@ -481,7 +593,7 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
             fb[k] = df_add(df_add(Iaw[k], t1[k]), t2[k]);
             fb[3 + k] = df_add(Ial[k], t3[k]);
         }
-        df* Id = reinterpret_cast<df*>(FI + kFiStride * b);   // m, h[3], Ibar[6]
+        df* Id = reinterpret_cast<df*>(raw(FI + kFiStride * b));   // m, h[3], Ibar[6]
         Id[0] = df_make(m);
         Id[1] = hd[0]; Id[2] = hd[1]; Id[3] = hd[2];
 #pragma unroll
@@ -494,11 +606,11 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
 template <int WPE>
 __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
-    float* FI = ws + H.w_fi;
-    df* FB = reinterpret_cast<df*>(ws + H.w_f);
-    const float* S = ws + H.w_S;
-    float* rhs = ws + H.w_rhs;
-    int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
+    auto FI = WS(float, H.w_fi);
+    auto FB = WS(df, H.w_f);
+    auto S = WS(const float, H.w_S);
+    auto rhs = WS(float, H.w_rhs);
+    auto racc = WS(int32_t, H.w_racc);
     // subtree sums, leaves first, along the body chains (maximal runs of single-child bodies):
     // every chain's 16 components (force 6, float-float inertia 10) go to their own lanes, which
     // walk the chain bottom to top carrying the running sum; the bottom body adds its children
@@ -509,7 +621,7 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
         for (int t = g.lane; t < 16 * (c1 - c0); t += g.N) {
             const int c = c0 + t / 16, comp = t % 16;
             const int j0 = T.cstart[c], j1 = T.cstart[c + 1];
-            df* base = comp < 6 ? FB + comp : reinterpret_cast<df*>(FI) + (comp - 6);
+            df* base = comp < 6 ? raw(FB + comp) : reinterpret_cast<df*>(raw(FI)) + (comp - 6);
             const int stride = comp < 6 ? 6 : kFiStride / 2;   // df entries per body
             const BodyRec& Bb = T.body[T.cbody[j0]];
             df f = base[stride * T.cbody[j0]];
@@ -571,14 +683,14 @@ __device__ __forceinline__ fac fac_decode(int32_t hi, int32_t lo) { return fx_de
 template <int WPE>
 __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float* evM) {
     const ImgHeader& H = *T.H;
-    const float* FI = ws + H.w_fi;
-    const float* S = ws + H.w_S;
-    fac* A = reinterpret_cast<fac*>(ws + H.w_A);
-    const int32_t* Ai = reinterpret_cast<const int32_t*>(ws + H.w_A);
+    auto FI = WS(const float, H.w_fi);
+    auto S = WS(const float, H.w_S);
+    auto A = WS(fac, H.w_A);
+    auto Ai = WS(const int32_t, H.w_A);
     for (int t = g.lane; t < H.n; t += g.N) {
         const int d = T.crba_order[t];
         const DofRec& D = T.dof[d];
-        const df* I = reinterpret_cast<const df*>(FI + kFiStride * D.body);
+        const df* I = reinterpret_cast<const df*>(raw(FI + kFiStride * D.body));
         const df m = I[0];
         const df h0 = I[1], h1 = I[2], h2 = I[3];
         const df* Ib = I + 4;   // xx yy zz xy xz yz
@@ -762,12 +874,12 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                                   float* act, float* eps, float* force_out, float* vm_out, const EvalPtrs* ev,
                                   const SurrCtx* sc) {
     const ImgHeader& H = *T.H;
-    const float* qd = ws + H.w_qd;
-    const float* frame = ws + H.w_frame;
-    const float* S = ws + H.w_S;
-    int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);   // damping sums, fixed point
-    int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
-    float* rk = ws + H.w_rk;                                  // [max_nx][N]
+    auto qd = WS(const float, H.w_qd);
+    auto frame = WS(const float, H.w_frame);
+    auto S = WS(const float, H.w_S);
+    auto Ai = WS(int32_t, H.w_A);   // damping sums, fixed point
+    auto racc = WS(int32_t, H.w_racc);
+    auto rk = WS(float, H.w_rk);                                  // [max_nx][N]
     bool bad = false;
     float se_len = 0.f, se_arm = 0.f;   // check: squared errors of the learned lengths and arms
     SUB_T0();
@@ -1000,12 +1112,12 @@ template <int MODE, int WPE>
 __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const EvalPtrs* ev) {
     const ImgHeader& H = *T.H;
     if (H.ns == 0) return;
-    const float* frame = ws + H.w_frame;
-    const float* qd = ws + H.w_qd;
-    const float* S = ws + H.w_S;
-    int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);
-    int32_t* racc = reinterpret_cast<int32_t*>(ws + H.w_racc);
-    float* sph = ws + H.w_sph;   // the moment-arm region, free after the muscles
+    auto frame = WS(const float, H.w_frame);
+    auto qd = WS(const float, H.w_qd);
+    auto S = WS(const float, H.w_S);
+    auto Ai = WS(int32_t, H.w_A);
+    auto racc = WS(int32_t, H.w_racc);
+    auto sph = WS(float, H.w_sph);   // the moment-arm region, free after the muscles
     for (int i = g.lane; i < H.ns; i += g.N) {
         const SphereRec& Sp = T.sph[i];
         const float* fr = frame + 12 * Sp.body;
@@ -1100,10 +1212,10 @@ __device__ void phase_contact(const Tables& T, float* ws, const Grp<WPE>& g, flo
 template <int MODE, int WPE>
 __device__ void phase_limits(const Tables& T, float* ws, const Grp<WPE>& g, float dt, const EvalPtrs* ev) {
     const ImgHeader& H = *T.H;
-    const float* q = ws + H.w_q;
-    const float* qd = ws + H.w_qd;
-    fac* A = reinterpret_cast<fac*>(ws + H.w_A);
-    float* rhs = ws + H.w_rhs;
+    auto q = WS(const float, H.w_q);
+    auto qd = WS(const float, H.w_qd);
+    auto A = WS(fac, H.w_A);
+    auto rhs = WS(float, H.w_rhs);
     for (int d = g.lane; d < H.n; d += g.N) {
         const DofRec& D = T.dof[d];
         const float qv = q[d], qdv = qd[d];
@@ -1143,10 +1255,10 @@ constexpr int kElimU = MSIM_ELIM_UNROLL;
 template <int WPE>
 __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g) {
     const ImgHeader& H = *T.H;
-    fac* A = reinterpret_cast<fac*>(ws + H.w_A);
-    const float* rhs = ws + H.w_rhs;
-    fac* Y = reinterpret_cast<fac*>(ws + H.w_y);
-    const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
+    auto A = WS(fac, H.w_A);
+    auto rhs = WS(const float, H.w_rhs);
+    auto Y = WS(fac, H.w_y);
+    auto racc = WS(const int32_t, H.w_racc);
     bool ok = true;
     SUB_T0();
     for (int d = g.lane; d < H.n; d += g.N) Y[d] = fac_add_f(fac_decode(racc[2 * d], racc[2 * d + 1]), rhs[d]);
@@ -1307,7 +1419,7 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     }
     if (MODE == kModeFk) {   // body origins only
         phase_kinematics(T, ws, g);
-        const float* frame = ws + H.w_frame;
+        auto frame = WS(const float, H.w_frame);
         for (int i = g.lane; i < 3 * H.nb; i += g.N) ev->xpos[i] = frame[12 * (i / 3) + 9 + i % 3];
         return 0u;
     }
@@ -1323,11 +1435,11 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     {   // fixed-point accumulator of the damping sums in the A storage (the velocities, bias
         // accelerations and body forces it held are no longer needed); the right-hand side's
         // accumulator already holds -C
-        int32_t* Ai = reinterpret_cast<int32_t*>(ws + H.w_A);
+        auto Ai = WS(int32_t, H.w_A);
         for (int t = g.lane; t < 2 * H.n_packed; t += g.N) Ai[t] = 0;
     }
     if ((MODE == kModeEval)) {
-        const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
+        auto racc = WS(const int32_t, H.w_racc);
         for (int d = g.lane; d < H.n; d += g.N) {
             const df c = fx_decode(racc[2 * d], racc[2 * d + 1]);
             if (ev->bias) ev->bias[d] = -(c.hi + c.lo);
@@ -1343,11 +1455,11 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     PHASE_MARK(2);
     phase_limits<MODE>(T, ws, g, dt, ev);
     PHASE_MARK(5);
-    const fac* A = reinterpret_cast<const fac*>(ws + H.w_A);
+    auto A = WS(const fac, H.w_A);
     if ((MODE == kModeEval)) {
         for (int t = g.lane; t < H.n_packed; t += g.N)
             if (ev->A) ev->A[t] = fac_f(A[t]);
-        const int32_t* racc = reinterpret_cast<const int32_t*>(ws + H.w_racc);
+        auto racc = WS(const int32_t, H.w_racc);
         for (int d = g.lane; d < H.n; d += g.N) {
             const df r = df_add_f(fx_decode(racc[2 * d], racc[2 * d + 1]), ws[H.w_rhs + d]);
             if (ev->rhs) ev->rhs[d] = r.hi + r.lo;
@@ -1357,10 +1469,10 @@ __device__ uint32_t substep(const Tables& T, float* ws, const Grp<WPE>& g, float
     const bool ok = phase_factor_solve(T, ws, g);
     PHASE_MARK(6);
     uint32_t st = (ok ? 0u : kEnvNotSpd) | (bad ? kEnvNonFinite : 0u) | ((mflags & 2u) ? 0x100u : 0u);
-    const fac* Y = reinterpret_cast<const fac*>(ws + H.w_y);
+    auto Y = WS(const fac, H.w_y);
     if (!(MODE == kModeEval)) {
-        float* q = ws + H.w_q;
-        float* qd = ws + H.w_qd;
+        auto q = WS(float, H.w_q);
+        auto qd = WS(float, H.w_qd);
         for (int d = g.lane; d < H.n; d += g.N) {
             const float v = qd[d] + dt * fac_f(Y[d]);
             qd[d] = v;
@@ -1462,7 +1574,7 @@ __device__ __forceinline__ void run_env(const StepArgs& a, const Tables& T, floa
             }
         }
         bool bad = false;
-        const fac* Y = reinterpret_cast<const fac*>(ws + H.w_y);
+        auto Y = WS(const fac, H.w_y);
         for (int d = g.lane; d < H.n; d += g.N) {
             const float v0 = ws[H.w_q + d], v1 = ws[H.w_qd + d];
             bad |= !(isfinite(v0) && isfinite(v1));
@@ -1778,3 +1890,16 @@ cudaError_t launch_reset(float* q, float* qd, float* act, float* eps, uint32_t* 
 }
 
 }  // namespace msim
+
+#ifdef MSIM_BOUNDS_CHECK
+// Bounds-checking build only (not part of the public ABI in include/msim.h): copies the record of
+// out-of-range indices through the kernels' views, [count, source line of the first, its index,
+// its extent], to out (host, 4 words) and clears it.  Returns a cudaError_t code.
+extern "C" __attribute__((visibility("default"))) int msim_debug_bounds(unsigned int* out) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, msim::g_bounds_rec, 4 * sizeof(unsigned int));
+    const unsigned int zero[4] = {0u, 0u, 0u, 0u};
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(msim::g_bounds_rec, zero, sizeof(zero));
+    return (int)e;
+}
+#endif
