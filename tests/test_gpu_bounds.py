@@ -37,7 +37,7 @@ def test_no_index_out_of_range_and_same_results(tmp_path):
     normal = _child(B.build(), str(tmp_path / "normal.npz"))
     assert checked["checking"] and not normal["checking"]
     print("\nbounds records [hits, first site (line), index, extent]:", checked["records"])
-    assert len(checked["records"]) == 8
+    assert len(checked["records"]) == 7
     for name, rec in checked["records"].items():
         assert rec[0] == 0, (name, rec)
     a, b = np.load(tmp_path / "check.npz"), np.load(tmp_path / "normal.npz")
