@@ -989,11 +989,20 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                 }
             } else {
                 L = Ls;
-                for (int i = 0; i < M.nx; ++i) {
-                    const float Rv = Yr[32 * (i + 1)];
-                    rk[i * g.N + g.lane] = Rv;
-                    ldot -= Rv * qd[cross_dof(T.cross[M.x0 + i])];
+                // every load of the record issued before the first use: one latency per record
+                float Rl[kMaxCross];
+                uint32_t cl[kMaxCross];
+#pragma unroll
+                for (int i = 0; i < kMaxCross; ++i) {
+                    Rl[i] = i < M.nx ? Yr[32 * (i + 1)] : 0.f;
+                    cl[i] = i < M.nx ? T.cross[M.x0 + i] : 0u;
                 }
+#pragma unroll
+                for (int i = 0; i < kMaxCross; ++i)
+                    if (i < M.nx) {
+                        rk[i * g.N + g.lane] = Rl[i];
+                        ldot -= Rl[i] * qd[cross_dof(cl[i])];
+                    }
             }
         }
         if (MODE == kModeGeom) {
