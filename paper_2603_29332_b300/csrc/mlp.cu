@@ -2,6 +2,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -83,8 +84,16 @@ __global__ void k_loss_grad(const float* Y, int ldy, const float* T, int ldt, in
         if (sig) g *= y * (1.f - y);
         dY[(size_t)r * ldd + c] = __float2bfloat16_rn(g);
     }
+    // the block's sum first (one atomic per block, not per warp: they all hit one address)
+    __shared__ float part[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(loss_acc, acc);
+    }
 }
 
 // dZ = dH * silu'(Z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)
@@ -98,12 +107,28 @@ __global__ void k_dsilu(const float* dH, const __nv_bfloat16* Z, int B, int N, i
     }
 }
 
-// db[c] = sum over rows of src[r][c]
-__global__ void k_colsum(const __nv_bfloat16* src, int B, int N, int ld, float* db) {
+// Column sums db[c] = sum over rows of src[r][c] in two deterministic stages: the rows in
+// chunks of kColChunk, one block per (128 columns, chunk), each thread summing its column over
+// the chunk (a warp's loads of a row are one contiguous run); then the chunks' partial sums in
+// chunk order.
+constexpr int kColChunk = 128;
+
+__global__ void k_colsum_part(const __nv_bfloat16* src, int B, int N, int ld, float* part) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r0 = blockIdx.y * kColChunk;
+    if (c >= N) return;
+    const int r1 = min(B, r0 + kColChunk);
+    float s = 0.f;
+#pragma unroll 8
+    for (int r = r0; r < r1; ++r) s += __bfloat162float(src[(size_t)r * ld + c]);
+    part[(size_t)blockIdx.y * N + c] = s;
+}
+
+__global__ void k_colsum_final(const float* part, int n_chunks, int N, float* db) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     float s = 0.f;
-    for (int r = 0; r < B; ++r) s += __bfloat162float(src[(size_t)r * ld + c]);
+    for (int k = 0; k < n_chunks; ++k) s += part[(size_t)k * N + c];
     db[c] = s;
 }
 
@@ -145,6 +170,13 @@ __global__ void k_spread_b1(float* P, size_t oW1, size_t ob1, int inp, int hid, 
     uint32_t ctr[4] = {(uint32_t)u, 0xb1a5u, 0u, 0u};
     philox4x32_10(ctr, k0, k1);
     P[ob1 + u] = r * (2.f * u01_from_bits(ctr[0]) - 1.f);
+}
+
+cudaError_t colsum(const __nv_bfloat16* src, int B, int N, int ld, float* part, float* db, cudaStream_t s) {
+    const int chunks = (B + kColChunk - 1) / kColChunk;
+    k_colsum_part<<<dim3((N + 127) / 128, chunks), 128, 0, s>>>(src, B, N, ld, part);
+    k_colsum_final<<<(N + 255) / 256, 256, 0, s>>>(part, chunks, N, db);
+    return cudaGetLastError();
 }
 
 int nblocks(size_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
@@ -206,6 +238,7 @@ cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp
     A((void**)&m->dZ1t, (size_t)hid * m->bp * 2); A((void**)&m->dZ2t, (size_t)hid * m->bp * 2);
     A((void**)&m->Y, B * m->outp * 4); A((void**)&m->dH, B * hid * 4);
     A((void**)&m->loss_acc, 8); A((void**)&m->err, 8);
+    A((void**)&m->colpart, (size_t)((max_batch + 127) / 128) * std::max(m->outp, hid) * 4);
     if (e != cudaSuccess) {
         mlp_destroy(m);
         return e;
@@ -218,7 +251,7 @@ void mlp_destroy(Mlp* m) {
     if (!m) return;
     void* ptrs[] = {m->P, m->G, m->Am, m->Av, m->Ph, m->W2t, m->W3t, m->H1, m->Z1, m->H2, m->Z2, m->dY, m->dZ1,
                     m->dZ2, m->Xt, m->H1t, m->H2t, m->dYt, m->dZ1t, m->dZ2t, m->Y, m->dH, m->loss_acc, m->err,
-                    m->mask};
+                    m->mask, m->colpart};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -320,8 +353,7 @@ cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T
     CK(transpose_bf16(m->dY, B, m->out, m->outp, m->dYt, bp, s));
     CK(transpose_bf16(m->H2, B, h, h, m->H2t, bp, s));
     CK(gemm(m->dYt, bp, m->H2t, bp, m->out, h, B, m->G + m->oW3, h, 0, nullptr, 0, nullptr, 0, m->err, s));
-    k_colsum<<<(m->out + 255) / 256, 256, 0, s>>>(m->dY, B, m->out, m->outp, m->G + m->ob3);
-    CK(cudaGetLastError());
+    CK(colsum(m->dY, B, m->out, m->outp, m->colpart, m->G + m->ob3, s));
     CK(gemm(m->dY, m->outp, m->W3t, m->outp, B, h, m->out, m->dH, h, 0, nullptr, 0, nullptr, 0, m->err, s));
     k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z2, B, h, h, m->dZ2);
     CK(cudaGetLastError());
@@ -329,8 +361,7 @@ cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T
     CK(transpose_bf16(m->dZ2, B, h, h, m->dZ2t, bp, s));
     CK(transpose_bf16(m->H1, B, h, h, m->H1t, bp, s));
     CK(gemm(m->dZ2t, bp, m->H1t, bp, h, h, B, m->G + m->oW2, h, 0, nullptr, 0, nullptr, 0, m->err, s));
-    k_colsum<<<(h + 255) / 256, 256, 0, s>>>(m->dZ2, B, h, h, m->G + m->ob2);
-    CK(cudaGetLastError());
+    CK(colsum(m->dZ2, B, h, h, m->colpart, m->G + m->ob2, s));
     CK(gemm(m->dZ2, h, m->W2t, h, B, h, h, m->dH, h, 0, nullptr, 0, nullptr, 0, m->err, s));
     k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z1, B, h, h, m->dZ1);
     CK(cudaGetLastError());
@@ -338,8 +369,7 @@ cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T
     CK(transpose_bf16(m->dZ1, B, h, h, m->dZ1t, bp, s));
     CK(transpose_bf16(X, B, m->inp, ldx, m->Xt, bp, s));
     CK(gemm(m->dZ1t, bp, m->Xt, bp, h, m->in, B, m->G + m->oW1, m->inp, 0, nullptr, 0, nullptr, 0, m->err, s));
-    k_colsum<<<(h + 255) / 256, 256, 0, s>>>(m->dZ1, B, h, h, m->G + m->ob1);
-    return cudaGetLastError();
+    return colsum(m->dZ1, B, h, h, m->colpart, m->G + m->ob1, s);
 }
 
 cudaError_t mlp_adam(Mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t s) {

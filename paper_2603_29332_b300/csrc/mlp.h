@@ -35,6 +35,7 @@ struct Mlp {
     uint32_t* err;         // device word: GEMM bounded-wait failures
     uint8_t* mask;         // [n_params] 1 = trainable, 0 = held at zero (nullptr: every parameter)
     uint64_t version;      // counts changes of the parameters (set, init, Adam steps)
+    float* colpart;        // [batch chunks][max(outp, hid)] partial column sums of the bias gradients
 };
 
 cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp** out_mlp);
