@@ -428,6 +428,26 @@ def run_surrogate(args, sim, model, excs, flush, exact_value, hidden=512):
                       "q_vs_exact_rollout_rad": {"median": float(dq.median()), "max": float(dq.max()),
                                                  "after_substeps": (args.warmup + args.steps) * sub},
                       "envs_non_finite": nonfinite, "status_flags": flags}
+    # q_dd of one learned substep against the exact geometry's (which matches the FP64 oracle
+    # within 1e-4) at the same states: the end of the last rollout
+    n = model.n_dofs
+    s0 = sim.state()
+    exc_n = excs[(args.warmup + args.steps) % n_buf]
+    sim.set_geometry_mode(0)
+    qdd_ex = sim.eval(s0["q"], s0["qd"], s0["act"], exc_n)["qdd"][:, :n].double()
+    sim.reset(s0["q"], s0["qd"], s0["act"])
+    sim.set_geometry_mode(1)
+    sim.surrogate_set_check(0.0, 1e-3)
+    sim.surrogate_stats(reset=True)
+    sim.step(exc_n, 1)
+    qdd_l = sim.state()["qdd"][:, :n].double()
+    learned_here = sim.surrogate_stats()["learned"] / E
+    sim.surrogate_set_check(0.01, 1e-3)
+    rel = (qdd_l - qdd_ex).norm(dim=1) / qdd_ex.norm(dim=1).clamp_min(1e-3)
+    qdd_err = {"median": float(rel.median()), "p90": float(rel.quantile(0.9)), "max": float(rel.max()),
+               "fraction_on_network": learned_here,
+               "definition": "|q_dd learned - q_dd exact| / max(|q_dd exact|, 1e-3) per env, one substep from "
+                             "the rollout's final states; the exact path matches the FP64 oracle within 1e-4"}
     sim.set_geometry_mode(0)
     # the network alone at this batch, for its tensor-pipe fraction (timed alone: burst peak)
     net = sim.surrogate_network()
@@ -459,7 +479,7 @@ def run_surrogate(args, sim, model, excs, flush, exact_value, hidden=512):
            "env_check_error_m": {"median": q(env_err, 0.5), "p99": q(env_err, 0.99),
                                  "fraction_within_tol": float((env_err <= 1e-3).float().mean()),
                                  "definition": "max(rms of the env's moment-arm errors, rms of its length errors)"},
-           "rollouts": runs,
+           "rollouts": runs, "qdd_rel_err_vs_exact": qdd_err,
            "mlp_forward": {"ms": mlp_ms, "tflops": mlp_tf, "peak_tflops": pk, "frac": mlp_tf / pk,
                            "peak_note": "bf16_tflops (burst) of measured: the forward is timed alone"},
            "network": "90 -> %d -> %d -> %d, SiLU, BF16, joint-block connectivity" % (net.hidden, net.hidden,

@@ -347,6 +347,8 @@ typedef struct {
     float train_loss;           /* mean squared normalised error, last training epoch */
     int32_t flagged_envs;       /* environments flagged now */
     int32_t trained;
+    int32_t structured;         /* 1: the trained network has the joint-block connectivity */
+    int32_t hidden;             /* its hidden width */
 } msim_surrogate_info;
 /* msim_surrogate_stats -- synchronises; counters since training or the last reset_counters. */
 MSIM_API msim_status msim_surrogate_stats(msim_handle h, msim_surrogate_info* out, int32_t reset_counters);

@@ -1622,6 +1622,8 @@ msim_status msim_surrogate_stats(msim_handle h, msim_surrogate_info* out, int32_
     for (uint8_t v : fb) nf += v != 0;
     out->flagged_envs = nf;
     out->trained = h->sur->trained;
+    out->structured = h->sur->structured;
+    out->hidden = h->sur->net ? h->sur->net->hid : 0;
     return MSIM_OK;
 }
 

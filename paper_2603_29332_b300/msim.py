@@ -63,7 +63,7 @@ class SurrogateInfo(C.Structure):
     _fields_ = [("env_substeps", C.c_uint64), ("learned", C.c_uint64), ("out_of_box", C.c_uint64),
                 ("flagged", C.c_uint64), ("checked", C.c_uint64), ("check_failed", C.c_uint64),
                 ("max_check_error", C.c_float), ("train_loss", C.c_float), ("flagged_envs", C.c_int32),
-                ("trained", C.c_int32)]
+                ("trained", C.c_int32), ("structured", C.c_int32), ("hidden", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -17,6 +17,7 @@ torch = pytest.importorskip("torch")
 from oracle import oracle as ora
 from paper_2603_29332_b300 import modelgen as mg
 from paper_2603_29332_b300 import msim
+from tests import handmodels as hm
 from tests.gpu_common import oracle_eval, qdd_rel_err, random_states, sample_envs
 
 pytestmark = pytest.mark.gpu
@@ -273,6 +274,36 @@ def test_learned_rollout_against_the_exact_rollout(trained):
     assert res["trained"][2] == 0 and torch.isfinite(res["trained"][1]).all()
     assert frac >= 0.9
     assert float(drift["trained"].median()) < 0.5 * float(drift["untrained"].median())
+
+
+def test_joint_structure_only_where_segments_cross_one_joint(trained):
+    """The joint-block connectivity is used when every path segment joins points on the same or on
+    adjacent bodies (the whole body), and the dense network otherwise: a chain whose only muscle
+    runs straight from the root body to the third body has a length depending jointly on two
+    joints, which the blocks could not represent."""
+    model, sim = trained
+    st = sim.surrogate_stats()
+    assert st["structured"] == 1 and st["hidden"] == 512
+    base = hm.chain(n_links=3, seed=2)
+    spans_two = mg.make_model("two_joint_segment", base.body_parent, base.body_ndof, base.body_offset,
+                              base.body_mass, base.body_com, base.body_inertia, base.dof_axis,
+                              [[(0, (0.05, 0.02, 0.1)), (2, (0.02, 0.03, -0.05))]], [500.0], [0.1],
+                              dof_limit=[[-1.0, 1.0]] * base.n_dofs)
+    s2 = msim.Sim(spans_two, 16, dt=DT)
+    s2.surrogate_set_width(64)
+    s2.train_surrogate(8192, 1, batch=1024, lr=3e-3)
+    assert s2.surrogate_stats()["structured"] == 0
+    one = mg.make_model("one_joint_segments", base.body_parent, base.body_ndof, base.body_offset,
+                        base.body_mass, base.body_com, base.body_inertia, base.dof_axis,
+                        [[(0, (0.05, 0.02, 0.1)), (1, (0.02, 0.03, -0.05)), (2, (0.02, 0.03, -0.05))]], [500.0],
+                        [0.1], dof_limit=[[-1.0, 1.0]] * base.n_dofs)
+    s3 = msim.Sim(one, 16, dt=DT)
+    s3.surrogate_set_width(64)
+    s3.train_surrogate(8192, 1, batch=1024, lr=3e-3)
+    assert s3.surrogate_stats()["structured"] == 1
+    s3.surrogate_set_structure(False)
+    s3.train_surrogate(8192, 1, batch=1024, lr=3e-3)
+    assert s3.surrogate_stats()["structured"] == 0
 
 
 def test_surrogate_argument_and_state_errors():
