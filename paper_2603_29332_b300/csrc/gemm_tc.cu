@@ -1,6 +1,10 @@
 // gemm_tc.cu -- BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-//   C[m][n] = act( sum_k A[m][k] B[n][k] + bias[n] )      (both operands K-contiguous)
+//   C[m][n] = act( sum_k A[m][k] B[n][k] + bias[n] )
+//
+// Each operand is read either K-contiguous (A [M][K], B [N][K]) or MN-contiguous (A stored as
+// [K][M], B as [K][N]: the MMA's transposed operand mode), so the gradients of an MLP,
+// dW = dY^T H and dH = dY W, read the stored activations, gradients and weights as they are.
 //
 // One 128 x BN output tile per block (two blocks per SM, so one block's epilogue overlaps the
 // other's main loop), 192 threads in three roles:
@@ -73,19 +77,28 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+// Shared-memory matrix descriptor, 128-byte swizzle.  Either layout is built from 1024-byte
+// atoms of 8 rows x 128 bytes, as the TMA writes a 64-element-wide box:
+//   K-major:  rows along M (N), 64 K-elements per row; 8-row groups 1024 bytes apart (stride
+//             byte offset); the leading offset is unused.  A K-step of 16 advances 32 bytes.
+//   MN-major: rows along K, 64 M- (N-) elements per row; 8-row K groups 1024 bytes apart (stride
+//             byte offset), 64-element M (N) blocks kMnBlock bytes apart (leading byte offset,
+//             one TMA box each).  A K-step of 16 advances two groups, 2048 bytes.
+constexpr uint32_t kMnBlock = 64 * 64 * 2;   // one 64 (MN) x 64 (K) BF16 box
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lead_bytes) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
-    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+    d |= (uint64_t)((lead_bytes >> 4) & 0x3FFF) << 16;   // leading byte offset
     d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
     d |= (uint64_t)1 << 46;                          // descriptor version
     d |= (uint64_t)2 << 61;                          // 128-byte swizzle
     return d;
 }
-// instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, both K-major, M x N
-__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, M x N; bits 15 / 16 select
+// the MN-major (transposed) form of A / B
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a_mn & 1) << 15) | ((uint32_t)(b_mn & 1) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // exponent clamped so that 1 + e^-x stays below 2^126, the range of the fast divide
@@ -153,6 +166,8 @@ __global__ void __launch_bounds__(192, 2)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+    static_assert(kABytes == (kBM / 64) * (int)kMnBlock && kBBytes == (BN / 64) * (int)kMnBlock,
+                  "an MN-major stage is whole 64 x 64 boxes");
     uint8_t* sA = smem;
     uint8_t* sB = smem + kStages * kABytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
@@ -198,12 +213,24 @@ __global__ void __launch_bounds__(192, 2)
                 break;
             }
             mbar_expect_tx(&full[s], kABytes + kBBytes);
-            tma_load_2d(sA + s * kABytes, &tmA, kt * kBK, m0, &full[s]);
-            tma_load_2d(sB + s * kBBytes, &tmB, kt * kBK, n0, &full[s]);
+            if (p.a_mn) {
+                for (int i = 0; i < kBM / 64; ++i)
+                    tma_load_2d(sA + s * kABytes + i * kMnBlock, &tmA, m0 + 64 * i, kt * kBK, &full[s]);
+            } else {
+                tma_load_2d(sA + s * kABytes, &tmA, kt * kBK, m0, &full[s]);
+            }
+            if (p.b_mn) {
+                for (int j = 0; j < BN / 64; ++j)
+                    tma_load_2d(sB + s * kBBytes + j * kMnBlock, &tmB, n0 + 64 * j, kt * kBK, &full[s]);
+            } else {
+                tma_load_2d(sB + s * kBBytes, &tmB, kt * kBK, n0, &full[s]);
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        constexpr uint32_t idesc = instr_desc(kBM, BN);
+        const uint32_t idesc = instr_desc(kBM, BN, p.a_mn, p.b_mn);
+        const uint32_t a_step = p.a_mn ? 2048u : 32u, b_step = p.b_mn ? 2048u : 32u;
+        const uint32_t a_lead = p.a_mn ? kMnBlock : 16u, b_lead = p.b_mn ? kMnBlock : 16u;
         for (int kt = 0; kt < ktiles; ++kt) {
             const int s = kt % kStages;
             const uint32_t ph = (kt / kStages) & 1;
@@ -215,7 +242,7 @@ __global__ void __launch_bounds__(192, 2)
             const uint32_t a0 = saddr(sA + s * kABytes), b0 = saddr(sB + s * kBBytes);
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk) {
-                const uint64_t ad = smem_desc(a0 + kk * 32), bd = smem_desc(b0 + kk * 32);
+                const uint64_t ad = smem_desc(a0 + kk * a_step, a_lead), bd = smem_desc(b0 + kk * b_step, b_lead);
                 const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -306,7 +333,8 @@ bool get_encode() {
 }
 
 // 2-D tensor map over a row-major [rows][ld] BF16 matrix with `cols` valid columns; box of
-// 64 columns x box_rows rows, 128-byte swizzle, zero fill out of range.
+// 64 columns x box_rows rows, 128-byte swizzle, zero fill out of range.  A K-major operand is
+// mapped as [M or N][K] with box rows = tile rows, an MN-major one as [K][M or N] with 64-row boxes.
 bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
@@ -362,7 +390,9 @@ int block_slots(int dev) {
 template <int BN, int kStages>
 cudaError_t launch_bn(const GemmArgs& a, const void* A, int lda, const void* B, int ldb, int dev, cudaStream_t s) {
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, a.M, a.K, lda, kBM) || !make_map(&mb, B, a.N, a.K, ldb, BN)) return cudaErrorInvalidValue;
+    const bool okA = a.a_mn ? make_map(&ma, A, a.K, a.M, lda, kBK) : make_map(&ma, A, a.M, a.K, lda, kBM);
+    const bool okB = a.b_mn ? make_map(&mb, B, a.K, a.N, ldb, kBK) : make_map(&mb, B, a.N, a.K, ldb, BN);
+    if (!okA || !okB) return cudaErrorInvalidValue;
     const cudaError_t e = ensure_smem_attr<BN, kStages>(dev);
     if (e != cudaSuccess) return e;
     dim3 grid((a.N + BN - 1) / BN, (a.M + kBM - 1) / kBM);
@@ -375,6 +405,8 @@ cudaError_t launch_bn(const GemmArgs& a, const void* A, int lda, const void* B, 
 cudaError_t gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, GemmArgs args, cudaStream_t s) {
     if (!get_encode()) return cudaErrorNotSupported;
     if (args.M <= 0 || args.N <= 0 || args.K <= 0) return cudaErrorInvalidValue;
+    args.a_mn = args.a_mn ? 1 : 0;
+    args.b_mn = args.b_mn ? 1 : 0;
     if ((lda % 8) || (ldb % 8) || (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
         return cudaErrorInvalidValue;
     const int vec_align = args.c_bf16 ? 8 : 4;

@@ -41,36 +41,6 @@ __global__ void k_to_bf16(const float* P, __nv_bfloat16* Ph, size_t n) {
         Ph[i] = __float2bfloat16_rn(P[i]);
 }
 
-// dst[c][r] = bf16(src[r][c]) for an R x C FP32 matrix (weights)
-__global__ void k_transpose_f32_to_bf16(const float* src, int R, int C, int lds, __nv_bfloat16* dst, int ldd) {
-    __shared__ float tile[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int r = r0 + j, c = c0 + threadIdx.x;
-        tile[j][threadIdx.x] = (r < R && c < C) ? src[(size_t)r * lds + c] : 0.f;
-    }
-    __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int c = c0 + j, r = r0 + threadIdx.x;
-        if (c < C && r < R) dst[(size_t)c * ldd + r] = __float2bfloat16_rn(tile[threadIdx.x][j]);
-    }
-}
-
-// dst[c][r] = src[r][c] for an R x C BF16 matrix
-__global__ void k_transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds, __nv_bfloat16* dst, int ldd) {
-    __shared__ __nv_bfloat16 tile[32][34];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int r = r0 + j, c = c0 + threadIdx.x;
-        tile[j][threadIdx.x] = (r < R && c < C) ? src[(size_t)r * lds + c] : __float2bfloat16_rn(0.f);
-    }
-    __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int c = c0 + j, r = r0 + threadIdx.x;
-        if (c < C && r < R) dst[(size_t)c * ldd + r] = tile[threadIdx.x][j];
-    }
-}
-
 // dY = d mean((y - t)^2) / dy (times y (1 - y) for a sigmoid output), as BF16; loss sum
 __global__ void k_loss_grad(const float* Y, int ldy, const float* T, int ldt, int B, int N, float scale, int sig,
                             __nv_bfloat16* dY, int ldd, float* loss_acc) {
@@ -181,21 +151,27 @@ cudaError_t colsum(const __nv_bfloat16* src, int B, int N, int ld, float* part, 
 
 int nblocks(size_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
 
-cudaError_t transpose_bf16(const __nv_bfloat16* src, int R, int C, int lds, __nv_bfloat16* dst, int ldd,
-                           cudaStream_t s) {
-    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
-    k_transpose_bf16<<<grid, block, 0, s>>>(src, R, C, lds, dst, ldd);
-    return cudaGetLastError();
-}
-
 cudaError_t gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, void* C, int ldc, int c_bf16,
                  const float* bias, int act, void* Z, int ldz, uint32_t* err, cudaStream_t s,
-                 const float* scale = nullptr, const float* shift = nullptr) {
+                 const float* scale = nullptr, const float* shift = nullptr, int a_mn = 0, int b_mn = 0) {
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));
     g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc; g.c_bf16 = c_bf16; g.bias = bias; g.act = act;
-    g.Z = Z; g.ldz = ldz; g.err = err; g.scale = scale; g.shift = shift;
+    g.Z = Z; g.ldz = ldz; g.err = err; g.scale = scale; g.shift = shift; g.a_mn = a_mn; g.b_mn = b_mn;
     return gemm_bf16_tc(A, lda, B, ldb, g, s);
+}
+
+// weight gradient G[M][N] (pitch ldg) = D^T S over the batch: D [B][M], S [B][N] as stored
+// (both operands MN-contiguous)
+cudaError_t gemm_dw(const __nv_bfloat16* D, int ldd, const __nv_bfloat16* S, int lds, int M, int N, int B, float* G,
+                    int ldg, uint32_t* err, cudaStream_t s) {
+    return gemm(D, ldd, S, lds, M, N, B, G, ldg, 0, nullptr, 0, nullptr, 0, err, s, nullptr, nullptr, 1, 1);
+}
+// input gradient dH[B][N] = D W for D [B][K] and the layer's weights W [K][N] as stored (W's
+// rows are the layer's outputs: the B operand is N-contiguous)
+cudaError_t gemm_dx(const __nv_bfloat16* D, int ldd, const __nv_bfloat16* W, int ldw, int B, int N, int K, float* dH,
+                    int ldh, uint32_t* err, cudaStream_t s) {
+    return gemm(D, ldd, W, ldw, B, N, K, dH, ldh, 0, nullptr, 0, nullptr, 0, err, s, nullptr, nullptr, 0, 1);
 }
 
 #define CK(x)                                  \
@@ -212,7 +188,7 @@ cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp
     Mlp* m = new Mlp();
     std::memset(m, 0, sizeof(Mlp));
     m->in = in; m->inp = pad8(in); m->hid = hid; m->out = out; m->outp = pad8(out); m->out_act = out_act;
-    m->max_batch = max_batch; m->bp = pad8(max_batch);
+    m->max_batch = max_batch;
     size_t o = 0;
     m->oW1 = o; o = pad8s(o + (size_t)hid * m->inp);
     m->ob1 = o; o = pad8s(o + hid);
@@ -229,13 +205,9 @@ cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp
     };
     A((void**)&m->P, np * 4); A((void**)&m->G, np * 4); A((void**)&m->Am, np * 4); A((void**)&m->Av, np * 4);
     A((void**)&m->Ph, np * 2);
-    A((void**)&m->W2t, (size_t)hid * hid * 2); A((void**)&m->W3t, (size_t)hid * m->outp * 2);
     A((void**)&m->H1, B * hid * 2); A((void**)&m->Z1, B * hid * 2); A((void**)&m->H2, B * hid * 2);
     A((void**)&m->Z2, B * hid * 2); A((void**)&m->dY, B * m->outp * 2); A((void**)&m->dZ1, B * hid * 2);
     A((void**)&m->dZ2, B * hid * 2);
-    A((void**)&m->Xt, (size_t)m->inp * m->bp * 2); A((void**)&m->H1t, (size_t)hid * m->bp * 2);
-    A((void**)&m->H2t, (size_t)hid * m->bp * 2); A((void**)&m->dYt, (size_t)m->outp * m->bp * 2);
-    A((void**)&m->dZ1t, (size_t)hid * m->bp * 2); A((void**)&m->dZ2t, (size_t)hid * m->bp * 2);
     A((void**)&m->Y, B * m->outp * 4); A((void**)&m->dH, B * hid * 4);
     A((void**)&m->loss_acc, 8); A((void**)&m->err, 8);
     A((void**)&m->colpart, (size_t)((max_batch + 127) / 128) * std::max(m->outp, hid) * 4);
@@ -249,9 +221,8 @@ cudaError_t mlp_create(int in, int hid, int out, int out_act, int max_batch, Mlp
 
 void mlp_destroy(Mlp* m) {
     if (!m) return;
-    void* ptrs[] = {m->P, m->G, m->Am, m->Av, m->Ph, m->W2t, m->W3t, m->H1, m->Z1, m->H2, m->Z2, m->dY, m->dZ1,
-                    m->dZ2, m->Xt, m->H1t, m->H2t, m->dYt, m->dZ1t, m->dZ2t, m->Y, m->dH, m->loss_acc, m->err,
-                    m->mask, m->colpart};
+    void* ptrs[] = {m->P, m->G, m->Am, m->Av, m->Ph, m->H1, m->Z1, m->H2, m->Z2, m->dY, m->dZ1, m->dZ2, m->Y, m->dH,
+                    m->loss_acc, m->err, m->mask, m->colpart};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m;
@@ -260,13 +231,6 @@ void mlp_destroy(Mlp* m) {
 cudaError_t mlp_sync_bf16(Mlp* m, cudaStream_t s) {
     ++m->version;
     k_to_bf16<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->Ph, m->n_params);
-    CK(cudaGetLastError());
-    dim3 block(32, 8);
-    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->hid + 31) / 32), block, 0, s>>>(
-        m->P + m->oW2, m->hid, m->hid, m->hid, m->W2t, m->hid);
-    CK(cudaGetLastError());
-    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->outp + 31) / 32), block, 0, s>>>(
-        m->P + m->oW3, m->outp, m->hid, m->hid, m->W3t, m->outp);
     return cudaGetLastError();
 }
 
@@ -342,33 +306,27 @@ cudaError_t mlp_infer_head(Mlp* m, const __nv_bfloat16* X, int ldx, int B, const
 
 cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T, int ldt, int B, cudaStream_t s) {
     if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;
-    const int h = m->hid, bp = pad8(B);
+    const int h = m->hid;
     CK(mlp_forward(m, X, ldx, B, m->Y, m->outp, s));
     CK(cudaMemsetAsync(m->loss_acc, 0, 4, s));
     const size_t nY = (size_t)B * m->out;
     k_loss_grad<<<nblocks(nY), 256, 0, s>>>(m->Y, m->outp, T, ldt, B, m->out, 2.f / (float)nY, m->out_act == 2, m->dY,
                                              m->outp, m->loss_acc);
     CK(cudaGetLastError());
-    // layer 3
-    CK(transpose_bf16(m->dY, B, m->out, m->outp, m->dYt, bp, s));
-    CK(transpose_bf16(m->H2, B, h, h, m->H2t, bp, s));
-    CK(gemm(m->dYt, bp, m->H2t, bp, m->out, h, B, m->G + m->oW3, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    // layer 3: dW3 = dY^T H2, db3 = column sums of dY, dH2 = dY W3
+    CK(gemm_dw(m->dY, m->outp, m->H2, h, m->out, h, B, m->G + m->oW3, h, m->err, s));
     CK(colsum(m->dY, B, m->out, m->outp, m->colpart, m->G + m->ob3, s));
-    CK(gemm(m->dY, m->outp, m->W3t, m->outp, B, h, m->out, m->dH, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    CK(gemm_dx(m->dY, m->outp, m->Ph + m->oW3, h, B, h, m->out, m->dH, h, m->err, s));
     k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z2, B, h, h, m->dZ2);
     CK(cudaGetLastError());
     // layer 2
-    CK(transpose_bf16(m->dZ2, B, h, h, m->dZ2t, bp, s));
-    CK(transpose_bf16(m->H1, B, h, h, m->H1t, bp, s));
-    CK(gemm(m->dZ2t, bp, m->H1t, bp, h, h, B, m->G + m->oW2, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    CK(gemm_dw(m->dZ2, h, m->H1, h, h, h, B, m->G + m->oW2, h, m->err, s));
     CK(colsum(m->dZ2, B, h, h, m->colpart, m->G + m->ob2, s));
-    CK(gemm(m->dZ2, h, m->W2t, h, B, h, h, m->dH, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    CK(gemm_dx(m->dZ2, h, m->Ph + m->oW2, h, B, h, h, m->dH, h, m->err, s));
     k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z1, B, h, h, m->dZ1);
     CK(cudaGetLastError());
     // layer 1
-    CK(transpose_bf16(m->dZ1, B, h, h, m->dZ1t, bp, s));
-    CK(transpose_bf16(X, B, m->inp, ldx, m->Xt, bp, s));
-    CK(gemm(m->dZ1t, bp, m->Xt, bp, h, m->in, B, m->G + m->oW1, m->inp, 0, nullptr, 0, nullptr, 0, m->err, s));
+    CK(gemm_dw(m->dZ1, h, X, ldx, h, m->in, B, m->G + m->oW1, m->inp, m->err, s));
     return colsum(m->dZ1, B, h, h, m->colpart, m->G + m->ob1, s);
 }
 
@@ -378,13 +336,6 @@ cudaError_t mlp_adam(Mlp* m, float lr, float beta1, float beta2, float eps, cuda
     const float bc1 = 1.f - powf(beta1, (float)m->adam_t), bc2 = 1.f - powf(beta2, (float)m->adam_t);
     k_adam<<<nblocks(m->n_params), 256, 0, s>>>(m->P, m->G, m->Am, m->Av, m->n_params, lr, beta1, beta2, eps, bc1,
                                                   bc2, m->Ph, m->mask);
-    CK(cudaGetLastError());
-    dim3 block(32, 8);
-    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->hid + 31) / 32), block, 0, s>>>(
-        m->P + m->oW2, m->hid, m->hid, m->hid, m->W2t, m->hid);
-    CK(cudaGetLastError());
-    k_transpose_f32_to_bf16<<<dim3((m->hid + 31) / 32, (m->outp + 31) / 32), block, 0, s>>>(
-        m->P + m->oW3, m->outp, m->hid, m->hid, m->W3t, m->outp);
     return cudaGetLastError();
 }
 

@@ -2,8 +2,9 @@
 //
 // Used by the muscle-geometry surrogate (trained on the GPU) and by the policy network of the
 // closed-loop rollout.  Parameters live in one flat FP32 buffer (master copy, Adam moments and
-// gradients share its layout) with a BF16 copy for the GEMMs, plus transposed BF16 copies of W2
-// and W3 for the input-gradient GEMMs.  Activations are BF16, accumulation FP32, the output FP32.
+// gradients share its layout) with a BF16 copy for the GEMMs.  Activations are BF16, accumulation
+// FP32, the output FP32.  The backward reads activations, gradients and weights as stored (the
+// GEMM's MN-contiguous operand mode), so no transposed copies exist.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -16,7 +17,7 @@ struct Mlp {
     int hid;               // hidden width (multiple of 8)
     int out, outp;         // output width and its pitch (multiple of 8)
     int out_act;           // 0 identity, 2 sigmoid
-    int max_batch, bp;     // batch capacity of the scratch buffers, batch pitch of transposes
+    int max_batch;         // batch capacity of the scratch buffers
     // flat parameter layout (FP32 element offsets; every segment starts at a multiple of 8)
     size_t oW1, ob1, oW2, ob2, oW3, ob3, n_params;
     float* P;              // master parameters
@@ -24,12 +25,9 @@ struct Mlp {
     float* Am;             // Adam first moments
     float* Av;             // Adam second moments
     __nv_bfloat16* Ph;     // BF16 copy of P (same offsets)
-    __nv_bfloat16* W2t;    // [hid][hid]  = W2^T
-    __nv_bfloat16* W3t;    // [hid][outp] = W3^T
     int adam_t;
     // scratch, max_batch rows
     __nv_bfloat16 *H1, *Z1, *H2, *Z2, *dY, *dZ1, *dZ2;
-    __nv_bfloat16 *Xt, *H1t, *H2t, *dYt, *dZ1t, *dZ2t;   // transposed, pitch bp
     float *Y, *dH;
     float* loss_acc;       // device scalar: sum of squared errors of the last backward
     uint32_t* err;         // device word: GEMM bounded-wait failures

@@ -1285,16 +1285,17 @@ msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_parent, i
     return MSIM_OK;
 }
 
-msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ldb, const float* bias, void* C,
-                           int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t c_bf16, int32_t act, void* Z,
-                           int32_t ldz, uint32_t* err, msim_stream_t stream) {
-    if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || lda < K || ldb < K || ldc < N || act < 0 || act > 2 ||
-        (Z && ldz < N))
+msim_status msim_gemm_bf16_mn(const void* A, int32_t lda, int32_t a_mn, const void* B, int32_t ldb, int32_t b_mn,
+                              const float* bias, void* C, int32_t ldc, int32_t M, int32_t N, int32_t K,
+                              int32_t c_bf16, int32_t act, void* Z, int32_t ldz, uint32_t* err,
+                              msim_stream_t stream) {
+    if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || (a_mn != 0 && a_mn != 1) || (b_mn != 0 && b_mn != 1) ||
+        lda < (a_mn ? M : K) || ldb < (b_mn ? N : K) || ldc < N || act < 0 || act > 2 || (Z && ldz < N))
         return arg_fail(nullptr, "msim_gemm_bf16: bad argument");
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));
     g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc; g.c_bf16 = c_bf16 ? 1 : 0; g.bias = bias; g.act = act;
-    g.Z = Z; g.ldz = ldz; g.err = err;
+    g.Z = Z; g.ldz = ldz; g.err = err; g.a_mn = a_mn; g.b_mn = b_mn;
     const cudaError_t e = gemm_bf16_tc(A, lda, B, ldb, g, (cudaStream_t)stream);
     if (e == cudaErrorNotSupported) {
         g_create_error = "msim_gemm_bf16: tensor-map encoding unavailable";
@@ -1302,6 +1303,12 @@ msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ld
     }
     if (e == cudaErrorInvalidValue) return arg_fail(nullptr, "msim_gemm_bf16: pitch or alignment not supported");
     return e == cudaSuccess ? MSIM_OK : cuda_fail(nullptr, e, "msim_gemm_bf16");
+}
+
+msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ldb, const float* bias, void* C,
+                           int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t c_bf16, int32_t act, void* Z,
+                           int32_t ldz, uint32_t* err, msim_stream_t stream) {
+    return msim_gemm_bf16_mn(A, lda, 0, B, ldb, 0, bias, C, ldc, M, N, K, c_bf16, act, Z, ldz, err, stream);
 }
 
 msim_status msim_mlp_create(int32_t in, int32_t hidden, int32_t out, int32_t out_act, int32_t max_batch, uint64_t seed,

@@ -92,7 +92,7 @@ class EvalOut(C.Structure):
 EXPORTS = ("msim_create", "msim_destroy", "msim_get_dims", "msim_reset", "msim_step", "msim_step_host",
            "msim_step_host_async", "msim_host_wait",
            "msim_get_state", "msim_get_status", "msim_clear_status", "msim_eval", "msim_get_layout",
-           "msim_set_launch", "msim_gemm_bf16", "msim_mlp_create", "msim_mlp_destroy", "msim_mlp_layout",
+           "msim_set_launch", "msim_gemm_bf16", "msim_gemm_bf16_mn", "msim_mlp_create", "msim_mlp_destroy", "msim_mlp_layout",
            "msim_mlp_get", "msim_mlp_set", "msim_mlp_forward", "msim_mlp_backward", "msim_mlp_adam",
            "msim_surrogate_train", "msim_set_geometry_mode", "msim_surrogate_set_check", "msim_surrogate_stats",
            "msim_surrogate_network", "msim_geometry", "msim_surrogate_predict", "msim_mlp_forward_noalloc",
@@ -131,6 +131,8 @@ def load_library(path=LIB_PATH):
     lib.msim_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     lib.msim_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                    C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
+    lib.msim_gemm_bf16_mn.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, C.c_int32,
+                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
     lib.msim_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_float,
                                     C.POINTER(vp)]
     lib.msim_mlp_destroy.argtypes = [vp]
@@ -502,19 +504,22 @@ def measure_fp32_peak(device=0):
     return v.value
 
 
-def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=None):
-    """C = act(A B^T + bias) on the tensor cores (msim_gemm_bf16).  A [M, K], B [N, K]: BF16 CUDA
-    tensors with unit column stride and row pitches multiple of 8."""
+def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=None, a_mn=False, b_mn=False):
+    """C = act(A B^T + bias) on the tensor cores (msim_gemm_bf16_mn).  A [M, K] (or, with a_mn, its
+    transpose [K, M] as stored), B [N, K] (with b_mn [K, N]): BF16 CUDA tensors with unit column
+    stride and row pitches multiple of 8."""
     import torch
     lib = load_library()
-    M, K = A.shape
-    N = B.shape[0]
+    M, K = (A.shape[1], A.shape[0]) if a_mn else A.shape
+    N = B.shape[1] if b_mn else B.shape[0]
+    if (B.shape[0] if b_mn else B.shape[1]) != K:
+        raise ValueError("gemm_bf16: inner dimensions differ")
     C = torch.empty((M, N), device=A.device, dtype=torch.bfloat16 if out_bf16 else torch.float32)
-    st = lib.msim_gemm_bf16(A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
-                            None if bias is None else bias.data_ptr(), C.data_ptr(), C.stride(0), M, N, K,
-                            1 if out_bf16 else 0, act, None if Z is None else Z.data_ptr(),
-                            0 if Z is None else Z.stride(0), None if err is None else err.data_ptr(),
-                            _stream_ptr(stream))
+    st = lib.msim_gemm_bf16_mn(A.data_ptr(), A.stride(0), 1 if a_mn else 0, B.data_ptr(), B.stride(0),
+                               1 if b_mn else 0, None if bias is None else bias.data_ptr(), C.data_ptr(), C.stride(0),
+                               M, N, K, 1 if out_bf16 else 0, act, None if Z is None else Z.data_ptr(),
+                               0 if Z is None else Z.stride(0), None if err is None else err.data_ptr(),
+                               _stream_ptr(stream))
     if st != MSIM_OK:
         raise MsimError(st, lib.msim_last_error(None).decode())
     return C

@@ -1,4 +1,4 @@
-"""The tcgen05 BF16 GEMM (msim_gemm_bf16) against a plain PyTorch FP32 reference of the same op."""
+"""The tcgen05 BF16 GEMM (msim_gemm_bf16, msim_gemm_bf16_mn) against a plain PyTorch FP32 reference of the same op."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -42,6 +42,48 @@ def test_gemm_matches_fp32_reference(M, N, K, act, bias):
     assert err.item() == 0
     # FP32 accumulation of exact BF16 products: error ~ K * 2^-24 * sum |a b|
     scale = (A[:, :K].float().abs() @ B[:, :K].float().abs().T) + 1.0
+    assert ((C - ref).abs() / scale).max().item() < 1e-5
+
+
+@pytest.mark.parametrize("M,N,K,a_mn,b_mn", [
+    (300, 200, 90, 1, 0),        # ragged, A stored [K][M]
+    (300, 200, 90, 0, 1),        # ragged, B stored [K][N]
+    (64, 48, 16, 1, 1),          # smaller than a tile, both transposed
+    (2448, 512, 4000, 1, 1),     # weight gradient dY^T H of the surrogate's output layer, ragged batch
+    (4096, 512, 2448, 0, 1),     # input gradient dY W3 (W3 stored [out][hidden])
+    (512, 90, 4096, 1, 1),       # first-layer weight gradient dZ1^T X
+    (8192, 2048, 200, 1, 1),     # 256-wide tiles (four 64-column boxes per B stage)
+])
+def test_gemm_mn_contiguous_operands(M, N, K, a_mn, b_mn):
+    """msim_gemm_bf16_mn reads A as [K][M] and / or B as [K][N] storage (the tensor cores'
+    transposed operand mode) and must give what the K-contiguous GEMM gives on the transposes."""
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 5 * K)
+    pad = lambda x: (x + 7) // 8 * 8
+    A = torch.randn((M, K), device="cuda", generator=g).bfloat16()
+    B = (torch.randn((N, K), device="cuda", generator=g) / K ** 0.5).bfloat16()
+    b = torch.randn(N, device="cuda", generator=g)
+    if a_mn:
+        As = torch.zeros((K, pad(M)), device="cuda", dtype=torch.bfloat16)
+        As[:, :M] = A.T
+        Aarg = As[:, :M]
+    else:
+        As = torch.zeros((M, pad(K)), device="cuda", dtype=torch.bfloat16)
+        As[:, :K] = A
+        Aarg = As[:, :K]
+    if b_mn:
+        Bs = torch.zeros((K, pad(N)), device="cuda", dtype=torch.bfloat16)
+        Bs[:, :N] = B.T
+        Barg = Bs[:, :N]
+    else:
+        Bs = torch.zeros((N, pad(K)), device="cuda", dtype=torch.bfloat16)
+        Bs[:, :K] = B
+        Barg = Bs[:, :K]
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = msim.gemm_bf16(Aarg, Barg, b, act=1, err=err, a_mn=bool(a_mn), b_mn=bool(b_mn))
+    torch.cuda.synchronize()
+    assert C.shape == (M, N) and err.item() == 0
+    ref, _ = _ref(A, B, b, 1)
+    scale = (A.float().abs() @ B.float().abs().T) + 1.0
     assert ((C - ref).abs() / scale).max().item() < 1e-5
 
 
