@@ -1515,7 +1515,7 @@ msim_status msim_surrogate_train(msim_handle h, int64_t n_samples, int32_t epoch
         if (e == cudaSuccess) e = geometry_launch(h, 0, qc, h->pitch_n, rows, T + (size_t)r0 * outp, outp, s);
         if (e == cudaSuccess) e = surr_col_stats(T + (size_t)r0 * outp, outp, rows, out, acc, s);
     }
-    if (e == cudaSuccess) e = surr_finalize(acc, out, outp, (double)N, 1e-4f, S->mu, S->sd, s);
+    if (e == cudaSuccess) e = surr_finalize(acc, out, outp, (double)N, kSurrSdFloor, S->mu, S->sd, s);
     if (e == cudaSuccess) e = surr_normalize(T, outp, N, out, S->mu, S->sd, s);
     // minibatches: contiguous blocks of the i.i.d. samples, visited in an affine-permuted order
     // per epoch; cosine learning-rate decay from lr to lr / 100

@@ -18,6 +18,13 @@ namespace msim {
 constexpr int kSurrHidden = 512;
 // joint-structured network: first-layer biases spread over each unit's input range at init
 constexpr bool kSurrSpreadBias = false;
+// Each output is normalised by its standard deviation over the labels, floored at this value
+// (metres: lengths and moment arms), so the training loss weighs an output's error by
+// 1 / max(sd, floor)^2 in physical units.
+#ifndef MSIM_SURR_SD_FLOOR
+#define MSIM_SURR_SD_FLOOR 1e-4f
+#endif
+constexpr float kSurrSdFloor = MSIM_SURR_SD_FLOOR;
 
 struct Surrogate {
     int n = 0, m = 0, nnz = 0, out = 0;   // DoFs, muscles, moment-arm entries, outputs m + nnz
