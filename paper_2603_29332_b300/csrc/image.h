@@ -157,12 +157,13 @@ __host__ __device__ inline int staged_bytes(const ImgHeader& h, int stage) {
 }
 
 // floats per environment slot for a group of `wpe` warps per environment (the moment-arm
-// region also holds the joint sines and cosines, and the contact scratch)
+// region also holds the joint sines and cosines, and the contact scratch); a multiple of 4, so
+// that every slot, and every region in it, starts on a 16-byte boundary
 __host__ __device__ inline int ws_floats(const ImgHeader& h, int wpe) {
     int r = h.max_nx * 32 * wpe;
     if (2 * h.n > r) r = 2 * h.n;
     if (12 * h.ns > r) r = 12 * h.ns;
-    return h.w_rk + r;
+    return (h.w_rk + r + 3) & ~3;
 }
 
 }  // namespace msim

@@ -238,6 +238,29 @@ __device__ __forceinline__ void cross3(const float a[3], const float b[3], float
 __device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
+// A body frame in the workspace is 12 floats, 16-byte aligned: the rotation row-major, then the
+// origin.  Read and written as three 16-byte words: lanes working on different bodies then meet
+// in shared memory as 16-byte accesses (a quarter-warp per wavefront) rather than as twelve
+// 4-byte accesses spread over only eight banks by the 12-float stride.
+__device__ __forceinline__ void frame_load(const float* f, float R[9], float p[3]) {
+    const float4 a = reinterpret_cast<const float4*>(f)[0];
+    const float4 b = reinterpret_cast<const float4*>(f)[1];
+    const float4 c = reinterpret_cast<const float4*>(f)[2];
+    R[0] = a.x; R[1] = a.y; R[2] = a.z; R[3] = a.w;
+    R[4] = b.x; R[5] = b.y; R[6] = b.z; R[7] = b.w;
+    R[8] = c.x; p[0] = c.y; p[1] = c.z; p[2] = c.w;
+}
+// the origin alone: the last 16-byte word (R22, origin)
+__device__ __forceinline__ void frame_origin(const float* f, float p[3]) {
+    const float4 c = reinterpret_cast<const float4*>(f)[2];
+    p[0] = c.y; p[1] = c.z; p[2] = c.w;
+}
+__device__ __forceinline__ void frame_store(float* f, const float R[9], const float p[3]) {
+    reinterpret_cast<float4*>(f)[0] = make_float4(R[0], R[1], R[2], R[3]);
+    reinterpret_cast<float4*>(f)[1] = make_float4(R[4], R[5], R[6], R[7]);
+    reinterpret_cast<float4*>(f)[2] = make_float4(R[8], p[0], p[1], p[2]);
+}
+
 // out = R v (R row-major 3x3)
 __device__ __forceinline__ void rot3(const float* R, const float v[3], float out[3]) {
     out[0] = R[0] * v[0] + R[1] * v[1] + R[2] * v[2];
@@ -501,30 +524,24 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
                 R[3 * r + 2] = cs * r2 + sn * x2 + omc * sv[r] * ax[2];
             }
         }
-        float* Fb = frame + 12 * b;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Fb[k] = R[k];
-        Fb[9] = p[0]; Fb[10] = p[1]; Fb[11] = p[2];
-        float* Vb = V + 6 * b;
-        float* Ab = Acc + 6 * b;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { Vb[k] = w[k]; Vb[3 + k] = vl[k]; Ab[k] = aw[k]; Ab[3 + k] = al[k]; }
+        frame_store(raw(frame + 12 * b), R, p);
+        float2* Vb = reinterpret_cast<float2*>(raw(V + 6 * b));     // 8-byte aligned (6 floats per body)
+        float2* Ab = reinterpret_cast<float2*>(raw(Acc + 6 * b));
+        Vb[0] = make_float2(w[0], w[1]); Vb[1] = make_float2(w[2], vl[0]); Vb[2] = make_float2(vl[1], vl[2]);
+        Ab[0] = make_float2(aw[0], aw[1]); Ab[1] = make_float2(aw[2], al[0]); Ab[2] = make_float2(al[1], al[2]);
     }
     g.sync();
     SUB_MARK(15);   // profiling builds: sines, cosines and the recursion
     // 3. spatial inertia and body force of every body, all bodies in parallel
     for (int b = g.lane; b < H.nb; b += g.N) {
         const BodyRec& B = T.body[b];
-        const float* Fb = frame + 12 * b;
-        const float* Vb = V + 6 * b;
-        const float* Ab = Acc + 6 * b;
-        float R[9], p[3], w[3], vl[3], aw[3], al[3];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) R[k] = Fb[k];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            p[k] = Fb[9 + k]; w[k] = Vb[k]; vl[k] = Vb[3 + k]; aw[k] = Ab[k]; al[k] = Ab[3 + k];
-        }
+        const float2* Vb = reinterpret_cast<const float2*>(raw(V + 6 * b));
+        const float2* Ab = reinterpret_cast<const float2*>(raw(Acc + 6 * b));
+        float R[9], p[3];
+        frame_load(raw(frame + 12 * b), R, p);
+        const float2 v0 = Vb[0], v1 = Vb[1], v2 = Vb[2], a0 = Ab[0], a1 = Ab[1], a2 = Ab[2];
+        const float w[3] = {v0.x, v0.y, v1.x}, vl[3] = {v1.y, v2.x, v2.y};
+        const float aw[3] = {a0.x, a0.y, a1.x}, al[3] = {a1.y, a2.x, a2.y};
         // spatial inertia about the world origin: m, h = m c, Ibar = R Ic R^T + m (|c|^2 1 - c c^T).
         // R Ic R^T in FP32 (a consistent perturbation of the body's own inertia); the
         // parallel-axis part, exact products of the FP32 COM, in float-float.
@@ -896,22 +913,27 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
             PointRec Pn = T.pt[M.p0 + 32];   // the next point is loaded one segment ahead
             int b = P.body_cross & 0xff;
             int cprev = P.body_cross >> 8;
-            const float* fb = frame + 12 * b;
             float x0[3];
-            rot3(fb, P.pos, x0);
-            x0[0] += fb[9]; x0[1] += fb[10]; x0[2] += fb[11];
+            {
+                float Rb[9], pb[3];
+                frame_load(raw(frame + 12 * b), Rb, pb);
+                rot3(Rb, P.pos, x0);
+                x0[0] += pb[0]; x0[1] += pb[1]; x0[2] += pb[2];
+            }
             // moment arms of the crossed DoFs [i0, i1) for a straight piece with unit direction
             // uu whose distal end xd moves with them: R = -dL/dq = -s_d . ((xd - o_d) x uu)
             auto arms = [&](int i0, int i1, const float xd[3], const float uu[3]) {
                 for (int i = i0; i < i1; ++i) {
                     const uint32_t ce = T.cross[M.x0 + i];
                     const int d = cross_dof(ce);
-                    const float* Sd = S + 6 * d;
-                    const float* o = frame + 12 * cross_body(ce) + 9;
+                    const float2 s01 = *reinterpret_cast<const float2*>(raw(S + 6 * d));   // 8-byte aligned
+                    const float s2 = S[6 * d + 2];
+                    float o[3];
+                    frame_origin(raw(frame + 12 * cross_body(ce)), o);
                     const float rr[3] = {xd[0] - o[0], xd[1] - o[1], xd[2] - o[2]};
                     float rxu[3];
                     cross3(rr, uu, rxu);
-                    const float Rv = -(Sd[0] * rxu[0] + Sd[1] * rxu[1] + Sd[2] * rxu[2]);
+                    const float Rv = -(s01.x * rxu[0] + s01.y * rxu[1] + s2 * rxu[2]);
                     rk[i * g.N + g.lane] = Rv;
                     ldot -= Rv * qd[d];
                 }
@@ -922,10 +944,13 @@ __device__ uint32_t phase_muscles(const Tables& T, float* ws, const Grp<WPE>& g,
                 if (j + 1 < M.np) Pn = T.pt[M.p0 + 32 * (j + 1)];
                 b = P.body_cross & 0xff;
                 const int c = P.body_cross >> 8;
-                fb = frame + 12 * b;
                 float x1[3];
-                rot3(fb, P.pos, x1);
-                x1[0] += fb[9]; x1[1] += fb[10]; x1[2] += fb[11];
+                {
+                    float Rb[9], pb[3];
+                    frame_load(raw(frame + 12 * b), Rb, pb);
+                    rot3(Rb, P.pos, x1);
+                    x1[0] += pb[0]; x1[1] += pb[1]; x1[2] += pb[2];
+                }
                 bool wrapped = false;
                 if (has_ext(MODE) && j == wseg) {
                     // the wrapped segment: tangent points held on the cylinder's body for the arms
