@@ -55,6 +55,11 @@ struct alignas(16) MuscleRec {  // 32 B
 // Crossed-DoF table entry: dof | body << 8 | packed row << 16.  A muscle's crossed DoFs form
 // one contiguous ancestor chain, so entry (d_i, d_j), j <= i, of the packed matrix is at
 // row(d_i) + dep0 + j.
+// a node of the factorisation's level order (the dorder table): DoF, depth, packed row start
+__host__ __device__ inline int node_dof(uint32_t w) { return w & 0xff; }
+__host__ __device__ inline int node_depth(uint32_t w) { return (w >> 8) & 0xff; }
+__host__ __device__ inline int node_row(uint32_t w) { return w >> 16; }
+
 __host__ __device__ inline int cross_dof(uint32_t c) { return c & 0xff; }
 __host__ __device__ inline int cross_body(uint32_t c) { return (c >> 8) & 0xff; }
 __host__ __device__ inline int cross_row(uint32_t c) { return c >> 16; }

@@ -168,14 +168,15 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         cround.push_back((int16_t)cstart.size());
         cstart.push_back((int16_t)cbody.size());
     }
-    // DoF levels
+    // DoF levels; each node of the factorisation as one word (node_dof / node_depth / node_row
+    // in image.h), so that its lanes need one shared-memory load per node, not two dependent ones
     const int n_dl = max_depth + 1;
-    std::vector<uint8_t> dorder;
+    std::vector<uint32_t> dorder;
     std::vector<int16_t> dlevel(n_dl + 1, 0);
     for (int l = 0; l < n_dl; ++l) {
         dlevel[l] = (int16_t)dorder.size();
         for (int i = 0; i < n; ++i)
-            if (depth[i] == l) dorder.push_back((uint8_t)i);
+            if (depth[i] == l) dorder.push_back((uint32_t)i | ((uint32_t)depth[i] << 8) | ((uint32_t)row[i] << 16));
     }
     dlevel[n_dl] = (int16_t)dorder.size();
     // CRBA work order: DoFs by decreasing packed-row length, dealt to the 32 lanes in a snake
@@ -183,7 +184,7 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     std::vector<int> byrow(n);
     for (int i = 0; i < n; ++i) byrow[i] = i;
     std::stable_sort(byrow.begin(), byrow.end(), [&](int a, int b) { return depth[a] > depth[b]; });
-    std::vector<uint8_t> crba_order(n);
+    std::vector<uint32_t> crba_order(2 * n);
     {
         std::vector<std::vector<int>> lanes(32);
         for (int i = 0; i < n; ++i) {
@@ -208,7 +209,13 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             slot[t] = next;
             used[next] = 1;
         }
-        for (int t = 0; t < n; ++t) crba_order[t] = (uint8_t)slot[t];
+        // entry t: DoF | body << 8 | depth << 16, then its packed row start (one 8-byte load
+        // per lane instead of a lookup of the DoF record)
+        for (int t = 0; t < n; ++t) {
+            const int dd = slot[t];
+            crba_order[2 * t] = (uint32_t)dd | ((uint32_t)dof_body[dd] << 8) | ((uint32_t)depth[dd] << 16);
+            crba_order[2 * t + 1] = (uint32_t)row[dd];
+        }
     }
     // pair table: p -> (ia, ib), ib <= ia, row by row
     std::vector<uint16_t> tri;
@@ -449,14 +456,14 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     h.o_blevel = place(sizeof(int16_t) * blevel.size());
     h.o_child = place(child.size());
     h.o_anc = place(anc.size());
-    h.o_dorder = place(dorder.size());
+    h.o_dorder = place(sizeof(uint32_t) * dorder.size());
     h.o_dlevel = place(sizeof(int16_t) * dlevel.size());
     h.n_crounds = (int32_t)cround.size() - 1;
     h.n_chains = (int32_t)cstart.size() - 1;
     h.o_chain = place(sizeof(int16_t) * (cround.size() + cstart.size()) + cbody.size());
     h.o_tri = place(sizeof(uint16_t) * tri.size());
     h.o_rowanc = place(sizeof(uint16_t) * rowanc.size());
-    h.o_crba = place(crba_order.size());
+    h.o_crba = place(sizeof(uint32_t) * crba_order.size());
     // last: the sections that may stay in global memory (staged_bytes in image.h)
     h.o_muscle = place(sizeof(MuscleRec) * m);
     h.o_cross = place(sizeof(uint32_t) * cross.size());
@@ -523,14 +530,14 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
     put(h.o_blevel, blevel.data(), sizeof(int16_t) * blevel.size());
     put(h.o_child, child.data(), child.size());
     put(h.o_anc, anc.data(), anc.size());
-    put(h.o_dorder, dorder.data(), dorder.size());
+    put(h.o_dorder, dorder.data(), sizeof(uint32_t) * dorder.size());
     put(h.o_dlevel, dlevel.data(), sizeof(int16_t) * dlevel.size());
     put(h.o_chain, cround.data(), sizeof(int16_t) * cround.size());
     put(h.o_chain + (int32_t)(sizeof(int16_t) * cround.size()), cstart.data(), sizeof(int16_t) * cstart.size());
     put(h.o_chain + (int32_t)(sizeof(int16_t) * (cround.size() + cstart.size())), cbody.data(), cbody.size());
     put(h.o_tri, tri.data(), sizeof(uint16_t) * tri.size());
     put(h.o_rowanc, rowanc.data(), sizeof(uint16_t) * rowanc.size());
-    put(h.o_crba, crba_order.data(), crba_order.size());
+    put(h.o_crba, crba_order.data(), sizeof(uint32_t) * crba_order.size());
 
     out.dof_parent.assign(dpar.begin(), dpar.end());
     out.dof_depth.assign(depth.begin(), depth.end());

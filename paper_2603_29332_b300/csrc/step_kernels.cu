@@ -150,11 +150,11 @@ struct Tables {
     VIEW_T(const int16_t) blevel;
     VIEW_T(const uint8_t) child;
     VIEW_T(const uint8_t) anc;
-    VIEW_T(const uint8_t) dorder;
+    VIEW_T(const uint32_t) dorder;     // factorisation nodes by level (node_dof / node_depth / node_row)
     VIEW_T(const int16_t) dlevel;
     VIEW_T(const uint16_t) tri;
     VIEW_T(const uint16_t) rowanc;
-    VIEW_T(const uint8_t) crba_order;
+    VIEW_T(const uint2) crba_order;    // CRBA lanes' DoFs: {DoF | body << 8 | depth << 16, packed row}
     VIEW_T(const TendonRec) ten;       // null: every tendon rigid
     VIEW_T(const int16_t) cround;      // body chains of the subtree sums (ImgHeader::o_chain)
     VIEW_T(const int16_t) cstart;
@@ -198,11 +198,11 @@ __device__ __forceinline__ Tables make_tables(const uint8_t* img) {
     t.blevel = TAB(const int16_t, img, h.o_blevel);
     t.child = TAB(const uint8_t, img, h.o_child);
     t.anc = TAB(const uint8_t, img, h.o_anc);
-    t.dorder = TAB(const uint8_t, img, h.o_dorder);
+    t.dorder = TAB(const uint32_t, img, h.o_dorder);
     t.dlevel = TAB(const int16_t, img, h.o_dlevel);
     t.tri = TAB(const uint16_t, img, h.o_tri);
     t.rowanc = TAB(const uint16_t, img, h.o_rowanc);
-    t.crba_order = TAB(const uint8_t, img, h.o_crba);
+    t.crba_order = TAB(const uint2, img, h.o_crba);
 #ifdef MSIM_BOUNDS_CHECK
     t.ten = h.n_tendons ? TAB(const TendonRec, img, h.o_tendon) : mkview<const TendonRec>(nullptr, 0, __LINE__);
 #else
@@ -604,17 +604,23 @@ __device__ void phase_kinematics(const Tables& T, float* ws, const Grp<WPE>& g) 
         xfd(w, Ivw, t1);
         xfd(vl, Ivl, t2);
         xfd(w, Ivl, t3);
-        df* fb = FB + 6 * b;
+        // force (6 float-float, 48 bytes) and inertia (m, h[3], Ibar[6]: 80 bytes) of the body,
+        // stored as 16-byte words
+        df fo[6];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            fb[k] = df_add(df_add(Iaw[k], t1[k]), t2[k]);
-            fb[3 + k] = df_add(Ial[k], t3[k]);
+            fo[k] = df_add(df_add(Iaw[k], t1[k]), t2[k]);
+            fo[3 + k] = df_add(Ial[k], t3[k]);
         }
-        df* Id = reinterpret_cast<df*>(raw(FI + kFiStride * b));   // m, h[3], Ibar[6]
-        Id[0] = df_make(m);
-        Id[1] = hd[0]; Id[2] = hd[1]; Id[3] = hd[2];
+        float4* fb4 = reinterpret_cast<float4*>(raw(FB + 6 * b));
 #pragma unroll
-        for (int e = 0; e < 6; ++e) Id[4 + e] = Ibd[e];
+        for (int k = 0; k < 3; ++k) fb4[k] = make_float4(fo[2 * k].hi, fo[2 * k].lo, fo[2 * k + 1].hi, fo[2 * k + 1].lo);
+        float4* I4 = reinterpret_cast<float4*>(raw(FI + kFiStride * b));
+        I4[0] = make_float4(m, 0.f, hd[0].hi, hd[0].lo);
+        I4[1] = make_float4(hd[1].hi, hd[1].lo, hd[2].hi, hd[2].lo);
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            I4[2 + e] = make_float4(Ibd[2 * e].hi, Ibd[2 * e].lo, Ibd[2 * e + 1].hi, Ibd[2 * e + 1].lo);
     }
     g.sync();
 }
@@ -656,8 +662,12 @@ __device__ void phase_subtree(const Tables& T, float* ws, const Grp<WPE>& g) {
     // -S^T f starts the exact fixed-point accumulator of the right-hand side (the muscle and
     // contact terms follow); rhs keeps the FP32 terms (limits, damping)
     for (int d = g.lane; d < H.n; d += g.N) {
-        const float* Sd = S + 6 * d;
-        const df* f = FB + 6 * T.dof[d].body;
+        const float2* S2 = reinterpret_cast<const float2*>(raw(S + 6 * d));
+        const float4* f4 = reinterpret_cast<const float4*>(raw(FB + 6 * T.dof[d].body));
+        const float2 s01 = S2[0], s23 = S2[1], s45 = S2[2];
+        const float4 fa = f4[0], fbb = f4[1], fc = f4[2];
+        const float Sd[6] = {s01.x, s01.y, s23.x, s23.y, s45.x, s45.y};
+        const df f[6] = {df{fa.x, fa.y}, df{fa.z, fa.w}, df{fbb.x, fbb.y}, df{fbb.z, fbb.w}, df{fc.x, fc.y}, df{fc.z, fc.w}};
         df c = df_mul_f(f[0], Sd[0]);
 #pragma unroll
         for (int k = 1; k < 6; ++k) c = df_fma_f(c, f[k], Sd[k]);
@@ -705,14 +715,21 @@ __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float*
     auto A = WS(fac, H.w_A);
     auto Ai = WS(const int32_t, H.w_A);
     for (int t = g.lane; t < H.n; t += g.N) {
-        const int d = T.crba_order[t];
-        const DofRec& D = T.dof[d];
-        const df* I = reinterpret_cast<const df*>(raw(FI + kFiStride * D.body));
-        const df m = I[0];
-        const df h0 = I[1], h1 = I[2], h2 = I[3];
-        const df* Ib = I + 4;   // xx yy zz xy xz yz
-        const float* Sd = S + 6 * d;
-        const float s0 = Sd[0], s1 = Sd[1], s2 = Sd[2], p0 = Sd[3], p1 = Sd[4], p2 = Sd[5];
+        const uint2 ce = T.crba_order[t];
+        const int d = ce.x & 0xff, body = (ce.x >> 8) & 0xff, dep = (ce.x >> 16) & 0xff;
+        // the body's composite inertia as five 16-byte words (80-byte stride): m, h, then
+        // Ibar xx yy zz xy xz yz, float-float each
+        df m, h0, h1, h2, Ib[6];
+        {
+            const float4* I4 = reinterpret_cast<const float4*>(raw(FI + kFiStride * body));
+            const float4 w0 = I4[0], w1 = I4[1], w2 = I4[2], w3 = I4[3], w4 = I4[4];
+            m = df{w0.x, w0.y}; h0 = df{w0.z, w0.w}; h1 = df{w1.x, w1.y}; h2 = df{w1.z, w1.w};
+            Ib[0] = df{w2.x, w2.y}; Ib[1] = df{w2.z, w2.w}; Ib[2] = df{w3.x, w3.y}; Ib[3] = df{w3.z, w3.w};
+            Ib[4] = df{w4.x, w4.y}; Ib[5] = df{w4.z, w4.w};
+        }
+        const float2* Sd = reinterpret_cast<const float2*>(raw(S + 6 * d));   // 8-byte aligned
+        const float2 sa = Sd[0], sb = Sd[1], sc = Sd[2];
+        const float s0 = sa.x, s1 = sa.y, s2 = sb.x, p0 = sb.y, p1 = sc.x, p2 = sc.y;
         // F = I^c S: Fw = Ibar s + h x ps, Fl = m ps - h x s
         df Fw[3], Fl[3];
         Fw[0] = df_add(df_add(df_add(df_mul_f(Ib[0], s0), df_mul_f(Ib[3], s1)), df_mul_f(Ib[4], s2)),
@@ -724,15 +741,16 @@ __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float*
         Fl[0] = df_add(df_mul_f(m, p0), df_neg(df_add(df_mul_f(h1, s2), df_neg(df_mul_f(h2, s1)))));
         Fl[1] = df_add(df_mul_f(m, p1), df_neg(df_add(df_mul_f(h2, s0), df_neg(df_mul_f(h0, s2)))));
         Fl[2] = df_add(df_mul_f(m, p2), df_neg(df_add(df_mul_f(h0, s1), df_neg(df_mul_f(h1, s0)))));
-        const int row = D.row;
-        for (int k = 0; k <= D.depth; ++k) {
-            const float* Sa = S + 6 * T.anc[row + k];
-            df acc = df_mul_f(Fw[0], Sa[0]);
-            acc = df_fma_f(acc, Fw[1], Sa[1]);
-            acc = df_fma_f(acc, Fw[2], Sa[2]);
-            acc = df_fma_f(acc, Fl[0], Sa[3]);
-            acc = df_fma_f(acc, Fl[1], Sa[4]);
-            acc = df_fma_f(acc, Fl[2], Sa[5]);
+        const int row = (int)ce.y;
+        for (int k = 0; k <= dep; ++k) {
+            const float2* Sa = reinterpret_cast<const float2*>(raw(S + 6 * T.anc[row + k]));
+            const float2 a01 = Sa[0], a23 = Sa[1], a45 = Sa[2];
+            df acc = df_mul_f(Fw[0], a01.x);
+            acc = df_fma_f(acc, Fw[1], a01.y);
+            acc = df_fma_f(acc, Fw[2], a23.x);
+            acc = df_fma_f(acc, Fl[0], a23.y);
+            acc = df_fma_f(acc, Fl[1], a45.x);
+            acc = df_fma_f(acc, Fl[2], a45.y);
             if (evM) evM[row + k] = acc.hi + acc.lo;
 #ifdef MSIM_FP64_FACTOR
             A[row + k] = fac_of(acc) + fac_decode(Ai[2 * (row + k)], Ai[2 * (row + k) + 1]);
@@ -1301,10 +1319,11 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
         const int i0 = T.dlevel[l], i1 = T.dlevel[l + 1];
         // pivots of this level (1 / L_kk into the diagonal slots)
         for (int i = i0 + g.lane; i < i1; i += g.N) {
-            const DofRec& D = T.dof[T.dorder[i]];
-            fac akk = A[D.row + D.depth];
+            const uint32_t nd = T.dorder[i];
+            const int kk = node_row(nd) + node_depth(nd);
+            fac akk = A[kk];
             if (!fac_pos(akk)) { ok = false; akk = fac_one(); }
-            A[D.row + D.depth] = fac_rsqrt(akk);
+            A[kk] = fac_rsqrt(akk);
         }
         g.sync();
         SUB_MARK(11);
@@ -1318,11 +1337,11 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int i = c0 + u;
-                    const int k = T.dorder[i < i1 ? i : i0];
-                    const DofRec& D = T.dof[k];
-                    on[u] = i < i1 && j <= D.depth;
-                    ptr[u] = j < D.depth ? &A[D.row + j] : &Y[k];
-                    inv[u] = A[D.row + D.depth];
+                    const uint32_t nd = T.dorder[i < i1 ? i : i0];
+                    const int k = node_dof(nd), dep = node_depth(nd), row = node_row(nd);
+                    on[u] = i < i1 && j <= dep;
+                    ptr[u] = j < dep ? &A[row + j] : &Y[k];
+                    inv[u] = A[row + dep];
                     val[u] = on[u] ? *ptr[u] : inv[u];
                 }
 #pragma unroll
@@ -1335,10 +1354,10 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
         // eliminate node by node: A_ab -= L_ka L_kb for ancestors b <= a of k (kElimU independent
         // updates per lane per iteration, loads first), then y_a -= L_ka y_k
         for (int i = i0; i < i1; ++i) {
-            const int k = T.dorder[i];
-            const DofRec& D = T.dof[k];
-            const int np = D.depth * (D.depth + 1) / 2;
-            const fac* Lk = A + D.row;
+            const uint32_t nd = T.dorder[i];
+            const int k = node_dof(nd), dep = node_depth(nd), row = node_row(nd);
+            const int np = dep * (dep + 1) / 2;
+            const fac* Lk = A + row;
             // U targets per lane per iteration, U as small as the node's triangle allows (the
             // group's lanes share the node, so the choice is uniform): a shallow node does not
             // issue updates for lanes that have none
@@ -1352,7 +1371,7 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
                         const int p = p0 + g.N * u;
                         const int tv = T.tri[p < np ? p : 0];
                         const int ja = tv & 0xff, jb = tv >> 8;      // jb <= ja < depth
-                        tg[u] = &A[T.rowanc[D.row + ja] + jb];
+                        tg[u] = &A[T.rowanc[row + ja] + jb];
                         xv[u] = Lk[ja];
                         yv[u] = Lk[jb];
                     }
@@ -1367,8 +1386,8 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
             else if (np <= 2 * g.N) eliminate(std::integral_constant<int, 2>{});
             else eliminate(std::integral_constant<int, kElimU>{});
             const fac yk = Y[k];
-            for (int j = g.lane; j < D.depth; j += g.N) {
-                fac* t = &Y[T.anc[D.row + j]];
+            for (int j = g.lane; j < dep; j += g.N) {
+                fac* t = &Y[T.anc[row + j]];
                 *t = fac_fms(*t, Lk[j], yk);
             }
             g.sync();
@@ -1381,17 +1400,17 @@ __device__ bool phase_factor_solve(const Tables& T, float* ws, const Grp<WPE>& g
     // received all its terms and is scaled by 1 / L_kk in the same pass.
     const int n_all = T.dlevel[H.n_dlevels];
     for (int i = g.lane; i < T.dlevel[1]; i += g.N) {   // roots
-        const DofRec& D = T.dof[T.dorder[i]];
-        Y[T.dorder[i]] = fac_mul(Y[T.dorder[i]], A[D.row + D.depth]);
+        const uint32_t nd = T.dorder[i];
+        Y[node_dof(nd)] = fac_mul(Y[node_dof(nd)], A[node_row(nd) + node_depth(nd)]);
     }
     g.sync();
     for (int l = 0; l + 1 < H.n_dlevels; ++l) {
         const int next_end = T.dlevel[l + 2];
         for (int i = T.dlevel[l + 1] + g.lane; i < n_all; i += g.N) {
-            const int k = T.dorder[i];
-            const DofRec& D = T.dof[k];
-            fac y = fac_fms(Y[k], A[D.row + l], Y[T.anc[D.row + l]]);
-            if (i < next_end) y = fac_mul(y, A[D.row + D.depth]);   // depth l + 1: complete
+            const uint32_t nd = T.dorder[i];
+            const int k = node_dof(nd), row = node_row(nd);
+            fac y = fac_fms(Y[k], A[row + l], Y[T.anc[row + l]]);
+            if (i < next_end) y = fac_mul(y, A[row + node_depth(nd)]);   // depth l + 1: complete
             Y[k] = y;
         }
         g.sync();
