@@ -12,7 +12,9 @@
 
 namespace msim {
 
-struct df {
+// 8-byte aligned, so that a pair in shared memory moves as one 8-byte access (a half-warp per
+// wavefront) rather than as two 4-byte accesses at an 8-byte stride (two-way bank conflicts)
+struct __align__(8) df {
     float hi, lo;
 };
 
