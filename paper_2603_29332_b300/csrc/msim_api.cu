@@ -342,7 +342,9 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
         mus_ptr[k + 1] = (int32_t)cross.size();
     }
     // records sorted by (compliant tendon, wrapped segment, points, crossed DoFs): a warp's 32
-    // lanes then share loop trip counts and take the tendon and wrapping branches together
+    // lanes then share loop trip counts and take the tendon and wrapping branches together;
+    // then by the bodies of the path points in order, so that lanes reading point j's body frame
+    // often read the same one (a broadcast instead of a bank conflict)
     std::vector<int> wseg(m, 0);
     for (int k = 0; k < m; ++k)
         if (mus[k].wrap) wseg[k] = d.wrap_segment[mus[k].wrap - 1];
@@ -353,7 +355,13 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             const MuscleRec &A = mus[a], &B = mus[b];
             if (compliant(A.orig) != compliant(B.orig)) return compliant(B.orig);
             if (wseg[a] != wseg[b]) return wseg[a] < wseg[b];
-            return A.np != B.np ? A.np < B.np : A.nx < B.nx;
+            if (A.np != B.np) return A.np < B.np;
+            if (A.nx != B.nx) return A.nx < B.nx;
+            const int* pa = d.point_body + d.muscle_point_start[A.orig];
+            const int* pb = d.point_body + d.muscle_point_start[B.orig];
+            for (int j = 0; j < A.np; ++j)
+                if (pa[j] != pb[j]) return pa[j] < pb[j];
+            return false;
         });
         std::vector<MuscleRec> sorted(m);
         for (int k = 0; k < m; ++k) sorted[k] = mus[order[k]];
