@@ -179,43 +179,18 @@ bool build_image(const msim_model_desc& d, ModelHost& out, std::string& err) {
             if (depth[i] == l) dorder.push_back((uint32_t)i | ((uint32_t)depth[i] << 8) | ((uint32_t)row[i] << 16));
     }
     dlevel[n_dl] = (int16_t)dorder.size();
-    // CRBA work order: DoFs by decreasing packed-row length, dealt to the 32 lanes in a snake
-    // (0..31, 31..0, ...) so that every lane gets a similar number of entries
+    // CRBA work order: DoFs by decreasing packed-row length; the kernel deals them to however
+    // many lanes a group has in a snake (0..N-1, N-1..0, ...), so that every lane gets a similar
+    // number of entries.  Entry t: DoF | body << 8 | depth << 16, then its packed row start (one
+    // 8-byte load per lane instead of a lookup of the DoF record).
     std::vector<int> byrow(n);
     for (int i = 0; i < n; ++i) byrow[i] = i;
     std::stable_sort(byrow.begin(), byrow.end(), [&](int a, int b) { return depth[a] > depth[b]; });
     std::vector<uint32_t> crba_order(2 * n);
-    {
-        std::vector<std::vector<int>> lanes(32);
-        for (int i = 0; i < n; ++i) {
-            const int round = i / 32, pos = i % 32;
-            lanes[(round % 2 == 0) ? pos : 31 - pos].push_back(byrow[i]);
-        }
-        // slot t = lane + 32 * r holds the r-th DoF of lane `lane`
-        std::vector<int> slot(n, -1);
-        for (int ln = 0; ln < 32; ++ln)
-            for (size_t r = 0; r < lanes[ln].size(); ++r) {
-                const size_t t = ln + 32 * r;
-                if (t < (size_t)n) slot[t] = lanes[ln][r];
-            }
-        // any slot left empty (ragged last round) takes the remaining DoFs in order
-        std::vector<char> used(n, 0);
-        for (int t = 0; t < n; ++t)
-            if (slot[t] >= 0) used[slot[t]] = 1;
-        int next = 0;
-        for (int t = 0; t < n; ++t) {
-            if (slot[t] >= 0) continue;
-            while (used[next]) ++next;
-            slot[t] = next;
-            used[next] = 1;
-        }
-        // entry t: DoF | body << 8 | depth << 16, then its packed row start (one 8-byte load
-        // per lane instead of a lookup of the DoF record)
-        for (int t = 0; t < n; ++t) {
-            const int dd = slot[t];
-            crba_order[2 * t] = (uint32_t)dd | ((uint32_t)dof_body[dd] << 8) | ((uint32_t)depth[dd] << 16);
-            crba_order[2 * t + 1] = (uint32_t)row[dd];
-        }
+    for (int t = 0; t < n; ++t) {
+        const int dd = byrow[t];
+        crba_order[2 * t] = (uint32_t)dd | ((uint32_t)dof_body[dd] << 8) | ((uint32_t)depth[dd] << 16);
+        crba_order[2 * t + 1] = (uint32_t)row[dd];
     }
     // pair table: p -> (ia, ib), ib <= ia, row by row
     std::vector<uint16_t> tri;

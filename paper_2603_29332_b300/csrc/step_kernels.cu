@@ -154,7 +154,7 @@ struct Tables {
     VIEW_T(const int16_t) dlevel;
     VIEW_T(const uint16_t) tri;
     VIEW_T(const uint16_t) rowanc;
-    VIEW_T(const uint2) crba_order;    // CRBA lanes' DoFs: {DoF | body << 8 | depth << 16, packed row}
+    VIEW_T(const uint2) crba_order;    // CRBA rows, longest first: {DoF | body << 8 | depth << 16, packed row}
     VIEW_T(const TendonRec) ten;       // null: every tendon rigid
     VIEW_T(const int16_t) cround;      // body chains of the subtree sums (ImgHeader::o_chain)
     VIEW_T(const int16_t) cstart;
@@ -706,7 +706,7 @@ __device__ __forceinline__ fac fac_decode(int32_t hi, int32_t lo) { return fx_de
 
 // ------------------------------------------------------------------ phase 3: CRBA (float-float)
 // Adds M to the damping sums already accumulated (fixed point) in the same storage.  DoFs are
-// taken in the image's balanced order (similar entry counts per lane).
+// taken longest row first and dealt to the lanes in a snake (similar entry counts per lane).
 template <int WPE>
 __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float* evM) {
     const ImgHeader& H = *T.H;
@@ -714,7 +714,10 @@ __device__ void phase_crba(const Tables& T, float* ws, const Grp<WPE>& g, float*
     auto S = WS(const float, H.w_S);
     auto A = WS(fac, H.w_A);
     auto Ai = WS(const int32_t, H.w_A);
-    for (int t = g.lane; t < H.n; t += g.N) {
+    // rows by decreasing length, dealt to the group's lanes in a snake (0..N-1, N-1..0, ...)
+    for (int r0 = 0; r0 < H.n; r0 += g.N) {
+        const int t = r0 + (((r0 / g.N) & 1) ? g.N - 1 - g.lane : g.lane);
+        if (t >= H.n) continue;
         const uint2 ce = T.crba_order[t];
         const int d = ce.x & 0xff, body = (ce.x >> 8) & 0xff, dep = (ce.x >> 16) & 0xff;
         // the body's composite inertia as five 16-byte words (80-byte stride): m, h, then
