@@ -248,16 +248,21 @@ MSIM_API msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, i
                                     int32_t ldz, uint32_t* err, msim_stream_t stream);
 
 /* msim_gemm_bf16_mn -- msim_gemm_bf16 with either operand stored MN-contiguous, read by the
- *   tensor cores' transposed operand mode (no transposed copy is made):
+ *   tensor cores' transposed operand mode (no transposed copy is made), and an optional FP32
+ *   addend: C = act(A B^T + bias + addend).
  *   a_mn = 0: A [M][K], pitch lda >= K;  a_mn = 1: A stored as its transpose [K][M], lda >= M;
  *   b_mn = 0: B [N][K], pitch ldb >= K;  b_mn = 1: B stored as its transpose [K][N], ldb >= N.
  *   So C = dY^T H (a_mn = b_mn = 1, K = rows of dY and H) and C = dY W (b_mn = 1) read the
- *   stored matrices as they are: the weight and input gradients of an MLP layer.  Pitches,
- *   alignment, outputs and errors as msim_gemm_bf16; a_mn, b_mn other than 0 or 1: MSIM_ERR_ARG. */
+ *   stored matrices as they are: the weight and input gradients of an MLP layer.
+ *   addend (may be NULL): device FP32 [M][ld_add], ld_add >= N, added to the FP32 accumulator
+ *   after the bias and before the activation: the product over a subset of K's columns kept from
+ *   an earlier call (the flow refinement reuses the observation's share of its first layer this
+ *   way).  Pitches, alignment, outputs and errors as msim_gemm_bf16; a_mn, b_mn other than 0 or 1,
+ *   or ld_add < N with an addend: MSIM_ERR_ARG. */
 MSIM_API msim_status msim_gemm_bf16_mn(const void* A, int32_t lda, int32_t a_mn, const void* B, int32_t ldb,
-                                       int32_t b_mn, const float* bias, void* C, int32_t ldc, int32_t M, int32_t N,
-                                       int32_t K, int32_t c_bf16, int32_t act, void* Z, int32_t ldz, uint32_t* err,
-                                       msim_stream_t stream);
+                                       int32_t b_mn, const float* bias, const float* addend, int32_t ld_add,
+                                       void* C, int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t c_bf16,
+                                       int32_t act, void* Z, int32_t ldz, uint32_t* err, msim_stream_t stream);
 
 /* ---- 3-layer MLP on the tensor cores (the surrogate's and the policy's network) ----------
  * A network x -> silu(W1 x + b1) -> silu(W2 h1 + b2) -> out(W3 h2 + b3), out = identity or

@@ -295,10 +295,24 @@ __global__ void __launch_bounds__(192, 2)
             const int cn = n0 + c;
             float v[32], z[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                z[j] = __uint_as_float(r[j]) + sbias[c + j];
-                v[j] = act_fn(z[j], p.act);
+            for (int j = 0; j < 32; ++j) z[j] = __uint_as_float(r[j]) + sbias[c + j];
+            if (p.addend && row0 + lane < p.M) {
+                // this lane's row of the addend: 32 consecutive floats (one 128-byte line)
+                const float* ad = p.addend + (size_t)(row0 + lane) * p.ld_add + cn;
+                if (p.add_vec_ok && cn + 32 <= p.N) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 w = __ldg(reinterpret_cast<const float4*>(ad + j));
+                        z[j] += w.x; z[j + 1] += w.y; z[j + 2] += w.z; z[j + 3] += w.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (cn + j < p.N) z[j] += __ldg(ad + j);
+                }
             }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = act_fn(z[j], p.act);
             if (p.scale) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = fmaf(v[j], sscale[c + j], sshift[c + j]);
@@ -412,6 +426,7 @@ cudaError_t gemm_bf16_tc(const void* A, int lda, const void* B, int ldb, GemmArg
     const int vec_align = args.c_bf16 ? 8 : 4;
     args.vec_ok = (args.ldc % vec_align == 0) && ((reinterpret_cast<uintptr_t>(args.C) & 15) == 0);
     args.z_vec_ok = args.Z && (args.ldz % 8 == 0) && ((reinterpret_cast<uintptr_t>(args.Z) & 15) == 0);
+    args.add_vec_ok = args.addend && (args.ld_add % 4 == 0) && ((reinterpret_cast<uintptr_t>(args.addend) & 15) == 0);
     // two blocks per SM (<= 113 KB of shared memory and <= 256 TMEM columns each).  Tile width:
     // fewest waves of tiles over the 2 x SMs block slots, a 128-wide tile costing half a 256-wide
     // one; ties go to 256 (more reuse of each A tile)

@@ -68,6 +68,8 @@ struct msim_handle_ {
     float* flow_a = nullptr;                 // [n_envs][pitch_m] the action being refined
     float* flow_mu = nullptr;                // [n_envs][pitch_m] the initial sampler's mean
     float* flow_v = nullptr;                 // [n_envs][flow out pitch] velocity
+    float* flow_pre = nullptr;               // [n_envs][flow hidden] first-layer share of the observation
+    int flow_split = 0;                      // its input columns (a multiple of 8; 0: no split)
     uint32_t* act_ctr = nullptr;             // device control-step counter of the noise draw
     // imitation reward (msim_reward_attach / msim_reward)
     msim::Mlp* disc = nullptr;               // borrowed: D(Delta), in = n + 3 nb, out = 1, sigmoid

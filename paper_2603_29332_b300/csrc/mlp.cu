@@ -295,6 +295,21 @@ cudaError_t mlp_infer(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, 
     return gemm(m->H2, h, m->Ph + m->oW3, h, B, m->out, h, Y, ldy, 0, m->P + m->ob3, m->out_act, nullptr, 0, m->err, s);
 }
 
+cudaError_t mlp_infer_split(Mlp* m, const __nv_bfloat16* X, int ldx, int B, int c, float* Hpre, int compute_pre,
+                            float* Y, int ldy, cudaStream_t s) {
+    if (B < 1 || B > m->max_batch || c < 8 || c % 8 || c >= m->in) return cudaErrorInvalidValue;
+    const int h = m->hid;
+    const __nv_bfloat16* W1 = m->Ph + m->oW1;
+    if (compute_pre) CK(gemm(X, ldx, W1, m->inp, B, h, c, Hpre, h, 0, nullptr, 0, nullptr, 0, m->err, s));
+    GemmArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = B; g.N = h; g.K = m->in - c; g.C = m->H1; g.ldc = h; g.c_bf16 = 1; g.bias = m->P + m->ob1; g.act = 1;
+    g.err = m->err; g.addend = Hpre; g.ld_add = h;
+    CK(gemm_bf16_tc(X + c, ldx, W1 + c, m->inp, g, s));
+    CK(gemm(m->H1, h, m->Ph + m->oW2, h, B, h, h, m->H2, h, 1, m->P + m->ob2, 1, nullptr, 0, m->err, s));
+    return gemm(m->H2, h, m->Ph + m->oW3, h, B, m->out, h, Y, ldy, 0, m->P + m->ob3, m->out_act, nullptr, 0, m->err, s);
+}
+
 cudaError_t mlp_infer_head(Mlp* m, const __nv_bfloat16* X, int ldx, int B, const __nv_bfloat16* W3, const float* b3,
                            int N, const float* scale, const float* shift, float* Y, int ldy, cudaStream_t s) {
     if (B < 1 || B > m->max_batch) return cudaErrorInvalidValue;

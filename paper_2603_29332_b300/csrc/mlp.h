@@ -47,6 +47,11 @@ cudaError_t mlp_sync_bf16(Mlp* m, cudaStream_t s);
 cudaError_t mlp_forward(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s);
 // the same without the pre-activation copies a later backward needs (inference)
 cudaError_t mlp_infer(Mlp* m, const __nv_bfloat16* X, int ldx, int B, float* Y, int ldy, cudaStream_t s);
+// inference whose input columns [0, c) are the same as in an earlier call (c a multiple of 8,
+// 8 <= c < in): their share of the first layer, X[:, :c] W1[:, :c]^T, is kept in Hpre [B][hid]
+// (FP32; computed when compute_pre is set) and only columns [c, in) are multiplied again
+cudaError_t mlp_infer_split(Mlp* m, const __nv_bfloat16* X, int ldx, int B, int c, float* Hpre, int compute_pre,
+                            float* Y, int ldy, cudaStream_t s);
 // inference with another output layer: layers 1-2 of m, then Y = (H2 W3^T + b3) * scale + shift
 // (W3 [N][hid] BF16, b3, scale, shift [N]; identity output activation)
 cudaError_t mlp_infer_head(Mlp* m, const __nv_bfloat16* X, int ldx, int B, const __nv_bfloat16* W3, const float* b3,

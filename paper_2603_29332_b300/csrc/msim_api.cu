@@ -757,6 +757,9 @@ void free_all(msim_handle h) {
     if (h->pipe_up) { cudaStreamDestroy(h->pipe_up); h->pipe_up = nullptr; }
     if (h->pipe_down) { cudaStreamDestroy(h->pipe_down); h->pipe_down = nullptr; }
     cudaFree(h->obs); cudaFree(h->exc_policy); cudaFree(h->inv_fmax);
+    cudaFree(h->flow_x); cudaFree(h->flow_a); cudaFree(h->flow_mu); cudaFree(h->flow_v); cudaFree(h->flow_pre);
+    cudaFree(h->act_ctr);
+    cudaFree(h->vm); cudaFree(h->xpos_sim); cudaFree(h->xpos_ref); cudaFree(h->delta_x); cudaFree(h->disc_out);
     if (h->timers) cudaFree(h->timers);
 }
 
@@ -1276,16 +1279,17 @@ msim_status msim_get_layout(msim_handle h, int32_t model, int32_t* dof_parent, i
 }
 
 msim_status msim_gemm_bf16_mn(const void* A, int32_t lda, int32_t a_mn, const void* B, int32_t ldb, int32_t b_mn,
-                              const float* bias, void* C, int32_t ldc, int32_t M, int32_t N, int32_t K,
-                              int32_t c_bf16, int32_t act, void* Z, int32_t ldz, uint32_t* err,
-                              msim_stream_t stream) {
+                              const float* bias, const float* addend, int32_t ld_add, void* C, int32_t ldc,
+                              int32_t M, int32_t N, int32_t K, int32_t c_bf16, int32_t act, void* Z, int32_t ldz,
+                              uint32_t* err, msim_stream_t stream) {
     if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || (a_mn != 0 && a_mn != 1) || (b_mn != 0 && b_mn != 1) ||
-        lda < (a_mn ? M : K) || ldb < (b_mn ? N : K) || ldc < N || act < 0 || act > 2 || (Z && ldz < N))
+        lda < (a_mn ? M : K) || ldb < (b_mn ? N : K) || ldc < N || act < 0 || act > 2 || (Z && ldz < N) ||
+        (addend && ld_add < N))
         return arg_fail(nullptr, "msim_gemm_bf16: bad argument");
     GemmArgs g;
     std::memset(&g, 0, sizeof(g));
     g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc; g.c_bf16 = c_bf16 ? 1 : 0; g.bias = bias; g.act = act;
-    g.Z = Z; g.ldz = ldz; g.err = err; g.a_mn = a_mn; g.b_mn = b_mn;
+    g.Z = Z; g.ldz = ldz; g.err = err; g.a_mn = a_mn; g.b_mn = b_mn; g.addend = addend; g.ld_add = ld_add;
     const cudaError_t e = gemm_bf16_tc(A, lda, B, ldb, g, (cudaStream_t)stream);
     if (e == cudaErrorNotSupported) {
         g_create_error = "msim_gemm_bf16: tensor-map encoding unavailable";
@@ -1298,7 +1302,7 @@ msim_status msim_gemm_bf16_mn(const void* A, int32_t lda, int32_t a_mn, const vo
 msim_status msim_gemm_bf16(const void* A, int32_t lda, const void* B, int32_t ldb, const float* bias, void* C,
                            int32_t ldc, int32_t M, int32_t N, int32_t K, int32_t c_bf16, int32_t act, void* Z,
                            int32_t ldz, uint32_t* err, msim_stream_t stream) {
-    return msim_gemm_bf16_mn(A, lda, 0, B, ldb, 0, bias, C, ldc, M, N, K, c_bf16, act, Z, ldz, err, stream);
+    return msim_gemm_bf16_mn(A, lda, 0, B, ldb, 0, bias, nullptr, 0, C, ldc, M, N, K, c_bf16, act, Z, ldz, err, stream);
 }
 
 msim_status msim_mlp_create(int32_t in, int32_t hidden, int32_t out, int32_t out_act, int32_t max_batch, uint64_t seed,
@@ -1721,9 +1725,14 @@ msim_status msim_policy_step(msim_handle h, int32_t n_substeps_per_act, int32_t 
                 e = launch_flow_init(h->flow_mu, h->pitch_m, h->flow_a, h->pitch_m, E, m, h->flow_sigma, h->seed,
                                      h->act_ctr, s);
             if (e == cudaSuccess) e = launch_copy_cols(h->obs, p->inp, E, p->in, h->flow_x, f->inp, s);
+            // the observation columns of the flow input do not change over the Euler steps: their
+            // share of the first layer is formed at the first step and reused
             for (int j = 0; j < h->flow_steps && e == cudaSuccess; ++j) {
                 e = launch_flow_input(h->flow_a, h->pitch_m, E, m, (float)j * h->flow_dt, h->flow_x, f->inp, off, s);
-                if (e == cudaSuccess) e = mlp_infer(f, h->flow_x, f->inp, E, h->flow_v, f->outp, s);
+                if (e == cudaSuccess)
+                    e = h->flow_split ? mlp_infer_split(f, h->flow_x, f->inp, E, h->flow_split, h->flow_pre, j == 0,
+                                                        h->flow_v, f->outp, s)
+                                      : mlp_infer(f, h->flow_x, f->inp, E, h->flow_v, f->outp, s);
                 if (e == cudaSuccess)
                     e = launch_flow_axpy(h->flow_a, h->pitch_m, h->flow_v, f->outp, E, m, h->flow_dt,
                                          j + 1 == h->flow_steps ? h->exc_policy : nullptr, h->pitch_m, s);
@@ -1755,7 +1764,10 @@ msim_status msim_flow_attach(msim_handle h, msim_mlp flow, int32_t n_steps, floa
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     cudaFree(h->flow_x); cudaFree(h->flow_a); cudaFree(h->flow_mu); cudaFree(h->flow_v); cudaFree(h->act_ctr);
+    cudaFree(h->flow_pre);
     h->flow_x = nullptr; h->flow_a = nullptr; h->flow_mu = nullptr; h->flow_v = nullptr; h->act_ctr = nullptr;
+    h->flow_pre = nullptr;
+    h->flow_split = 0;
     h->flow = nullptr;
     if (!flow) return MSIM_OK;   // detach
     if (!h->policy) {
@@ -1778,10 +1790,19 @@ msim_status msim_flow_attach(msim_handle h, msim_mlp flow, int32_t n_steps, floa
     if (e == cudaSuccess) e = cudaMemset(h->flow_a, 0, (size_t)h->n_envs * h->pitch_m * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(h->flow_mu, 0, (size_t)h->n_envs * h->pitch_m * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(h->flow_v, 0, (size_t)h->n_envs * f->outp * sizeof(float));
+    // first-layer columns shared by every Euler step: the observation's, rounded down to 8
+    const int split = (h->policy->in / 8) * 8;
+    if (e == cudaSuccess && split >= 8 && split < f->in) {
+        e = cudaMalloc(&h->flow_pre, (size_t)h->n_envs * f->hid * sizeof(float));
+        if (e == cudaSuccess) h->flow_split = split;
+    }
     if (e == cudaSuccess) e = cudaMemset(h->act_ctr, 0, sizeof(uint32_t));
     if (e != cudaSuccess) {
         cudaFree(h->flow_x); cudaFree(h->flow_a); cudaFree(h->flow_mu); cudaFree(h->flow_v); cudaFree(h->act_ctr);
+        cudaFree(h->flow_pre);
         h->flow_x = nullptr; h->flow_a = nullptr; h->flow_mu = nullptr; h->flow_v = nullptr; h->act_ctr = nullptr;
+        h->flow_pre = nullptr;
+        h->flow_split = 0;
         return cuda_fail(h, e, "msim_flow_attach");
     }
     h->flow = f;

@@ -131,8 +131,9 @@ def load_library(path=LIB_PATH):
     lib.msim_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     lib.msim_gemm_bf16.argtypes = [vp, C.c_int32, vp, C.c_int32, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                    C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
-    lib.msim_gemm_bf16_mn.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, C.c_int32,
-                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, C.c_int32, vp, vp]
+    lib.msim_gemm_bf16_mn.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int32, C.c_int32, vp, vp, C.c_int32, vp,
+                                      C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp,
+                                      C.c_int32, vp, vp]
     lib.msim_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_float,
                                     C.POINTER(vp)]
     lib.msim_mlp_destroy.argtypes = [vp]
@@ -504,10 +505,12 @@ def measure_fp32_peak(device=0):
     return v.value
 
 
-def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=None, a_mn=False, b_mn=False):
-    """C = act(A B^T + bias) on the tensor cores (msim_gemm_bf16_mn).  A [M, K] (or, with a_mn, its
-    transpose [K, M] as stored), B [N, K] (with b_mn [K, N]): BF16 CUDA tensors with unit column
-    stride and row pitches multiple of 8."""
+def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=None, a_mn=False, b_mn=False,
+              addend=None):
+    """C = act(A B^T + bias + addend) on the tensor cores (msim_gemm_bf16_mn).  A [M, K] (or, with
+    a_mn, its transpose [K, M] as stored), B [N, K] (with b_mn [K, N]): BF16 CUDA tensors with unit
+    column stride and row pitches multiple of 8; addend (optional) FP32 [M, N] with unit column
+    stride."""
     import torch
     lib = load_library()
     M, K = (A.shape[1], A.shape[0]) if a_mn else A.shape
@@ -516,7 +519,9 @@ def gemm_bf16(A, B, bias=None, act=0, out_bf16=False, Z=None, err=None, stream=N
         raise ValueError("gemm_bf16: inner dimensions differ")
     C = torch.empty((M, N), device=A.device, dtype=torch.bfloat16 if out_bf16 else torch.float32)
     st = lib.msim_gemm_bf16_mn(A.data_ptr(), A.stride(0), 1 if a_mn else 0, B.data_ptr(), B.stride(0),
-                               1 if b_mn else 0, None if bias is None else bias.data_ptr(), C.data_ptr(), C.stride(0),
+                               1 if b_mn else 0, None if bias is None else bias.data_ptr(),
+                               None if addend is None else addend.data_ptr(), 0 if addend is None else addend.stride(0),
+                               C.data_ptr(), C.stride(0),
                                M, N, K, 1 if out_bf16 else 0, act, None if Z is None else Z.data_ptr(),
                                0 if Z is None else Z.stride(0), None if err is None else err.data_ptr(),
                                _stream_ptr(stream))

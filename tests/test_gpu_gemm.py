@@ -87,6 +87,36 @@ def test_gemm_mn_contiguous_operands(M, N, K, a_mn, b_mn):
     assert ((C - ref).abs() / scale).max().item() < 1e-5
 
 
+@pytest.mark.parametrize("M,N,K", [(300, 200, 90), (16384, 1024, 707), (4096, 3104, 512)])
+def test_gemm_addend(M, N, K):
+    """An FP32 addend [M][N] joins the accumulator with the bias, before the activation: the
+    product over a column subset of K kept from an earlier call completes to the whole product."""
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    Kp = (K + 7) // 8 * 8
+    A = torch.zeros((M, Kp), device="cuda", dtype=torch.bfloat16)
+    B = torch.zeros((N, Kp), device="cuda", dtype=torch.bfloat16)
+    A[:, :K] = torch.randn((M, K), device="cuda", generator=g).bfloat16()
+    B[:, :K] = (torch.randn((N, K), device="cuda", generator=g) / K ** 0.5).bfloat16()
+    b = torch.randn(N, device="cuda", generator=g)
+    add = torch.randn((M, N), device="cuda", generator=g)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = msim.gemm_bf16(A[:, :K], B[:, :K], b, act=1, err=err, addend=add)
+    Z = msim.gemm_bf16(A[:, :K], B[:, :K], b, act=0, err=err, addend=add)
+    torch.cuda.synchronize()
+    assert err.item() == 0
+    z = A[:, :K].float() @ B[:, :K].float().T + b + add
+    scale = (A[:, :K].float().abs() @ B[:, :K].float().abs().T) + add.abs() + 1.0
+    assert ((Z - z).abs() / scale).max().item() < 1e-5
+    assert ((C - z * torch.sigmoid(z)).abs() / scale).max().item() < 1e-5
+    # splitting K at a multiple of 8 and carrying the first part as the addend
+    c = (K // 2) // 8 * 8
+    if c >= 8:
+        pre = msim.gemm_bf16(A[:, :c], B[:, :c])
+        Zs = msim.gemm_bf16(A[:, c:K], B[:, c:K], b, addend=pre)
+        torch.cuda.synchronize()
+        assert ((Zs - (z - add)).abs() / scale).max().item() < 1e-5
+
+
 def test_gemm_bf16_output_and_preactivation():
     M, N, K = 256, 384, 160
     g = torch.Generator(device="cuda").manual_seed(3)

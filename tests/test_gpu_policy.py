@@ -115,10 +115,27 @@ def _obs(sim, model, pitch):
     return obs
 
 
+def _flow_velocity_split(flow, params, xb, pre, c):
+    """The flow network's forward as the library evaluates it inside the refinement loop, from
+    public GEMM calls: the first layer's share of input columns [0, c) (the observation, the same at
+    every Euler step) is the FP32 addend `pre`, and only columns [c, in) are multiplied again."""
+    W1, b1, W2, b2, W3, b3 = [torch.as_tensor(np.asarray(x, np.float32)).cuda() for x in params]
+    W1p = torch.zeros((W1.shape[0], flow.in_pitch), device="cuda")
+    W1p[:, : W1.shape[1]] = W1
+    W1b, W2b, W3b = W1p.bfloat16(), W2.bfloat16(), W3.bfloat16()
+    if pre is None:
+        pre = msim.gemm_bf16(xb[:, :c], W1b[:, :c])
+    h1 = msim.gemm_bf16(xb[:, c:flow.d_in], W1b[:, c:flow.d_in], b1, act=1, out_bf16=True, addend=pre)
+    h2 = msim.gemm_bf16(h1, W2b, b2, act=1, out_bf16=True)
+    return msim.gemm_bf16(h2, W3b, b3), pre
+
+
 def test_flow_refined_loop_equals_the_loop_assembled_by_hand():
     E, n_steps, dt = 128, 20, 0.05
     model, a, b, net, flow = _flow_setup(E, seed=7, n_steps=n_steps, dt=dt)
     m = model.n_muscles
+    params = flow.unflatten(flow.get(0))
+    c = (OBS // 8) * 8   # the observation columns the library keeps across the Euler steps
     for _ in range(2):
         a.policy_step(2, 1)
         obs = _obs(b, model, net.in_pitch)
@@ -126,10 +143,12 @@ def test_flow_refined_loop_equals_the_loop_assembled_by_hand():
         act = mu.clone()
         x = torch.zeros((E, flow.in_pitch), dtype=torch.float32, device="cuda")
         x[:, :OBS] = obs[:, :OBS]
+        pre = None
         for j in range(n_steps):
             x[:, OBS:OBS + m] = act
             x[:, OBS + m] = j * dt
-            v = flow.forward(x.bfloat16())[:, :m]
+            v, pre = _flow_velocity_split(flow, params, x.bfloat16(), pre, c)
+            v = v[:, :m]
             act = act + torch.tensor(dt, dtype=torch.float32) * v
         exc = torch.zeros((E, b.pitch_m), device="cuda")
         exc[:, :m] = act.clamp(0.0, 1.0)
