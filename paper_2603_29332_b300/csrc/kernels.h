@@ -104,7 +104,8 @@ cudaError_t launch_reset(float* q, float* qd, float* act, float* eps, uint32_t* 
                          int n_envs, cudaStream_t s);
 // flow refinement of the policy's action (policy.cu): a = mu + sigma N(0, 1) (advances *act_ctr),
 // the per-step input columns [a | t] of the flow network, the observation columns, and the Euler
-// step a += dt v (with u = clamp(a, 0, 1) when u is given)
+// step a += dt v (with u = clamp(a, 0, 1) when u is given, and the next step's input columns
+// [a | t_next] when X is given)
 cudaError_t launch_flow_init(const float* mu, int ldmu, float* a, int lda, int n_envs, int m, float sigma,
                              uint32_t seed, uint32_t* act_ctr, cudaStream_t s);
 cudaError_t launch_flow_input(const float* a, int lda, int n_envs, int m, float t, __nv_bfloat16* X, int ldx, int off,
@@ -112,7 +113,7 @@ cudaError_t launch_flow_input(const float* a, int lda, int n_envs, int m, float 
 cudaError_t launch_copy_cols(const __nv_bfloat16* src, int lds, int n_envs, int cols, __nv_bfloat16* dst, int ldd,
                              cudaStream_t s);
 cudaError_t launch_flow_axpy(float* a, int lda, const float* v, int ldv, int n_envs, int m, float dt, float* u, int ldu,
-                             cudaStream_t s);
+                             __nv_bfloat16* X, int ldx, int off, float t_next, cudaStream_t s);
 // imitation reward (policy.cu): tracking-error rows of the discriminator, then the reward
 cudaError_t launch_delta(const float* q, const float* qr, int pitch_n, const float* xs, const float* xr, int n, int nb,
                          int n_envs, __nv_bfloat16* X, int ldx, float* D, int ldd, cudaStream_t s);

@@ -1727,18 +1727,22 @@ msim_status msim_policy_step(msim_handle h, int32_t n_substeps_per_act, int32_t 
             if (e == cudaSuccess) e = launch_copy_cols(h->obs, p->inp, E, p->in, h->flow_x, f->inp, s);
             // the observation columns of the flow input do not change over the Euler steps: their
             // share of the first layer is formed at the first step and reused
+            // (each Euler step's update also writes the next step's [a | t] input columns)
+            if (e == cudaSuccess && h->flow_steps > 0)
+                e = launch_flow_input(h->flow_a, h->pitch_m, E, m, 0.f, h->flow_x, f->inp, off, s);
             for (int j = 0; j < h->flow_steps && e == cudaSuccess; ++j) {
-                e = launch_flow_input(h->flow_a, h->pitch_m, E, m, (float)j * h->flow_dt, h->flow_x, f->inp, off, s);
-                if (e == cudaSuccess)
-                    e = h->flow_split ? mlp_infer_split(f, h->flow_x, f->inp, E, h->flow_split, h->flow_pre, j == 0,
-                                                        h->flow_v, f->outp, s)
-                                      : mlp_infer(f, h->flow_x, f->inp, E, h->flow_v, f->outp, s);
+                e = h->flow_split ? mlp_infer_split(f, h->flow_x, f->inp, E, h->flow_split, h->flow_pre, j == 0,
+                                                    h->flow_v, f->outp, s)
+                                  : mlp_infer(f, h->flow_x, f->inp, E, h->flow_v, f->outp, s);
                 if (e == cudaSuccess)
                     e = launch_flow_axpy(h->flow_a, h->pitch_m, h->flow_v, f->outp, E, m, h->flow_dt,
-                                         j + 1 == h->flow_steps ? h->exc_policy : nullptr, h->pitch_m, s);
+                                         j + 1 == h->flow_steps ? h->exc_policy : nullptr, h->pitch_m,
+                                         j + 1 == h->flow_steps ? nullptr : h->flow_x, f->inp, off,
+                                         (float)(j + 1) * h->flow_dt, s);
             }
             if (e == cudaSuccess && h->flow_steps == 0)   // no refinement: u = clamp(a0)
-                e = launch_flow_axpy(h->flow_a, h->pitch_m, h->flow_v, f->outp, E, m, 0.f, h->exc_policy, h->pitch_m, s);
+                e = launch_flow_axpy(h->flow_a, h->pitch_m, h->flow_v, f->outp, E, m, 0.f, h->exc_policy, h->pitch_m,
+                                     nullptr, 0, 0, 0.f, s);
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "msim_policy_step (policy)");
         const msim_status st = msim_step(h, h->exc_policy, n_substeps_per_act, stream);
