@@ -45,15 +45,15 @@ __global__ void k_to_bf16(const float* P, __nv_bfloat16* Ph, size_t n) {
 __global__ void k_loss_grad(const float* Y, int ldy, const float* T, int ldt, int B, int N, float scale, int sig,
                             __nv_bfloat16* dY, int ldd, float* loss_acc) {
     float acc = 0.f;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)B * N; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / N), c = (int)(i % N);
-        const float y = Y[(size_t)r * ldy + c];
-        const float d = y - T[(size_t)r * ldt + c];
-        acc += d * d;
-        float g = scale * d;
-        if (sig) g *= y * (1.f - y);
-        dY[(size_t)r * ldd + c] = __float2bfloat16_rn(g);
-    }
+    for (int r = blockIdx.x; r < B; r += gridDim.x)   // rows per block, no flat-index division
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            const float y = Y[(size_t)r * ldy + c];
+            const float d = y - T[(size_t)r * ldt + c];
+            acc += d * d;
+            float g = scale * d;
+            if (sig) g *= y * (1.f - y);
+            dY[(size_t)r * ldd + c] = __float2bfloat16_rn(g);
+        }
     // the block's sum first (one atomic per block, not per warp: they all hit one address)
     __shared__ float part[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -68,13 +68,13 @@ __global__ void k_loss_grad(const float* Y, int ldy, const float* T, int ldt, in
 
 // dZ = dH * silu'(Z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z)
 __global__ void k_dsilu(const float* dH, const __nv_bfloat16* Z, int B, int N, int ld, __nv_bfloat16* dZ) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)B * N; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / N), c = (int)(i % N);
-        const size_t o = (size_t)r * ld + c;
-        const float z = __bfloat162float(Z[o]);
-        const float sgm = 1.f / (1.f + expf(-z));
-        dZ[o] = __float2bfloat16_rn(dH[o] * sgm * (1.f + z * (1.f - sgm)));
-    }
+    for (int r = blockIdx.x; r < B; r += gridDim.x)
+        for (int c = threadIdx.x; c < N; c += blockDim.x) {
+            const size_t o = (size_t)r * ld + c;
+            const float z = __bfloat162float(Z[o]);
+            const float sgm = 1.f / (1.f + expf(-z));
+            dZ[o] = __float2bfloat16_rn(dH[o] * sgm * (1.f + z * (1.f - sgm)));
+        }
 }
 
 // Column sums db[c] = sum over rows of src[r][c] in two deterministic stages: the rows in
@@ -325,20 +325,20 @@ cudaError_t mlp_backward(Mlp* m, const __nv_bfloat16* X, int ldx, const float* T
     CK(mlp_forward(m, X, ldx, B, m->Y, m->outp, s));
     CK(cudaMemsetAsync(m->loss_acc, 0, 4, s));
     const size_t nY = (size_t)B * m->out;
-    k_loss_grad<<<nblocks(nY), 256, 0, s>>>(m->Y, m->outp, T, ldt, B, m->out, 2.f / (float)nY, m->out_act == 2, m->dY,
+    k_loss_grad<<<std::min(B, 8192), 256, 0, s>>>(m->Y, m->outp, T, ldt, B, m->out, 2.f / (float)nY, m->out_act == 2, m->dY,
                                              m->outp, m->loss_acc);
     CK(cudaGetLastError());
     // layer 3: dW3 = dY^T H2, db3 = column sums of dY, dH2 = dY W3
     CK(gemm_dw(m->dY, m->outp, m->H2, h, m->out, h, B, m->G + m->oW3, h, m->err, s));
     CK(colsum(m->dY, B, m->out, m->outp, m->colpart, m->G + m->ob3, s));
     CK(gemm_dx(m->dY, m->outp, m->Ph + m->oW3, h, B, h, m->out, m->dH, h, m->err, s));
-    k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z2, B, h, h, m->dZ2);
+    k_dsilu<<<std::min(B, 8192), 256, 0, s>>>(m->dH, m->Z2, B, h, h, m->dZ2);
     CK(cudaGetLastError());
     // layer 2
     CK(gemm_dw(m->dZ2, h, m->H1, h, h, h, B, m->G + m->oW2, h, m->err, s));
     CK(colsum(m->dZ2, B, h, h, m->colpart, m->G + m->ob2, s));
     CK(gemm_dx(m->dZ2, h, m->Ph + m->oW2, h, B, h, h, m->dH, h, m->err, s));
-    k_dsilu<<<nblocks((size_t)B * h), 256, 0, s>>>(m->dH, m->Z1, B, h, h, m->dZ1);
+    k_dsilu<<<std::min(B, 8192), 256, 0, s>>>(m->dH, m->Z1, B, h, h, m->dZ1);
     CK(cudaGetLastError());
     // layer 1
     CK(gemm_dw(m->dZ1, h, X, ldx, h, m->in, B, m->G + m->oW1, m->inp, m->err, s));

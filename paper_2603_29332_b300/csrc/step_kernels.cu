@@ -1915,18 +1915,18 @@ cudaError_t launch_surr_step(const StepArgs& a, int grid, size_t smem, cudaStrea
 __global__ void k_surr_input(const float* q, int pitch_n, int env_begin, int n_envs, const float* c, const float* sc,
                              int n, __nv_bfloat16* X, int ldx, uint32_t* step_ctr) {
     if (step_ctr && blockIdx.x == 0 && threadIdx.x == 0) *step_ctr += 1u;   // read by the next step kernel
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_envs * ldx;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / ldx), j = (int)(i % ldx);
-        const float v = j < n ? (q[(size_t)(env_begin + r) * pitch_n + j] - c[j]) / sc[j] : 0.f;
-        X[(size_t)r * ldx + j] = __float2bfloat16_rn(v);
-    }
+    // a warp per row (rows are short), no flat-index division
+    const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < n_envs; r += gridDim.x * wpb)
+        for (int j = lane; j < ldx; j += 32) {
+            const float v = j < n ? (q[(size_t)(env_begin + r) * pitch_n + j] - c[j]) / sc[j] : 0.f;
+            X[(size_t)r * ldx + j] = __float2bfloat16_rn(v);
+        }
 }
 
 cudaError_t launch_surr_input(const float* q, int pitch_n, int env_begin, int n_envs, const float* c, const float* sc,
                               int n, __nv_bfloat16* X, int ldx, uint32_t* step_ctr, cudaStream_t s) {
-    const size_t tot = (size_t)n_envs * ldx;
-    const int blocks = (int)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
+    const int blocks = std::max(1, std::min((n_envs + 7) / 8, 4096));   // eight rows per block
     k_surr_input<<<blocks, 256, 0, s>>>(q, pitch_n, env_begin, n_envs, c, sc, n, X, ldx, step_ctr);
     return cudaGetLastError();
 }
