@@ -30,8 +30,12 @@ def _np(t, cols):
     return t[:, :cols].double().cpu().numpy()
 
 
-@pytest.mark.parametrize("name,E,k", [("c0_tiny", 64, 64), ("c1_whole", 4096, 48)])
+@pytest.mark.parametrize("name,E,k", [("c0_tiny", 64, 64), ("c1_whole", 4096, 48), ("c1_whole", 16384, 16),
+                                      ("c2_upper", 2458, 32), ("c2_lower", 2458, 32)])
 def test_stage_parity(name, E, k):
+    """Every stage of one substep on sampled environments of a launch at the workloads' sizes:
+    the tiny model, the whole body at 4096 environments (the benchmark) and 16384 (the closed
+    loop), and the two extra skeletons of the mixed batch at their share of its 8192."""
     model = mg.config_model(name)
     om = ora.OracleModel(model)
     sim = _sim(model, E)
@@ -287,3 +291,35 @@ def test_mixed_models_in_one_handle_match_separate_handles():
     s_all, s_a, s_b = both.state(), sa.state(), sb.state()
     assert torch.equal(s_all["q"][:Ea, : ma.n_dofs], s_a["q"][:, : ma.n_dofs])
     assert torch.equal(s_all["q"][Ea:, : mb.n_dofs], s_b["q"][:, : mb.n_dofs])
+
+
+def test_mixed_batch_trajectory_parity():
+    """The mixed batch's persistent launch (three skeletons in one kernel, 0.5 ms substeps, as the
+    mixed-batch workload runs them): 100 substeps against the oracle on sampled environments of
+    every skeleton, q within 1e-3 rad."""
+    names = ("c2_upper", "c2_lower", "c1_whole")
+    models = [mg.config_model(nm) for nm in names]
+    envs = [96, 96, 64]
+    dt = 5e-4
+    sim = msim.Sim(models, envs, dt=dt)
+    sim.set_mixed_launch(True)
+    states = [mg.initial_state(mm, e, seed=21 + i) for i, (mm, e) in enumerate(zip(models, envs))]
+    steps = 100
+    excs = [mg.smooth_excitations(mm, e, steps, seed=21 + i, dt=dt) for i, (mm, e) in enumerate(zip(models, envs))]
+    sim.reset(torch.cat([sim.pad_n(s[0]) for s in states]), torch.cat([sim.pad_n(s[1]) for s in states]),
+              torch.cat([sim.pad_m(s[2]) for s in states]))
+    for t in range(steps):
+        sim.step(torch.cat([sim.pad_m(x[t]) for x in excs]), 1)
+    qg = sim.state()["q"].double().cpu().numpy()
+    assert sim.status() == (0, 0)
+    row0 = 0
+    for mm, e, (q0, qd0, a0), ex in zip(models, envs, states, excs):
+        om = ora.OracleModel(mm)
+        idx = sample_envs(e, 8)
+        q, qd, act = q0[idx].astype(np.float64), qd0[idx].astype(np.float64), a0[idx].astype(np.float64)
+        for t in range(steps):
+            q, qd, act, *_ = ora.step(om, dt, q, qd, act, ex[t][idx].astype(np.float64), 1)
+        dq = np.abs(qg[row0 + np.asarray(idx), : mm.n_dofs] - q).max(axis=1)
+        print("\n%s (mixed launch) q max-abs diff after %d substeps: %.2e" % (mm.name, steps, dq.max()))
+        assert dq.max() <= 1e-3
+        row0 += e
